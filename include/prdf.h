@@ -1,0 +1,148 @@
+/*
+ * prdf.h - C ABI of the GB300 (sm_103a) Dynamic Frontier PageRank library (libprdf.so).
+ *
+ * The method is S. Sahu, "An Incrementally Expanding Approach for Updating PageRank on
+ * Dynamic Graphs" (arXiv 2401.03256).  A graph lives on one GPU behind an opaque handle;
+ * a batch of edge deletions and insertions is applied to it, and the ranks are brought
+ * up to date by Static, Naive-dynamic or Dynamic Frontier PageRank.
+ *
+ * Conventions for every entry point:
+ *  - Vertex ids are uint32 in [0, n) (Section 5.1.2: 32-bit vertex ids).
+ *  - Array arguments may be host or device pointers; the library finds out which with
+ *    cudaPointerGetAttributes and copies as needed.  The caller keeps ownership of
+ *    every array it passes; nothing is retained after the call returns.
+ *  - The handle owns all device memory it allocates until pr_graph_destroy.
+ *  - All device work of a handle runs on the stream given at creation (NULL = the
+ *    legacy default stream).  Every call returns after that work has finished.
+ *  - Errors: every call returns a pr_status.  Arguments are validated before anything
+ *    is changed, so on PR_ERR_INVALID_ARG / PR_ERR_VERTEX_RANGE the graph and its
+ *    ranks are as before the call.  pr_last_error gives a one-line message.
+ *  - One writer per handle (Section 3.2: one writer on the graph at a time).  Calls on
+ *    the same handle must not overlap; different handles are independent.
+ *  - Not converging within max_iter is not an error: the call returns PR_OK with
+ *    stats.converged = 0 (Algorithm 1 returns its ranks at MAX_ITERATIONS).
+ */
+#ifndef PRDF_H
+#define PRDF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pr_graph pr_graph; /* opaque handle */
+
+typedef enum {
+    PR_OK = 0,
+    PR_ERR_INVALID_ARG = 1,    /* bad parameter, size or NULL pointer */
+    PR_ERR_VERTEX_RANGE = 2,   /* a vertex id >= n */
+    PR_ERR_OUT_OF_MEMORY = 3,  /* device allocation failed; the handle is unchanged */
+    PR_ERR_CUDA = 4,           /* a CUDA runtime call failed (message in pr_last_error) */
+    PR_ERR_DEVICE_TIMEOUT = 5, /* a bounded device-side wait gave up; ranks are undefined */
+    PR_ERR_CAPACITY = 6        /* the graph would exceed 2^32 - 1 stored edges */
+} pr_status;
+
+typedef enum { PR_F64 = 0, PR_F32 = 1 } pr_precision;
+
+/* Dead ends (Section 3.1): the paper adds a self-loop to every vertex so no vertex has
+ * out-degree 0.  PR_DEADEND_TELEPORT adds none and spreads a dead end's rank over all
+ * vertices instead (the "global teleport contribution" the paper avoids). */
+typedef enum { PR_DEADEND_SELFLOOP = 0, PR_DEADEND_TELEPORT = 1 } pr_deadend;
+
+typedef struct {
+    double alpha;         /* damping factor; 0.85 (Section 5.1.2) */
+    double tol;           /* iteration tolerance tau on the L-inf norm; 1e-10 (Section 5.1.2) */
+    double frontier_tol;  /* frontier tolerance tau_f; tau / 1e5 (Section 4.3) */
+    int32_t max_iter;     /* MAX_ITERATIONS; 500 (Section 5.1.2); at most 1000 */
+    int32_t precision;    /* pr_precision: rank and contribution storage (FP64 or FP32) */
+    int32_t dead_end;     /* pr_deadend */
+    int32_t bin_lo;       /* in-degree <= bin_lo: one thread per vertex (0 = default 16) */
+    int32_t bin_hi;       /* in-degree >  bin_hi: one block per vertex (0 = default 4096) */
+    int32_t reserved;     /* must be 0 */
+} pr_params;
+
+typedef struct {
+    int32_t iterations;         /* iterations run (Algorithm 1's loop count) */
+    int32_t converged;          /* 1 if the L-inf change fell to <= tol */
+    int64_t affected_final;     /* vertices marked affected by the end (all n for sweeps) */
+    int64_t vertices_processed; /* sum over iterations of vertices whose rank was computed */
+    int64_t edges_processed;    /* sum over iterations of their in-edges */
+    double bytes_algorithmic;   /* algorithmic bytes moved by the rank kernel */
+    double last_delta;          /* L-inf change of the last iteration */
+    double ms_apply;            /* device time of pr_apply_batch calls since the last rank call */
+    double ms_rank;             /* device time of this call's rank computation */
+} pr_stats;
+
+/* Fills the paper's defaults: alpha 0.85, tol 1e-10, frontier_tol 1e-15, max_iter 500,
+ * FP64, self-loops, default degree bins. */
+void pr_params_default(pr_params *params);
+
+/* Builds a graph on the current CUDA device from m pairs (src[i], dst[i]).
+ * Duplicates are dropped, pairs with src == dst are dropped, and in self-loop mode a
+ * self-loop is added to every vertex (Section 3.1, Section 5.1.4).  Both adjacencies
+ * (in-edges for the pull computation of Eq. 1, out-edges for the frontier marking of
+ * Algorithm 1) are stored with each row sorted.  Ranks start at 1/n.
+ * n >= 1; m >= 0; src/dst may be NULL when m == 0; params may be NULL for defaults;
+ * cuda_stream is a cudaStream_t or NULL.  *out receives the handle. */
+pr_status pr_graph_create(uint32_t n, int64_t m, const uint32_t *src, const uint32_t *dst,
+                          const pr_params *params, void *cuda_stream, pr_graph **out);
+
+/* Frees all device memory of the handle.  NULL is accepted. */
+pr_status pr_graph_destroy(pr_graph *g);
+
+/* Applies one batch update (Section 3.2): E^t = (E^{t-1} \ D) U I, D = the n_del
+ * deletions, I = the n_ins insertions.  Pairs with src == dst, deletions of absent edges,
+ * insertions of present edges and duplicates have no effect; an edge both deleted and
+ * inserted is present afterwards.  The effective changes Delta^- = E^{t-1} \ E^t and
+ * Delta^+ = E^t \ E^{t-1} are remembered as pending marks for the next
+ * pr_dynamic_frontier (they accumulate over several calls; any rank call consumes them).
+ * Contributions of sources whose out-degree changed are refreshed. */
+pr_status pr_apply_batch(pr_graph *g, int64_t n_del, const uint32_t *del_src, const uint32_t *del_dst,
+                         int64_t n_ins, const uint32_t *ins_src, const uint32_t *ins_dst);
+
+/* Static PageRank (Section 3.1, Eq. 1): ranks restart at 1/n; every vertex is updated
+ * each iteration until the L-inf change is <= tol or max_iter iterations ran.
+ * stats may be NULL. */
+pr_status pr_static(pr_graph *g, pr_stats *stats);
+
+/* Naive-dynamic PageRank (Section 3.3.1): as pr_static but starting from the current ranks. */
+pr_status pr_naive_dynamic(pr_graph *g, pr_stats *stats);
+
+/* Dynamic Frontier PageRank (Algorithm 1, synchronous form of Section 4.2): marks the
+ * out-neighbours of every source of the pending changes (and the deleted targets, which
+ * are G^{t-1}.out(u) \ G^t.out(u)), then iterates over affected vertices only; a vertex
+ * whose rank changes by more than frontier_tol marks its out-neighbours, which join from
+ * the next iteration.  Stops when the L-inf change is <= tol or after max_iter iterations. */
+pr_status pr_dynamic_frontier(pr_graph *g, pr_stats *stats);
+
+/* Copies the n ranks (widened to double in FP32 mode) into out (host or device). */
+pr_status pr_get_ranks(pr_graph *g, double *out, uint32_t n);
+
+/* Replaces the ranks with in[0..n) (host or device), e.g. to resume or to start every
+ * implementation from the same previous ranks.  Pending marks are kept. */
+pr_status pr_set_ranks(pr_graph *g, const double *in, uint32_t n);
+
+/* Number of vertices and of stored edges (self-loops included). */
+pr_status pr_graph_info(const pr_graph *g, uint32_t *n, int64_t *m);
+
+/* Exports one adjacency in packed CSR form into host arrays: dir 0 = out-edges (rows by
+ * source), 1 = in-edges (rows by target); offs has n + 1 entries, cols has m entries
+ * (m from pr_graph_info); each row ascending. */
+pr_status pr_get_csr(pr_graph *g, int32_t dir, uint64_t *offs, uint32_t *cols);
+
+/* Vertices marked affected by the last pr_dynamic_frontier call, in no particular order,
+ * into a host array of capacity cap; *count receives the total number. */
+pr_status pr_get_affected(pr_graph *g, uint32_t *out, int64_t cap, int64_t *count);
+
+/* Message of the last failed call on g (or of the last failed pr_graph_create if g is NULL). */
+const char *pr_last_error(const pr_graph *g);
+
+/* Short name of a status code. */
+const char *pr_status_string(pr_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PRDF_H */

@@ -1,0 +1,317 @@
+// capi.cu - the extern "C" entry points declared in include/prdf.h.
+//
+// Validation happens here, before any device state is touched, so that a rejected call
+// leaves the graph and its ranks as they were.  Host arrays are copied to the device;
+// device arrays are used in place.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "prdf_graph.cuh"
+
+struct pr_graph {
+  prdf::Graph g;
+  double *stage = nullptr;  // n doubles for host <-> device rank copies
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+// Makes the handle's device current for the duration of a call.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+bool is_device_ptr(const void *p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+pr_status invalid(prdf::Graph *g, const char *msg) {
+  if (g) g->err = msg; else g_create_err = msg;
+  return PR_ERR_INVALID_ARG;
+}
+
+pr_status check_params(const pr_params &p, std::string *why) {
+  if (!(p.alpha > 0.0 && p.alpha < 1.0)) { *why = "alpha must be in (0, 1)"; return PR_ERR_INVALID_ARG; }
+  if (!(p.tol >= 0.0) || !(p.frontier_tol >= 0.0) || std::isnan(p.tol) || std::isnan(p.frontier_tol)) {
+    *why = "tolerances must be >= 0";
+    return PR_ERR_INVALID_ARG;
+  }
+  if (p.max_iter < 0 || p.max_iter > prdf::kMaxIterLimit) { *why = "max_iter must be in [0, 1000]"; return PR_ERR_INVALID_ARG; }
+  if (p.precision != PR_F64 && p.precision != PR_F32) { *why = "unknown precision"; return PR_ERR_INVALID_ARG; }
+  if (p.dead_end != PR_DEADEND_SELFLOOP && p.dead_end != PR_DEADEND_TELEPORT) { *why = "unknown dead-end mode"; return PR_ERR_INVALID_ARG; }
+  if (p.bin_lo < 0 || p.bin_hi < 0 || p.bin_hi < p.bin_lo) { *why = "need 0 <= bin_lo <= bin_hi"; return PR_ERR_INVALID_ARG; }
+  if (p.reserved != 0) { *why = "reserved must be 0"; return PR_ERR_INVALID_ARG; }
+  return PR_OK;
+}
+
+}  // namespace
+
+using prdf::Graph;
+
+extern "C" {
+
+void pr_params_default(pr_params *p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->alpha = 0.85;
+  p->tol = 1e-10;
+  p->frontier_tol = p->tol / 1e5;
+  p->max_iter = 500;
+  p->precision = PR_F64;
+  p->dead_end = PR_DEADEND_SELFLOOP;
+  p->bin_lo = 16;
+  p->bin_hi = 4096;
+  p->reserved = 0;
+}
+
+const char *pr_status_string(pr_status s) {
+  switch (s) {
+    case PR_OK: return "PR_OK";
+    case PR_ERR_INVALID_ARG: return "PR_ERR_INVALID_ARG";
+    case PR_ERR_VERTEX_RANGE: return "PR_ERR_VERTEX_RANGE";
+    case PR_ERR_OUT_OF_MEMORY: return "PR_ERR_OUT_OF_MEMORY";
+    case PR_ERR_CUDA: return "PR_ERR_CUDA";
+    case PR_ERR_DEVICE_TIMEOUT: return "PR_ERR_DEVICE_TIMEOUT";
+    case PR_ERR_CAPACITY: return "PR_ERR_CAPACITY";
+  }
+  return "unknown status";
+}
+
+const char *pr_last_error(const pr_graph *h) { return h ? h->g.err.c_str() : g_create_err.c_str(); }
+
+pr_status pr_graph_create(uint32_t n, int64_t m, const uint32_t *src, const uint32_t *dst, const pr_params *params,
+                          void *cuda_stream, pr_graph **out) {
+  if (!out) return invalid(nullptr, "out is NULL");
+  *out = nullptr;
+  if (n == 0) return invalid(nullptr, "n must be >= 1");
+  if (m < 0 || (m > 0 && (!src || !dst))) return invalid(nullptr, "bad edge arrays");
+  if ((uint64_t)m >= 0xFFFFFFFFull) {
+    g_create_err = "more than 2^32 - 1 input pairs";
+    return PR_ERR_CAPACITY;
+  }
+  pr_params p;
+  if (params) p = *params; else pr_params_default(&p);
+  if (p.bin_lo == 0 && p.bin_hi == 0) {
+    p.bin_lo = 16;
+    p.bin_hi = 4096;
+  }
+  std::string why;
+  if (check_params(p, &why) != PR_OK) return invalid(nullptr, why.c_str());
+
+  pr_graph *h = new (std::nothrow) pr_graph;
+  if (!h) {
+    g_create_err = "host allocation failed";
+    return PR_ERR_OUT_OF_MEMORY;
+  }
+  Graph &g = h->g;
+  g.n = n;
+  g.p = p;
+  g.f32 = p.precision == PR_F32;
+  g.teleport = p.dead_end == PR_DEADEND_TELEPORT;
+  g.st = (cudaStream_t)cuda_stream;
+  pr_status rc = PR_OK;
+  uint32_t *tmp = nullptr;
+  do {
+    cudaError_t e = cudaGetDevice(&g.device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g.sm_count, cudaDevAttrMultiProcessorCount, g.device);
+    int coop = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, g.device);
+    if (e != cudaSuccess) { rc = prdf::cuda_fail(&g, e, "device query"); break; }
+    if (!coop) { g.err = "device does not support cooperative launch"; rc = PR_ERR_CUDA; break; }
+    const uint32_t *sd = src, *dd = dst;
+    if (m > 0 && !(is_device_ptr(src) && is_device_ptr(dst))) {
+      e = cudaMalloc((void **)&tmp, 8ull * (uint64_t)m);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, src, 4ull * m, cudaMemcpyDefault, g.st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(tmp + m, dst, 4ull * m, cudaMemcpyDefault, g.st);
+      if (e != cudaSuccess) { rc = prdf::cuda_fail(&g, e, "upload edges"); break; }
+      sd = tmp;
+      dd = tmp + m;
+    }
+    rc = prdf::graph_build(&g, (uint64_t)m, sd, dd);
+    if (rc != PR_OK) break;
+    rc = prdf::rank_setup(&g);
+  } while (0);
+  if (tmp) {
+    cudaStreamSynchronize(g.st);
+    cudaFree(tmp);
+  }
+  if (rc != PR_OK) {
+    g_create_err = g.err;
+    prdf::graph_free(&g);
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return PR_OK;
+}
+
+pr_status pr_graph_destroy(pr_graph *h) {
+  if (!h) return PR_OK;
+  {
+    DeviceGuard dg(h->g.device);
+    cudaStreamSynchronize(h->g.st);
+    prdf::graph_free(&h->g);
+    cudaFree(h->stage);
+  }
+  delete h;
+  return PR_OK;
+}
+
+pr_status pr_apply_batch(pr_graph *h, int64_t n_del, const uint32_t *del_src, const uint32_t *del_dst,
+                         int64_t n_ins, const uint32_t *ins_src, const uint32_t *ins_dst) {
+  if (!h) return invalid(nullptr, "graph is NULL");
+  Graph &g = h->g;
+  if (n_del < 0 || n_ins < 0) return invalid(&g, "negative batch size");
+  if ((n_del > 0 && (!del_src || !del_dst)) || (n_ins > 0 && (!ins_src || !ins_dst)))
+    return invalid(&g, "batch array is NULL");
+  const uint64_t N = (uint64_t)n_del + (uint64_t)n_ins;
+  if (N == 0) return PR_OK;
+  if (N > (1ull << 31)) return invalid(&g, "batch too large (more than 2^31 pairs)");
+  DeviceGuard dg(g.device);
+  const uint32_t *arr[4] = {del_src, del_dst, ins_src, ins_dst};
+  const uint64_t len[4] = {(uint64_t)n_del, (uint64_t)n_del, (uint64_t)n_ins, (uint64_t)n_ins};
+  // host arrays are checked here, before anything is copied or changed
+  for (int k = 0; k < 4; k++) {
+    if (!len[k] || is_device_ptr(arr[k])) continue;
+    for (uint64_t i = 0; i < len[k]; i++)
+      if (arr[k][i] >= g.n) {
+        g.err = "vertex id out of range";
+        return PR_ERR_VERTEX_RANGE;
+      }
+  }
+  pr_status rc = prdf::apply_scratch(&g, N);
+  if (rc != PR_OK) return rc;
+  cudaError_t e = cudaEventRecord(g.ev0, g.st);
+  const uint32_t *dev[4];
+  uint32_t *stage = g.sc.pairs;
+  for (int k = 0; k < 4 && e == cudaSuccess; k++) {
+    if (!len[k] || is_device_ptr(arr[k])) {
+      dev[k] = arr[k];
+    } else {
+      e = cudaMemcpyAsync(stage, arr[k], 4ull * len[k], cudaMemcpyHostToDevice, g.st);
+      dev[k] = stage;
+    }
+    stage += len[k];
+  }
+  if (e != cudaSuccess) return prdf::cuda_fail(&g, e, "upload batch");
+  rc = prdf::graph_apply(&g, (uint64_t)n_del, dev[0], dev[1], (uint64_t)n_ins, dev[2], dev[3]);
+  if (rc != PR_OK) return rc;
+  e = cudaEventRecord(g.ev1, g.st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(g.ev1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, g.ev0, g.ev1);
+  if (e != cudaSuccess) return prdf::cuda_fail(&g, e, "apply timing");
+  g.ms_apply += ms;
+  return PR_OK;
+}
+
+static pr_status run(pr_graph *h, prdf::RankMode mode, pr_stats *stats) {
+  if (!h) return invalid(nullptr, "graph is NULL");
+  DeviceGuard dg(h->g.device);
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  return prdf::rank_run(&h->g, mode, stats);
+}
+
+pr_status pr_static(pr_graph *h, pr_stats *stats) { return run(h, prdf::kModeStatic, stats); }
+pr_status pr_naive_dynamic(pr_graph *h, pr_stats *stats) { return run(h, prdf::kModeNaive, stats); }
+pr_status pr_dynamic_frontier(pr_graph *h, pr_stats *stats) { return run(h, prdf::kModeDF, stats); }
+
+static pr_status ensure_stage(pr_graph *h) {
+  if (h->stage) return PR_OK;
+  cudaError_t e = cudaMalloc((void **)&h->stage, sizeof(double) * h->g.n);
+  if (e != cudaSuccess) return prdf::cuda_fail(&h->g, e, "rank staging buffer");
+  return PR_OK;
+}
+
+pr_status pr_get_ranks(pr_graph *h, double *out, uint32_t n) {
+  if (!h) return invalid(nullptr, "graph is NULL");
+  Graph &g = h->g;
+  if (!out || n != g.n) return invalid(&g, "out must hold exactly n doubles");
+  DeviceGuard dg(g.device);
+  pr_status rc;
+  cudaError_t e;
+  if (is_device_ptr(out)) {
+    if ((rc = prdf::rank_get(&g, out)) != PR_OK) return rc;
+    e = cudaStreamSynchronize(g.st);
+  } else {
+    if ((rc = ensure_stage(h)) != PR_OK) return rc;
+    if ((rc = prdf::rank_get(&g, h->stage)) != PR_OK) return rc;
+    e = cudaMemcpyAsync(out, h->stage, sizeof(double) * n, cudaMemcpyDeviceToHost, g.st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g.st);
+  }
+  if (e != cudaSuccess) return prdf::cuda_fail(&g, e, "get ranks");
+  return PR_OK;
+}
+
+pr_status pr_set_ranks(pr_graph *h, const double *in, uint32_t n) {
+  if (!h) return invalid(nullptr, "graph is NULL");
+  Graph &g = h->g;
+  if (!in || n != g.n) return invalid(&g, "in must hold exactly n doubles");
+  DeviceGuard dg(g.device);
+  if (is_device_ptr(in)) return prdf::rank_set(&g, in);
+  pr_status rc = ensure_stage(h);
+  if (rc != PR_OK) return rc;
+  cudaError_t e = cudaMemcpyAsync(h->stage, in, sizeof(double) * n, cudaMemcpyHostToDevice, g.st);
+  if (e != cudaSuccess) return prdf::cuda_fail(&g, e, "set ranks");
+  return prdf::rank_set(&g, h->stage);
+}
+
+pr_status pr_graph_info(const pr_graph *h, uint32_t *n, int64_t *m) {
+  if (!h) return invalid(nullptr, "graph is NULL");
+  if (n) *n = h->g.n;
+  if (m) *m = (int64_t)h->g.m;
+  return PR_OK;
+}
+
+pr_status pr_get_csr(pr_graph *h, int32_t dir, uint64_t *offs, uint32_t *cols) {
+  if (!h) return invalid(nullptr, "graph is NULL");
+  Graph &g = h->g;
+  if ((dir != 0 && dir != 1) || !offs || (!cols && g.m > 0)) return invalid(&g, "bad arguments");
+  DeviceGuard dg(g.device);
+  return prdf::graph_export(&g, dir, offs, cols);
+}
+
+pr_status pr_get_affected(pr_graph *h, uint32_t *out, int64_t cap, int64_t *count) {
+  if (!h) return invalid(nullptr, "graph is NULL");
+  Graph &g = h->g;
+  if (!count || cap < 0 || (cap > 0 && !out)) return invalid(&g, "bad arguments");
+  DeviceGuard dg(g.device);
+  if (g.last_full) {
+    *count = g.n;
+    for (int64_t i = 0; i < cap && i < (int64_t)g.n; i++) out[i] = (uint32_t)i;
+    return PR_OK;
+  }
+  int64_t total = 0;
+  for (int b = 0; b < 3; b++) {
+    int64_t c = g.last_list_cnt[b];
+    int64_t take = std::max<int64_t>(0, std::min<int64_t>(c, cap - total));
+    if (take > 0) {
+      cudaError_t e = cudaMemcpyAsync(out + total, g.list[b], 4ull * take, cudaMemcpyDeviceToHost, g.st);
+      if (e != cudaSuccess) return prdf::cuda_fail(&g, e, "get affected");
+    }
+    total += c;
+  }
+  cudaError_t e = cudaStreamSynchronize(g.st);
+  if (e != cudaSuccess) return prdf::cuda_fail(&g, e, "get affected");
+  *count = total;
+  return PR_OK;
+}
+
+}  // extern "C"

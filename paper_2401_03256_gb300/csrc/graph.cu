@@ -1,0 +1,849 @@
+// graph.cu - device graph store: build from pairs, batch update, repack, export.
+//
+// Section 3.2 of the paper defines a batch update as E^t = (E^{t-1} \ D) U I with
+// effective deletions Delta^- = E^{t-1} \ E^t and insertions Delta^+ = E^t \ E^{t-1};
+// Section 3.1 / 5.1.4 add a self-loop to every vertex (kept fixed across updates).
+//
+// Update pipeline (all on the handle's stream):
+//   keys (u << b | v) of the requested pairs -> sort -> filter to the effective changes
+//   (drop self pairs, duplicates, deletions of absent edges, deletions that are
+//   re-inserted, insertions of present edges) -> tagged change list sorted by (u, v)
+//   and a transposed copy sorted by (v, u) -> segments = touched rows -> one block
+//   per touched row merges the row with its changes, in place if the row's slots
+//   suffice, else into freshly allocated tail slots.  The out-row merge also refreshes
+//   the row's contribution alpha R[u] / |out(u)| and records the pending marks
+//   (sources and deleted targets) for the next Dynamic Frontier call.
+#include <algorithm>
+#include <vector>
+
+#include "prdf_graph.cuh"
+
+namespace prdf {
+
+#define CK(call)                                            \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail(g, e_, #call);  \
+  } while (0)
+
+pr_status cuda_fail(Graph *g, cudaError_t e, const char *what) {
+  g->err = std::string(what) + ": " + cudaGetErrorString(e);
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? PR_ERR_OUT_OF_MEMORY : PR_ERR_CUDA;
+}
+
+template <class T>
+static cudaError_t dalloc(T **p, uint64_t count) {
+  *p = nullptr;
+  return cudaMalloc((void **)p, sizeof(T) * (count ? count : 1));
+}
+
+static inline unsigned grid_for(uint64_t n, int threads = 256) {
+  uint64_t g = (n + threads - 1) / threads;
+  return (unsigned)std::max<uint64_t>(1, g);
+}
+
+constexpr int kMergeThreads = 256;
+constexpr uint32_t kSmemRow = 2048;  // rows up to this length are staged in shared memory
+
+// ------------------------------------------------------------------- kernels ----
+
+__global__ void k_validate_pairs(const uint32_t *src, const uint32_t *dst, uint64_t m, uint32_t n, uint32_t *bad) {
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m && (src[i] >= n || dst[i] >= n)) atomicOr(bad, 1u);
+}
+
+// Keys (u << b | v) of the input pairs (self pairs become the sentinel), followed by the
+// n self-loop keys when self_loops is set.
+__global__ void k_make_keys(const uint32_t *src, const uint32_t *dst, uint64_t m_in, uint32_t n, int b,
+                            int self_loops, uint64_t *keys) {
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m_in) {
+    uint64_t u = src[i], v = dst[i];
+    keys[i] = u == v ? kSentinel : ((u << b) | v);
+  } else if (self_loops && i < m_in + n) {
+    uint64_t v = i - m_in;
+    keys[i] = (v << b) | v;
+  }
+}
+
+__device__ __forceinline__ uint32_t unique_flag(const uint64_t *keys, uint64_t i) {
+  uint64_t k = keys[i];
+  return (k != kSentinel && (i == 0 || keys[i - 1] != k)) ? 1u : 0u;
+}
+
+__global__ void k_unique_flags(const uint64_t *keys, uint64_t m, uint32_t *flags) {
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) flags[i] = unique_flag(keys, i);
+}
+
+__global__ void k_compact_unique(const uint64_t *keys, const uint32_t *pos, uint64_t m, uint64_t *out,
+                                 uint32_t *count) {
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  uint32_t f = unique_flag(keys, i);
+  if (f) out[pos[i]] = keys[i];
+  if (i == m - 1) *count = pos[i] + f;
+}
+
+__global__ void k_transpose_keys(const uint64_t *keys, uint64_t m, int b, uint64_t *out) {
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  uint64_t k = keys[i], mask = (1ull << b) - 1;
+  out[i] = ((k & mask) << b) | (k >> b);
+}
+
+// off[r] = index of the first key of row r (rows are key >> b); off[n] = m.
+__global__ void k_row_bounds(const uint64_t *keys, uint64_t m, int b, uint32_t n, uint32_t *off) {
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > m) return;
+  int64_t prev = i == 0 ? -1 : (int64_t)(keys[i - 1] >> b);
+  int64_t cur = i == m ? (int64_t)n : (int64_t)(keys[i] >> b);
+  for (int64_t r = prev + 1; r <= cur; r++) off[r] = (uint32_t)i;
+}
+
+__global__ void k_row_caps(const uint32_t *off, uint32_t n, uint32_t *cap) {
+  uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < n) cap[v] = slack_cap(off[v + 1] - off[v]);
+}
+
+__global__ void k_row_desc(const uint32_t *start, const uint32_t *off, uint32_t n, uint2 *rd) {
+  uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < n) rd[v] = make_uint2(start[v], off[v + 1] - off[v]);
+}
+
+__global__ void k_scatter_cols(const uint64_t *keys, uint64_t m, int b, const uint32_t *off, const uint2 *rd,
+                               uint32_t *col) {
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  uint64_t k = keys[i];
+  uint32_t r = (uint32_t)(k >> b);
+  col[rd[r].x + (uint32_t)(i - off[r])] = (uint32_t)(k & ((1ull << b) - 1));
+}
+
+template <class T>
+__global__ void k_init_rank(const uint2 *out_rd, uint32_t n, double alpha, T *adeg, T *R0, T *R1, T *C0, T *C1) {
+  uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  uint32_t d = out_rd[v].y;
+  T a = d ? (T)(alpha / (double)d) : (T)0;
+  T r = (T)(1.0 / (double)n);
+  adeg[v] = a;
+  R0[v] = r;
+  R1[v] = r;
+  C0[v] = r * a;
+  C1[v] = r * a;
+}
+
+// ---- batch update ----
+
+__device__ __forceinline__ bool row_has(const uint2 *rd, const uint32_t *col, uint32_t u, uint32_t v) {
+  uint2 d = rd[u];
+  const uint32_t *c = col + d.x;
+  uint32_t lo = 0, hi = d.y;
+  while (lo < hi) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (c[mid] < v) lo = mid + 1; else hi = mid;
+  }
+  return lo < d.y && c[lo] == v;
+}
+
+__device__ __forceinline__ bool sorted_has(const uint64_t *a, uint64_t n, uint64_t x) {
+  uint64_t lo = 0, hi = n;
+  while (lo < hi) {
+    uint64_t mid = (lo + hi) >> 1;
+    if (a[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo < n && a[lo] == x;
+}
+
+__global__ void k_batch_keys(const uint32_t *ds, const uint32_t *dd, uint64_t nd, const uint32_t *is,
+                             const uint32_t *id, uint64_t ni, uint32_t n, int b, uint64_t *kd, uint64_t *ki,
+                             ApplyCtl *actl) {
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nd + ni) return;
+  uint64_t u, v;
+  if (i < nd) { u = ds[i]; v = dd[i]; } else { u = is[i - nd]; v = id[i - nd]; }
+  uint64_t key;
+  if (u >= n || v >= n) {
+    atomicOr(&actl->bad_id, 1u);
+    key = kSentinel;
+  } else {
+    key = u == v ? kSentinel : ((u << b) | v);
+  }
+  if (i < nd) kd[i] = key; else ki[i - nd] = key;
+}
+
+// flags[i] = 1 for an effective change: deletions (i < nd) of present edges not also
+// inserted, insertions of absent edges; duplicates and self pairs never.
+__global__ void k_filter(const uint64_t *kd, uint64_t nd, const uint64_t *ki, uint64_t ni, const uint2 *rd,
+                         const uint32_t *col, int b, uint32_t *flags) {
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nd + ni) return;
+  const uint64_t mask = (1ull << b) - 1;
+  uint32_t keep = 0;
+  if (i < nd) {
+    uint64_t k = kd[i];
+    if (k != kSentinel && (i == 0 || kd[i - 1] != k))
+      keep = row_has(rd, col, (uint32_t)(k >> b), (uint32_t)(k & mask)) && !sorted_has(ki, ni, k);
+  } else {
+    uint64_t j = i - nd, k = ki[j];
+    if (k != kSentinel && (j == 0 || ki[j - 1] != k))
+      keep = !row_has(rd, col, (uint32_t)(k >> b), (uint32_t)(k & mask));
+  }
+  flags[i] = keep;
+}
+
+// Tagged change keys: (key << 1) | is_insertion, in row-major (u, v) and transposed (v, u) form.
+__global__ void k_emit_changes(const uint64_t *kd, uint64_t nd, const uint64_t *ki, uint64_t ni,
+                               const uint32_t *flags, const uint32_t *pos, int b, uint64_t *chg, uint64_t *chg_t,
+                               ApplyCtl *actl) {
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint64_t N = nd + ni;
+  if (i >= N) return;
+  if (flags[i]) {
+    uint64_t k = i < nd ? kd[i] : ki[i - nd];
+    uint64_t tag = i < nd ? 0 : 1;
+    uint64_t mask = (1ull << b) - 1;
+    uint64_t kt = ((k & mask) << b) | (k >> b);
+    chg[pos[i]] = (k << 1) | tag;
+    chg_t[pos[i]] = (kt << 1) | tag;
+  }
+  if (i == N - 1) {
+    actl->n_eff = pos[i] + flags[i];
+    actl->n_eff_del = nd < N ? pos[nd] : pos[i] + flags[i];
+  }
+}
+
+__device__ __forceinline__ uint32_t chg_row(uint64_t c, int b) { return (uint32_t)((c >> 1) >> b); }
+__device__ __forceinline__ uint32_t chg_col(uint64_t c, int b) { return (uint32_t)((c >> 1) & ((1ull << b) - 1)); }
+
+// flags[j] = start of a row segment; tags[j] = is_insertion; tags[K] = 0.
+__global__ void k_seg_flags(const uint64_t *chg, uint32_t K, int b, uint32_t *flags, uint32_t *tags) {
+  uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < K) {
+    flags[j] = (j == 0 || chg_row(chg[j], b) != chg_row(chg[j - 1], b)) ? 1u : 0u;
+    tags[j] = (uint32_t)(chg[j] & 1);
+  } else if (j == K) {
+    tags[j] = 0;
+  }
+}
+
+__global__ void k_seg_emit(const uint32_t *flags, const uint32_t *pos, uint32_t K, uint32_t *seg, uint32_t *nseg) {
+  uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= K) return;
+  if (flags[j]) seg[pos[j]] = j;
+  if (j == K - 1) {
+    uint32_t c = pos[j] + flags[j];
+    seg[c] = K;
+    *nseg = c;
+  }
+}
+
+// Words the moved rows need, and the long rows' staging words.
+__global__ void k_plan(const uint2 *rd, const uint32_t *cap, const uint64_t *chg, uint32_t K, int b,
+                       const uint32_t *seg, const uint32_t *nseg, const uint32_t *tagpref,
+                       unsigned long long *reloc, unsigned long long *big_need) {
+  uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= *nseg) return;
+  uint32_t s0 = seg[s], e = seg[s + 1];
+  uint32_t r = chg_row(chg[s0], b);
+  uint32_t nI = tagpref[e] - tagpref[s0], nD = (e - s0) - nI;
+  uint32_t len = rd[r].y;
+  uint32_t new_len = len - nD + nI;
+  if (new_len > cap[r]) atomicAdd(reloc, (unsigned long long)move_cap(new_len));
+  if (len > kSmemRow) atomicAdd(big_need, (unsigned long long)len);
+}
+
+// Extra work done by the merge of an out-row (source u): contribution refresh and
+// pending marks.  Disabled (is_out == false) for in-rows.
+template <class T>
+struct OutRowHook {
+  bool is_out;
+  double alpha;
+  T *adeg, *R0, *C0, *C1;
+  uint32_t *pend_src, *pend_tgt;
+  uint32_t pend_cap;
+};
+
+// One block per touched row: merges the row with its sorted changes.
+template <class T>
+__global__ void __launch_bounds__(kMergeThreads) k_merge(uint2 *rd, uint32_t *cap, uint32_t *col, const uint64_t *chg,
+                                                         int b, const uint32_t *seg, const uint32_t *nseg,
+                                                         const uint32_t *tagpref, unsigned long long *tail,
+                                                         unsigned long long *garbage, uint32_t *big,
+                                                         unsigned long long *big_cursor, uint64_t col_cap,
+                                                         uint64_t big_cap, ApplyCtl *actl, OutRowHook<T> hook) {
+  __shared__ uint32_t srow[kSmemRow];
+  __shared__ uint32_t s_dest, s_big;
+  const uint32_t s = blockIdx.x;
+  if (s >= *nseg) return;
+  const uint32_t tid = threadIdx.x;
+  const uint32_t s0 = seg[s], e = seg[s + 1];
+  const uint32_t r = chg_row(chg[s0], b);
+  const uint2 d = rd[r];
+  const uint32_t len = d.y, cap_r = cap[r];
+  const uint32_t nI = tagpref[e] - tagpref[s0], nD = (e - s0) - nI;
+  const uint32_t new_len = len - nD + nI;
+  const bool moves = new_len > cap_r;
+  uint32_t *src_row = srow;
+  __shared__ int s_ok;
+  if (tid == 0) {
+    unsigned long long dest = moves ? atomicAdd(tail, (unsigned long long)move_cap(new_len)) : d.x;
+    unsigned long long bg = len > kSmemRow ? atomicAdd(big_cursor, (unsigned long long)len) : 0ull;
+    s_ok = (!moves || dest + move_cap(new_len) <= col_cap) && (len <= kSmemRow || bg + len <= big_cap);
+    if (!s_ok) atomicOr(&actl->overflow, 1u);
+    s_dest = (uint32_t)dest;
+    s_big = (uint32_t)bg;
+  }
+  __syncthreads();
+  if (!s_ok) return;  // no room: the row is left as it was and the host reports the failure
+  if (len > kSmemRow) src_row = big + s_big;
+  for (uint32_t j = tid; j < len; j += kMergeThreads) src_row[j] = col[d.x + j];
+  __syncthreads();
+  uint32_t *dst = col + s_dest;
+  for (uint32_t j = tid; j < len; j += kMergeThreads) {
+    uint32_t x = src_row[j];
+    uint32_t lo = s0, hi = e;  // first change with column >= x
+    while (lo < hi) {
+      uint32_t mid = (lo + hi) >> 1;
+      if (chg_col(chg[mid], b) < x) lo = mid + 1; else hi = mid;
+    }
+    if (lo < e && chg_col(chg[lo], b) == x) continue;  // deleted
+    uint32_t ib = tagpref[lo] - tagpref[s0];
+    uint32_t db = (lo - s0) - ib;
+    dst[j - db + ib] = x;
+  }
+  for (uint32_t q = s0 + tid; q < e; q += kMergeThreads) {
+    uint64_t c = chg[q];
+    if (!(c & 1)) continue;
+    uint32_t y = chg_col(c, b);
+    uint32_t lo = 0, hi = len;  // old entries below y
+    while (lo < hi) {
+      uint32_t mid = (lo + hi) >> 1;
+      if (src_row[mid] < y) lo = mid + 1; else hi = mid;
+    }
+    uint32_t ib = tagpref[q] - tagpref[s0];
+    uint32_t db = (q - s0) - ib;
+    dst[lo - db + ib] = y;
+  }
+  if (hook.is_out) {
+    for (uint32_t q = s0 + tid; q < e; q += kMergeThreads) {
+      uint64_t c = chg[q];
+      if (c & 1) continue;
+      uint32_t p = atomicAdd(&actl->n_pend_tgt, 1u);
+      if (p < hook.pend_cap) hook.pend_tgt[p] = chg_col(c, b);
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    rd[r] = make_uint2(s_dest, new_len);
+    if (moves) {
+      cap[r] = move_cap(new_len);
+      atomicAdd(garbage, (unsigned long long)cap_r);
+    }
+    if (hook.is_out) {
+      T a = new_len ? (T)(hook.alpha / (double)new_len) : (T)0;
+      hook.adeg[r] = a;
+      T c = hook.R0[r] * a;
+      hook.C0[r] = c;
+      hook.C1[r] = c;
+      if ((len == 0) != (new_len == 0)) actl->dead_changed = 1;
+      uint32_t p = atomicAdd(&actl->n_pend_src, 1u);
+      if (p < hook.pend_cap) hook.pend_src[p] = r;
+    }
+  }
+}
+
+// ---- repack / export / bins ----
+
+__global__ void k_len_caps(const uint2 *rd, uint32_t n, uint32_t *cap) {
+  uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < n) cap[v] = slack_cap(rd[v].y);
+}
+
+// One warp per row: copies the row to new_col + start[v] and points rd at it.
+__global__ void k_repack_rows(uint2 *rd, uint32_t n, const uint32_t *old_col, uint32_t *new_col,
+                              const uint32_t *start) {
+  uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  uint32_t lane = threadIdx.x & 31;
+  if (w >= n) return;
+  uint2 d = rd[w];
+  uint32_t s = start[w];
+  for (uint32_t j = lane; j < d.y; j += 32) new_col[s + j] = old_col[d.x + j];
+  __syncwarp();
+  if (lane == 0) rd[w] = make_uint2(s, d.y);
+}
+
+__global__ void k_row_len(const uint2 *rd, uint32_t n, uint32_t *len) {
+  uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < n) len[v] = rd[v].y;
+  else if (v == n) len[v] = 0;
+}
+
+__global__ void k_pack_rows(const uint2 *rd, uint32_t n, const uint32_t *col, const uint32_t *off, uint32_t *packed) {
+  uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  uint32_t lane = threadIdx.x & 31;
+  if (w >= n) return;
+  uint2 d = rd[w];
+  uint32_t o = off[w];
+  for (uint32_t j = lane; j < d.y; j += 32) packed[o + j] = col[d.x + j];
+}
+
+__global__ void k_bin_flags(const uint2 *rd, uint32_t n, uint32_t lo, uint32_t hi, int bin, uint32_t *flags) {
+  uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  uint32_t len = rd[v].y;
+  int b = len <= lo ? 0 : (len <= hi ? 1 : 2);
+  flags[v] = b == bin;
+}
+
+__global__ void k_dead_flags(const uint2 *rd, uint32_t n, uint32_t *flags) {
+  uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < n) flags[v] = rd[v].y == 0;
+}
+
+// Stable compaction of the ids whose flag is set; count = total.
+__global__ void k_compact_ids(const uint32_t *flags, const uint32_t *pos, uint32_t n, uint32_t *out, uint32_t *count) {
+  uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  if (flags[v]) out[pos[v]] = v;
+  if (v == n - 1) *count = pos[v] + flags[v];
+}
+
+// ------------------------------------------------------------------ host side ---
+
+static pr_status build_adj(Graph *g, const uint64_t *keys, uint64_t m, Adj &A, uint32_t *off, uint32_t *tmp,
+                           uint32_t *scan_tmp) {
+  const uint32_t n = g->n;
+  cudaStream_t st = g->st;
+  CK(dalloc(&A.rd, n));
+  CK(dalloc(&A.cap, n));
+  k_row_bounds<<<grid_for(m + 1), 256, 0, st>>>(keys, m, g->b, n, off);
+  k_row_caps<<<grid_for(n), 256, 0, st>>>(off, n, A.cap);
+  exclusive_scan_u32(A.cap, tmp, n, scan_tmp, st);
+  uint32_t last[2];
+  CK(cudaMemcpyAsync(&last[0], tmp + (n - 1), 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&last[1], A.cap + (n - 1), 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  uint64_t total = (uint64_t)last[0] + last[1];
+  uint64_t reserve = std::max<uint64_t>(total / 4, 1024);
+  reserve = (reserve + 3) & ~3ull;
+  if (total + reserve > 0xFFFFFFFFull) {
+    g->err = "graph too large: more than 2^32 - 1 column slots";
+    return PR_ERR_CAPACITY;
+  }
+  A.col_cap = total + reserve;
+  CK(dalloc(&A.col, A.col_cap));
+  CK(cudaMemsetAsync(A.col, 0, sizeof(uint32_t) * A.col_cap, st));
+  k_row_desc<<<grid_for(n), 256, 0, st>>>(tmp, off, n, A.rd);
+  k_scatter_cols<<<grid_for(m), 256, 0, st>>>(keys, m, g->b, off, A.rd, A.col);
+  A.used = total;
+  A.garbage = 0;
+  CK(cudaGetLastError());
+  return PR_OK;
+}
+
+pr_status graph_build(Graph *g, uint64_t m_in, const uint32_t *src_d, const uint32_t *dst_d) {
+  const uint32_t n = g->n;
+  cudaStream_t st = g->st;
+  g->b = bits_for(n);
+  const bool sl = !g->teleport;
+  const uint64_t mk = m_in + (sl ? n : 0);
+  // validation before anything else
+  uint32_t *flag = nullptr;
+  CK(dalloc(&flag, 1));
+  CK(cudaMemsetAsync(flag, 0, 4, st));
+  if (m_in) k_validate_pairs<<<grid_for(m_in), 256, 0, st>>>(src_d, dst_d, m_in, n, flag);
+  uint32_t bad = 0;
+  CK(cudaMemcpyAsync(&bad, flag, 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  cudaFree(flag);
+  if (bad) {
+    g->err = "vertex id out of range";
+    return PR_ERR_VERTEX_RANGE;
+  }
+  if ((double)mk * 1.13 + 6.0 * n > 4.0e9) {
+    g->err = "graph too large: more than 2^32 - 1 column slots";
+    return PR_ERR_CAPACITY;
+  }
+  // scratch for the build
+  uint64_t *keys = nullptr, *alt = nullptr;
+  uint32_t *flags = nullptr, *pos = nullptr, *hist = nullptr, *stmp = nullptr, *cnt = nullptr;
+  const uint64_t mk1 = std::max<uint64_t>(mk, 1);
+  const uint64_t big = std::max<uint64_t>(mk1 + 1, (uint64_t)n + 1);
+  pr_status rc = PR_OK;
+  auto cleanup = [&]() {
+    cudaFree(keys); cudaFree(alt); cudaFree(flags); cudaFree(pos); cudaFree(hist); cudaFree(stmp); cudaFree(cnt);
+  };
+  cudaError_t e = cudaSuccess;
+  if ((e = dalloc(&keys, mk1)) != cudaSuccess || (e = dalloc(&alt, mk1)) != cudaSuccess ||
+      (e = dalloc(&flags, big)) != cudaSuccess || (e = dalloc(&pos, big)) != cudaSuccess ||
+      (e = dalloc(&hist, std::max(radix_hist_words(mk1), scan_tmp_words(big)) + 1)) != cudaSuccess ||
+      (e = dalloc(&stmp, scan_tmp_words(std::max<uint64_t>(big, radix_hist_words(mk1))) + 1)) != cudaSuccess ||
+      (e = dalloc(&cnt, 1)) != cudaSuccess) {
+    cleanup();
+    return cuda_fail(g, e, "graph build scratch");
+  }
+  do {
+    if (mk) k_make_keys<<<grid_for(mk), 256, 0, st>>>(src_d, dst_d, m_in, n, g->b, sl ? 1 : 0, keys);
+    uint64_t *sorted = sort_u64(keys, alt, mk, 2 * g->b, hist, stmp, st);
+    uint64_t *other = sorted == keys ? alt : keys;
+    uint32_t m = 0;
+    if (mk) {
+      k_unique_flags<<<grid_for(mk), 256, 0, st>>>(sorted, mk, flags);
+      exclusive_scan_u32(flags, pos, mk, stmp, st);
+      k_compact_unique<<<grid_for(mk), 256, 0, st>>>(sorted, pos, mk, other, cnt);
+      if ((e = cudaMemcpyAsync(&m, cnt, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess) break;
+      if ((e = cudaStreamSynchronize(st)) != cudaSuccess) break;
+    }
+    g->m = m;
+    // out-adjacency from keys sorted by (u, v)
+    rc = build_adj(g, other, m, g->out, flags, pos, stmp);
+    if (rc != PR_OK) break;
+    // in-adjacency from transposed keys sorted by (v, u)
+    if (m) k_transpose_keys<<<grid_for(m), 256, 0, st>>>(other, m, g->b, sorted);
+    uint64_t *tsorted = sort_u64(sorted, other, m, 2 * g->b, hist, stmp, st);
+    rc = build_adj(g, tsorted, m, g->in, flags, pos, stmp);
+    if (rc != PR_OK) break;
+    e = cudaStreamSynchronize(st);
+  } while (0);
+  cleanup();
+  if (e != cudaSuccess) return cuda_fail(g, e, "graph build");
+  if (rc != PR_OK) return rc;
+
+  // rank state
+  const size_t es = g->f32 ? 4 : 8;
+  for (int i = 0; i < 2; i++) {
+    CK(cudaMalloc(&g->R[i], es * n));
+    CK(cudaMalloc(&g->C[i], es * n));
+  }
+  CK(cudaMalloc(&g->adeg, es * n));
+  const uint32_t words = (n + 31) / 32;
+  CK(dalloc(&g->bitmap, words));
+  CK(cudaMemsetAsync(g->bitmap, 0, 4ull * words, st));
+  for (int i = 0; i < 3; i++) CK(dalloc(&g->list[i], n));
+  CK(dalloc(&g->ident, n));
+  CK(dalloc(&g->dead, n));
+  CK(dalloc(&g->gen_tmp, (uint64_t)n + 2));
+  CK(dalloc(&g->gen_tmp2, (uint64_t)n + 2));
+  CK(dalloc(&g->scan_tmp, scan_tmp_words((uint64_t)n + 2) + 1));
+  g->pend_cap = std::max<uint32_t>(1u << 16, std::min<uint32_t>(n, 1u << 22));
+  CK(dalloc(&g->pend_src, g->pend_cap));
+  CK(dalloc(&g->pend_tgt, g->pend_cap));
+  CK(dalloc(&g->actl, 1));
+  CK(cudaMallocHost((void **)&g->actl_h, sizeof(ApplyCtl)));
+  if (g->f32)
+    k_init_rank<float><<<grid_for(n), 256, 0, st>>>(g->out.rd, n, g->p.alpha, (float *)g->adeg, (float *)g->R[0],
+                                                    (float *)g->R[1], (float *)g->C[0], (float *)g->C[1]);
+  else
+    k_init_rank<double><<<grid_for(n), 256, 0, st>>>(g->out.rd, n, g->p.alpha, (double *)g->adeg, (double *)g->R[0],
+                                                     (double *)g->R[1], (double *)g->C[0], (double *)g->C[1]);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  g->ident_dirty = true;
+  g->dead_dirty = true;
+  return PR_OK;
+}
+
+pr_status apply_scratch(Graph *g, uint64_t N) {
+  ApplyScratch &s = g->sc;
+  if (N <= s.cap && s.pairs) return PR_OK;
+  uint64_t cap = std::max<uint64_t>(N, 4096);
+  cudaFree(s.pairs); cudaFree(s.kd); cudaFree(s.ki); cudaFree(s.tmp); cudaFree(s.tmp2);
+  cudaFree(s.chg); cudaFree(s.chg_t); cudaFree(s.flags); cudaFree(s.pos); cudaFree(s.seg);
+  cudaFree(s.tagpref); cudaFree(s.radix_hist); cudaFree(s.scan_tmp);
+  s = ApplyScratch{};
+  CK(dalloc(&s.pairs, 2 * cap));
+  CK(dalloc(&s.kd, cap));
+  CK(dalloc(&s.ki, cap));
+  CK(dalloc(&s.tmp, cap));
+  CK(dalloc(&s.tmp2, cap));
+  CK(dalloc(&s.chg, cap));
+  CK(dalloc(&s.chg_t, cap));
+  CK(dalloc(&s.flags, cap + 2));
+  CK(dalloc(&s.pos, cap + 2));
+  CK(dalloc(&s.seg, 2 * (cap + 2)));
+  CK(dalloc(&s.tagpref, 2 * (cap + 2)));
+  s.radix_hist_cap = radix_hist_words(cap) + 256;
+  CK(dalloc(&s.radix_hist, s.radix_hist_cap));
+  s.scan_tmp_cap = scan_tmp_words(std::max<uint64_t>(cap + 2, s.radix_hist_cap)) + 1;
+  CK(dalloc(&s.scan_tmp, s.scan_tmp_cap));
+  s.cap = cap;
+  return PR_OK;
+}
+
+// Rebuilds adjacency A with fresh slack and at least `reserve` free tail words.
+static pr_status repack_adj(Graph *g, Adj &A, uint64_t reserve) {
+  const uint32_t n = g->n;
+  cudaStream_t st = g->st;
+  k_len_caps<<<grid_for(n), 256, 0, st>>>(A.rd, n, A.cap);
+  exclusive_scan_u32(A.cap, g->gen_tmp, n, g->scan_tmp, st);
+  uint32_t last[2];
+  CK(cudaMemcpyAsync(&last[0], g->gen_tmp + (n - 1), 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&last[1], A.cap + (n - 1), 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  uint64_t total = (uint64_t)last[0] + last[1];
+  reserve = std::max<uint64_t>(reserve, std::max<uint64_t>(total / 4, 1024));
+  reserve = (reserve + 3) & ~3ull;
+  if (total + reserve > 0xFFFFFFFFull) {
+    g->err = "graph too large: more than 2^32 - 1 column slots";
+    return PR_ERR_CAPACITY;
+  }
+  uint32_t *nc = nullptr;
+  CK(dalloc(&nc, total + reserve));
+  CK(cudaMemsetAsync(nc, 0, sizeof(uint32_t) * (total + reserve), st));
+  k_repack_rows<<<grid_for((uint64_t)n * 32), 256, 0, st>>>(A.rd, n, A.col, nc, g->gen_tmp);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  cudaFree(A.col);
+  A.col = nc;
+  A.col_cap = total + reserve;
+  A.used = total;
+  A.garbage = 0;
+  return PR_OK;
+}
+
+pr_status graph_apply(Graph *g, uint64_t nd, const uint32_t *ds, const uint32_t *dd, uint64_t ni, const uint32_t *is,
+                      const uint32_t *id) {
+  const uint64_t N = nd + ni;
+  if (N == 0) return PR_OK;
+  cudaStream_t st = g->st;
+  pr_status rc = apply_scratch(g, N);
+  if (rc != PR_OK) return rc;
+  ApplyScratch &s = g->sc;
+  const int b = g->b;
+  const int kbits = 2 * b + 1;
+
+  ApplyCtl &h = *g->actl_h;
+  memset(&h, 0, sizeof(ApplyCtl));
+  h.n_pend_src = g->n_pend_src;
+  h.n_pend_tgt = g->n_pend_tgt;
+  h.tail_out = g->out.used;
+  h.tail_in = g->in.used;
+  CK(cudaMemcpyAsync(g->actl, &h, sizeof(ApplyCtl), cudaMemcpyHostToDevice, st));
+
+  k_batch_keys<<<grid_for(N), 256, 0, st>>>(ds, dd, nd, is, id, ni, g->n, b, s.kd, s.ki, g->actl);
+  uint64_t *kd = sort_u64(s.kd, s.tmp, nd, 2 * b, s.radix_hist, s.scan_tmp, st);
+  uint64_t *ki = sort_u64(s.ki, s.tmp2, ni, 2 * b, s.radix_hist, s.scan_tmp, st);
+  k_filter<<<grid_for(N), 256, 0, st>>>(kd, nd, ki, ni, g->out.rd, g->out.col, b, s.flags);
+  exclusive_scan_u32(s.flags, s.pos, N, s.scan_tmp, st);
+  uint64_t *chg = kd == s.kd ? s.tmp : s.kd;     // free buffers after the sorts
+  uint64_t *chg_t = ki == s.ki ? s.tmp2 : s.ki;
+  k_emit_changes<<<grid_for(N), 256, 0, st>>>(kd, nd, ki, ni, s.flags, s.pos, b, s.chg, s.chg_t, g->actl);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(&h, g->actl, sizeof(ApplyCtl), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (h.bad_id) {
+    g->err = "vertex id out of range";
+    return PR_ERR_VERTEX_RANGE;
+  }
+  const uint32_t K = h.n_eff;
+  const uint32_t K_del = h.n_eff_del;
+  if (K == 0) return PR_OK;
+
+  uint64_t *co = sort_u64(s.chg, chg, K, kbits, s.radix_hist, s.scan_tmp, st);
+  uint64_t *ci = sort_u64(s.chg_t, chg_t, K, kbits, s.radix_hist, s.scan_tmp, st);
+  uint32_t *seg_o = s.seg, *seg_i = s.seg + (s.cap + 2);
+  uint32_t *tp_o = s.tagpref, *tp_i = s.tagpref + (s.cap + 2);
+  ApplyCtl *dctl = g->actl;
+  // segments of the out-row changes
+  k_seg_flags<<<grid_for(K + 1), 256, 0, st>>>(co, K, b, s.flags, tp_o);
+  exclusive_scan_u32(s.flags, s.pos, K, s.scan_tmp, st);
+  exclusive_scan_u32(tp_o, tp_o, K + 1, s.scan_tmp, st);
+  k_seg_emit<<<grid_for(K), 256, 0, st>>>(s.flags, s.pos, K, seg_o, &dctl->n_seg_out);
+  k_plan<<<grid_for(K), 256, 0, st>>>(g->out.rd, g->out.cap, co, K, b, seg_o, &dctl->n_seg_out, tp_o,
+                                      &dctl->reloc_out, &dctl->big_cursor);
+  // segments of the in-row changes
+  k_seg_flags<<<grid_for(K + 1), 256, 0, st>>>(ci, K, b, s.flags, tp_i);
+  exclusive_scan_u32(s.flags, s.pos, K, s.scan_tmp, st);
+  exclusive_scan_u32(tp_i, tp_i, K + 1, s.scan_tmp, st);
+  k_seg_emit<<<grid_for(K), 256, 0, st>>>(s.flags, s.pos, K, seg_i, &dctl->n_seg_in);
+  k_plan<<<grid_for(K), 256, 0, st>>>(g->in.rd, g->in.cap, ci, K, b, seg_i, &dctl->n_seg_in, tp_i,
+                                      &dctl->reloc_in, &dctl->big_cursor);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(&h, g->actl, sizeof(ApplyCtl), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+
+  // room for moved rows and staging of long rows; a repack gives rows fresh (possibly
+  // smaller) slack, so the plan is redone after one
+  for (int round = 0; round < 4; round++) {
+    bool again = false;
+    if (g->out.used + h.reloc_out > g->out.col_cap) {
+      rc = repack_adj(g, g->out, 2 * h.reloc_out);
+      if (rc != PR_OK) return rc;
+      again = true;
+    }
+    if (g->in.used + h.reloc_in > g->in.col_cap) {
+      rc = repack_adj(g, g->in, 2 * h.reloc_in);
+      if (rc != PR_OK) return rc;
+      again = true;
+    }
+    if (!again) break;
+    CK(cudaMemsetAsync(&dctl->reloc_out, 0, 16, st));  // reloc_out, reloc_in
+    CK(cudaMemsetAsync(&dctl->big_cursor, 0, 8, st));
+    k_plan<<<grid_for(K), 256, 0, st>>>(g->out.rd, g->out.cap, co, K, b, seg_o, &dctl->n_seg_out, tp_o,
+                                        &dctl->reloc_out, &dctl->big_cursor);
+    k_plan<<<grid_for(K), 256, 0, st>>>(g->in.rd, g->in.cap, ci, K, b, seg_i, &dctl->n_seg_in, tp_i,
+                                        &dctl->reloc_in, &dctl->big_cursor);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(&h, g->actl, sizeof(ApplyCtl), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  if (h.big_cursor > g->big_cap) {
+    cudaFree(g->big);
+    g->big = nullptr;
+    g->big_cap = 0;
+    uint64_t c = std::max<uint64_t>(h.big_cursor * 2, 1u << 20);
+    CK(dalloc(&g->big, c));
+    g->big_cap = c;
+  }
+  h.tail_out = g->out.used;
+  h.tail_in = g->in.used;
+  h.big_cursor = 0;
+  CK(cudaMemcpyAsync(&dctl->tail_out, &h.tail_out, 16, cudaMemcpyHostToDevice, st));  // tail_out, tail_in
+  CK(cudaMemsetAsync(&dctl->big_cursor, 0, 8, st));
+
+  if (g->f32) {
+    OutRowHook<float> ho{true, g->p.alpha, (float *)g->adeg, (float *)g->R[0], (float *)g->C[0], (float *)g->C[1],
+                         g->pend_src, g->pend_tgt, g->pend_cap};
+    OutRowHook<float> hi{};
+    k_merge<float><<<K, kMergeThreads, 0, st>>>(g->out.rd, g->out.cap, g->out.col, co, b, seg_o, &dctl->n_seg_out,
+                                                tp_o, &dctl->tail_out, &dctl->garbage_out, g->big, &dctl->big_cursor,
+                                                g->out.col_cap, g->big_cap, dctl, ho);
+    k_merge<float><<<K, kMergeThreads, 0, st>>>(g->in.rd, g->in.cap, g->in.col, ci, b, seg_i, &dctl->n_seg_in, tp_i,
+                                                &dctl->tail_in, &dctl->garbage_in, g->big, &dctl->big_cursor,
+                                                g->in.col_cap, g->big_cap, dctl, hi);
+  } else {
+    OutRowHook<double> ho{true, g->p.alpha, (double *)g->adeg, (double *)g->R[0], (double *)g->C[0],
+                          (double *)g->C[1], g->pend_src, g->pend_tgt, g->pend_cap};
+    OutRowHook<double> hi{};
+    k_merge<double><<<K, kMergeThreads, 0, st>>>(g->out.rd, g->out.cap, g->out.col, co, b, seg_o, &dctl->n_seg_out,
+                                                 tp_o, &dctl->tail_out, &dctl->garbage_out, g->big, &dctl->big_cursor,
+                                                 g->out.col_cap, g->big_cap, dctl, ho);
+    k_merge<double><<<K, kMergeThreads, 0, st>>>(g->in.rd, g->in.cap, g->in.col, ci, b, seg_i, &dctl->n_seg_in, tp_i,
+                                                 &dctl->tail_in, &dctl->garbage_in, g->big, &dctl->big_cursor,
+                                                 g->in.col_cap, g->big_cap, dctl, hi);
+  }
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(&h, g->actl, sizeof(ApplyCtl), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (h.overflow) {
+    g->err = "internal error: no room for a moved row (graph rows partly updated)";
+    return PR_ERR_CUDA;
+  }
+
+  g->m = g->m + (uint64_t)(K - K_del) - (uint64_t)K_del;
+  g->out.used = h.tail_out;
+  g->in.used = h.tail_in;
+  g->out.garbage += h.garbage_out;
+  g->in.garbage += h.garbage_in;
+  g->n_pend_src = std::min(h.n_pend_src, g->pend_cap);
+  g->n_pend_tgt = std::min(h.n_pend_tgt, g->pend_cap);
+  if (h.n_pend_src > g->pend_cap || h.n_pend_tgt > g->pend_cap) g->pend_all = true;
+  if (h.dead_changed) g->dead_dirty = true;
+  g->ident_dirty = true;
+  // give abandoned slots back once they dominate
+  if (g->out.garbage > g->out.used / 2 && g->out.garbage > 1024) {
+    rc = repack_adj(g, g->out, 0);
+    if (rc != PR_OK) return rc;
+  }
+  if (g->in.garbage > g->in.used / 2 && g->in.garbage > 1024) {
+    rc = repack_adj(g, g->in, 0);
+    if (rc != PR_OK) return rc;
+  }
+  return PR_OK;
+}
+
+pr_status graph_export(Graph *g, int dir, uint64_t *offs_h, uint32_t *cols_h) {
+  const uint32_t n = g->n;
+  cudaStream_t st = g->st;
+  Adj &A = dir ? g->in : g->out;
+  k_row_len<<<grid_for((uint64_t)n + 1), 256, 0, st>>>(A.rd, n, g->gen_tmp);
+  exclusive_scan_u32(g->gen_tmp, g->gen_tmp2, (uint64_t)n + 1, g->scan_tmp, st);
+  uint32_t *packed = nullptr;
+  CK(dalloc(&packed, std::max<uint64_t>(g->m, 1)));
+  k_pack_rows<<<grid_for((uint64_t)n * 32), 256, 0, st>>>(A.rd, n, A.col, g->gen_tmp2, packed);
+  std::vector<uint32_t> off(n + 1);
+  cudaError_t e = cudaMemcpyAsync(off.data(), g->gen_tmp2, 4ull * (n + 1), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(cols_h, packed, 4ull * g->m, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(packed);
+  if (e != cudaSuccess) return cuda_fail(g, e, "export csr");
+  for (uint32_t v = 0; v <= n; v++) offs_h[v] = off[v];
+  return PR_OK;
+}
+
+pr_status graph_refresh_ident(Graph *g) {
+  if (!g->ident_dirty) return PR_OK;
+  const uint32_t n = g->n;
+  cudaStream_t st = g->st;
+  uint32_t *cnt = (uint32_t *)&g->actl->n_seg_out;  // reuse a device word
+  uint32_t base = 0;
+  for (int bin = 0; bin < 3; bin++) {
+    k_bin_flags<<<grid_for(n), 256, 0, st>>>(g->in.rd, n, (uint32_t)g->p.bin_lo, (uint32_t)g->p.bin_hi, bin,
+                                            g->gen_tmp);
+    exclusive_scan_u32(g->gen_tmp, g->gen_tmp2, n, g->scan_tmp, st);
+    k_compact_ids<<<grid_for(n), 256, 0, st>>>(g->gen_tmp, g->gen_tmp2, n, g->ident + base, cnt);
+    uint32_t c = 0;
+    CK(cudaMemcpyAsync(&c, cnt, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    g->ident_cnt[bin] = c;
+    base += c;
+  }
+  g->ident_dirty = false;
+  return PR_OK;
+}
+
+pr_status graph_refresh_dead(Graph *g) {
+  if (!g->dead_dirty) return PR_OK;
+  const uint32_t n = g->n;
+  cudaStream_t st = g->st;
+  uint32_t *cnt = (uint32_t *)&g->actl->n_seg_in;
+  k_dead_flags<<<grid_for(n), 256, 0, st>>>(g->out.rd, n, g->gen_tmp);
+  exclusive_scan_u32(g->gen_tmp, g->gen_tmp2, n, g->scan_tmp, st);
+  k_compact_ids<<<grid_for(n), 256, 0, st>>>(g->gen_tmp, g->gen_tmp2, n, g->dead, cnt);
+  uint32_t c = 0;
+  CK(cudaMemcpyAsync(&c, cnt, 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  g->n_dead = c;
+  g->dead_dirty = false;
+  return PR_OK;
+}
+
+void graph_free(Graph *g) {
+  Adj *adjs[2] = {&g->out, &g->in};
+  for (Adj *A : adjs) {
+    cudaFree(A->rd);
+    cudaFree(A->cap);
+    cudaFree(A->col);
+  }
+  for (int i = 0; i < 2; i++) {
+    cudaFree(g->R[i]);
+    cudaFree(g->C[i]);
+  }
+  cudaFree(g->adeg);
+  cudaFree(g->bitmap);
+  for (int i = 0; i < 3; i++) cudaFree(g->list[i]);
+  cudaFree(g->ident);
+  cudaFree(g->dead);
+  cudaFree(g->pend_src);
+  cudaFree(g->pend_tgt);
+  cudaFree(g->ctl);
+  if (g->ctl_h) cudaFreeHost(g->ctl_h);
+  cudaFree(g->dpart);
+  ApplyScratch &s = g->sc;
+  cudaFree(s.pairs); cudaFree(s.kd); cudaFree(s.ki); cudaFree(s.tmp); cudaFree(s.tmp2);
+  cudaFree(s.chg); cudaFree(s.chg_t); cudaFree(s.flags); cudaFree(s.pos); cudaFree(s.seg);
+  cudaFree(s.tagpref); cudaFree(s.radix_hist); cudaFree(s.scan_tmp);
+  cudaFree(g->actl);
+  if (g->actl_h) cudaFreeHost(g->actl_h);
+  cudaFree(g->big);
+  cudaFree(g->gen_tmp);
+  cudaFree(g->gen_tmp2);
+  cudaFree(g->scan_tmp);
+  if (g->ev0) cudaEventDestroy(g->ev0);
+  if (g->ev1) cudaEventDestroy(g->ev1);
+}
+
+}  // namespace prdf

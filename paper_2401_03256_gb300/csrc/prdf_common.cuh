@@ -1,0 +1,128 @@
+// prdf_common.cuh - internal declarations of the GB300 Dynamic Frontier PageRank library.
+//
+// Graph storage is a "slack-row" paired CSR: for each adjacency (in-edges, out-edges)
+// row v is described by rd[v] = {start, len} into one column array, rows are kept
+// sorted, every row starts on a 16-byte boundary (start % 4 == 0) and owns cap[v] >= len
+// slots, so a batch update rewrites only the rows it touches (in place while they fit,
+// otherwise the row moves to the free tail of the column array).  The packed canonical
+// CSR is produced on demand by pr_get_csr.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace prdf {
+
+constexpr int kMaxIterLimit = 1000;       // hard cap on max_iter (control arrays are sized by it)
+constexpr uint64_t kSentinel = ~0ull;     // key of a dropped pair
+constexpr int kRankBlock = 256;           // threads per block of the rank kernel
+constexpr uint32_t kSmallSort = 4096;     // largest key count sorted by one block
+
+// ----------------------------------------------------------------- device helpers ---
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void red_release_add_u32(uint32_t *p, uint32_t v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// ------------------------------------------------------------------- structures ---
+
+// One adjacency (in- or out-edges) in slack-row form.
+struct Adj {
+  uint2 *rd = nullptr;      // [n] {start, len}
+  uint32_t *cap = nullptr;  // [n] slots owned by the row (multiple of 4)
+  uint32_t *col = nullptr;  // [col_cap]
+  uint64_t col_cap = 0;     // words allocated for col
+  uint64_t used = 0;        // words handed out (host mirror, refreshed after updates)
+  uint64_t garbage = 0;     // words of rows abandoned by moves (host mirror)
+};
+
+// Device control block of the rank kernel; zeroed before every launch.
+struct RankCtl {
+  uint32_t bar;                                   // grid barrier arrivals (monotonic)
+  uint32_t err;                                   // nonzero: a bounded wait gave up
+  uint32_t err_where;
+  uint32_t iterations;
+  uint32_t converged;
+  uint32_t full_from;                             // iteration from which all of V is affected (+1; 0 = never)
+  uint32_t final_cnt[3];                          // affected-list lengths at the end (Dynamic Frontier)
+  uint32_t pad;
+  double last_delta;                              // L-inf change of the last iteration
+  double D_final;                                 // dead-end mass of the final ranks (teleport mode)
+  unsigned long long dR_bits[kMaxIterLimit + 1];  // per-iteration L-inf (bits of a non-negative double)
+  uint32_t tail[kMaxIterLimit + 2][4];            // per-iteration appends per bin ([0] = initial marks)
+  uint32_t blk_next[kMaxIterLimit + 1];           // dynamic index into the block bin
+  unsigned long long vproc, eproc, expv, expe, appended;
+};
+
+// Per-block Neumaier partials of the dead-end mass, double-buffered by iteration parity.
+struct DeadPart {
+  double s, c;
+};
+
+// Scratch of a batch update.
+struct ApplyScratch {
+  uint64_t cap = 0;             // capacity in pairs
+  uint32_t *pairs = nullptr;    // 4 * cap: del_src, del_dst, ins_src, ins_dst
+  uint64_t *kd = nullptr, *ki = nullptr, *tmp = nullptr, *tmp2 = nullptr;  // keys [2 cap] each
+  uint64_t *chg = nullptr, *chg_t = nullptr;   // tagged change lists [2 cap]
+  uint32_t *flags = nullptr, *pos = nullptr;   // [2 cap + 1]
+  uint32_t *seg = nullptr;                      // segment starts [2 cap + 1]
+  uint32_t *tagpref = nullptr;                  // [2 cap + 1]
+  uint32_t *radix_hist = nullptr;               // radix histogram scratch
+  uint64_t radix_hist_cap = 0;
+  uint32_t *scan_tmp = nullptr;                 // scan block sums
+  uint64_t scan_tmp_cap = 0;
+};
+
+// Device-side counters of a batch update (one struct, read back once).
+struct ApplyCtl {
+  uint32_t bad_id;
+  uint32_t n_eff;        // effective changes (deletions + insertions)
+  uint32_t n_seg_out, n_seg_in;
+  unsigned long long reloc_out, reloc_in;   // words needed by rows that must move
+  unsigned long long tail_out, tail_in;     // running allocation cursors (device)
+  unsigned long long garbage_out, garbage_in;
+  uint32_t n_pend_src, n_pend_tgt;          // pending marks after this update
+  uint32_t pend_overflow;
+  uint32_t dead_changed;
+  uint32_t n_eff_del;                       // effective deletions among n_eff
+  uint32_t overflow;                        // a merge found no room (graph left unchanged rows)
+  unsigned long long big_cursor;            // global scratch cursor for long rows
+};
+
+// ------------------------------------------------------------------- primitives ---
+// All run on `st`; counts are host values.  Implemented in prim.cu.
+
+// Exclusive scan of n uint32 values (out may alias in); returns nothing; tmp sized by
+// scan_tmp_words(n).
+size_t scan_tmp_words(uint64_t n);
+void exclusive_scan_u32(const uint32_t *in, uint32_t *out, uint64_t n, uint32_t *tmp, cudaStream_t st);
+
+// Sort n 64-bit keys on their low `bits` bits (stable LSD radix; one block when
+// n <= kSmallSort).  keys and alt are both n long; the result is returned (one of them).
+size_t radix_hist_words(uint64_t n);
+uint64_t *sort_u64(uint64_t *keys, uint64_t *alt, uint64_t n, int bits, uint32_t *hist,
+                   uint32_t *scan_tmp, cudaStream_t st);
+
+int bits_for(uint32_t n);  // bits needed for ids in [0, n), at least 1
+
+}  // namespace prdf

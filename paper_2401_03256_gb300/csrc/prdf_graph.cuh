@@ -1,0 +1,91 @@
+// prdf_graph.cuh - the graph handle behind the opaque pr_graph of the C ABI.
+#pragma once
+
+#include <string>
+
+#include "prdf_common.cuh"
+#include "../../include/prdf.h"
+
+namespace prdf {
+
+// Rows get room to grow: cap = round4(len + 2 + len / 8) at build / repack time,
+// round4(2 len + 2) when a row outgrows its slots and moves to the free tail.
+__host__ __device__ inline uint32_t slack_cap(uint32_t len) {
+  uint64_t c = (uint64_t)len + 2 + len / 8;
+  return (uint32_t)((c + 3) & ~3ull);
+}
+__host__ __device__ inline uint32_t move_cap(uint32_t len) {
+  uint64_t c = 2ull * len + 2;
+  return (uint32_t)((c + 3) & ~3ull);
+}
+
+struct Graph {
+  int device = 0;
+  cudaStream_t st = nullptr;
+  int sm_count = 0;
+  uint32_t n = 0;
+  int b = 1;             // bits of a vertex id in packed keys
+  uint64_t m = 0;        // stored edges (self-loops included)
+  pr_params p{};
+  bool f32 = false;
+  bool teleport = false;
+
+  Adj out, in;
+  void *R[2] = {nullptr, nullptr};   // ranks, both parities equal between calls
+  void *C[2] = {nullptr, nullptr};   // contributions alpha R[u] / |out(u)|
+  void *adeg = nullptr;              // alpha / |out(u)| (0 for a dead end)
+  uint32_t *bitmap = nullptr;        // affected flags, all zero between calls
+  uint32_t *list[3] = {nullptr, nullptr, nullptr};  // affected vertices by in-degree bin
+  uint32_t *ident = nullptr;         // all vertices grouped by bin (for full sweeps)
+  uint32_t ident_cnt[3] = {0, 0, 0};
+  bool ident_dirty = true;
+  uint32_t *dead = nullptr;          // vertices with out-degree 0 (teleport mode)
+  uint32_t n_dead = 0;
+  bool dead_dirty = true;
+  double D_ref = 0.0;                // dead-end mass of the ranks under the graph they were computed on
+
+  uint32_t *pend_src = nullptr, *pend_tgt = nullptr;  // pending marks of applied batches
+  uint32_t pend_cap = 0;
+  uint32_t n_pend_src = 0, n_pend_tgt = 0;
+  bool pend_all = false;
+
+  RankCtl *ctl = nullptr;            // device
+  RankCtl *ctl_h = nullptr;          // pinned host mirror
+  DeadPart *dpart = nullptr;         // [2][rank_grid]
+  int rank_grid = 0;                 // cooperative grid of the rank kernel
+  uint32_t last_list_cnt[3] = {0, 0, 0};
+  bool last_full = false;
+
+  ApplyScratch sc;
+  ApplyCtl *actl = nullptr, *actl_h = nullptr;
+  uint32_t *big = nullptr;           // scratch for rows longer than shared memory
+  uint64_t big_cap = 0;
+  uint32_t *gen_tmp = nullptr;       // general scratch (scans, flags) sized n + 1
+  uint32_t *gen_tmp2 = nullptr;
+  uint32_t *scan_tmp = nullptr;      // block sums of scans over n
+  double ms_apply = 0.0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::string err;
+};
+
+// graph.cu
+pr_status graph_build(Graph *g, uint64_t m_in, const uint32_t *src_d, const uint32_t *dst_d);
+pr_status graph_apply(Graph *g, uint64_t nd, const uint32_t *ds_d, const uint32_t *dd_d, uint64_t ni,
+                      const uint32_t *is_d, const uint32_t *id_d);
+pr_status apply_scratch(Graph *g, uint64_t N);
+pr_status graph_export(Graph *g, int dir, uint64_t *offs_h, uint32_t *cols_h);
+pr_status graph_refresh_ident(Graph *g);
+pr_status graph_refresh_dead(Graph *g);
+void graph_free(Graph *g);
+pr_status cuda_fail(Graph *g, cudaError_t e, const char *what);
+
+// rank.cu
+enum RankMode { kModeDF = 0, kModeNaive = 1, kModeStatic = 2 };
+pr_status rank_setup(Graph *g);  // grid size, control block
+pr_status rank_run(Graph *g, RankMode mode, pr_stats *stats);
+pr_status rank_init_contrib(Graph *g);  // C = R * adeg for all v, both parities
+pr_status rank_set(Graph *g, const double *in_d);
+pr_status rank_get(Graph *g, double *out_d);
+pr_status rank_dead_mass(Graph *g, double *D);
+
+}  // namespace prdf

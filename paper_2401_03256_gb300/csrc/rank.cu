@@ -1,0 +1,743 @@
+// rank.cu - the rank engine: Static, Naive-dynamic and Dynamic Frontier PageRank in one
+// persistent cooperative kernel per call.
+//
+// Eq. 1 (Section 3.1) in pull form: R[v] = (1 - alpha)/n + sum_{u in in(v)} C[u] with the
+// cached contribution C[u] = alpha R[u] / |out(u)|; in teleport mode a dead end's rank is
+// spread over all vertices (+ alpha D / n, D = sum of ranks of dead ends).
+//
+// Algorithm 1, synchronous form (Section 4.2):
+//   phase 0   initial marking: every vertex of G^t.out(u) for each source u of the
+//             pending changes, plus the deleted targets (= G^{t-1}.out(u) \ G^t.out(u)),
+//             is set in the affected bitmap and appended to one of three lists by
+//             in-degree (thread / warp / block per vertex).
+//   iteration i: every listed vertex v reads ranks and contributions of parity i & 1 and
+//             writes parity (i + 1) & 1; |r - R[v]| feeds the L-inf max (atomicMax on the
+//             bits of a non-negative double) and, if it exceeds tau_f, the out-neighbours
+//             of v are marked and appended; they are processed from iteration i + 1.
+//             One grid barrier per iteration; all blocks read the same L-inf value and
+//             stop together when it is <= tau.
+//   writeback the final parity is copied to the other for every listed vertex (both
+//             parities hold the current ranks between calls) and the bitmap is cleared.
+// Static and Naive-dynamic run the same loop over all vertices (grouped by bin once per
+// graph change) without marking.
+//
+// Every value written by another block during the kernel (ranks, contributions, lists,
+// per-iteration counters) is read with ld.global.cg (L2), never from a possibly stale L1.
+// The grid barrier's wait is bounded (globaltimer); on time-out the kernel records an
+// error and every block returns.
+#include <algorithm>
+
+#include "prdf_graph.cuh"
+
+namespace prdf {
+
+constexpr uint64_t kBarrierTimeoutNs = 4000000000ull;  // 4 s
+constexpr int kWarps = kRankBlock / 32;
+constexpr uint32_t kFull = 0xffffffffu;
+
+template <class T>
+struct RankArgs {
+  uint32_t n;
+  const uint2 *in_rd;
+  const uint32_t *in_col;
+  const uint2 *out_rd;
+  const uint32_t *out_col;
+  T *R0, *R1, *C0, *C1;
+  const T *adeg;
+  uint32_t *bitmap;
+  uint32_t *list0, *list1, *list2;
+  const uint32_t *ident;
+  uint32_t id_cnt0, id_cnt1, id_cnt2;
+  const uint32_t *pend_src;
+  uint32_t n_pend_src;
+  const uint32_t *pend_tgt;
+  uint32_t n_pend_tgt;
+  const uint32_t *dead;
+  uint32_t n_dead;
+  DeadPart *dpart;  // [2][gridDim.x]
+  double base;      // (1 - alpha) / n
+  double tele;      // alpha / n in teleport mode, else 0
+  double alpha_over_n;
+  double D_ref;     // dead-end mass of the previous ranks on the previous graph
+  double tol, ftol;
+  int max_iter;
+  int mode;         // RankMode
+  int teleport;
+  int start_full;   // Dynamic Frontier with every vertex affected from iteration 0
+  uint32_t bin_lo, bin_hi;
+  RankCtl *ctl;
+};
+
+// Neumaier's compensated summation (Neumaier 1974).
+struct Neu {
+  double s = 0.0, c = 0.0;
+  __device__ __forceinline__ void add(double x) {
+    double t = s + x;
+    if (fabs(s) >= fabs(x)) c += (s - t) + x; else c += (x - t) + s;
+    s = t;
+  }
+  __device__ __forceinline__ void merge(double os, double oc) {
+    add(os);
+    c += oc;
+  }
+};
+
+__device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
+__device__ __forceinline__ float ldcg(const float *p) { return __ldcg(p); }
+__device__ __forceinline__ uint32_t ldcg(const uint32_t *p) { return __ldcg(p); }
+
+// Grid-wide barrier with a bounded wait.  Returns false (in every thread of the block)
+// if the device control block holds an error.
+__device__ __forceinline__ bool grid_sync(RankCtl *ctl, uint32_t &epoch, uint32_t *s_err) {
+  __syncthreads();
+  epoch++;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    red_release_add_u32(&ctl->bar, 1u);
+    const uint32_t target = epoch * gridDim.x;
+    uint64_t t0 = 0;
+    uint32_t spins = 0;
+    while (ld_acquire_u32(&ctl->bar) < target) {
+      if (*(volatile uint32_t *)&ctl->err) break;
+      __nanosleep(32);
+      if ((++spins & 127) == 0) {
+        uint64_t t = globaltimer_ns();
+        if (t0 == 0) {
+          t0 = t;
+        } else if (t - t0 > kBarrierTimeoutNs) {
+          atomicExch(&ctl->err_where, epoch);
+          atomicOr(&ctl->err, 1u);
+          break;
+        }
+      }
+    }
+    __threadfence();
+    *s_err = *(volatile uint32_t *)&ctl->err;
+  }
+  __syncthreads();
+  return *s_err == 0;
+}
+
+__device__ __forceinline__ int bin_of(uint32_t deg, uint32_t lo, uint32_t hi) {
+  return deg <= lo ? 0 : (deg <= hi ? 1 : 2);
+}
+
+// Appends, per bin, the lanes' newly marked vertices with one atomic per bin and warp.
+template <class T>
+__device__ __forceinline__ void warp_append(const RankArgs<T> &a, int bin, uint32_t w, uint32_t slot,
+                                            const uint32_t cnt[3], uint32_t lane) {
+  uint32_t *lists[3] = {a.list0, a.list1, a.list2};
+#pragma unroll
+  for (int bb = 0; bb < 3; bb++) {
+    uint32_t mask = __ballot_sync(kFull, bin == bb);
+    if (mask) {
+      uint32_t leader = __ffs(mask) - 1;
+      uint32_t base = 0;
+      if (lane == leader) base = atomicAdd(&a.ctl->tail[slot][bb], (uint32_t)__popc(mask));
+      base = __shfl_sync(kFull, base, leader);
+      if (bin == bb) lists[bb][cnt[bb] + base + __popc(mask & lanemask_lt())] = w;
+    }
+  }
+}
+
+// Marks the out-neighbours cols[first + 32 k + lane] (k = 0, 1, ...; stride `stride`).
+// Called by a whole warp (uniform trip count).
+template <class T>
+__device__ __forceinline__ uint32_t warp_mark_range(const RankArgs<T> &a, const uint32_t *cols, uint32_t len,
+                                                    uint32_t first, uint32_t stride, uint32_t slot,
+                                                    const uint32_t cnt[3], uint32_t lane) {
+  uint32_t newly_total = 0;
+  for (uint32_t j0 = first; j0 < len; j0 += stride) {
+    uint32_t j = j0 + lane;
+    int bin = -1;
+    uint32_t w = 0;
+    if (j < len) {
+      w = __ldg(cols + j);
+      uint32_t bit = 1u << (w & 31);
+      uint32_t *word = a.bitmap + (w >> 5);
+      if (!(ldcg(word) & bit)) {
+        uint32_t old = atomicOr(word, bit);
+        if (!(old & bit)) bin = bin_of(__ldg(&a.in_rd[w]).y, a.bin_lo, a.bin_hi);
+      }
+    }
+    newly_total += bin >= 0;
+    warp_append(a, bin, w, slot, cnt, lane);
+  }
+  return newly_total;
+}
+
+// Sum of C over an aligned run of 4 columns, `valid` of which count.
+template <class T>
+__device__ __forceinline__ T gather4(const T *C, uint4 q, uint32_t valid) {
+  T s = (T)0;
+  if (valid > 0) s += ldcg(C + q.x);
+  if (valid > 1) s += ldcg(C + q.y);
+  if (valid > 2) s += ldcg(C + q.z);
+  if (valid > 3) s += ldcg(C + q.w);
+  return s;
+}
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+  return x;
+}
+
+__device__ __forceinline__ double warp_max(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(kFull, x, o));
+  return x;
+}
+
+struct Iter {
+  uint32_t it;
+  bool full;
+  double D;
+};
+
+// Rank of v from its in-edge sum; writes the new rank and contribution, returns |r - R[v]|.
+template <class T>
+__device__ __forceinline__ double finish_vertex(const RankArgs<T> &a, const T *Rin, T *Rout, T *Cout, uint32_t v,
+                                                T sum, const Iter &I, Neu &dacc) {
+  T r = (T)a.base + sum;
+  if (a.teleport) r += (T)(a.tele * I.D);
+  T rold = ldcg(Rin + v);
+  T ad = __ldg(a.adeg + v);
+  Rout[v] = r;
+  Cout[v] = r * ad;
+  if (a.teleport && ad == (T)0) dacc.add(I.full ? (double)r : (double)r - (double)rold);
+  return fabs((double)r - (double)rold);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kRankBlock) k_rank(const RankArgs<T> a) {
+  __shared__ uint32_t s_q[2][kRankBlock];
+  __shared__ uint32_t s_qn[2];
+  __shared__ uint32_t s_idx, s_err;
+  __shared__ T s_part[kWarps];
+  __shared__ double s_dmax[kWarps];
+  __shared__ double s_ds[kWarps], s_dc[kWarps];
+  __shared__ double s_bcast;
+
+  const uint32_t tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
+  const uint32_t nblk = gridDim.x;
+  const uint32_t nthreads = nblk * kRankBlock;
+  const uint32_t gtid = blockIdx.x * kRankBlock + tid;
+  const uint32_t nwarps = nthreads >> 5, gwarp = gtid >> 5;
+  RankCtl *ctl = a.ctl;
+  uint32_t epoch = 0;
+  const bool df = a.mode == kModeDF;
+  unsigned long long my_v = 0, my_e = 0, my_xv = 0, my_xe = 0, my_app = 0;
+  if (tid < 2) s_qn[tid] = 0;
+
+  // ---------------------------------------------------------------- phase 0
+  Neu dacc;
+  if (a.mode == kModeStatic) {
+    const T r = (T)(1.0 / (double)a.n);
+    for (uint32_t v = gtid; v < a.n; v += nthreads) {
+      T c = r * __ldg(a.adeg + v);
+      a.R0[v] = r;
+      a.R1[v] = r;
+      a.C0[v] = c;
+      a.C1[v] = c;
+    }
+    if (a.teleport)
+      for (uint32_t k = gtid; k < a.n_dead; k += nthreads) dacc.add((double)r);
+  } else if (a.teleport) {
+    for (uint32_t k = gtid; k < a.n_dead; k += nthreads) dacc.add((double)ldcg(a.R0 + __ldg(a.dead + k)));
+  }
+  const uint32_t zero_cnt[3] = {0, 0, 0};
+  if (df && !a.start_full) {
+    // sources: mark G^t.out(u), one warp per source
+    for (uint32_t k = gwarp; k < a.n_pend_src; k += nwarps) {
+      uint32_t u = __ldg(a.pend_src + k);
+      uint2 od = __ldg(&a.out_rd[u]);
+      my_app += warp_mark_range(a, a.out_col + od.x, od.y, 0, 32, 0, zero_cnt, lane);
+    }
+    // deleted targets, 32 per warp round
+    for (uint32_t k0 = gwarp * 32; k0 < a.n_pend_tgt; k0 += nwarps * 32) {
+      uint32_t cnt_left = min(32u, a.n_pend_tgt - k0);
+      my_app += warp_mark_range(a, a.pend_tgt + k0, cnt_left, 0, 32, 0, zero_cnt, lane);
+    }
+  }
+  // dead-end mass of the starting ranks
+  auto block_dead_partial = [&](int parity) {
+    double s = dacc.s, c = dacc.c;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      double os = __shfl_xor_sync(kFull, s, o), oc = __shfl_xor_sync(kFull, c, o);
+      Neu t;
+      t.s = s;
+      t.c = c;
+      t.merge(os, oc);
+      s = t.s;
+      c = t.c;
+    }
+    if (lane == 0) {
+      s_ds[wib] = s;
+      s_dc[wib] = c;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      Neu t;
+      for (int w = 0; w < kWarps; w++) t.merge(s_ds[w], s_dc[w]);
+      a.dpart[parity * nblk + blockIdx.x] = DeadPart{t.s, t.c};
+    }
+    dacc = Neu();
+  };
+  auto grid_dead_total = [&](int parity) {
+    Neu t;
+    for (uint32_t k = 0; k < nblk; k++) {
+      const double *p = &a.dpart[parity * nblk + k].s;
+      t.merge(__ldcg(p), __ldcg(p + 1));
+    }
+    return t.s + t.c;
+  };
+  if (a.teleport) block_dead_partial(0);
+  if (!grid_sync(ctl, epoch, &s_err)) return;
+
+  uint32_t cnt[3];
+#pragma unroll
+  for (int bb = 0; bb < 3; bb++) cnt[bb] = df && !a.start_full ? ldcg(&ctl->tail[0][bb]) : 0u;
+  double D = a.teleport ? grid_dead_total(0) : 0.0;
+  double D_prev = a.D_ref;
+  bool ever_full = !df || a.start_full;
+  uint32_t iters = 0;
+  bool converged = false;
+  double last = 0.0;
+
+  // ------------------------------------------------------------- iterations
+  for (int it = 0; it < a.max_iter; it++) {
+    Iter I;
+    I.it = (uint32_t)it;
+    I.D = D;
+    if (df && a.teleport && !ever_full && a.alpha_over_n * fabs(D - D_prev) > a.ftol) {
+      ever_full = true;
+      if (blockIdx.x == 0 && tid == 0) ctl->full_from = (uint32_t)it + 1;
+    }
+    D_prev = D;
+    I.full = ever_full;
+    const int par = it & 1;
+    const T *Rin = par ? a.R1 : a.R0;
+    const T *Cin = par ? a.C1 : a.C0;
+    T *Rout = par ? a.R0 : a.R1;
+    T *Cout = par ? a.C0 : a.C1;
+    const uint32_t *L0, *L1, *L2;
+    uint32_t c0, c1, c2;
+    if (I.full) {
+      L0 = a.ident;
+      c0 = a.id_cnt0;
+      L1 = a.ident + a.id_cnt0;
+      c1 = a.id_cnt1;
+      L2 = a.ident + a.id_cnt0 + a.id_cnt1;
+      c2 = a.id_cnt2;
+    } else {
+      L0 = a.list0;
+      c0 = cnt[0];
+      L1 = a.list1;
+      c1 = cnt[1];
+      L2 = a.list2;
+      c2 = cnt[2];
+    }
+    const bool expand = df && !I.full;
+    const uint32_t slot = (uint32_t)it + 1;
+    double my_max = 0.0;
+
+    // block bin: one block per vertex, taken dynamically
+    for (;;) {
+      if (tid == 0) s_idx = atomicAdd(&ctl->blk_next[it], 1u);
+      __syncthreads();
+      const uint32_t idx = s_idx;
+      __syncthreads();
+      if (idx >= c2) break;
+      const uint32_t v = ldcg(L2 + idx);
+      const uint2 d = __ldg(&a.in_rd[v]);
+      const uint32_t *cols = a.in_col + d.x;
+      T sum = (T)0;
+      for (uint32_t j = tid * 4; j < d.y; j += kRankBlock * 4) {
+        uint4 q = __ldg(reinterpret_cast<const uint4 *>(cols + j));
+        sum += gather4(Cin, q, min(4u, d.y - j));
+      }
+      sum = warp_sum(sum);
+      if (lane == 0) s_part[wib] = sum;
+      __syncthreads();
+      if (tid == 0) {
+        T tot = (T)0;
+        for (int w = 0; w < kWarps; w++) tot += s_part[w];
+        double dr = finish_vertex(a, Rin, Rout, Cout, v, tot, I, dacc);
+        s_bcast = dr;
+        my_max = fmax(my_max, dr);
+        my_v++;
+        my_e += d.y;
+      }
+      __syncthreads();
+      if (expand && s_bcast > a.ftol) {
+        const uint2 od = __ldg(&a.out_rd[v]);
+        my_app += warp_mark_range(a, a.out_col + od.x, od.y, wib * 32, kRankBlock, slot, cnt, lane);
+        if (tid == 0) {
+          my_xv++;
+          my_xe += od.y;
+        }
+      }
+    }
+
+    // warp bin: one warp per vertex
+    for (uint32_t i = gwarp; i < c1; i += nwarps) {
+      const uint32_t v = ldcg(L1 + i);
+      const uint2 d = __ldg(&a.in_rd[v]);
+      const uint32_t *cols = a.in_col + d.x;
+      T sum = (T)0;
+      for (uint32_t j = lane * 4; j < d.y; j += 128) {
+        uint4 q = __ldg(reinterpret_cast<const uint4 *>(cols + j));
+        sum += gather4(Cin, q, min(4u, d.y - j));
+      }
+      sum = warp_sum(sum);
+      double dr = 0.0;
+      if (lane == 0) {
+        dr = finish_vertex(a, Rin, Rout, Cout, v, sum, I, dacc);
+        my_max = fmax(my_max, dr);
+        my_v++;
+        my_e += d.y;
+      }
+      dr = __shfl_sync(kFull, dr, 0);
+      if (expand && dr > a.ftol) {
+        const uint2 od = __ldg(&a.out_rd[v]);
+        my_app += warp_mark_range(a, a.out_col + od.x, od.y, 0, 32, slot, cnt, lane);
+        if (lane == 0) {
+          my_xv++;
+          my_xe += od.y;
+        }
+      }
+    }
+
+    // thread bin: one thread per vertex
+    if (!expand) {
+      for (uint32_t i = gtid; i < c0; i += nthreads) {
+        const uint32_t v = ldcg(L0 + i);
+        const uint2 d = __ldg(&a.in_rd[v]);
+        const uint32_t *cols = a.in_col + d.x;
+        T sum = (T)0;
+        for (uint32_t j = 0; j < d.y; j += 4) {
+          uint4 q = __ldg(reinterpret_cast<const uint4 *>(cols + j));
+          sum += gather4(Cin, q, min(4u, d.y - j));
+        }
+        double dr = finish_vertex(a, Rin, Rout, Cout, v, sum, I, dacc);
+        my_max = fmax(my_max, dr);
+        my_v++;
+        my_e += d.y;
+      }
+    } else {
+      // rounds of one vertex per thread; expanding vertices are queued in shared memory
+      // and their out-rows marked by whole warps (counter and queue double-buffered by
+      // round parity, one block barrier per round)
+      uint32_t round = 0;
+      for (uint32_t b0 = blockIdx.x * kRankBlock; b0 < c0; b0 += nthreads, round++) {
+        const uint32_t qp = round & 1;
+        const uint32_t i = b0 + tid;
+        int push = 0;
+        uint32_t v = 0;
+        if (i < c0) {
+          v = ldcg(L0 + i);
+          const uint2 d = __ldg(&a.in_rd[v]);
+          const uint32_t *cols = a.in_col + d.x;
+          T sum = (T)0;
+          for (uint32_t j = 0; j < d.y; j += 4) {
+            uint4 q = __ldg(reinterpret_cast<const uint4 *>(cols + j));
+            sum += gather4(Cin, q, min(4u, d.y - j));
+          }
+          double dr = finish_vertex(a, Rin, Rout, Cout, v, sum, I, dacc);
+          my_max = fmax(my_max, dr);
+          my_v++;
+          my_e += d.y;
+          if (dr > a.ftol) {
+            push = 1;
+            s_q[qp][atomicAdd(&s_qn[qp], 1u)] = v;
+          }
+        }
+        const uint32_t qn = __syncthreads_count(push);
+        // every push of this round is in; the counter is next used two rounds later,
+        // after the next round's barrier, which thread 0 reaches only after this reset
+        if (tid == 0) s_qn[qp] = 0;
+        for (uint32_t k = wib; k < qn; k += kWarps) {
+          const uint32_t x = s_q[qp][k];
+          const uint2 od = __ldg(&a.out_rd[x]);
+          my_app += warp_mark_range(a, a.out_col + od.x, od.y, 0, 32, slot, cnt, lane);
+          if (lane == 0) {
+            my_xv++;
+            my_xe += od.y;
+          }
+        }
+      }
+    }
+
+    // block reductions: L-inf (and dead-end mass) of this iteration
+    {
+      double m = warp_max(my_max);
+      if (lane == 0) s_dmax[wib] = m;
+      __syncthreads();
+      if (tid == 0) {
+        double bm = 0.0;
+        for (int w = 0; w < kWarps; w++) bm = fmax(bm, s_dmax[w]);
+        if (bm > 0.0) atomicMax(&ctl->dR_bits[it], (unsigned long long)__double_as_longlong(bm));
+      }
+    }
+    if (a.teleport) block_dead_partial((it + 1) & 1);
+    if (!grid_sync(ctl, epoch, &s_err)) return;
+
+    const double dR = __longlong_as_double((long long)__ldcg(&ctl->dR_bits[it]));
+    if (df && !I.full) {
+#pragma unroll
+      for (int bb = 0; bb < 3; bb++) cnt[bb] += ldcg(&ctl->tail[slot][bb]);
+    }
+    if (a.teleport) {
+      double part = grid_dead_total((it + 1) & 1);
+      D = I.full ? part : D + part;
+    }
+    iters = (uint32_t)it + 1;
+    last = dR;
+    if (dR <= a.tol) {
+      converged = true;
+      break;
+    }
+  }
+
+  // -------------------------------------------------------------- writeback
+  const int fp = iters & 1;
+  const T *Rf = fp ? a.R1 : a.R0;
+  const T *Cf = fp ? a.C1 : a.C0;
+  T *Ro = fp ? a.R0 : a.R1;
+  T *Co = fp ? a.C0 : a.C1;
+  if (ever_full) {
+    for (uint32_t v = gtid; v < a.n; v += nthreads) {
+      Ro[v] = ldcg(Rf + v);
+      Co[v] = ldcg(Cf + v);
+    }
+  }
+  if (df) {
+    const uint32_t *lists[3] = {a.list0, a.list1, a.list2};
+    for (int bb = 0; bb < 3; bb++) {
+      for (uint32_t k = gtid; k < cnt[bb]; k += nthreads) {
+        const uint32_t v = ldcg(lists[bb] + k);
+        if (!ever_full) {
+          Ro[v] = ldcg(Rf + v);
+          Co[v] = ldcg(Cf + v);
+        }
+        a.bitmap[v >> 5] = 0u;
+      }
+    }
+  }
+  // counters
+  {
+    unsigned long long vals[5] = {my_v, my_e, my_xv, my_xe, my_app};
+    unsigned long long *dst[5] = {&ctl->vproc, &ctl->eproc, &ctl->expv, &ctl->expe, &ctl->appended};
+#pragma unroll
+    for (int k = 0; k < 5; k++) {
+      unsigned long long x = vals[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+      if (lane == 0 && x) atomicAdd(dst[k], x);
+    }
+  }
+  if (blockIdx.x == 0 && tid == 0) {
+    ctl->iterations = iters;
+    ctl->converged = converged ? 1u : 0u;
+    ctl->last_delta = last;
+    ctl->D_final = D;
+    for (int bb = 0; bb < 3; bb++) ctl->final_cnt[bb] = cnt[bb];
+  }
+}
+
+// ------------------------------------------------------------------ host side ---
+
+#define CK(call)                                            \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail(g, e_, #call);  \
+  } while (0)
+
+template <class T>
+static cudaError_t grid_blocks(int sm_count, int *blocks) {
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rank<T>, kRankBlock, 0);
+  if (e != cudaSuccess) return e;
+  per_sm = std::max(1, std::min(per_sm, 4));
+  *blocks = per_sm * sm_count;
+  return cudaSuccess;
+}
+
+pr_status rank_setup(Graph *g) {
+  int blocks = 0;
+  CK(g->f32 ? grid_blocks<float>(g->sm_count, &blocks) : grid_blocks<double>(g->sm_count, &blocks));
+  g->rank_grid = blocks;
+  CK(cudaMalloc((void **)&g->ctl, sizeof(RankCtl)));
+  CK(cudaMallocHost((void **)&g->ctl_h, sizeof(RankCtl)));
+  CK(cudaMalloc((void **)&g->dpart, sizeof(DeadPart) * 2 * (size_t)blocks));
+  CK(cudaEventCreate(&g->ev0));
+  CK(cudaEventCreate(&g->ev1));
+  return PR_OK;
+}
+
+template <class T>
+static pr_status launch(Graph *g, RankMode mode, bool start_full) {
+  RankArgs<T> a{};
+  a.n = g->n;
+  a.in_rd = g->in.rd;
+  a.in_col = g->in.col;
+  a.out_rd = g->out.rd;
+  a.out_col = g->out.col;
+  a.R0 = (T *)g->R[0];
+  a.R1 = (T *)g->R[1];
+  a.C0 = (T *)g->C[0];
+  a.C1 = (T *)g->C[1];
+  a.adeg = (const T *)g->adeg;
+  a.bitmap = g->bitmap;
+  a.list0 = g->list[0];
+  a.list1 = g->list[1];
+  a.list2 = g->list[2];
+  a.ident = g->ident;
+  a.id_cnt0 = g->ident_cnt[0];
+  a.id_cnt1 = g->ident_cnt[1];
+  a.id_cnt2 = g->ident_cnt[2];
+  a.pend_src = g->pend_src;
+  a.n_pend_src = g->n_pend_src;
+  a.pend_tgt = g->pend_tgt;
+  a.n_pend_tgt = g->n_pend_tgt;
+  a.dead = g->dead;
+  a.n_dead = g->teleport ? g->n_dead : 0;
+  a.dpart = g->dpart;
+  a.base = (1.0 - g->p.alpha) / (double)g->n;
+  a.teleport = g->teleport ? 1 : 0;
+  a.tele = g->teleport ? g->p.alpha / (double)g->n : 0.0;
+  a.alpha_over_n = g->p.alpha / (double)g->n;
+  a.D_ref = g->D_ref;
+  a.tol = g->p.tol;
+  a.ftol = g->p.frontier_tol;
+  a.max_iter = g->p.max_iter;
+  a.mode = (int)mode;
+  a.start_full = start_full ? 1 : 0;
+  a.bin_lo = (uint32_t)g->p.bin_lo;
+  a.bin_hi = (uint32_t)g->p.bin_hi;
+  a.ctl = g->ctl;
+  void *args[] = {(void *)&a};
+  CK(cudaLaunchCooperativeKernel((const void *)k_rank<T>, dim3(g->rank_grid), dim3(kRankBlock), args, 0, g->st));
+  return PR_OK;
+}
+
+pr_status rank_run(Graph *g, RankMode mode, pr_stats *stats) {
+  pr_status rc;
+  const bool start_full = mode == kModeDF && g->pend_all;
+  if (g->teleport && (rc = graph_refresh_dead(g)) != PR_OK) return rc;
+  if (mode != kModeDF || start_full || g->teleport) {
+    if ((rc = graph_refresh_ident(g)) != PR_OK) return rc;
+  }
+  CK(cudaMemsetAsync(g->ctl, 0, sizeof(RankCtl), g->st));
+  CK(cudaEventRecord(g->ev0, g->st));
+  rc = g->f32 ? launch<float>(g, mode, start_full) : launch<double>(g, mode, start_full);
+  if (rc != PR_OK) return rc;
+  CK(cudaEventRecord(g->ev1, g->st));
+  CK(cudaMemcpyAsync(g->ctl_h, g->ctl, offsetof(RankCtl, dR_bits), cudaMemcpyDeviceToHost, g->st));
+  CK(cudaMemcpyAsync(&g->ctl_h->vproc, &g->ctl->vproc, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                     g->st));
+  CK(cudaStreamSynchronize(g->st));
+  const RankCtl &h = *g->ctl_h;
+  if (h.err) {
+    g->err = "rank kernel: a grid barrier wait timed out";
+    return PR_ERR_DEVICE_TIMEOUT;
+  }
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, g->ev0, g->ev1));
+  const bool full = mode != kModeDF || start_full || h.full_from != 0;
+  g->last_full = full;
+  for (int b = 0; b < 3; b++) g->last_list_cnt[b] = mode == kModeDF ? h.final_cnt[b] : 0;
+  g->n_pend_src = 0;
+  g->n_pend_tgt = 0;
+  g->pend_all = false;
+  if (g->teleport) g->D_ref = h.D_final;
+  if (stats) {
+    const double vb = g->f32 ? 24.0 : 36.0, eb = g->f32 ? 8.0 : 12.0;
+    stats->iterations = (int32_t)h.iterations;
+    stats->converged = (int32_t)h.converged;
+    stats->affected_final =
+        full ? (int64_t)g->n : (int64_t)h.final_cnt[0] + h.final_cnt[1] + h.final_cnt[2];
+    stats->vertices_processed = (int64_t)h.vproc;
+    stats->edges_processed = (int64_t)h.eproc;
+    stats->bytes_algorithmic = vb * (double)h.vproc + eb * (double)h.eproc + 8.0 * (double)h.expv +
+                               4.0 * (double)h.expe + 4.0 * (double)h.appended;
+    stats->last_delta = h.last_delta;
+    stats->ms_apply = g->ms_apply;
+    stats->ms_rank = ms;
+  }
+  g->ms_apply = 0.0;
+  return PR_OK;
+}
+
+template <class T>
+__global__ void k_set_ranks(const double *in, uint32_t n, const T *adeg, T *R0, T *R1, T *C0, T *C1) {
+  uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  T r = (T)in[v];
+  T c = r * adeg[v];
+  R0[v] = r;
+  R1[v] = r;
+  C0[v] = c;
+  C1[v] = c;
+}
+
+template <class T>
+__global__ void k_get_ranks(const T *R, uint32_t n, double *out) {
+  uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < n) out[v] = (double)R[v];
+}
+
+__global__ void k_dead_mass(const uint32_t *dead, uint32_t n_dead, const double *R, double *out) {
+  // one block; plain sequential-order per thread, then ordered combine
+  __shared__ double s[256];
+  double acc = 0.0;
+  for (uint32_t k = threadIdx.x; k < n_dead; k += 256) acc += R[dead[k]];
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < 256; i++) t += s[i];
+    *out = t;
+  }
+}
+
+pr_status rank_set(Graph *g, const double *in_d) {
+  unsigned grid = (g->n + 255) / 256;
+  if (g->f32)
+    k_set_ranks<float><<<grid, 256, 0, g->st>>>(in_d, g->n, (const float *)g->adeg, (float *)g->R[0],
+                                                (float *)g->R[1], (float *)g->C[0], (float *)g->C[1]);
+  else
+    k_set_ranks<double><<<grid, 256, 0, g->st>>>(in_d, g->n, (const double *)g->adeg, (double *)g->R[0],
+                                                 (double *)g->R[1], (double *)g->C[0], (double *)g->C[1]);
+  CK(cudaGetLastError());
+  if (g->teleport) {
+    pr_status rc = graph_refresh_dead(g);
+    if (rc != PR_OK) return rc;
+    double *dm = nullptr;
+    CK(cudaMalloc((void **)&dm, sizeof(double)));
+    k_dead_mass<<<1, 256, 0, g->st>>>(g->dead, g->n_dead, in_d, dm);
+    double D = 0.0;
+    cudaError_t e = cudaMemcpyAsync(&D, dm, sizeof(double), cudaMemcpyDeviceToHost, g->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+    cudaFree(dm);
+    if (e != cudaSuccess) return cuda_fail(g, e, "dead-end mass");
+    g->D_ref = D;
+  }
+  CK(cudaStreamSynchronize(g->st));
+  return PR_OK;
+}
+
+pr_status rank_get(Graph *g, double *out_d) {
+  unsigned grid = (g->n + 255) / 256;
+  if (g->f32)
+    k_get_ranks<float><<<grid, 256, 0, g->st>>>((const float *)g->R[0], g->n, out_d);
+  else
+    k_get_ranks<double><<<grid, 256, 0, g->st>>>((const double *)g->R[0], g->n, out_d);
+  CK(cudaGetLastError());
+  return PR_OK;
+}
+
+}  // namespace prdf

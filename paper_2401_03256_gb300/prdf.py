@@ -1,0 +1,282 @@
+"""Thin ctypes binding of libprdf.so (include/prdf.h); argument marshalling only.
+
+Every function here has the name of the C entry point it calls.  Arrays may be numpy
+arrays (host) or torch tensors (host or CUDA); they are passed as raw pointers and the
+library copies what it needs.  A non-OK status raises PrdfError with pr_last_error's
+message.  There is no fallback: if the CUDA library is missing this module fails to
+import its functions with an OSError.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libprdf.so")
+
+PR_OK = 0
+PR_ERR_INVALID_ARG = 1
+PR_ERR_VERTEX_RANGE = 2
+PR_ERR_OUT_OF_MEMORY = 3
+PR_ERR_CUDA = 4
+PR_ERR_DEVICE_TIMEOUT = 5
+PR_ERR_CAPACITY = 6
+PR_F64 = 0
+PR_F32 = 1
+PR_DEADEND_SELFLOOP = 0
+PR_DEADEND_TELEPORT = 1
+
+EXPORTED = (
+    "pr_params_default", "pr_graph_create", "pr_graph_destroy", "pr_apply_batch", "pr_static",
+    "pr_naive_dynamic", "pr_dynamic_frontier", "pr_get_ranks", "pr_set_ranks", "pr_graph_info",
+    "pr_get_csr", "pr_get_affected", "pr_last_error", "pr_status_string",
+)
+
+
+class pr_params(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("tol", ctypes.c_double), ("frontier_tol", ctypes.c_double),
+                ("max_iter", ctypes.c_int32), ("precision", ctypes.c_int32), ("dead_end", ctypes.c_int32),
+                ("bin_lo", ctypes.c_int32), ("bin_hi", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class pr_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("affected_final", ctypes.c_int64), ("vertices_processed", ctypes.c_int64),
+                ("edges_processed", ctypes.c_int64), ("bytes_algorithmic", ctypes.c_double),
+                ("last_delta", ctypes.c_double), ("ms_apply", ctypes.c_double), ("ms_rank", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class PrdfError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_status_name(status)}: {message}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads libprdf.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"libprdf.so not found at {path}; build it with paper_2401_03256_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, u32, i32, i64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int32, ctypes.c_int64
+    lib.pr_params_default.restype = None
+    lib.pr_params_default.argtypes = [ctypes.POINTER(pr_params)]
+    lib.pr_graph_create.restype = ctypes.c_int
+    lib.pr_graph_create.argtypes = [u32, i64, vp, vp, ctypes.POINTER(pr_params), vp, ctypes.POINTER(vp)]
+    lib.pr_graph_destroy.restype = ctypes.c_int
+    lib.pr_graph_destroy.argtypes = [vp]
+    lib.pr_apply_batch.restype = ctypes.c_int
+    lib.pr_apply_batch.argtypes = [vp, i64, vp, vp, i64, vp, vp]
+    for name in ("pr_static", "pr_naive_dynamic", "pr_dynamic_frontier"):
+        f = getattr(lib, name)
+        f.restype = ctypes.c_int
+        f.argtypes = [vp, ctypes.POINTER(pr_stats)]
+    lib.pr_get_ranks.restype = ctypes.c_int
+    lib.pr_get_ranks.argtypes = [vp, vp, u32]
+    lib.pr_set_ranks.restype = ctypes.c_int
+    lib.pr_set_ranks.argtypes = [vp, vp, u32]
+    lib.pr_graph_info.restype = ctypes.c_int
+    lib.pr_graph_info.argtypes = [vp, ctypes.POINTER(u32), ctypes.POINTER(i64)]
+    lib.pr_get_csr.restype = ctypes.c_int
+    lib.pr_get_csr.argtypes = [vp, i32, vp, vp]
+    lib.pr_get_affected.restype = ctypes.c_int
+    lib.pr_get_affected.argtypes = [vp, vp, i64, ctypes.POINTER(i64)]
+    lib.pr_last_error.restype = ctypes.c_char_p
+    lib.pr_last_error.argtypes = [vp]
+    lib.pr_status_string.restype = ctypes.c_char_p
+    lib.pr_status_string.argtypes = [ctypes.c_int]
+    _lib = lib
+    return lib
+
+
+def _status_name(status: int) -> str:
+    try:
+        return load().pr_status_string(status).decode()
+    except OSError:
+        return str(status)
+
+
+def _check(status: int, handle=None):
+    if status != PR_OK:
+        msg = load().pr_last_error(handle)
+        raise PrdfError(status, msg.decode() if msg else "")
+
+
+def _ptr(a):
+    """Raw pointer and length of a numpy array or torch tensor (contiguous)."""
+    if a is None:
+        return None, 0
+    if hasattr(a, "data_ptr"):  # torch tensor
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), int(a.numel())
+    if not isinstance(a, np.ndarray) or not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("expected a C-contiguous numpy array or a torch tensor")
+    return a.ctypes.data, int(a.size)
+
+
+def _u32(a):
+    if a is None or hasattr(a, "data_ptr"):
+        return a
+    return np.ascontiguousarray(np.asarray(a, dtype=np.uint32))
+
+
+def pr_params_default() -> pr_params:
+    p = pr_params()
+    load().pr_params_default(ctypes.byref(p))
+    return p
+
+
+def pr_graph_create(n: int, src, dst, params: pr_params | None = None, stream: int | None = None) -> int:
+    """Returns the opaque handle (an int)."""
+    src, dst = _u32(src), _u32(dst)
+    ps, ms = _ptr(src)
+    pd, md = _ptr(dst)
+    if ms != md:
+        raise ValueError("src and dst differ in length")
+    h = ctypes.c_void_p()
+    st = load().pr_graph_create(n, ms, ps, pd, ctypes.byref(params) if params is not None else None,
+                                stream, ctypes.byref(h))
+    _check(st, None)
+    return h.value
+
+
+def pr_graph_destroy(h: int) -> None:
+    _check(load().pr_graph_destroy(h), None)
+
+
+def pr_apply_batch(h: int, del_src, del_dst, ins_src, ins_dst) -> None:
+    del_src, del_dst, ins_src, ins_dst = _u32(del_src), _u32(del_dst), _u32(ins_src), _u32(ins_dst)
+    a, na = _ptr(del_src)
+    b, nb = _ptr(del_dst)
+    c, nc = _ptr(ins_src)
+    d, nd = _ptr(ins_dst)
+    if na != nb or nc != nd:
+        raise ValueError("source and target arrays differ in length")
+    _check(load().pr_apply_batch(h, na, a, b, nc, c, d), h)
+
+
+def _rank(fn, h: int) -> pr_stats:
+    s = pr_stats()
+    _check(fn(h, ctypes.byref(s)), h)
+    return s
+
+
+def pr_static(h: int) -> pr_stats:
+    return _rank(load().pr_static, h)
+
+
+def pr_naive_dynamic(h: int) -> pr_stats:
+    return _rank(load().pr_naive_dynamic, h)
+
+
+def pr_dynamic_frontier(h: int) -> pr_stats:
+    return _rank(load().pr_dynamic_frontier, h)
+
+
+def pr_graph_info(h: int):
+    n = ctypes.c_uint32()
+    m = ctypes.c_int64()
+    _check(load().pr_graph_info(h, ctypes.byref(n), ctypes.byref(m)), h)
+    return n.value, m.value
+
+
+def pr_get_ranks(h: int, out=None):
+    """Ranks as float64; into `out` (numpy or CUDA tensor) if given, else a new numpy array."""
+    n, _ = pr_graph_info(h)
+    if out is None:
+        out = np.empty(n, np.float64)
+    p, k = _ptr(out)
+    if k != n:
+        raise ValueError("out must hold n values")
+    _check(load().pr_get_ranks(h, p, n), h)
+    return out
+
+
+def pr_set_ranks(h: int, ranks) -> None:
+    n, _ = pr_graph_info(h)
+    if not hasattr(ranks, "data_ptr"):
+        ranks = np.ascontiguousarray(np.asarray(ranks, dtype=np.float64))
+    p, k = _ptr(ranks)
+    if k != n:
+        raise ValueError("ranks must hold n values")
+    _check(load().pr_set_ranks(h, p, n), h)
+
+
+def pr_get_csr(h: int, direction: int):
+    """(offsets uint64[n+1], columns uint32[m]) of the out (0) or in (1) adjacency."""
+    n, m = pr_graph_info(h)
+    off = np.empty(n + 1, np.uint64)
+    col = np.empty(max(m, 1), np.uint32)
+    _check(load().pr_get_csr(h, direction, off.ctypes.data, col.ctypes.data), h)
+    return off, col[:m]
+
+
+def pr_get_affected(h: int) -> np.ndarray:
+    """Vertices marked affected by the last pr_dynamic_frontier call (unordered)."""
+    cnt = ctypes.c_int64()
+    _check(load().pr_get_affected(h, None, 0, ctypes.byref(cnt)), h)
+    out = np.empty(max(cnt.value, 1), np.uint32)
+    _check(load().pr_get_affected(h, out.ctypes.data, cnt.value, ctypes.byref(cnt)), h)
+    return out[: cnt.value]
+
+
+class Graph:
+    """Owning wrapper of a handle: ``with Graph(n, src, dst) as g: g.static()``."""
+
+    def __init__(self, n: int, src, dst, params: pr_params | None = None, stream: int | None = None):
+        self.h = pr_graph_create(n, src, dst, params, stream)
+
+    def apply(self, del_src, del_dst, ins_src, ins_dst):
+        pr_apply_batch(self.h, del_src, del_dst, ins_src, ins_dst)
+
+    def static(self) -> pr_stats:
+        return pr_static(self.h)
+
+    def naive(self) -> pr_stats:
+        return pr_naive_dynamic(self.h)
+
+    def frontier(self) -> pr_stats:
+        return pr_dynamic_frontier(self.h)
+
+    def ranks(self, out=None):
+        return pr_get_ranks(self.h, out)
+
+    def set_ranks(self, r):
+        pr_set_ranks(self.h, r)
+
+    def csr(self, direction: int):
+        return pr_get_csr(self.h, direction)
+
+    def affected(self):
+        return pr_get_affected(self.h)
+
+    def info(self):
+        return pr_graph_info(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            pr_graph_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
