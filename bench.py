@@ -1,0 +1,430 @@
+#!/usr/bin/env python3
+"""Dynamic Frontier PageRank benchmark on one GB300 (or N replicas, one per GPU).
+
+Workload: directed R-MAT scale 22, edge factor 16 (a, b, c, d = 0.57, 0.19, 0.19,
+0.05, duplicates removed, self-loops added), FP64 ranks, and a batch-size sweep of
+uniformly random 80/20 insertion/deletion batches of 1e-7 ... 1e-3 |E| (Section 5.1.4).
+
+One step = for every batch size f: apply one batch to the device-resident graph, bring
+the ranks up to date with Dynamic Frontier (the measured update), then recompute the
+same snapshot with Naive-dynamic (from the previous ranks) and Static (from 1/n) as the
+paper's comparators (Section 5.2), then continue the chain from the DF ranks.
+
+value = geometric mean over f of the mean DF update time (CUDA events on the library's
+stream around the rank kernel: marking, iterations and convergence detection, as timed
+in Section 5.1.5; graph update excluded and reported as apply_ms).  e2e = the same per
+update measured on the host around the public C-ABI calls with pinned host buffers:
+pr_apply_batch (host batch -> device), pr_dynamic_frontier, pr_get_ranks (all n ranks
+device -> host).  L2 is flushed (256 MB write) before every timed call.
+
+--impl reference times the FP64 sequential oracle (Algorithm 1, synchronous) on the
+host cores on the same workload, one update per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "DF update ms & processed-edge GB/s vs GPU Static/Naive; serving p50/p99 ms"
+FRACS = [1e-7, 1e-6, 1e-5, 1e-4, 1e-3]
+FALLBACK_HBM_GBS = 6800.0
+
+
+def geomean(xs):
+    xs = [x for x in xs if x > 0]
+    return math.exp(sum(math.log(x) for x in xs) / len(xs)) if xs else None
+
+
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ------------------------------------------------------------------ clocks ----
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, name in enumerate(names):
+                if r[5 + k].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ------------------------------------------------------------ CPU baseline ----
+
+def oracle_sample(scale: int, ef: int, seed: int, fracs, q=None):
+    """Times the FP64 sequential oracle's Dynamic Frontier update (Algorithm 1, sync) on
+    one batch per fraction, chained from the oracle's own Static ranks.  1 core."""
+    import oracle
+    import synth
+
+    oracle.build()
+    t_setup = time.perf_counter()
+    g = synth.rmat(scale, ef, seed=seed)
+    G = oracle.Graph.build(g.n, g.src, g.dst)
+    R, _ = oracle.static_pr(G)
+    s = synth.BatchStream(g, seed=seed)
+    setup_s = time.perf_counter() - t_setup
+    per = {}
+    for f in fracs:
+        b = s.next(f)
+        H, ed, ei = G.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+        t = time.perf_counter()
+        R, _, st = oracle.df_sync(G, H, ed, ei, R)
+        per[f] = (time.perf_counter() - t) * 1e3
+        G = H
+    res = {"per_frac_ms": per, "setup_s": setup_s}
+    if q is not None:
+        q.put(res)
+    return res
+
+
+def _cpu_worker(scale, ef, seed, fracs, q):
+    try:
+        oracle_sample(scale, ef, seed, fracs, q)
+    except Exception as e:  # reported, not fatal
+        q.put({"error": repr(e)})
+
+
+# ------------------------------------------------------------- GPU arm ----
+
+def run_ours(args, rank: int, world: int, local_rank: int):
+    ctx = mp.get_context("spawn")
+    q = None
+    proc = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # started before the first GPU call; runs on its own core while the GPU works
+        q = ctx.Queue()
+        proc = ctx.Process(target=_cpu_worker, args=(args.scale, args.ef, 1, FRACS, q), daemon=True)
+        proc.start()
+
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2401_03256_gb300 import build as libbuild
+
+    libbuild.build()
+    from paper_2401_03256_gb300 import prdf
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+
+    seed = 1 + rank
+    g = synth.rmat(args.scale, args.ef, seed=seed)
+    params = prdf.pr_params_default()
+    params.precision = prdf.PR_F32 if args.precision == "fp32" else prdf.PR_F64
+    stream = torch.cuda.Stream(device=dev)
+    W, K = args.warmup, args.steps
+    with torch.cuda.stream(stream):
+        G = prdf.Graph(g.n, g.src, g.dst, params, stream.cuda_stream)
+        n, m = G.info()
+        G.static()
+        bs = synth.BatchStream(g, seed=seed)
+        batches = [[bs.next(f) for f in FRACS] for _ in range(W + K)]
+        e2e_batches = [[bs.next(f) for f in FRACS] for _ in range(K)]
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+        R_prev = torch.empty(n, dtype=torch.float64, device=dev)
+        R_cur = torch.empty(n, dtype=torch.float64, device=dev)
+        rec = {f: {"df": [], "naive": [], "static": [], "apply": [], "df_iters": [], "df_affected": [],
+                   "df_bytes": [], "naive_iters": [], "static_iters": [], "static_bytes": [], "naive_bytes": [],
+                   "df_edges": []} for f in FRACS}
+
+        def step(i, record):
+            for fi, f in enumerate(FRACS):
+                b = batches[i][fi]
+                G.ranks(R_prev)
+                G.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+                flush.zero_()
+                sd = G.frontier()
+                G.ranks(R_cur)
+                G.set_ranks(R_prev)
+                flush.zero_()
+                sn = G.naive()
+                flush.zero_()
+                ss = G.static()
+                G.set_ranks(R_cur)
+                if record:
+                    r = rec[f]
+                    r["df"].append(sd.ms_rank)
+                    r["apply"].append(sd.ms_apply)
+                    r["naive"].append(sn.ms_rank)
+                    r["static"].append(ss.ms_rank)
+                    r["df_iters"].append(sd.iterations)
+                    r["df_affected"].append(sd.affected_final)
+                    r["df_bytes"].append(sd.bytes_algorithmic)
+                    r["df_edges"].append(sd.edges_processed)
+                    r["naive_iters"].append(sn.iterations)
+                    r["static_iters"].append(ss.iterations)
+                    r["static_bytes"].append(ss.bytes_algorithmic)
+                    r["naive_bytes"].append(sn.bytes_algorithmic)
+
+        for i in range(W):
+            step(i, False)
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        clocks = ClockSampler(local_rank)
+        clocks.start()
+        l0 = prdf.pr_kernel_launches()
+        t0 = time.perf_counter()
+        for i in range(K):
+            step(W + i, True)
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        t1 = time.perf_counter()
+        launches = prdf.pr_kernel_launches() - l0
+        clk = clocks.stop()
+
+        # end to end through the C ABI with pinned host buffers
+        out_h = torch.empty(n, dtype=torch.float64, pin_memory=True)
+        e2e = {f: [] for f in FRACS}
+        h2d = 0
+        pinned = []
+        for i in range(K):
+            row = []
+            for fi in range(len(FRACS)):
+                b = e2e_batches[i][fi]
+                row.append([torch.from_numpy(a.astype(np.int32)).pin_memory() for a in
+                            (b.del_src, b.del_dst, b.ins_src, b.ins_dst)])
+            pinned.append(row)
+        for i in range(K):
+            for fi, f in enumerate(FRACS):
+                ds, dd, is_, id_ = pinned[i][fi]
+                h2d += 4 * (ds.numel() + dd.numel() + is_.numel() + id_.numel())
+                flush.zero_()
+                torch.cuda.synchronize(dev)
+                t = time.perf_counter()
+                G.apply(ds, dd, is_, id_)
+                G.frontier()
+                G.ranks(out_h)
+                e2e[f].append((time.perf_counter() - t) * 1e3)
+        G.close()
+
+    def mean(xs):
+        return sum(xs) / len(xs) if xs else float("nan")
+
+    df_ms = {f: mean(rec[f]["df"]) for f in FRACS}
+    value = geomean(df_ms.values())
+    static_bytes = sum(sum(rec[f]["static_bytes"]) for f in FRACS)
+    static_ms = sum(sum(rec[f]["static"]) for f in FRACS)
+    static_launches = sum(len(rec[f]["static"]) for f in FRACS)
+    all_bytes = static_bytes + sum(sum(rec[f]["naive_bytes"]) + sum(rec[f]["df_bytes"]) for f in FRACS)
+    all_ms = static_ms + sum(sum(rec[f]["naive"]) + sum(rec[f]["df"]) for f in FRACS)
+    peak, peak_kind = hbm_peak()
+    achieved = (static_bytes / static_launches) / ((static_ms / static_launches) * 1e-3) / 1e9
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "k_rank_traffic.json")
+    try:
+        with open(tr_path) as f:
+            tr = json.load(f)
+        import hashlib
+
+        src = open(os.path.join(ROOT, "paper_2401_03256_gb300", "csrc", "rank.cu"), "rb").read()
+        if tr.get("rank_cu_sha256") == hashlib.sha256(src).hexdigest() and tr.get("precision") == args.precision:
+            traffic = tr.get("static_launch_bytes_full_size")
+    except Exception:
+        traffic = None
+
+    per_f = {}
+    for f in FRACS:
+        r = rec[f]
+        per_f[f"{f:g}"] = {
+            "df_ms": df_ms[f], "naive_ms": mean(r["naive"]), "static_ms": mean(r["static"]),
+            "apply_ms": mean(r["apply"]), "speedup_vs_static": mean(r["static"]) / df_ms[f],
+            "speedup_vs_naive": mean(r["naive"]) / df_ms[f], "df_iterations": mean(r["df_iters"]),
+            "naive_iterations": mean(r["naive_iters"]), "static_iterations": mean(r["static_iters"]),
+            "df_affected": mean(r["df_affected"]),
+            "df_gbs": (sum(r["df_bytes"]) / (sum(r["df"]) * 1e-3) / 1e9) if sum(r["df"]) > 0 else None,
+            "e2e_ms": mean(e2e[f]),
+        }
+    e2e_value = geomean([mean(e2e[f]) for f in FRACS])
+    ms_per_step = (t1 - t0) / K * 1e3
+
+    if dist:
+        t = torch.tensor([value, e2e_value, ms_per_step], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        value, e2e_value, ms_per_step = t.tolist()
+
+    cpu = None
+    if proc is not None:
+        try:
+            res = q.get(timeout=args.cpu_timeout)
+        except Exception:
+            res = {"error": "timed out"}
+        proc.join(timeout=5)
+        if proc.is_alive():
+            proc.terminate()
+        if "per_frac_ms" in res:
+            cpu_val = geomean(res["per_frac_ms"].values())
+            cpu = {"value": cpu_val, "unit": "ms", "cores": 1, "kind": "oracle",
+                   "sample": (f"sequential FP64 oracle, Algorithm 1 synchronous, one 80/20 batch per f in "
+                              f"{[f'{x:g}' for x in FRACS]} on the same R-MAT s{args.scale} ef{args.ef} graph, "
+                              f"chained from its own Static ranks (setup {res['setup_s']:.0f} s untimed)"),
+                   "per_frac_ms": {f"{k:g}": v for k, v in res["per_frac_ms"].items()}}
+        else:
+            cpu = {"value": None, "unit": "ms", "cores": 1, "kind": "oracle", "sample": res.get("error")}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "ms", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": f"R-MAT scale {args.scale} edge factor {args.ef}, 80/20 batches f=1e-7..1e-3 |E|, "
+                               f"Dynamic Frontier vs Static vs Naive-dynamic",
+                   "n": n, "m_with_self_loops": m, "batch_fracs": FRACS,
+                   "precision": args.precision, "l2": "flushed (256 MB write) before every timed call",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "e2e": {"value": e2e_value, "unit": "ms", "h2d_bytes_per_step": h2d // K,
+                "d2h_bytes_per_step": 8 * n * len(FRACS)},
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "kernel": "k_rank (Static full sweep launches)",
+                     "all_rank_launches_gbs": all_bytes / (all_ms * 1e-3) / 1e9},
+        "per_frac": per_f,
+        "speedup_vs_static_geomean": geomean([per_f[k]["speedup_vs_static"] for k in per_f]),
+        "speedup_vs_naive_geomean": geomean([per_f[k]["speedup_vs_naive"] for k in per_f]),
+        "clocks": clk,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+# -------------------------------------------------------- reference arm ----
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    import oracle
+    import synth
+
+    oracle.build()
+    g = synth.rmat(args.scale, args.ef, seed=1)
+    G = oracle.Graph.build(g.n, g.src, g.dst)
+    R, _ = oracle.static_pr(G)
+    s = synth.BatchStream(g, seed=1)
+    W, K = args.warmup, args.steps
+    times = {f: [] for f in FRACS}
+    for i in range(W + K):
+        f = FRACS[i % len(FRACS)]
+        b = s.next(f)
+        H, ed, ei = G.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+        t = time.perf_counter()
+        R, _, st = oracle.df_sync(G, H, ed, ei, R)
+        dt = (time.perf_counter() - t) * 1e3
+        if i >= W:
+            times[f].append(dt)
+        G = H
+    means = [sum(v) / len(v) for v in times.values() if v]
+    value = geomean(means)
+    all_t = [x for v in times.values() for x in v]
+    sample = (f"sequential FP64 oracle (Algorithm 1, synchronous) on R-MAT s{args.scale} ef{args.ef}; step i "
+              f"updates one 80/20 batch of f = FRACS[i mod 5]; {K} timed steps after {W} warm-up steps")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": sum(all_t) / len(all_t) if all_t else None, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"R-MAT scale {args.scale} edge factor {args.ef}, 80/20 batches f=1e-7..1e-3 |E|, "
+                               f"Dynamic Frontier vs Static vs Naive-dynamic", "batch_fracs": FRACS,
+                   "precision": "fp64"},
+        "cpu_baseline": {"value": value, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "per_frac_ms": {f"{f:g}": (sum(v) / len(v) if v else None) for f, v in times.items()},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--scale", type=int, default=22)
+    ap.add_argument("--ef", type=int, default=16)
+    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-timeout", type=float, default=600.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -135,6 +135,10 @@ pr_status pr_get_csr(pr_graph *g, int32_t dir, uint64_t *offs, uint32_t *cols);
  * into a host array of capacity cap; *count receives the total number. */
 pr_status pr_get_affected(pr_graph *g, uint32_t *out, int64_t cap, int64_t *count);
 
+/* Number of CUDA kernels this library has launched in this process (all handles),
+ * for accounting of device work.  Never fails. */
+uint64_t pr_kernel_launches(void);
+
 /* Message of the last failed call on g (or of the last failed pr_graph_create if g is NULL). */
 const char *pr_last_error(const pr_graph *g);
 

@@ -98,6 +98,18 @@ static int has_key(const uint64_t *a, uint64_t n, uint64_t x)
     return lo < n && a[lo] == x;
 }
 
+/* Union of two ascending key arrays without repeats (a and b each have none). */
+static uint64_t merge_sets(const uint64_t *a, uint64_t na, const uint64_t *b, uint64_t nb, uint64_t *out)
+{
+    uint64_t i = 0, j = 0, w = 0;
+    while (i < na || j < nb) {
+        if (j >= nb || (i < na && a[i] < b[j])) out[w++] = a[i++];
+        else if (i >= na || b[j] < a[i]) out[w++] = b[j++];
+        else { out[w++] = a[i++]; j++; }
+    }
+    return w;
+}
+
 /* Build both adjacencies from a sorted unique key set E (no self pairs); adds the
  * self-loop (v, v) of every vertex if self_loops is set.  Takes ownership of nothing. */
 static or_graph *graph_from_set(uint32_t n, const uint64_t *E, uint64_t e, int self_loops)
@@ -107,10 +119,14 @@ static or_graph *graph_from_set(uint32_t n, const uint64_t *E, uint64_t e, int s
     g->self_loops = self_loops;
     g->m = e + (self_loops ? n : 0);
     uint64_t *all = (uint64_t *)malloc(sizeof(uint64_t) * (g->m ? g->m : 1));
-    memcpy(all, E, sizeof(uint64_t) * e);
-    if (self_loops)
-        for (uint32_t v = 0; v < n; v++) all[e + v] = ((uint64_t)v << 32) | v;
-    qsort(all, g->m, sizeof(uint64_t), cmp_u64);
+    if (self_loops) {
+        uint64_t *loops = (uint64_t *)malloc(sizeof(uint64_t) * (n ? n : 1));
+        for (uint32_t v = 0; v < n; v++) loops[v] = ((uint64_t)v << 32) | v;
+        merge_sets(E, e, loops, n, all);
+        free(loops);
+    } else {
+        memcpy(all, E, sizeof(uint64_t) * e);
+    }
 
     /* out-adjacency: rows by source, each row ascending by target */
     g->out_off = (uint64_t *)calloc((size_t)n + 1, sizeof(uint64_t));
@@ -199,27 +215,27 @@ or_graph *or_apply_batch(const or_graph *g, uint64_t nd, const uint32_t *ds, con
     uint64_t *D = pair_set(nd, ds, dd, &c_del);
     uint64_t *I = pair_set(ni, is, id, &c_ins);
 
-    uint64_t *Enew = (uint64_t *)malloc(sizeof(uint64_t) * (e_old + c_ins + 1));
+    /* E minus D, then union with I (all ascending) */
+    uint64_t *Ekeep = (uint64_t *)malloc(sizeof(uint64_t) * (e_old + 1));
     uint64_t w = 0;
     for (uint64_t i = 0; i < e_old; i++)
-        if (!has_key(D, c_del, E[i])) Enew[w++] = E[i];
-    for (uint64_t i = 0; i < c_ins; i++) Enew[w++] = I[i];
-    qsort(Enew, w, sizeof(uint64_t), cmp_u64);
-    uint64_t e_new = 0;
-    for (uint64_t i = 0; i < w; i++)
-        if (e_new == 0 || Enew[e_new - 1] != Enew[i]) Enew[e_new++] = Enew[i];
+        if (!has_key(D, c_del, E[i])) Ekeep[w++] = E[i];
+    uint64_t *Enew = (uint64_t *)malloc(sizeof(uint64_t) * (w + c_ins + 1));
+    uint64_t e_new = merge_sets(Ekeep, w, I, c_ins, Enew);
+    free(Ekeep);
 
-    uint64_t a = 0;
-    for (uint64_t i = 0; i < e_old; i++)
-        if (!has_key(Enew, e_new, E[i])) {
-            eds[a] = (uint32_t)(E[i] >> 32); edd[a] = (uint32_t)E[i]; a++;
+    /* Delta^- = E^{t-1} \ E^t and Delta^+ = E^t \ E^{t-1}, by one walk over both sets */
+    uint64_t a = 0, b = 0, i = 0, j = 0;
+    while (i < e_old || j < e_new) {
+        if (j >= e_new || (i < e_old && E[i] < Enew[j])) {
+            eds[a] = (uint32_t)(E[i] >> 32); edd[a] = (uint32_t)E[i]; a++; i++;
+        } else if (i >= e_old || Enew[j] < E[i]) {
+            eis[b] = (uint32_t)(Enew[j] >> 32); eid[b] = (uint32_t)Enew[j]; b++; j++;
+        } else {
+            i++; j++;
         }
+    }
     *n_eff_del = a;
-    uint64_t b = 0;
-    for (uint64_t i = 0; i < e_new; i++)
-        if (!has_key(E, e_old, Enew[i])) {
-            eis[b] = (uint32_t)(Enew[i] >> 32); eid[b] = (uint32_t)Enew[i]; b++;
-        }
     *n_eff_ins = b;
 
     or_graph *h = graph_from_set(g->n, Enew, e_new, g->self_loops);

@@ -3,6 +3,7 @@
 // Validation happens here, before any device state is touched, so that a rejected call
 // leaves the graph and its ranks as they were.  Host arrays are copied to the device;
 // device arrays are used in place.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -65,6 +66,11 @@ pr_status check_params(const pr_params &p, std::string *why) {
 
 using prdf::Graph;
 
+namespace prdf {
+static std::atomic<unsigned long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace prdf
+
 extern "C" {
 
 void pr_params_default(pr_params *p) {
@@ -93,6 +99,8 @@ const char *pr_status_string(pr_status s) {
   }
   return "unknown status";
 }
+
+uint64_t pr_kernel_launches(void) { return prdf::g_launches.load(std::memory_order_relaxed); }
 
 const char *pr_last_error(const pr_graph *h) { return h ? h->g.err.c_str() : g_create_err.c_str(); }
 

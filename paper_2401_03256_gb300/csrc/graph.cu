@@ -419,8 +419,8 @@ static pr_status build_adj(Graph *g, const uint64_t *keys, uint64_t m, Adj &A, u
   cudaStream_t st = g->st;
   CK(dalloc(&A.rd, n));
   CK(dalloc(&A.cap, n));
-  k_row_bounds<<<grid_for(m + 1), 256, 0, st>>>(keys, m, g->b, n, off);
-  k_row_caps<<<grid_for(n), 256, 0, st>>>(off, n, A.cap);
+  k_row_bounds<<<grid_for(m + 1), 256, 0, st>>>(keys, m, g->b, n, off); count_launch();
+  k_row_caps<<<grid_for(n), 256, 0, st>>>(off, n, A.cap); count_launch();
   exclusive_scan_u32(A.cap, tmp, n, scan_tmp, st);
   uint32_t last[2];
   CK(cudaMemcpyAsync(&last[0], tmp + (n - 1), 4, cudaMemcpyDeviceToHost, st));
@@ -436,8 +436,8 @@ static pr_status build_adj(Graph *g, const uint64_t *keys, uint64_t m, Adj &A, u
   A.col_cap = total + reserve;
   CK(dalloc(&A.col, A.col_cap));
   CK(cudaMemsetAsync(A.col, 0, sizeof(uint32_t) * A.col_cap, st));
-  k_row_desc<<<grid_for(n), 256, 0, st>>>(tmp, off, n, A.rd);
-  k_scatter_cols<<<grid_for(m), 256, 0, st>>>(keys, m, g->b, off, A.rd, A.col);
+  k_row_desc<<<grid_for(n), 256, 0, st>>>(tmp, off, n, A.rd); count_launch();
+  k_scatter_cols<<<grid_for(m), 256, 0, st>>>(keys, m, g->b, off, A.rd, A.col); count_launch();
   A.used = total;
   A.garbage = 0;
   CK(cudaGetLastError());
@@ -454,7 +454,10 @@ pr_status graph_build(Graph *g, uint64_t m_in, const uint32_t *src_d, const uint
   uint32_t *flag = nullptr;
   CK(dalloc(&flag, 1));
   CK(cudaMemsetAsync(flag, 0, 4, st));
-  if (m_in) k_validate_pairs<<<grid_for(m_in), 256, 0, st>>>(src_d, dst_d, m_in, n, flag);
+  if (m_in) {
+    k_validate_pairs<<<grid_for(m_in), 256, 0, st>>>(src_d, dst_d, m_in, n, flag);
+    count_launch();
+  }
   uint32_t bad = 0;
   CK(cudaMemcpyAsync(&bad, flag, 4, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -486,14 +489,17 @@ pr_status graph_build(Graph *g, uint64_t m_in, const uint32_t *src_d, const uint
     return cuda_fail(g, e, "graph build scratch");
   }
   do {
-    if (mk) k_make_keys<<<grid_for(mk), 256, 0, st>>>(src_d, dst_d, m_in, n, g->b, sl ? 1 : 0, keys);
+    if (mk) {
+    k_make_keys<<<grid_for(mk), 256, 0, st>>>(src_d, dst_d, m_in, n, g->b, sl ? 1 : 0, keys);
+    count_launch();
+  }
     uint64_t *sorted = sort_u64(keys, alt, mk, 2 * g->b, hist, stmp, st);
     uint64_t *other = sorted == keys ? alt : keys;
     uint32_t m = 0;
     if (mk) {
-      k_unique_flags<<<grid_for(mk), 256, 0, st>>>(sorted, mk, flags);
+      k_unique_flags<<<grid_for(mk), 256, 0, st>>>(sorted, mk, flags); count_launch();
       exclusive_scan_u32(flags, pos, mk, stmp, st);
-      k_compact_unique<<<grid_for(mk), 256, 0, st>>>(sorted, pos, mk, other, cnt);
+      k_compact_unique<<<grid_for(mk), 256, 0, st>>>(sorted, pos, mk, other, cnt); count_launch();
       if ((e = cudaMemcpyAsync(&m, cnt, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess) break;
       if ((e = cudaStreamSynchronize(st)) != cudaSuccess) break;
     }
@@ -502,7 +508,10 @@ pr_status graph_build(Graph *g, uint64_t m_in, const uint32_t *src_d, const uint
     rc = build_adj(g, other, m, g->out, flags, pos, stmp);
     if (rc != PR_OK) break;
     // in-adjacency from transposed keys sorted by (v, u)
-    if (m) k_transpose_keys<<<grid_for(m), 256, 0, st>>>(other, m, g->b, sorted);
+    if (m) {
+    k_transpose_keys<<<grid_for(m), 256, 0, st>>>(other, m, g->b, sorted);
+    count_launch();
+  }
     uint64_t *tsorted = sort_u64(sorted, other, m, 2 * g->b, hist, stmp, st);
     rc = build_adj(g, tsorted, m, g->in, flags, pos, stmp);
     if (rc != PR_OK) break;
@@ -539,6 +548,7 @@ pr_status graph_build(Graph *g, uint64_t m_in, const uint32_t *src_d, const uint
   else
     k_init_rank<double><<<grid_for(n), 256, 0, st>>>(g->out.rd, n, g->p.alpha, (double *)g->adeg, (double *)g->R[0],
                                                      (double *)g->R[1], (double *)g->C[0], (double *)g->C[1]);
+  count_launch();
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(st));
   g->ident_dirty = true;
@@ -577,7 +587,7 @@ pr_status apply_scratch(Graph *g, uint64_t N) {
 static pr_status repack_adj(Graph *g, Adj &A, uint64_t reserve) {
   const uint32_t n = g->n;
   cudaStream_t st = g->st;
-  k_len_caps<<<grid_for(n), 256, 0, st>>>(A.rd, n, A.cap);
+  k_len_caps<<<grid_for(n), 256, 0, st>>>(A.rd, n, A.cap); count_launch();
   exclusive_scan_u32(A.cap, g->gen_tmp, n, g->scan_tmp, st);
   uint32_t last[2];
   CK(cudaMemcpyAsync(&last[0], g->gen_tmp + (n - 1), 4, cudaMemcpyDeviceToHost, st));
@@ -593,7 +603,7 @@ static pr_status repack_adj(Graph *g, Adj &A, uint64_t reserve) {
   uint32_t *nc = nullptr;
   CK(dalloc(&nc, total + reserve));
   CK(cudaMemsetAsync(nc, 0, sizeof(uint32_t) * (total + reserve), st));
-  k_repack_rows<<<grid_for((uint64_t)n * 32), 256, 0, st>>>(A.rd, n, A.col, nc, g->gen_tmp);
+  k_repack_rows<<<grid_for((uint64_t)n * 32), 256, 0, st>>>(A.rd, n, A.col, nc, g->gen_tmp); count_launch();
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(st));
   cudaFree(A.col);
@@ -623,14 +633,14 @@ pr_status graph_apply(Graph *g, uint64_t nd, const uint32_t *ds, const uint32_t 
   h.tail_in = g->in.used;
   CK(cudaMemcpyAsync(g->actl, &h, sizeof(ApplyCtl), cudaMemcpyHostToDevice, st));
 
-  k_batch_keys<<<grid_for(N), 256, 0, st>>>(ds, dd, nd, is, id, ni, g->n, b, s.kd, s.ki, g->actl);
+  k_batch_keys<<<grid_for(N), 256, 0, st>>>(ds, dd, nd, is, id, ni, g->n, b, s.kd, s.ki, g->actl); count_launch();
   uint64_t *kd = sort_u64(s.kd, s.tmp, nd, 2 * b, s.radix_hist, s.scan_tmp, st);
   uint64_t *ki = sort_u64(s.ki, s.tmp2, ni, 2 * b, s.radix_hist, s.scan_tmp, st);
-  k_filter<<<grid_for(N), 256, 0, st>>>(kd, nd, ki, ni, g->out.rd, g->out.col, b, s.flags);
+  k_filter<<<grid_for(N), 256, 0, st>>>(kd, nd, ki, ni, g->out.rd, g->out.col, b, s.flags); count_launch();
   exclusive_scan_u32(s.flags, s.pos, N, s.scan_tmp, st);
   uint64_t *chg = kd == s.kd ? s.tmp : s.kd;     // free buffers after the sorts
   uint64_t *chg_t = ki == s.ki ? s.tmp2 : s.ki;
-  k_emit_changes<<<grid_for(N), 256, 0, st>>>(kd, nd, ki, ni, s.flags, s.pos, b, s.chg, s.chg_t, g->actl);
+  k_emit_changes<<<grid_for(N), 256, 0, st>>>(kd, nd, ki, ni, s.flags, s.pos, b, s.chg, s.chg_t, g->actl); count_launch();
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(&h, g->actl, sizeof(ApplyCtl), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -648,19 +658,19 @@ pr_status graph_apply(Graph *g, uint64_t nd, const uint32_t *ds, const uint32_t 
   uint32_t *tp_o = s.tagpref, *tp_i = s.tagpref + (s.cap + 2);
   ApplyCtl *dctl = g->actl;
   // segments of the out-row changes
-  k_seg_flags<<<grid_for(K + 1), 256, 0, st>>>(co, K, b, s.flags, tp_o);
+  k_seg_flags<<<grid_for(K + 1), 256, 0, st>>>(co, K, b, s.flags, tp_o); count_launch();
   exclusive_scan_u32(s.flags, s.pos, K, s.scan_tmp, st);
   exclusive_scan_u32(tp_o, tp_o, K + 1, s.scan_tmp, st);
-  k_seg_emit<<<grid_for(K), 256, 0, st>>>(s.flags, s.pos, K, seg_o, &dctl->n_seg_out);
+  k_seg_emit<<<grid_for(K), 256, 0, st>>>(s.flags, s.pos, K, seg_o, &dctl->n_seg_out); count_launch();
   k_plan<<<grid_for(K), 256, 0, st>>>(g->out.rd, g->out.cap, co, K, b, seg_o, &dctl->n_seg_out, tp_o,
-                                      &dctl->reloc_out, &dctl->big_cursor);
+                                      &dctl->reloc_out, &dctl->big_cursor); count_launch();
   // segments of the in-row changes
-  k_seg_flags<<<grid_for(K + 1), 256, 0, st>>>(ci, K, b, s.flags, tp_i);
+  k_seg_flags<<<grid_for(K + 1), 256, 0, st>>>(ci, K, b, s.flags, tp_i); count_launch();
   exclusive_scan_u32(s.flags, s.pos, K, s.scan_tmp, st);
   exclusive_scan_u32(tp_i, tp_i, K + 1, s.scan_tmp, st);
-  k_seg_emit<<<grid_for(K), 256, 0, st>>>(s.flags, s.pos, K, seg_i, &dctl->n_seg_in);
+  k_seg_emit<<<grid_for(K), 256, 0, st>>>(s.flags, s.pos, K, seg_i, &dctl->n_seg_in); count_launch();
   k_plan<<<grid_for(K), 256, 0, st>>>(g->in.rd, g->in.cap, ci, K, b, seg_i, &dctl->n_seg_in, tp_i,
-                                      &dctl->reloc_in, &dctl->big_cursor);
+                                      &dctl->reloc_in, &dctl->big_cursor); count_launch();
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(&h, g->actl, sizeof(ApplyCtl), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -683,9 +693,9 @@ pr_status graph_apply(Graph *g, uint64_t nd, const uint32_t *ds, const uint32_t 
     CK(cudaMemsetAsync(&dctl->reloc_out, 0, 16, st));  // reloc_out, reloc_in
     CK(cudaMemsetAsync(&dctl->big_cursor, 0, 8, st));
     k_plan<<<grid_for(K), 256, 0, st>>>(g->out.rd, g->out.cap, co, K, b, seg_o, &dctl->n_seg_out, tp_o,
-                                        &dctl->reloc_out, &dctl->big_cursor);
+                                        &dctl->reloc_out, &dctl->big_cursor); count_launch();
     k_plan<<<grid_for(K), 256, 0, st>>>(g->in.rd, g->in.cap, ci, K, b, seg_i, &dctl->n_seg_in, tp_i,
-                                        &dctl->reloc_in, &dctl->big_cursor);
+                                        &dctl->reloc_in, &dctl->big_cursor); count_launch();
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(&h, g->actl, sizeof(ApplyCtl), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -710,20 +720,20 @@ pr_status graph_apply(Graph *g, uint64_t nd, const uint32_t *ds, const uint32_t 
     OutRowHook<float> hi{};
     k_merge<float><<<K, kMergeThreads, 0, st>>>(g->out.rd, g->out.cap, g->out.col, co, b, seg_o, &dctl->n_seg_out,
                                                 tp_o, &dctl->tail_out, &dctl->garbage_out, g->big, &dctl->big_cursor,
-                                                g->out.col_cap, g->big_cap, dctl, ho);
+                                                g->out.col_cap, g->big_cap, dctl, ho); count_launch();
     k_merge<float><<<K, kMergeThreads, 0, st>>>(g->in.rd, g->in.cap, g->in.col, ci, b, seg_i, &dctl->n_seg_in, tp_i,
                                                 &dctl->tail_in, &dctl->garbage_in, g->big, &dctl->big_cursor,
-                                                g->in.col_cap, g->big_cap, dctl, hi);
+                                                g->in.col_cap, g->big_cap, dctl, hi); count_launch();
   } else {
     OutRowHook<double> ho{true, g->p.alpha, (double *)g->adeg, (double *)g->R[0], (double *)g->C[0],
                           (double *)g->C[1], g->pend_src, g->pend_tgt, g->pend_cap};
     OutRowHook<double> hi{};
     k_merge<double><<<K, kMergeThreads, 0, st>>>(g->out.rd, g->out.cap, g->out.col, co, b, seg_o, &dctl->n_seg_out,
                                                  tp_o, &dctl->tail_out, &dctl->garbage_out, g->big, &dctl->big_cursor,
-                                                 g->out.col_cap, g->big_cap, dctl, ho);
+                                                 g->out.col_cap, g->big_cap, dctl, ho); count_launch();
     k_merge<double><<<K, kMergeThreads, 0, st>>>(g->in.rd, g->in.cap, g->in.col, ci, b, seg_i, &dctl->n_seg_in, tp_i,
                                                  &dctl->tail_in, &dctl->garbage_in, g->big, &dctl->big_cursor,
-                                                 g->in.col_cap, g->big_cap, dctl, hi);
+                                                 g->in.col_cap, g->big_cap, dctl, hi); count_launch();
   }
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(&h, g->actl, sizeof(ApplyCtl), cudaMemcpyDeviceToHost, st));
@@ -759,11 +769,11 @@ pr_status graph_export(Graph *g, int dir, uint64_t *offs_h, uint32_t *cols_h) {
   const uint32_t n = g->n;
   cudaStream_t st = g->st;
   Adj &A = dir ? g->in : g->out;
-  k_row_len<<<grid_for((uint64_t)n + 1), 256, 0, st>>>(A.rd, n, g->gen_tmp);
+  k_row_len<<<grid_for((uint64_t)n + 1), 256, 0, st>>>(A.rd, n, g->gen_tmp); count_launch();
   exclusive_scan_u32(g->gen_tmp, g->gen_tmp2, (uint64_t)n + 1, g->scan_tmp, st);
   uint32_t *packed = nullptr;
   CK(dalloc(&packed, std::max<uint64_t>(g->m, 1)));
-  k_pack_rows<<<grid_for((uint64_t)n * 32), 256, 0, st>>>(A.rd, n, A.col, g->gen_tmp2, packed);
+  k_pack_rows<<<grid_for((uint64_t)n * 32), 256, 0, st>>>(A.rd, n, A.col, g->gen_tmp2, packed); count_launch();
   std::vector<uint32_t> off(n + 1);
   cudaError_t e = cudaMemcpyAsync(off.data(), g->gen_tmp2, 4ull * (n + 1), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(cols_h, packed, 4ull * g->m, cudaMemcpyDeviceToHost, st);
@@ -782,9 +792,9 @@ pr_status graph_refresh_ident(Graph *g) {
   uint32_t base = 0;
   for (int bin = 0; bin < 3; bin++) {
     k_bin_flags<<<grid_for(n), 256, 0, st>>>(g->in.rd, n, (uint32_t)g->p.bin_lo, (uint32_t)g->p.bin_hi, bin,
-                                            g->gen_tmp);
+                                            g->gen_tmp); count_launch();
     exclusive_scan_u32(g->gen_tmp, g->gen_tmp2, n, g->scan_tmp, st);
-    k_compact_ids<<<grid_for(n), 256, 0, st>>>(g->gen_tmp, g->gen_tmp2, n, g->ident + base, cnt);
+    k_compact_ids<<<grid_for(n), 256, 0, st>>>(g->gen_tmp, g->gen_tmp2, n, g->ident + base, cnt); count_launch();
     uint32_t c = 0;
     CK(cudaMemcpyAsync(&c, cnt, 4, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -800,9 +810,9 @@ pr_status graph_refresh_dead(Graph *g) {
   const uint32_t n = g->n;
   cudaStream_t st = g->st;
   uint32_t *cnt = (uint32_t *)&g->actl->n_seg_in;
-  k_dead_flags<<<grid_for(n), 256, 0, st>>>(g->out.rd, n, g->gen_tmp);
+  k_dead_flags<<<grid_for(n), 256, 0, st>>>(g->out.rd, n, g->gen_tmp); count_launch();
   exclusive_scan_u32(g->gen_tmp, g->gen_tmp2, n, g->scan_tmp, st);
-  k_compact_ids<<<grid_for(n), 256, 0, st>>>(g->gen_tmp, g->gen_tmp2, n, g->dead, cnt);
+  k_compact_ids<<<grid_for(n), 256, 0, st>>>(g->gen_tmp, g->gen_tmp2, n, g->dead, cnt); count_launch();
   uint32_t c = 0;
   CK(cudaMemcpyAsync(&c, cnt, 4, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));

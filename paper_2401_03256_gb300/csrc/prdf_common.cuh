@@ -43,6 +43,9 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
+// Kernel-launch accounting (pr_kernel_launches); bumped after every launch.
+void count_launch();
+
 // ------------------------------------------------------------------- structures ---
 
 // One adjacency (in- or out-edges) in slack-row form.

@@ -70,13 +70,13 @@ size_t scan_tmp_words(uint64_t n) {
 void exclusive_scan_u32(const uint32_t *in, uint32_t *out, uint64_t n, uint32_t *tmp, cudaStream_t st) {
   if (n == 0) return;
   if (n <= (uint64_t)kScanTile) {
-    k_scan_tiles<<<1, kScanThreads, 0, st>>>(in, out, n, nullptr);
+    k_scan_tiles<<<1, kScanThreads, 0, st>>>(in, out, n, nullptr); count_launch();
     return;
   }
   uint64_t nb = (n + kScanTile - 1) / kScanTile;
-  k_scan_tiles<<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, tmp);
+  k_scan_tiles<<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, tmp); count_launch();
   exclusive_scan_u32(tmp, tmp, nb, tmp + nb, st);
-  k_scan_add<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(out, n, tmp);
+  k_scan_add<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(out, n, tmp); count_launch();
 }
 
 // ------------------------------------------------------------------ small sort ---
@@ -192,15 +192,15 @@ uint64_t *sort_u64(uint64_t *keys, uint64_t *alt, uint64_t n, int bits, uint32_t
                    cudaStream_t st) {
   if (n < 2) return keys;
   if (n <= kSmallSort) {
-    k_block_sort<<<1, 1024, 0, st>>>(keys, (uint32_t)n);
+    k_block_sort<<<1, 1024, 0, st>>>(keys, (uint32_t)n); count_launch();
     return keys;
   }
   const uint32_t nblocks = (uint32_t)((n + kRadixTile - 1) / kRadixTile);
   uint64_t *src = keys, *dst = alt;
   for (int shift = 0; shift < bits; shift += 8) {
-    k_radix_hist<<<nblocks, kRadixThreads, 0, st>>>(src, n, shift, hist, nblocks);
+    k_radix_hist<<<nblocks, kRadixThreads, 0, st>>>(src, n, shift, hist, nblocks); count_launch();
     exclusive_scan_u32(hist, hist, (uint64_t)256 * nblocks, scan_tmp, st);
-    k_radix_scatter<<<nblocks, kRadixThreads, 0, st>>>(src, dst, n, shift, hist, nblocks);
+    k_radix_scatter<<<nblocks, kRadixThreads, 0, st>>>(src, dst, n, shift, hist, nblocks); count_launch();
     uint64_t *t = src;
     src = dst;
     dst = t;

@@ -621,6 +621,7 @@ static pr_status launch(Graph *g, RankMode mode, bool start_full) {
   a.ctl = g->ctl;
   void *args[] = {(void *)&a};
   CK(cudaLaunchCooperativeKernel((const void *)k_rank<T>, dim3(g->rank_grid), dim3(kRankBlock), args, 0, g->st));
+  count_launch();
   return PR_OK;
 }
 
@@ -712,13 +713,14 @@ pr_status rank_set(Graph *g, const double *in_d) {
   else
     k_set_ranks<double><<<grid, 256, 0, g->st>>>(in_d, g->n, (const double *)g->adeg, (double *)g->R[0],
                                                  (double *)g->R[1], (double *)g->C[0], (double *)g->C[1]);
+  count_launch();
   CK(cudaGetLastError());
   if (g->teleport) {
     pr_status rc = graph_refresh_dead(g);
     if (rc != PR_OK) return rc;
     double *dm = nullptr;
     CK(cudaMalloc((void **)&dm, sizeof(double)));
-    k_dead_mass<<<1, 256, 0, g->st>>>(g->dead, g->n_dead, in_d, dm);
+    k_dead_mass<<<1, 256, 0, g->st>>>(g->dead, g->n_dead, in_d, dm); count_launch();
     double D = 0.0;
     cudaError_t e = cudaMemcpyAsync(&D, dm, sizeof(double), cudaMemcpyDeviceToHost, g->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
@@ -736,6 +738,7 @@ pr_status rank_get(Graph *g, double *out_d) {
     k_get_ranks<float><<<grid, 256, 0, g->st>>>((const float *)g->R[0], g->n, out_d);
   else
     k_get_ranks<double><<<grid, 256, 0, g->st>>>((const double *)g->R[0], g->n, out_d);
+  count_launch();
   CK(cudaGetLastError());
   return PR_OK;
 }

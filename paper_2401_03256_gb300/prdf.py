@@ -31,7 +31,7 @@ PR_DEADEND_TELEPORT = 1
 EXPORTED = (
     "pr_params_default", "pr_graph_create", "pr_graph_destroy", "pr_apply_batch", "pr_static",
     "pr_naive_dynamic", "pr_dynamic_frontier", "pr_get_ranks", "pr_set_ranks", "pr_graph_info",
-    "pr_get_csr", "pr_get_affected", "pr_last_error", "pr_status_string",
+    "pr_get_csr", "pr_get_affected", "pr_kernel_launches", "pr_last_error", "pr_status_string",
 )
 
 
@@ -91,6 +91,8 @@ def load(path: str = LIB_PATH):
     lib.pr_get_csr.argtypes = [vp, i32, vp, vp]
     lib.pr_get_affected.restype = ctypes.c_int
     lib.pr_get_affected.argtypes = [vp, vp, i64, ctypes.POINTER(i64)]
+    lib.pr_kernel_launches.restype = ctypes.c_uint64
+    lib.pr_kernel_launches.argtypes = []
     lib.pr_last_error.restype = ctypes.c_char_p
     lib.pr_last_error.argtypes = [vp]
     lib.pr_status_string.restype = ctypes.c_char_p
@@ -220,6 +222,11 @@ def pr_get_csr(h: int, direction: int):
     col = np.empty(max(m, 1), np.uint32)
     _check(load().pr_get_csr(h, direction, off.ctypes.data, col.ctypes.data), h)
     return off, col[:m]
+
+
+def pr_kernel_launches() -> int:
+    """Kernels launched by libprdf.so in this process so far."""
+    return int(load().pr_kernel_launches())
 
 
 def pr_get_affected(h: int) -> np.ndarray:

@@ -244,9 +244,9 @@ def _df_case(prdf, g, frac, batches, seed, params=None, oparams=None, check_affe
     with prdf.Graph(g.n, g.src, g.dst, params) as dg:
         for t in range(batches):
             b = s.next(frac)
+            dg.set_ranks(R_or)                 # both sides start from the same R^{t-1} on G^{t-1}
             dg.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
             H, ed, ei = G.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
-            dg.set_ranks(R_or)                 # both sides start from the same R^{t-1}
             st = dg.frontier()
             R_df, aff, st_or = oracle.df_sync(G, H, ed, ei, R_or, oparams)
             R = dg.ranks()
@@ -404,9 +404,9 @@ def test_fp32_static_and_df_against_fp64_oracle(prdf):
         assert np.max(np.abs(dg.ranks() - R_or)) <= TOL32
         for t in range(3):
             b = s.next(1e-3)
+            dg.set_ranks(R_or)
             dg.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
             H, ed, ei = G.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
-            dg.set_ranks(R_or)
             dg.frontier()
             R_or, _, _ = oracle.df_sync(G, H, ed, ei, R_or)
             G = H
