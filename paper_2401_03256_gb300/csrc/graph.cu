@@ -121,18 +121,21 @@ __global__ void k_scatter_cols(const uint64_t *keys, uint64_t m, int b, const ui
   col[rd[r].x + (uint32_t)(i - off[r])] = (uint32_t)(k & ((1ull << b) - 1));
 }
 
-template <class T>
-__global__ void k_init_rank(const uint2 *out_rd, uint32_t n, double alpha, T *adeg, T *R0, T *R1, T *C0, T *C1) {
+template <bool F32>
+__global__ void k_init_rank(const uint2 *out_rd, uint32_t n, double alpha, typename Store<F32>::A *adeg,
+                            typename Store<F32>::R *R0, typename Store<F32>::R *R1, typename Store<F32>::C *C0,
+                            typename Store<F32>::C *C1) {
+  using S = Store<F32>;
   uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= n) return;
-  uint32_t d = out_rd[v].y;
-  T a = d ? (T)(alpha / (double)d) : (T)0;
-  T r = (T)(1.0 / (double)n);
+  typename S::A a = S::factor(alpha, out_rd[v].y);
+  typename S::R r = (typename S::R)(1.0 / (double)n);
+  typename S::C c = S::contrib(r, a);
   adeg[v] = a;
   R0[v] = r;
   R1[v] = r;
-  C0[v] = r * a;
-  C1[v] = r * a;
+  C0[v] = c;
+  C1[v] = c;
 }
 
 // ---- batch update ----
@@ -255,25 +258,32 @@ __global__ void k_plan(const uint2 *rd, const uint32_t *cap, const uint64_t *chg
   if (len > kSmemRow) atomicAdd(big_need, (unsigned long long)len);
 }
 
-// Extra work done by the merge of an out-row (source u): contribution refresh and
-// pending marks.  Disabled (is_out == false) for in-rows.
-template <class T>
-struct OutRowHook {
+// Extra work done by the merge of a row.  Out-rows (source u): contribution refresh and
+// pending marks.  In-rows: note an in-degree that crosses a bin threshold.
+template <bool F32>
+struct RowHook {
   bool is_out;
   double alpha;
-  T *adeg, *R0, *C0, *C1;
+  typename Store<F32>::A *adeg;
+  typename Store<F32>::R *R0;
+  typename Store<F32>::C *C0, *C1;
   uint32_t *pend_src, *pend_tgt;
   uint32_t pend_cap;
+  uint32_t bin_lo, bin_hi;
 };
 
+__device__ __forceinline__ int degree_bin(uint32_t d, uint32_t lo, uint32_t hi) {
+  return d <= lo ? 0 : (d <= hi ? 1 : 2);
+}
+
 // One block per touched row: merges the row with its sorted changes.
-template <class T>
+template <bool F32>
 __global__ void __launch_bounds__(kMergeThreads) k_merge(uint2 *rd, uint32_t *cap, uint32_t *col, const uint64_t *chg,
                                                          int b, const uint32_t *seg, const uint32_t *nseg,
                                                          const uint32_t *tagpref, unsigned long long *tail,
                                                          unsigned long long *garbage, uint32_t *big,
                                                          unsigned long long *big_cursor, uint64_t col_cap,
-                                                         uint64_t big_cap, ApplyCtl *actl, OutRowHook<T> hook) {
+                                                         uint64_t big_cap, ApplyCtl *actl, RowHook<F32> hook) {
   __shared__ uint32_t srow[kSmemRow];
   __shared__ uint32_t s_dest, s_big;
   const uint32_t s = blockIdx.x;
@@ -342,10 +352,13 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(uint2 *rd, uint32_t *ca
       cap[r] = move_cap(new_len);
       atomicAdd(garbage, (unsigned long long)cap_r);
     }
+    if (!hook.is_out && degree_bin(len, hook.bin_lo, hook.bin_hi) != degree_bin(new_len, hook.bin_lo, hook.bin_hi))
+      actl->bins_changed = 1;
     if (hook.is_out) {
-      T a = new_len ? (T)(hook.alpha / (double)new_len) : (T)0;
+      using S = Store<F32>;
+      typename S::A a = S::factor(hook.alpha, new_len);
       hook.adeg[r] = a;
-      T c = hook.R0[r] * a;
+      typename S::C c = S::contrib(hook.R0[r], a);
       hook.C0[r] = c;
       hook.C1[r] = c;
       if ((len == 0) != (new_len == 0)) actl->dead_changed = 1;
@@ -531,6 +544,10 @@ pr_status graph_build(Graph *g, uint64_t m_in, const uint32_t *src_d, const uint
   const uint32_t words = (n + 31) / 32;
   CK(dalloc(&g->bitmap, words));
   CK(cudaMemsetAsync(g->bitmap, 0, 4ull * words, st));
+  CK(dalloc(&g->xbits, words));
+  CK(cudaMemsetAsync(g->xbits, 0, 4ull * words, st));
+  CK(dalloc(&g->stamp, n));
+  CK(cudaMemsetAsync(g->stamp, 0xFF, 2ull * n, st));
   for (int i = 0; i < 3; i++) CK(dalloc(&g->list[i], n));
   CK(dalloc(&g->ident, n));
   CK(dalloc(&g->dead, n));
@@ -542,18 +559,21 @@ pr_status graph_build(Graph *g, uint64_t m_in, const uint32_t *src_d, const uint
   CK(dalloc(&g->pend_tgt, g->pend_cap));
   CK(dalloc(&g->actl, 1));
   CK(cudaMallocHost((void **)&g->actl_h, sizeof(ApplyCtl)));
-  if (g->f32)
-    k_init_rank<float><<<grid_for(n), 256, 0, st>>>(g->out.rd, n, g->p.alpha, (float *)g->adeg, (float *)g->R[0],
-                                                    (float *)g->R[1], (float *)g->C[0], (float *)g->C[1]);
-  else
-    k_init_rank<double><<<grid_for(n), 256, 0, st>>>(g->out.rd, n, g->p.alpha, (double *)g->adeg, (double *)g->R[0],
-                                                     (double *)g->R[1], (double *)g->C[0], (double *)g->C[1]);
+  if (g->f32) {
+    using S = Store<true>;
+    k_init_rank<true><<<grid_for(n), 256, 0, st>>>(g->out.rd, n, g->p.alpha, (S::A *)g->adeg, (S::R *)g->R[0],
+                                                   (S::R *)g->R[1], (S::C *)g->C[0], (S::C *)g->C[1]);
+  } else {
+    using S = Store<false>;
+    k_init_rank<false><<<grid_for(n), 256, 0, st>>>(g->out.rd, n, g->p.alpha, (S::A *)g->adeg, (S::R *)g->R[0],
+                                                    (S::R *)g->R[1], (S::C *)g->C[0], (S::C *)g->C[1]);
+  }
   count_launch();
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(st));
   g->ident_dirty = true;
   g->dead_dirty = true;
-  return PR_OK;
+  return graph_refresh_ident(g);
 }
 
 pr_status apply_scratch(Graph *g, uint64_t N) {
@@ -714,26 +734,33 @@ pr_status graph_apply(Graph *g, uint64_t nd, const uint32_t *ds, const uint32_t 
   CK(cudaMemcpyAsync(&dctl->tail_out, &h.tail_out, 16, cudaMemcpyHostToDevice, st));  // tail_out, tail_in
   CK(cudaMemsetAsync(&dctl->big_cursor, 0, 8, st));
 
+  const uint32_t lo = (uint32_t)g->p.bin_lo, hi_b = (uint32_t)g->p.bin_hi;
   if (g->f32) {
-    OutRowHook<float> ho{true, g->p.alpha, (float *)g->adeg, (float *)g->R[0], (float *)g->C[0], (float *)g->C[1],
-                         g->pend_src, g->pend_tgt, g->pend_cap};
-    OutRowHook<float> hi{};
-    k_merge<float><<<K, kMergeThreads, 0, st>>>(g->out.rd, g->out.cap, g->out.col, co, b, seg_o, &dctl->n_seg_out,
-                                                tp_o, &dctl->tail_out, &dctl->garbage_out, g->big, &dctl->big_cursor,
-                                                g->out.col_cap, g->big_cap, dctl, ho); count_launch();
-    k_merge<float><<<K, kMergeThreads, 0, st>>>(g->in.rd, g->in.cap, g->in.col, ci, b, seg_i, &dctl->n_seg_in, tp_i,
-                                                &dctl->tail_in, &dctl->garbage_in, g->big, &dctl->big_cursor,
-                                                g->in.col_cap, g->big_cap, dctl, hi); count_launch();
+    using S = Store<true>;
+    RowHook<true> ho{true, g->p.alpha, (S::A *)g->adeg, (S::R *)g->R[0], (S::C *)g->C[0], (S::C *)g->C[1],
+                     g->pend_src, g->pend_tgt, g->pend_cap, lo, hi_b};
+    RowHook<true> hin{false, g->p.alpha, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, lo, hi_b};
+    k_merge<true><<<K, kMergeThreads, 0, st>>>(g->out.rd, g->out.cap, g->out.col, co, b, seg_o, &dctl->n_seg_out,
+                                               tp_o, &dctl->tail_out, &dctl->garbage_out, g->big, &dctl->big_cursor,
+                                               g->out.col_cap, g->big_cap, dctl, ho);
+    count_launch();
+    k_merge<true><<<K, kMergeThreads, 0, st>>>(g->in.rd, g->in.cap, g->in.col, ci, b, seg_i, &dctl->n_seg_in, tp_i,
+                                               &dctl->tail_in, &dctl->garbage_in, g->big, &dctl->big_cursor,
+                                               g->in.col_cap, g->big_cap, dctl, hin);
+    count_launch();
   } else {
-    OutRowHook<double> ho{true, g->p.alpha, (double *)g->adeg, (double *)g->R[0], (double *)g->C[0],
-                          (double *)g->C[1], g->pend_src, g->pend_tgt, g->pend_cap};
-    OutRowHook<double> hi{};
-    k_merge<double><<<K, kMergeThreads, 0, st>>>(g->out.rd, g->out.cap, g->out.col, co, b, seg_o, &dctl->n_seg_out,
-                                                 tp_o, &dctl->tail_out, &dctl->garbage_out, g->big, &dctl->big_cursor,
-                                                 g->out.col_cap, g->big_cap, dctl, ho); count_launch();
-    k_merge<double><<<K, kMergeThreads, 0, st>>>(g->in.rd, g->in.cap, g->in.col, ci, b, seg_i, &dctl->n_seg_in, tp_i,
-                                                 &dctl->tail_in, &dctl->garbage_in, g->big, &dctl->big_cursor,
-                                                 g->in.col_cap, g->big_cap, dctl, hi); count_launch();
+    using S = Store<false>;
+    RowHook<false> ho{true, g->p.alpha, (S::A *)g->adeg, (S::R *)g->R[0], (S::C *)g->C[0], (S::C *)g->C[1],
+                      g->pend_src, g->pend_tgt, g->pend_cap, lo, hi_b};
+    RowHook<false> hin{false, g->p.alpha, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, lo, hi_b};
+    k_merge<false><<<K, kMergeThreads, 0, st>>>(g->out.rd, g->out.cap, g->out.col, co, b, seg_o, &dctl->n_seg_out,
+                                                tp_o, &dctl->tail_out, &dctl->garbage_out, g->big, &dctl->big_cursor,
+                                                g->out.col_cap, g->big_cap, dctl, ho);
+    count_launch();
+    k_merge<false><<<K, kMergeThreads, 0, st>>>(g->in.rd, g->in.cap, g->in.col, ci, b, seg_i, &dctl->n_seg_in, tp_i,
+                                                &dctl->tail_in, &dctl->garbage_in, g->big, &dctl->big_cursor,
+                                                g->in.col_cap, g->big_cap, dctl, hin);
+    count_launch();
   }
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(&h, g->actl, sizeof(ApplyCtl), cudaMemcpyDeviceToHost, st));
@@ -752,7 +779,7 @@ pr_status graph_apply(Graph *g, uint64_t nd, const uint32_t *ds, const uint32_t 
   g->n_pend_tgt = std::min(h.n_pend_tgt, g->pend_cap);
   if (h.n_pend_src > g->pend_cap || h.n_pend_tgt > g->pend_cap) g->pend_all = true;
   if (h.dead_changed) g->dead_dirty = true;
-  g->ident_dirty = true;
+  if (h.bins_changed) g->ident_dirty = true;
   // give abandoned slots back once they dominate
   if (g->out.garbage > g->out.used / 2 && g->out.garbage > 1024) {
     rc = repack_adj(g, g->out, 0);
@@ -762,7 +789,8 @@ pr_status graph_apply(Graph *g, uint64_t nd, const uint32_t *ds, const uint32_t 
     rc = repack_adj(g, g->in, 0);
     if (rc != PR_OK) return rc;
   }
-  return PR_OK;
+  // the degree-binned vertex order used by full and dense sweeps follows the graph
+  return graph_refresh_ident(g);
 }
 
 pr_status graph_export(Graph *g, int dir, uint64_t *offs_h, uint32_t *cols_h) {
@@ -834,6 +862,8 @@ void graph_free(Graph *g) {
   }
   cudaFree(g->adeg);
   cudaFree(g->bitmap);
+  cudaFree(g->xbits);
+  cudaFree(g->stamp);
   for (int i = 0; i < 3; i++) cudaFree(g->list[i]);
   cudaFree(g->ident);
   cudaFree(g->dead);

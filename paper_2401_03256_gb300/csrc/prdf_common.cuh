@@ -46,6 +46,42 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 // Kernel-launch accounting (pr_kernel_launches); bumped after every launch.
 void count_launch();
 
+// ------------------------------------------------------------- rank storage ---
+// Ranks R, cached contributions C[u] = alpha R[u] / |out(u)| and the per-vertex factor A
+// that turns a rank into a contribution.
+//
+// FP64 mode keeps R in IEEE double.  C is kept as an exact fixed-point integer in units
+// of 2^-62 (A = alpha / |out(u)| * 2^62), so the in-edge sums of Eq. 1 are exact int64
+// additions on the integer pipes: GB300 issues FP64 arithmetic at a small fraction of
+// its integer and FP32 rates, and one FP64 add per gathered edge would bound the sweep
+// far below HBM bandwidth.  All of R is below 1 and every in-sum is at most R[v], so the
+// sums stay below 2^62; each contribution is rounded once to the nearest 2^-62
+// (about 2.2e-19 absolute), and the sums carry no rounding at all.
+// FP32 mode keeps R, C and A in float.
+template <bool F32>
+struct Store;
+
+template <>
+struct Store<false> {
+  using R = double;
+  using C = long long;
+  using A = double;
+  static constexpr double kOne = 4611686018427387904.0;  // 2^62
+  __host__ __device__ static A factor(double alpha, uint32_t d) { return d ? alpha / (double)d * kOne : 0.0; }
+  __device__ static C contrib(R r, A a) { return __double2ll_rn(r * a); }
+  __device__ static R from_sum(double base, C sum) { return (double)sum * (1.0 / kOne) + base; }
+};
+
+template <>
+struct Store<true> {
+  using R = float;
+  using C = float;
+  using A = float;
+  __host__ __device__ static A factor(double alpha, uint32_t d) { return d ? (float)(alpha / (double)d) : 0.0f; }
+  __device__ static C contrib(R r, A a) { return r * a; }
+  __device__ static R from_sum(double base, C sum) { return (float)base + sum; }
+};
+
 // ------------------------------------------------------------------- structures ---
 
 // One adjacency (in- or out-edges) in slack-row form.
@@ -109,6 +145,8 @@ struct ApplyCtl {
   uint32_t dead_changed;
   uint32_t n_eff_del;                       // effective deletions among n_eff
   uint32_t overflow;                        // a merge found no room (graph left unchanged rows)
+  uint32_t bins_changed;                    // an in-degree crossed a bin threshold
+  uint32_t pad2;
   unsigned long long big_cursor;            // global scratch cursor for long rows
 };
 

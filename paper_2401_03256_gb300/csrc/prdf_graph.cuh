@@ -35,6 +35,8 @@ struct Graph {
   void *C[2] = {nullptr, nullptr};   // contributions alpha R[u] / |out(u)|
   void *adeg = nullptr;              // alpha / |out(u)| (0 for a dead end)
   uint32_t *bitmap = nullptr;        // affected flags, all zero between calls
+  uint32_t *xbits = nullptr;         // out-row scanned in this call, all zero between calls
+  uint16_t *stamp = nullptr;         // iteration a vertex joins the affected set, 0xFFFF between calls
   uint32_t *list[3] = {nullptr, nullptr, nullptr};  // affected vertices by in-degree bin
   uint32_t *ident = nullptr;         // all vertices grouped by bin (for full sweeps)
   uint32_t ident_cnt[3] = {0, 0, 0};

@@ -2,30 +2,38 @@
 // persistent cooperative kernel per call.
 //
 // Eq. 1 (Section 3.1) in pull form: R[v] = (1 - alpha)/n + sum_{u in in(v)} C[u] with the
-// cached contribution C[u] = alpha R[u] / |out(u)|; in teleport mode a dead end's rank is
-// spread over all vertices (+ alpha D / n, D = sum of ranks of dead ends).
+// cached contribution C[u] = alpha R[u] / |out(u)| (see Store<> for its representation);
+// in teleport mode a dead end's rank is spread over all vertices (+ alpha D / n, D = sum
+// of the ranks of dead ends).
 //
 // Algorithm 1, synchronous form (Section 4.2):
 //   phase 0   initial marking: every vertex of G^t.out(u) for each source u of the
 //             pending changes, plus the deleted targets (= G^{t-1}.out(u) \ G^t.out(u)),
-//             is set in the affected bitmap and appended to one of three lists by
-//             in-degree (thread / warp / block per vertex).
-//   iteration i: every listed vertex v reads ranks and contributions of parity i & 1 and
-//             writes parity (i + 1) & 1; |r - R[v]| feeds the L-inf max (atomicMax on the
-//             bits of a non-negative double) and, if it exceeds tau_f, the out-neighbours
-//             of v are marked and appended; they are processed from iteration i + 1.
-//             One grid barrier per iteration; all blocks read the same L-inf value and
-//             stop together when it is <= tau.
-//   writeback the final parity is copied to the other for every listed vertex (both
-//             parities hold the current ranks between calls) and the bitmap is cleared.
-// Static and Naive-dynamic run the same loop over all vertices (grouped by bin once per
-// graph change) without marking.
+//             is set in the affected bitmap, stamped with the iteration it joins (0) and
+//             appended to one of three lists by in-degree (thread / warp / block per
+//             vertex).
+//   iteration i: every affected vertex v reads ranks and contributions of parity i & 1
+//             and writes parity (i + 1) & 1; |r - R[v]| feeds the L-inf max (atomicMax on
+//             the bits of a non-negative double) and, if it exceeds tau_f, the
+//             out-neighbours of v are marked (stamped i + 1) and appended, so they join in
+//             iteration i + 1.  A vertex scans its out-row at most once per call: marks
+//             persist, so a second scan could not mark anything new.  One grid barrier
+//             per iteration; all blocks read the same L-inf value and stop together when
+//             it is <= tau.
+//             Sparse iterations walk the affected lists; once they hold more than
+//             n / kDenseDiv vertices an iteration walks all vertices in bin order and
+//             skips those whose stamp is later than i (same set, better locality).
+//   writeback the final parity is copied to the other for every affected vertex (both
+//             parities hold the current ranks between calls) and the per-call marks are
+//             cleared.
+// Static and Naive-dynamic run the same loop over all vertices without marking.
 //
 // Every value written by another block during the kernel (ranks, contributions, lists,
-// per-iteration counters) is read with ld.global.cg (L2), never from a possibly stale L1.
-// The grid barrier's wait is bounded (globaltimer); on time-out the kernel records an
-// error and every block returns.
+// stamps, per-iteration counters) is read with ld.global.cg (L2), never from a possibly
+// stale L1.  The grid barrier's wait is bounded (globaltimer); on time-out the kernel
+// records an error and every block returns.
 #include <algorithm>
+#include <type_traits>
 
 #include "prdf_graph.cuh"
 
@@ -34,17 +42,23 @@ namespace prdf {
 constexpr uint64_t kBarrierTimeoutNs = 4000000000ull;  // 4 s
 constexpr int kWarps = kRankBlock / 32;
 constexpr uint32_t kFull = 0xffffffffu;
+constexpr uint32_t kDenseDiv = 16;        // dense iteration once affected > n / kDenseDiv
+constexpr uint16_t kNoStamp = 0xFFFF;
 
-template <class T>
+template <bool F32>
 struct RankArgs {
+  using S = Store<F32>;
   uint32_t n;
   const uint2 *in_rd;
   const uint32_t *in_col;
   const uint2 *out_rd;
   const uint32_t *out_col;
-  T *R0, *R1, *C0, *C1;
-  const T *adeg;
-  uint32_t *bitmap;
+  typename S::R *R0, *R1;
+  typename S::C *C0, *C1;
+  const typename S::A *adeg;
+  uint32_t *bitmap;      // affected (ever marked in this call)
+  uint32_t *xbits;       // out-row already scanned in this call
+  uint16_t *stamp;       // iteration a vertex joins (kNoStamp = not affected)
   uint32_t *list0, *list1, *list2;
   const uint32_t *ident;
   uint32_t id_cnt0, id_cnt1, id_cnt2;
@@ -84,7 +98,9 @@ struct Neu {
 
 __device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
 __device__ __forceinline__ float ldcg(const float *p) { return __ldcg(p); }
+__device__ __forceinline__ long long ldcg(const long long *p) { return __ldcg(p); }
 __device__ __forceinline__ uint32_t ldcg(const uint32_t *p) { return __ldcg(p); }
+__device__ __forceinline__ uint16_t ldcg(const uint16_t *p) { return __ldcg(reinterpret_cast<const unsigned short *>(p)); }
 
 // Grid-wide barrier with a bounded wait.  Returns false (in every thread of the block)
 // if the device control block holds an error.
@@ -123,8 +139,8 @@ __device__ __forceinline__ int bin_of(uint32_t deg, uint32_t lo, uint32_t hi) {
 }
 
 // Appends, per bin, the lanes' newly marked vertices with one atomic per bin and warp.
-template <class T>
-__device__ __forceinline__ void warp_append(const RankArgs<T> &a, int bin, uint32_t w, uint32_t slot,
+template <bool F32>
+__device__ __forceinline__ void warp_append(const RankArgs<F32> &a, int bin, uint32_t w, uint32_t slot,
                                             const uint32_t cnt[3], uint32_t lane) {
   uint32_t *lists[3] = {a.list0, a.list1, a.list2};
 #pragma unroll
@@ -140,10 +156,10 @@ __device__ __forceinline__ void warp_append(const RankArgs<T> &a, int bin, uint3
   }
 }
 
-// Marks the out-neighbours cols[first + 32 k + lane] (k = 0, 1, ...; stride `stride`).
-// Called by a whole warp (uniform trip count).
-template <class T>
-__device__ __forceinline__ uint32_t warp_mark_range(const RankArgs<T> &a, const uint32_t *cols, uint32_t len,
+// Marks cols[first + 32 k + lane] (k = 0, 1, ...; stride `stride`), stamping newly marked
+// vertices with `slot` (the iteration they join).  Called by a whole warp.
+template <bool F32>
+__device__ __forceinline__ uint32_t warp_mark_range(const RankArgs<F32> &a, const uint32_t *cols, uint32_t len,
                                                     uint32_t first, uint32_t stride, uint32_t slot,
                                                     const uint32_t cnt[3], uint32_t lane) {
   uint32_t newly_total = 0;
@@ -157,7 +173,10 @@ __device__ __forceinline__ uint32_t warp_mark_range(const RankArgs<T> &a, const 
       uint32_t *word = a.bitmap + (w >> 5);
       if (!(ldcg(word) & bit)) {
         uint32_t old = atomicOr(word, bit);
-        if (!(old & bit)) bin = bin_of(__ldg(&a.in_rd[w]).y, a.bin_lo, a.bin_hi);
+        if (!(old & bit)) {
+          bin = bin_of(__ldg(&a.in_rd[w]).y, a.bin_lo, a.bin_hi);
+          a.stamp[w] = (uint16_t)slot;
+        }
       }
     }
     newly_total += bin >= 0;
@@ -166,27 +185,26 @@ __device__ __forceinline__ uint32_t warp_mark_range(const RankArgs<T> &a, const 
   return newly_total;
 }
 
-// Sum of C over an aligned run of 4 columns, `valid` of which count.
-template <class T>
-__device__ __forceinline__ T gather4(const T *C, uint4 q, uint32_t valid) {
-  T s = (T)0;
-  if (valid > 0) s += ldcg(C + q.x);
-  if (valid > 1) s += ldcg(C + q.y);
-  if (valid > 2) s += ldcg(C + q.z);
-  if (valid > 3) s += ldcg(C + q.w);
+// True the first time v asks (per call): its out-row is then scanned by the caller.
+__device__ __forceinline__ bool first_expansion(uint32_t *xbits, uint32_t v) {
+  uint32_t bit = 1u << (v & 31);
+  return !(atomicOr(xbits + (v >> 5), bit) & bit);
+}
+
+template <class C>
+__device__ __forceinline__ C gather4(const C *Cv, uint4 q, uint32_t valid) {
+  C s = (C)0;
+  if (valid > 0) s += ldcg(Cv + q.x);
+  if (valid > 1) s += ldcg(Cv + q.y);
+  if (valid > 2) s += ldcg(Cv + q.z);
+  if (valid > 3) s += ldcg(Cv + q.w);
   return s;
 }
 
-template <class T>
-__device__ __forceinline__ T warp_sum(T x) {
+template <class X>
+__device__ __forceinline__ X warp_sum(X x) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
-  return x;
-}
-
-__device__ __forceinline__ double warp_max(double x) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(kFull, x, o));
   return x;
 }
 
@@ -196,29 +214,51 @@ struct Iter {
   double D;
 };
 
-// Rank of v from its in-edge sum; writes the new rank and contribution, returns |r - R[v]|.
-template <class T>
-__device__ __forceinline__ double finish_vertex(const RankArgs<T> &a, const T *Rin, T *Rout, T *Cout, uint32_t v,
-                                                T sum, const Iter &I, Neu &dacc) {
-  T r = (T)a.base + sum;
-  if (a.teleport) r += (T)(a.tele * I.D);
-  T rold = ldcg(Rin + v);
-  T ad = __ldg(a.adeg + v);
+// |x| of a rank difference as its IEEE bit pattern: non-negative floats order like
+// unsigned integers, so the frontier test and the L-inf max run on the integer pipes.
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+__device__ __forceinline__ unsigned int abs_bits(float x) { return (unsigned int)__float_as_int(x) & 0x7fffffffu; }
+__device__ __forceinline__ double from_bits(unsigned long long b) { return __longlong_as_double((long long)b); }
+__device__ __forceinline__ double from_bits(unsigned int b) { return (double)__int_as_float((int)b); }
+
+template <bool F32>
+using DBits = typename std::conditional<F32, unsigned int, unsigned long long>::type;
+
+// Rank of v from its in-edge sum; writes the new rank and contribution, returns the bits
+// of |r - R[v]| in the rank's precision.
+template <bool F32>
+__device__ __forceinline__ DBits<F32> finish_vertex(const RankArgs<F32> &a,
+                                                                const typename Store<F32>::R *Rin,
+                                                                typename Store<F32>::R *Rout,
+                                                                typename Store<F32>::C *Cout, uint32_t v,
+                                                                typename Store<F32>::C sum, const Iter &I,
+                                                                Neu &dacc) {
+  using S = Store<F32>;
+  using R = typename S::R;
+  R r = S::from_sum(a.base, sum);
+  if (a.teleport) r += (R)(a.tele * I.D);
+  const R rold = ldcg(Rin + v);
+  const typename S::A ad = __ldg(a.adeg + v);
   Rout[v] = r;
-  Cout[v] = r * ad;
-  if (a.teleport && ad == (T)0) dacc.add(I.full ? (double)r : (double)r - (double)rold);
-  return fabs((double)r - (double)rold);
+  Cout[v] = S::contrib(r, ad);
+  if (a.teleport && ad == (typename S::A)0) dacc.add(I.full ? (double)r : (double)r - (double)rold);
+  return abs_bits(r - rold);
 }
 
-template <class T>
-__global__ void __launch_bounds__(kRankBlock) k_rank(const RankArgs<T> a) {
+template <bool F32>
+__global__ void __launch_bounds__(kRankBlock) k_rank(const RankArgs<F32> a) {
+  using S = Store<F32>;
+  using R = typename S::R;
+  using C = typename S::C;
   __shared__ uint32_t s_q[2][kRankBlock];
   __shared__ uint32_t s_qn[2];
   __shared__ uint32_t s_idx, s_err;
-  __shared__ T s_part[kWarps];
+  __shared__ C s_part[kWarps];
   __shared__ double s_dmax[kWarps];
   __shared__ double s_ds[kWarps], s_dc[kWarps];
-  __shared__ double s_bcast;
+  __shared__ int s_expand;
 
   const uint32_t tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
   const uint32_t nblk = gridDim.x;
@@ -228,15 +268,17 @@ __global__ void __launch_bounds__(kRankBlock) k_rank(const RankArgs<T> a) {
   RankCtl *ctl = a.ctl;
   uint32_t epoch = 0;
   const bool df = a.mode == kModeDF;
+  using B = DBits<F32>;
+  const B ftol = abs_bits((R)a.ftol);
   unsigned long long my_v = 0, my_e = 0, my_xv = 0, my_xe = 0, my_app = 0;
   if (tid < 2) s_qn[tid] = 0;
 
   // ---------------------------------------------------------------- phase 0
   Neu dacc;
   if (a.mode == kModeStatic) {
-    const T r = (T)(1.0 / (double)a.n);
+    const R r = (R)(1.0 / (double)a.n);
     for (uint32_t v = gtid; v < a.n; v += nthreads) {
-      T c = r * __ldg(a.adeg + v);
+      C c = S::contrib(r, __ldg(a.adeg + v));
       a.R0[v] = r;
       a.R1[v] = r;
       a.C0[v] = c;
@@ -261,7 +303,6 @@ __global__ void __launch_bounds__(kRankBlock) k_rank(const RankArgs<T> a) {
       my_app += warp_mark_range(a, a.pend_tgt + k0, cnt_left, 0, 32, 0, zero_cnt, lane);
     }
   }
-  // dead-end mass of the starting ranks
   auto block_dead_partial = [&](int parity) {
     double s = dacc.s, c = dacc.c;
 #pragma unroll
@@ -306,6 +347,7 @@ __global__ void __launch_bounds__(kRankBlock) k_rank(const RankArgs<T> a) {
   uint32_t iters = 0;
   bool converged = false;
   double last = 0.0;
+  const uint32_t dense_at = a.n / kDenseDiv;
 
   // ------------------------------------------------------------- iterations
   for (int it = 0; it < a.max_iter; it++) {
@@ -319,13 +361,15 @@ __global__ void __launch_bounds__(kRankBlock) k_rank(const RankArgs<T> a) {
     D_prev = D;
     I.full = ever_full;
     const int par = it & 1;
-    const T *Rin = par ? a.R1 : a.R0;
-    const T *Cin = par ? a.C1 : a.C0;
-    T *Rout = par ? a.R0 : a.R1;
-    T *Cout = par ? a.C0 : a.C1;
+    const R *Rin = par ? a.R1 : a.R0;
+    const C *Cin = par ? a.C1 : a.C0;
+    R *Rout = par ? a.R0 : a.R1;
+    C *Cout = par ? a.C0 : a.C1;
+    // dense: walk all vertices in bin order, skip those not yet affected in iteration it
+    const bool dense = !I.full && (cnt[0] + cnt[1] + cnt[2] > dense_at);
     const uint32_t *L0, *L1, *L2;
     uint32_t c0, c1, c2;
-    if (I.full) {
+    if (I.full || dense) {
       L0 = a.ident;
       c0 = a.id_cnt0;
       L1 = a.ident + a.id_cnt0;
@@ -342,7 +386,7 @@ __global__ void __launch_bounds__(kRankBlock) k_rank(const RankArgs<T> a) {
     }
     const bool expand = df && !I.full;
     const uint32_t slot = (uint32_t)it + 1;
-    double my_max = 0.0;
+    B my_max = 0;
 
     // block bin: one block per vertex, taken dynamically
     for (;;) {
@@ -352,9 +396,10 @@ __global__ void __launch_bounds__(kRankBlock) k_rank(const RankArgs<T> a) {
       __syncthreads();
       if (idx >= c2) break;
       const uint32_t v = ldcg(L2 + idx);
+      if (dense && ldcg(a.stamp + v) > (uint16_t)it) continue;
       const uint2 d = __ldg(&a.in_rd[v]);
       const uint32_t *cols = a.in_col + d.x;
-      T sum = (T)0;
+      C sum = (C)0;
       for (uint32_t j = tid * 4; j < d.y; j += kRankBlock * 4) {
         uint4 q = __ldg(reinterpret_cast<const uint4 *>(cols + j));
         sum += gather4(Cin, q, min(4u, d.y - j));
@@ -363,16 +408,16 @@ __global__ void __launch_bounds__(kRankBlock) k_rank(const RankArgs<T> a) {
       if (lane == 0) s_part[wib] = sum;
       __syncthreads();
       if (tid == 0) {
-        T tot = (T)0;
+        C tot = (C)0;
         for (int w = 0; w < kWarps; w++) tot += s_part[w];
-        double dr = finish_vertex(a, Rin, Rout, Cout, v, tot, I, dacc);
-        s_bcast = dr;
-        my_max = fmax(my_max, dr);
+        B dr = finish_vertex(a, Rin, Rout, Cout, v, tot, I, dacc);
+        my_max = dr > my_max ? dr : my_max;
         my_v++;
         my_e += d.y;
+        s_expand = expand && dr > ftol && first_expansion(a.xbits, v);
       }
       __syncthreads();
-      if (expand && s_bcast > a.ftol) {
+      if (s_expand) {
         const uint2 od = __ldg(&a.out_rd[v]);
         my_app += warp_mark_range(a, a.out_col + od.x, od.y, wib * 32, kRankBlock, slot, cnt, lane);
         if (tid == 0) {
@@ -385,23 +430,25 @@ __global__ void __launch_bounds__(kRankBlock) k_rank(const RankArgs<T> a) {
     // warp bin: one warp per vertex
     for (uint32_t i = gwarp; i < c1; i += nwarps) {
       const uint32_t v = ldcg(L1 + i);
+      if (dense && ldcg(a.stamp + v) > (uint16_t)it) continue;
       const uint2 d = __ldg(&a.in_rd[v]);
       const uint32_t *cols = a.in_col + d.x;
-      T sum = (T)0;
+      C sum = (C)0;
       for (uint32_t j = lane * 4; j < d.y; j += 128) {
         uint4 q = __ldg(reinterpret_cast<const uint4 *>(cols + j));
         sum += gather4(Cin, q, min(4u, d.y - j));
       }
       sum = warp_sum(sum);
-      double dr = 0.0;
+      int exp_now = 0;
       if (lane == 0) {
-        dr = finish_vertex(a, Rin, Rout, Cout, v, sum, I, dacc);
-        my_max = fmax(my_max, dr);
+        B dr = finish_vertex(a, Rin, Rout, Cout, v, sum, I, dacc);
+        my_max = dr > my_max ? dr : my_max;
         my_v++;
         my_e += d.y;
+        exp_now = expand && dr > ftol && first_expansion(a.xbits, v);
       }
-      dr = __shfl_sync(kFull, dr, 0);
-      if (expand && dr > a.ftol) {
+      exp_now = __shfl_sync(kFull, exp_now, 0);
+      if (exp_now) {
         const uint2 od = __ldg(&a.out_rd[v]);
         my_app += warp_mark_range(a, a.out_col + od.x, od.y, 0, 32, slot, cnt, lane);
         if (lane == 0) {
@@ -417,18 +464,18 @@ __global__ void __launch_bounds__(kRankBlock) k_rank(const RankArgs<T> a) {
         const uint32_t v = ldcg(L0 + i);
         const uint2 d = __ldg(&a.in_rd[v]);
         const uint32_t *cols = a.in_col + d.x;
-        T sum = (T)0;
+        C sum = (C)0;
         for (uint32_t j = 0; j < d.y; j += 4) {
           uint4 q = __ldg(reinterpret_cast<const uint4 *>(cols + j));
           sum += gather4(Cin, q, min(4u, d.y - j));
         }
-        double dr = finish_vertex(a, Rin, Rout, Cout, v, sum, I, dacc);
-        my_max = fmax(my_max, dr);
+        B dr = finish_vertex(a, Rin, Rout, Cout, v, sum, I, dacc);
+        my_max = dr > my_max ? dr : my_max;
         my_v++;
         my_e += d.y;
       }
     } else {
-      // rounds of one vertex per thread; expanding vertices are queued in shared memory
+      // rounds of one vertex per thread; vertices to expand are queued in shared memory
       // and their out-rows marked by whole warps (counter and queue double-buffered by
       // round parity, one block barrier per round)
       uint32_t round = 0;
@@ -436,23 +483,24 @@ __global__ void __launch_bounds__(kRankBlock) k_rank(const RankArgs<T> a) {
         const uint32_t qp = round & 1;
         const uint32_t i = b0 + tid;
         int push = 0;
-        uint32_t v = 0;
         if (i < c0) {
-          v = ldcg(L0 + i);
-          const uint2 d = __ldg(&a.in_rd[v]);
-          const uint32_t *cols = a.in_col + d.x;
-          T sum = (T)0;
-          for (uint32_t j = 0; j < d.y; j += 4) {
-            uint4 q = __ldg(reinterpret_cast<const uint4 *>(cols + j));
-            sum += gather4(Cin, q, min(4u, d.y - j));
-          }
-          double dr = finish_vertex(a, Rin, Rout, Cout, v, sum, I, dacc);
-          my_max = fmax(my_max, dr);
-          my_v++;
-          my_e += d.y;
-          if (dr > a.ftol) {
-            push = 1;
-            s_q[qp][atomicAdd(&s_qn[qp], 1u)] = v;
+          const uint32_t v = ldcg(L0 + i);
+          if (!dense || ldcg(a.stamp + v) <= (uint16_t)it) {
+            const uint2 d = __ldg(&a.in_rd[v]);
+            const uint32_t *cols = a.in_col + d.x;
+            C sum = (C)0;
+            for (uint32_t j = 0; j < d.y; j += 4) {
+              uint4 q = __ldg(reinterpret_cast<const uint4 *>(cols + j));
+              sum += gather4(Cin, q, min(4u, d.y - j));
+            }
+            B dr = finish_vertex(a, Rin, Rout, Cout, v, sum, I, dacc);
+            my_max = dr > my_max ? dr : my_max;
+            my_v++;
+            my_e += d.y;
+            if (dr > ftol && first_expansion(a.xbits, v)) {
+              push = 1;
+              s_q[qp][atomicAdd(&s_qn[qp], 1u)] = v;
+            }
           }
         }
         const uint32_t qn = __syncthreads_count(push);
@@ -473,7 +521,9 @@ __global__ void __launch_bounds__(kRankBlock) k_rank(const RankArgs<T> a) {
 
     // block reductions: L-inf (and dead-end mass) of this iteration
     {
-      double m = warp_max(my_max);
+      double m = from_bits(my_max);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(kFull, m, o));
       if (lane == 0) s_dmax[wib] = m;
       __syncthreads();
       if (tid == 0) {
@@ -504,10 +554,10 @@ __global__ void __launch_bounds__(kRankBlock) k_rank(const RankArgs<T> a) {
 
   // -------------------------------------------------------------- writeback
   const int fp = iters & 1;
-  const T *Rf = fp ? a.R1 : a.R0;
-  const T *Cf = fp ? a.C1 : a.C0;
-  T *Ro = fp ? a.R0 : a.R1;
-  T *Co = fp ? a.C0 : a.C1;
+  const R *Rf = fp ? a.R1 : a.R0;
+  const C *Cf = fp ? a.C1 : a.C0;
+  R *Ro = fp ? a.R0 : a.R1;
+  C *Co = fp ? a.C0 : a.C1;
   if (ever_full) {
     for (uint32_t v = gtid; v < a.n; v += nthreads) {
       Ro[v] = ldcg(Rf + v);
@@ -524,6 +574,8 @@ __global__ void __launch_bounds__(kRankBlock) k_rank(const RankArgs<T> a) {
           Co[v] = ldcg(Cf + v);
         }
         a.bitmap[v >> 5] = 0u;
+        a.xbits[v >> 5] = 0u;
+        a.stamp[v] = kNoStamp;
       }
     }
   }
@@ -556,10 +608,10 @@ __global__ void __launch_bounds__(kRankBlock) k_rank(const RankArgs<T> a) {
     if (e_ != cudaSuccess) return cuda_fail(g, e_, #call);  \
   } while (0)
 
-template <class T>
+template <bool F32>
 static cudaError_t grid_blocks(int sm_count, int *blocks) {
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rank<T>, kRankBlock, 0);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rank<F32>, kRankBlock, 0);
   if (e != cudaSuccess) return e;
   per_sm = std::max(1, std::min(per_sm, 4));
   *blocks = per_sm * sm_count;
@@ -568,7 +620,7 @@ static cudaError_t grid_blocks(int sm_count, int *blocks) {
 
 pr_status rank_setup(Graph *g) {
   int blocks = 0;
-  CK(g->f32 ? grid_blocks<float>(g->sm_count, &blocks) : grid_blocks<double>(g->sm_count, &blocks));
+  CK(g->f32 ? grid_blocks<true>(g->sm_count, &blocks) : grid_blocks<false>(g->sm_count, &blocks));
   g->rank_grid = blocks;
   CK(cudaMalloc((void **)&g->ctl, sizeof(RankCtl)));
   CK(cudaMallocHost((void **)&g->ctl_h, sizeof(RankCtl)));
@@ -578,20 +630,23 @@ pr_status rank_setup(Graph *g) {
   return PR_OK;
 }
 
-template <class T>
+template <bool F32>
 static pr_status launch(Graph *g, RankMode mode, bool start_full) {
-  RankArgs<T> a{};
+  using S = Store<F32>;
+  RankArgs<F32> a{};
   a.n = g->n;
   a.in_rd = g->in.rd;
   a.in_col = g->in.col;
   a.out_rd = g->out.rd;
   a.out_col = g->out.col;
-  a.R0 = (T *)g->R[0];
-  a.R1 = (T *)g->R[1];
-  a.C0 = (T *)g->C[0];
-  a.C1 = (T *)g->C[1];
-  a.adeg = (const T *)g->adeg;
+  a.R0 = (typename S::R *)g->R[0];
+  a.R1 = (typename S::R *)g->R[1];
+  a.C0 = (typename S::C *)g->C[0];
+  a.C1 = (typename S::C *)g->C[1];
+  a.adeg = (const typename S::A *)g->adeg;
   a.bitmap = g->bitmap;
+  a.xbits = g->xbits;
+  a.stamp = g->stamp;
   a.list0 = g->list[0];
   a.list1 = g->list[1];
   a.list2 = g->list[2];
@@ -620,7 +675,7 @@ static pr_status launch(Graph *g, RankMode mode, bool start_full) {
   a.bin_hi = (uint32_t)g->p.bin_hi;
   a.ctl = g->ctl;
   void *args[] = {(void *)&a};
-  CK(cudaLaunchCooperativeKernel((const void *)k_rank<T>, dim3(g->rank_grid), dim3(kRankBlock), args, 0, g->st));
+  CK(cudaLaunchCooperativeKernel((const void *)k_rank<F32>, dim3(g->rank_grid), dim3(kRankBlock), args, 0, g->st));
   count_launch();
   return PR_OK;
 }
@@ -629,12 +684,10 @@ pr_status rank_run(Graph *g, RankMode mode, pr_stats *stats) {
   pr_status rc;
   const bool start_full = mode == kModeDF && g->pend_all;
   if (g->teleport && (rc = graph_refresh_dead(g)) != PR_OK) return rc;
-  if (mode != kModeDF || start_full || g->teleport) {
-    if ((rc = graph_refresh_ident(g)) != PR_OK) return rc;
-  }
+  if ((rc = graph_refresh_ident(g)) != PR_OK) return rc;
   CK(cudaMemsetAsync(g->ctl, 0, sizeof(RankCtl), g->st));
   CK(cudaEventRecord(g->ev0, g->st));
-  rc = g->f32 ? launch<float>(g, mode, start_full) : launch<double>(g, mode, start_full);
+  rc = g->f32 ? launch<true>(g, mode, start_full) : launch<false>(g, mode, start_full);
   if (rc != PR_OK) return rc;
   CK(cudaEventRecord(g->ev1, g->st));
   CK(cudaMemcpyAsync(g->ctl_h, g->ctl, offsetof(RankCtl, dR_bits), cudaMemcpyDeviceToHost, g->st));
@@ -673,26 +726,29 @@ pr_status rank_run(Graph *g, RankMode mode, pr_stats *stats) {
   return PR_OK;
 }
 
-template <class T>
-__global__ void k_set_ranks(const double *in, uint32_t n, const T *adeg, T *R0, T *R1, T *C0, T *C1) {
+template <bool F32>
+__global__ void k_set_ranks(const double *in, uint32_t n, const typename Store<F32>::A *adeg,
+                            typename Store<F32>::R *R0, typename Store<F32>::R *R1, typename Store<F32>::C *C0,
+                            typename Store<F32>::C *C1) {
+  using S = Store<F32>;
   uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= n) return;
-  T r = (T)in[v];
-  T c = r * adeg[v];
+  typename S::R r = (typename S::R)in[v];
+  typename S::C c = S::contrib(r, adeg[v]);
   R0[v] = r;
   R1[v] = r;
   C0[v] = c;
   C1[v] = c;
 }
 
-template <class T>
-__global__ void k_get_ranks(const T *R, uint32_t n, double *out) {
+template <class R>
+__global__ void k_get_ranks(const R *Rv, uint32_t n, double *out) {
   uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v < n) out[v] = (double)R[v];
+  if (v < n) out[v] = (double)Rv[v];
 }
 
 __global__ void k_dead_mass(const uint32_t *dead, uint32_t n_dead, const double *R, double *out) {
-  // one block; plain sequential-order per thread, then ordered combine
+  // one block; plain sums per thread, then an ordered combine
   __shared__ double s[256];
   double acc = 0.0;
   for (uint32_t k = threadIdx.x; k < n_dead; k += 256) acc += R[dead[k]];
@@ -708,11 +764,11 @@ __global__ void k_dead_mass(const uint32_t *dead, uint32_t n_dead, const double 
 pr_status rank_set(Graph *g, const double *in_d) {
   unsigned grid = (g->n + 255) / 256;
   if (g->f32)
-    k_set_ranks<float><<<grid, 256, 0, g->st>>>(in_d, g->n, (const float *)g->adeg, (float *)g->R[0],
-                                                (float *)g->R[1], (float *)g->C[0], (float *)g->C[1]);
+    k_set_ranks<true><<<grid, 256, 0, g->st>>>(in_d, g->n, (const float *)g->adeg, (float *)g->R[0],
+                                               (float *)g->R[1], (float *)g->C[0], (float *)g->C[1]);
   else
-    k_set_ranks<double><<<grid, 256, 0, g->st>>>(in_d, g->n, (const double *)g->adeg, (double *)g->R[0],
-                                                 (double *)g->R[1], (double *)g->C[0], (double *)g->C[1]);
+    k_set_ranks<false><<<grid, 256, 0, g->st>>>(in_d, g->n, (const double *)g->adeg, (double *)g->R[0],
+                                                (double *)g->R[1], (long long *)g->C[0], (long long *)g->C[1]);
   count_launch();
   CK(cudaGetLastError());
   if (g->teleport) {
@@ -720,7 +776,8 @@ pr_status rank_set(Graph *g, const double *in_d) {
     if (rc != PR_OK) return rc;
     double *dm = nullptr;
     CK(cudaMalloc((void **)&dm, sizeof(double)));
-    k_dead_mass<<<1, 256, 0, g->st>>>(g->dead, g->n_dead, in_d, dm); count_launch();
+    k_dead_mass<<<1, 256, 0, g->st>>>(g->dead, g->n_dead, in_d, dm);
+    count_launch();
     double D = 0.0;
     cudaError_t e = cudaMemcpyAsync(&D, dm, sizeof(double), cudaMemcpyDeviceToHost, g->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
