@@ -333,7 +333,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     line = {
         "metric": METRIC, "value": value, "unit": "ms", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+        "dtype": "f32" if args.precision == "fp32" else "i64", "data": "synthetic",
         "config": {"workload": f"R-MAT scale {args.scale} edge factor {args.ef}, 80/20 batches f=1e-7..1e-3 |E|, "
                                f"Dynamic Frontier vs Static vs Naive-dynamic",
                    "n": n, "m_with_self_loops": m, "batch_fracs": FRACS,

@@ -129,7 +129,7 @@ __global__ void k_init_rank(const uint2 *out_rd, uint32_t n, double alpha, typen
   uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= n) return;
   typename S::A a = S::factor(alpha, out_rd[v].y);
-  typename S::R r = (typename S::R)(1.0 / (double)n);
+  typename S::R r = S::from_double(1.0 / (double)n);
   typename S::C c = S::contrib(r, a);
   adeg[v] = a;
   R0[v] = r;

@@ -50,26 +50,36 @@ void count_launch();
 // Ranks R, cached contributions C[u] = alpha R[u] / |out(u)| and the per-vertex factor A
 // that turns a rank into a contribution.
 //
-// FP64 mode keeps R in IEEE double.  C is kept as an exact fixed-point integer in units
-// of 2^-62 (A = alpha / |out(u)| * 2^62), so the in-edge sums of Eq. 1 are exact int64
-// additions on the integer pipes: GB300 issues FP64 arithmetic at a small fraction of
-// its integer and FP32 rates, and one FP64 add per gathered edge would bound the sweep
-// far below HBM bandwidth.  All of R is below 1 and every in-sum is at most R[v], so the
-// sums stay below 2^62; each contribution is rounded once to the nearest 2^-62
-// (about 2.2e-19 absolute), and the sums carry no rounding at all.
-// FP32 mode keeps R, C and A in float.
+// 64-bit mode (PR_F64) computes in exact 64-bit fixed point with 62 fractional bits:
+// R and C are int64 counts of 2^-62 (about 2.2e-19), A = alpha / |out(u)| as an unsigned
+// 64-bit fraction, and C = round(R * A / 2^64) with one 64x64 -> 128-bit multiply.  Ranks
+// enter and leave the library as IEEE doubles.  Why: GB300 issues FP64 arithmetic at a
+// small fraction of its integer rate, and an FP64 add per gathered edge (plus a few FP64
+// operations per vertex) bounded the sweep far below HBM bandwidth.  Every quantity the
+// method compares is absolute (L-inf change <= tau, rank change > tau_f), so a fixed
+// absolute resolution of 2^-62 serves it exactly: in-edge sums, L-inf maxima and the
+// dead-end mass are exact integer operations, and each contribution is rounded once.
+// All ranks are below 1 and every in-sum is at most its vertex's rank, so no value
+// reaches 2^62.
+// FP32 mode (PR_F32) keeps R, C and A in float.
 template <bool F32>
 struct Store;
 
 template <>
 struct Store<false> {
-  using R = double;
+  using R = long long;
   using C = long long;
-  using A = double;
-  static constexpr double kOne = 4611686018427387904.0;  // 2^62
-  __host__ __device__ static A factor(double alpha, uint32_t d) { return d ? alpha / (double)d * kOne : 0.0; }
-  __device__ static C contrib(R r, A a) { return __double2ll_rn(r * a); }
-  __device__ static R from_sum(double base, C sum) { return (double)sum * (1.0 / kOne) + base; }
+  using A = unsigned long long;
+  static constexpr double kOne = 4611686018427387904.0;   // 2^62
+  static constexpr double kFrac = 18446744073709551616.0;  // 2^64
+  __device__ static A factor(double alpha, uint32_t d) { return d ? __double2ull_rn(alpha / (double)d * kFrac) : 0ull; }
+  __device__ static C contrib(R r, A a) {
+    const unsigned long long ur = (unsigned long long)r;
+    const unsigned long long lo = ur * a, hi = __umul64hi(ur, a);
+    return (long long)(hi + (lo >> 63));
+  }
+  __device__ static R from_double(double x) { return __double2ll_rn(x * kOne); }
+  __device__ static double to_double(R r) { return (double)r * (1.0 / kOne); }
 };
 
 template <>
@@ -77,9 +87,10 @@ struct Store<true> {
   using R = float;
   using C = float;
   using A = float;
-  __host__ __device__ static A factor(double alpha, uint32_t d) { return d ? (float)(alpha / (double)d) : 0.0f; }
+  __device__ static A factor(double alpha, uint32_t d) { return d ? (float)(alpha / (double)d) : 0.0f; }
   __device__ static C contrib(R r, A a) { return r * a; }
-  __device__ static R from_sum(double base, C sum) { return (float)base + sum; }
+  __device__ static R from_double(double x) { return (float)x; }
+  __device__ static double to_double(R r) { return (double)r; }
 };
 
 // ------------------------------------------------------------------- structures ---
@@ -104,8 +115,9 @@ struct RankCtl {
   uint32_t full_from;                             // iteration from which all of V is affected (+1; 0 = never)
   uint32_t final_cnt[3];                          // affected-list lengths at the end (Dynamic Frontier)
   uint32_t pad;
-  double last_delta;                              // L-inf change of the last iteration
-  double D_final;                                 // dead-end mass of the final ranks (teleport mode)
+  unsigned long long last_key;                    // L-inf change of the last iteration (see Num<>::key)
+  double D_final;                                 // dead-end mass of the final ranks (FP32 mode)
+  long long D_final_n;                            // the same in 2^-62 units (64-bit mode)
   unsigned long long dR_bits[kMaxIterLimit + 1];  // per-iteration L-inf (bits of a non-negative double)
   uint32_t tail[kMaxIterLimit + 2][4];            // per-iteration appends per bin ([0] = initial marks)
   uint32_t blk_next[kMaxIterLimit + 1];           // dynamic index into the block bin

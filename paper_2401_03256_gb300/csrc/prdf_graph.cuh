@@ -45,6 +45,7 @@ struct Graph {
   uint32_t n_dead = 0;
   bool dead_dirty = true;
   double D_ref = 0.0;                // dead-end mass of the ranks under the graph they were computed on
+  long long D_ref_n = 0;             // the same in 2^-62 units (64-bit mode)
 
   uint32_t *pend_src = nullptr, *pend_tgt = nullptr;  // pending marks of applied batches
   uint32_t pend_cap = 0;

@@ -2,7 +2,7 @@
 // persistent cooperative kernel per call.
 //
 // Eq. 1 (Section 3.1) in pull form: R[v] = (1 - alpha)/n + sum_{u in in(v)} C[u] with the
-// cached contribution C[u] = alpha R[u] / |out(u)| (see Store<> for its representation);
+// cached contribution C[u] = alpha R[u] / |out(u)| (Store<> gives the representation);
 // in teleport mode a dead end's rank is spread over all vertices (+ alpha D / n, D = sum
 // of the ranks of dead ends).
 //
@@ -13,13 +13,12 @@
 //             appended to one of three lists by in-degree (thread / warp / block per
 //             vertex).
 //   iteration i: every affected vertex v reads ranks and contributions of parity i & 1
-//             and writes parity (i + 1) & 1; |r - R[v]| feeds the L-inf max (atomicMax on
-//             the bits of a non-negative double) and, if it exceeds tau_f, the
-//             out-neighbours of v are marked (stamped i + 1) and appended, so they join in
-//             iteration i + 1.  A vertex scans its out-row at most once per call: marks
-//             persist, so a second scan could not mark anything new.  One grid barrier
-//             per iteration; all blocks read the same L-inf value and stop together when
-//             it is <= tau.
+//             and writes parity (i + 1) & 1; |r - R[v]| feeds the L-inf max and, if it
+//             exceeds tau_f, the out-neighbours of v are marked (stamped i + 1) and
+//             appended, so they join in iteration i + 1.  A vertex scans its out-row at
+//             most once per call: marks persist, so a second scan could not mark
+//             anything new.  One grid barrier per iteration; all blocks read the same
+//             L-inf value and stop together when it is <= tau.
 //             Sparse iterations walk the affected lists; once they hold more than
 //             n / kDenseDiv vertices an iteration walks all vertices in bin order and
 //             skips those whose stamp is later than i (same set, better locality).
@@ -28,11 +27,15 @@
 //             cleared.
 // Static and Naive-dynamic run the same loop over all vertices without marking.
 //
+// Memory: column runs stream through L2 with evict-first priority, contributions are
+// gathered and stored with evict-last priority so the contribution array stays in L2.
 // Every value written by another block during the kernel (ranks, contributions, lists,
 // stamps, per-iteration counters) is read with ld.global.cg (L2), never from a possibly
 // stale L1.  The grid barrier's wait is bounded (globaltimer); on time-out the kernel
 // records an error and every block returns.
 #include <algorithm>
+#include <cmath>
+#include <cstring>
 #include <type_traits>
 
 #include "prdf_graph.cuh"
@@ -42,23 +45,52 @@ namespace prdf {
 constexpr uint64_t kBarrierTimeoutNs = 4000000000ull;  // 4 s
 constexpr int kWarps = kRankBlock / 32;
 constexpr uint32_t kFull = 0xffffffffu;
-constexpr uint32_t kDenseDiv = 16;        // dense iteration once affected > n / kDenseDiv
+constexpr uint32_t kDenseDiv = 16;  // dense iteration once affected > n / kDenseDiv
 constexpr uint16_t kNoStamp = 0xFFFF;
+
+// Per-mode arithmetic of the kernel.  Rank changes are compared as "delta bits"
+// (non-negative values that order like unsigned integers) and reduced to an L-inf key
+// (uint64, same order) for the grid-wide max and the convergence test.
+template <bool F32>
+struct Num;
+
+template <>
+struct Num<false> {  // 64-bit fixed point, 2^-62 units
+  using R = long long;
+  using B = unsigned long long;
+  __device__ static B delta(R r, R rold) {
+    long long d = r - rold;
+    return (B)(d < 0 ? -d : d);
+  }
+  __device__ static unsigned long long key(B d) { return d; }
+};
+
+template <>
+struct Num<true> {  // float ranks; the key is the bits of the change widened to double
+  using R = float;
+  using B = unsigned int;
+  __device__ static B delta(R r, R rold) { return __float_as_uint(fabsf(r - rold)); }
+  __device__ static unsigned long long key(B d) {
+    return (unsigned long long)__double_as_longlong((double)__uint_as_float(d));
+  }
+};
 
 template <bool F32>
 struct RankArgs {
   using S = Store<F32>;
+  using R = typename S::R;
+  using B = typename Num<F32>::B;
   uint32_t n;
   const uint2 *in_rd;
   const uint32_t *in_col;
   const uint2 *out_rd;
   const uint32_t *out_col;
-  typename S::R *R0, *R1;
+  R *R0, *R1;
   typename S::C *C0, *C1;
   const typename S::A *adeg;
-  uint32_t *bitmap;      // affected (ever marked in this call)
-  uint32_t *xbits;       // out-row already scanned in this call
-  uint16_t *stamp;       // iteration a vertex joins (kNoStamp = not affected)
+  uint32_t *bitmap;  // affected (ever marked in this call)
+  uint32_t *xbits;   // out-row already scanned in this call
+  uint16_t *stamp;   // iteration a vertex joins (kNoStamp = not affected)
   uint32_t *list0, *list1, *list2;
   const uint32_t *ident;
   uint32_t id_cnt0, id_cnt1, id_cnt2;
@@ -68,21 +100,24 @@ struct RankArgs {
   uint32_t n_pend_tgt;
   const uint32_t *dead;
   uint32_t n_dead;
-  DeadPart *dpart;  // [2][gridDim.x]
-  double base;      // (1 - alpha) / n
-  double tele;      // alpha / n in teleport mode, else 0
-  double alpha_over_n;
-  double D_ref;     // dead-end mass of the previous ranks on the previous graph
-  double tol, ftol;
+  DeadPart *dpart;        // [2][gridDim.x]
+  R base;                 // (1 - alpha) / n in the rank representation
+  R init;                 // 1 / n (Static start)
+  B ftol;                 // tau_f as delta bits
+  unsigned long long tol_key;  // tau as an L-inf key
+  unsigned long long tele_frac;  // alpha / n * 2^64 (64-bit mode, teleport)
+  double tele_d;          // alpha / n (FP32 mode, teleport)
+  long long D_ref_n;      // dead-end mass of the previous ranks on the previous graph
+  double D_ref_d;
   int max_iter;
-  int mode;         // RankMode
+  int mode;  // RankMode
   int teleport;
-  int start_full;   // Dynamic Frontier with every vertex affected from iteration 0
+  int start_full;  // Dynamic Frontier with every vertex affected from iteration 0
   uint32_t bin_lo, bin_hi;
   RankCtl *ctl;
 };
 
-// Neumaier's compensated summation (Neumaier 1974).
+// Neumaier's compensated summation (Neumaier 1974), for the FP32 mode's dead-end mass.
 struct Neu {
   double s = 0.0, c = 0.0;
   __device__ __forceinline__ void add(double x) {
@@ -96,11 +131,49 @@ struct Neu {
   }
 };
 
-__device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
-__device__ __forceinline__ float ldcg(const float *p) { return __ldcg(p); }
+// ------------------------------------------------------------ memory access ----
+
+__device__ __forceinline__ unsigned long long l2_evict_first() {
+  unsigned long long p;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ unsigned long long l2_evict_last() {
+  unsigned long long p;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+// Four column ids of a 16-byte aligned run (read-only during the kernel).
+__device__ __forceinline__ uint4 ld_cols(const uint32_t *p, unsigned long long pol) {
+  uint4 r;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+               : "l"(p), "l"(pol));
+  return r;
+}
+__device__ __forceinline__ long long ld_keep(const long long *p, unsigned long long pol) {
+  long long r;
+  asm("ld.global.cg.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(r) : "l"(p), "l"(pol));
+  return r;
+}
+__device__ __forceinline__ float ld_keep(const float *p, unsigned long long pol) {
+  float r;
+  asm("ld.global.cg.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(r) : "l"(p), "l"(pol));
+  return r;
+}
+__device__ __forceinline__ void st_keep(long long *p, long long v, unsigned long long pol) {
+  asm volatile("st.global.L2::cache_hint.b64 [%0], %1, %2;" ::"l"(p), "l"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_keep(float *p, float v, unsigned long long pol) {
+  asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
+}
+
 __device__ __forceinline__ long long ldcg(const long long *p) { return __ldcg(p); }
+__device__ __forceinline__ float ldcg(const float *p) { return __ldcg(p); }
 __device__ __forceinline__ uint32_t ldcg(const uint32_t *p) { return __ldcg(p); }
-__device__ __forceinline__ uint16_t ldcg(const uint16_t *p) { return __ldcg(reinterpret_cast<const unsigned short *>(p)); }
+__device__ __forceinline__ uint16_t ldcg(const uint16_t *p) {
+  return __ldcg(reinterpret_cast<const unsigned short *>(p));
+}
 
 // Grid-wide barrier with a bounded wait.  Returns false (in every thread of the block)
 // if the device control block holds an error.
@@ -192,13 +265,31 @@ __device__ __forceinline__ bool first_expansion(uint32_t *xbits, uint32_t v) {
 }
 
 template <class C>
-__device__ __forceinline__ C gather4(const C *Cv, uint4 q, uint32_t valid) {
+__device__ __forceinline__ C gather4(const C *Cv, uint4 q, uint32_t valid, unsigned long long pol) {
   C s = (C)0;
-  if (valid > 0) s += ldcg(Cv + q.x);
-  if (valid > 1) s += ldcg(Cv + q.y);
-  if (valid > 2) s += ldcg(Cv + q.z);
-  if (valid > 3) s += ldcg(Cv + q.w);
+  if (valid > 0) s += ld_keep(Cv + q.x, pol);
+  if (valid > 1) s += ld_keep(Cv + q.y, pol);
+  if (valid > 2) s += ld_keep(Cv + q.z, pol);
+  if (valid > 3) s += ld_keep(Cv + q.w, pol);
   return s;
+}
+
+// Sum of C over one whole row by one thread: runs of 16 columns, all loads of a run in
+// flight together.
+template <class C>
+__device__ __forceinline__ C row_sum_thread(const C *Cv, const uint32_t *cols, uint32_t len,
+                                            unsigned long long pol_cols, unsigned long long pol_c) {
+  C sum = (C)0;
+  for (uint32_t j0 = 0; j0 < len; j0 += 16) {
+    uint4 q[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+      if (j0 + 4 * k < len) q[k] = ld_cols(cols + j0 + 4 * k, pol_cols);
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+      if (j0 + 4 * k < len) sum += gather4(Cv, q[k], min(4u, len - j0 - 4 * k), pol_c);
+  }
+  return sum;
 }
 
 template <class X>
@@ -208,43 +299,48 @@ __device__ __forceinline__ X warp_sum(X x) {
   return x;
 }
 
-struct Iter {
-  uint32_t it;
-  bool full;
-  double D;
+// Dead-end mass accumulator: exact integer in 64-bit mode, Neumaier pair in FP32 mode.
+template <bool F32>
+struct Mass;
+template <>
+struct Mass<false> {
+  long long s = 0;
+  __device__ void add(long long x) { s += x; }
+};
+template <>
+struct Mass<true> {
+  Neu n;
+  __device__ void add(double x) { n.add(x); }
 };
 
-// |x| of a rank difference as its IEEE bit pattern: non-negative floats order like
-// unsigned integers, so the frontier test and the L-inf max run on the integer pipes.
-__device__ __forceinline__ unsigned long long abs_bits(double x) {
-  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
-}
-__device__ __forceinline__ unsigned int abs_bits(float x) { return (unsigned int)__float_as_int(x) & 0x7fffffffu; }
-__device__ __forceinline__ double from_bits(unsigned long long b) { return __longlong_as_double((long long)b); }
-__device__ __forceinline__ double from_bits(unsigned int b) { return (double)__int_as_float((int)b); }
-
 template <bool F32>
-using DBits = typename std::conditional<F32, unsigned int, unsigned long long>::type;
+struct Iter {
+  bool full;
+  typename Store<F32>::R tele;  // alpha D / n in the rank representation
+};
 
-// Rank of v from its in-edge sum; writes the new rank and contribution, returns the bits
-// of |r - R[v]| in the rank's precision.
+// Rank of v from its in-edge sum; writes the new rank and contribution; returns the
+// delta bits of |r - R[v]|.
 template <bool F32>
-__device__ __forceinline__ DBits<F32> finish_vertex(const RankArgs<F32> &a,
-                                                                const typename Store<F32>::R *Rin,
-                                                                typename Store<F32>::R *Rout,
-                                                                typename Store<F32>::C *Cout, uint32_t v,
-                                                                typename Store<F32>::C sum, const Iter &I,
-                                                                Neu &dacc) {
+__device__ __forceinline__ typename Num<F32>::B finish_vertex(const RankArgs<F32> &a,
+                                                              const typename Store<F32>::R *Rin,
+                                                              typename Store<F32>::R *Rout,
+                                                              typename Store<F32>::C *Cout, uint32_t v,
+                                                              typename Store<F32>::C sum, const Iter<F32> &I,
+                                                              Mass<F32> &dacc, unsigned long long pol_c) {
   using S = Store<F32>;
   using R = typename S::R;
-  R r = S::from_sum(a.base, sum);
-  if (a.teleport) r += (R)(a.tele * I.D);
+  R r = a.base + sum;
+  if (a.teleport) r += I.tele;
   const R rold = ldcg(Rin + v);
   const typename S::A ad = __ldg(a.adeg + v);
   Rout[v] = r;
-  Cout[v] = S::contrib(r, ad);
-  if (a.teleport && ad == (typename S::A)0) dacc.add(I.full ? (double)r : (double)r - (double)rold);
-  return abs_bits(r - rold);
+  st_keep(Cout + v, S::contrib(r, ad), pol_c);
+  if (a.teleport && ad == (typename S::A)0) {
+    if constexpr (F32) dacc.add(I.full ? (double)r : (double)r - (double)rold);
+    else dacc.add(I.full ? r : r - rold);
+  }
+  return Num<F32>::delta(r, rold);
 }
 
 template <bool F32>
@@ -252,11 +348,12 @@ __global__ void __launch_bounds__(kRankBlock) k_rank(const RankArgs<F32> a) {
   using S = Store<F32>;
   using R = typename S::R;
   using C = typename S::C;
+  using B = typename Num<F32>::B;
   __shared__ uint32_t s_q[2][kRankBlock];
   __shared__ uint32_t s_qn[2];
   __shared__ uint32_t s_idx, s_err;
   __shared__ C s_part[kWarps];
-  __shared__ double s_dmax[kWarps];
+  __shared__ unsigned long long s_key[kWarps];
   __shared__ double s_ds[kWarps], s_dc[kWarps];
   __shared__ int s_expand;
 
@@ -268,15 +365,75 @@ __global__ void __launch_bounds__(kRankBlock) k_rank(const RankArgs<F32> a) {
   RankCtl *ctl = a.ctl;
   uint32_t epoch = 0;
   const bool df = a.mode == kModeDF;
-  using B = DBits<F32>;
-  const B ftol = abs_bits((R)a.ftol);
+  const unsigned long long pol_cols = l2_evict_first();
+  const unsigned long long pol_c = l2_evict_last();
   unsigned long long my_v = 0, my_e = 0, my_xv = 0, my_xe = 0, my_app = 0;
   if (tid < 2) s_qn[tid] = 0;
 
+  // dead-end mass: per-block partials (double-buffered by parity) and their grid total
+  Mass<F32> dacc;
+  auto block_dead_partial = [&](int parity) {
+    if constexpr (F32) {
+      double s = dacc.n.s, c = dacc.n.c;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        double os = __shfl_xor_sync(kFull, s, o), oc = __shfl_xor_sync(kFull, c, o);
+        Neu t;
+        t.s = s;
+        t.c = c;
+        t.merge(os, oc);
+        s = t.s;
+        c = t.c;
+      }
+      if (lane == 0) {
+        s_ds[wib] = s;
+        s_dc[wib] = c;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        Neu t;
+        for (int w = 0; w < kWarps; w++) t.merge(s_ds[w], s_dc[w]);
+        a.dpart[parity * nblk + blockIdx.x] = DeadPart{t.s, t.c};
+      }
+    } else {
+      long long s = warp_sum(dacc.s);
+      if (lane == 0) s_ds[wib] = __longlong_as_double(s);
+      __syncthreads();
+      if (tid == 0) {
+        long long t = 0;
+        for (int w = 0; w < kWarps; w++) t += __double_as_longlong(s_ds[w]);
+        a.dpart[parity * nblk + blockIdx.x] = DeadPart{__longlong_as_double(t), 0.0};
+      }
+    }
+    dacc = Mass<F32>();
+  };
+  // the grid total, as a rank-representation value (exact sum in 64-bit mode)
+  auto grid_dead_total = [&](int parity, double *as_double) -> long long {
+    if constexpr (F32) {
+      Neu t;
+      for (uint32_t k = 0; k < nblk; k++) {
+        const double *p = &a.dpart[parity * nblk + k].s;
+        t.merge(__ldcg(p), __ldcg(p + 1));
+      }
+      *as_double = t.s + t.c;
+      return 0;
+    } else {
+      long long t = 0;
+      for (uint32_t k = 0; k < nblk; k++)
+        t += __double_as_longlong(__ldcg(&a.dpart[parity * nblk + k].s));
+      *as_double = 0.0;
+      return t;
+    }
+  };
+  // alpha D / n in the rank representation
+  auto tele_of = [&](long long Dn, double Dd) -> R {
+    if constexpr (F32) return (float)(a.tele_d * Dd);
+    else return S::contrib(Dn, a.tele_frac);
+  };
+
   // ---------------------------------------------------------------- phase 0
-  Neu dacc;
   if (a.mode == kModeStatic) {
-    const R r = (R)(1.0 / (double)a.n);
+    const R r = a.init;
     for (uint32_t v = gtid; v < a.n; v += nthreads) {
       C c = S::contrib(r, __ldg(a.adeg + v));
       a.R0[v] = r;
@@ -285,9 +442,9 @@ __global__ void __launch_bounds__(kRankBlock) k_rank(const RankArgs<F32> a) {
       a.C1[v] = c;
     }
     if (a.teleport)
-      for (uint32_t k = gtid; k < a.n_dead; k += nthreads) dacc.add((double)r);
+      for (uint32_t k = gtid; k < a.n_dead; k += nthreads) dacc.add(r);
   } else if (a.teleport) {
-    for (uint32_t k = gtid; k < a.n_dead; k += nthreads) dacc.add((double)ldcg(a.R0 + __ldg(a.dead + k)));
+    for (uint32_t k = gtid; k < a.n_dead; k += nthreads) dacc.add(ldcg(a.R0 + __ldg(a.dead + k)));
   }
   const uint32_t zero_cnt[3] = {0, 0, 0};
   if (df && !a.start_full) {
@@ -303,62 +460,32 @@ __global__ void __launch_bounds__(kRankBlock) k_rank(const RankArgs<F32> a) {
       my_app += warp_mark_range(a, a.pend_tgt + k0, cnt_left, 0, 32, 0, zero_cnt, lane);
     }
   }
-  auto block_dead_partial = [&](int parity) {
-    double s = dacc.s, c = dacc.c;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      double os = __shfl_xor_sync(kFull, s, o), oc = __shfl_xor_sync(kFull, c, o);
-      Neu t;
-      t.s = s;
-      t.c = c;
-      t.merge(os, oc);
-      s = t.s;
-      c = t.c;
-    }
-    if (lane == 0) {
-      s_ds[wib] = s;
-      s_dc[wib] = c;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      Neu t;
-      for (int w = 0; w < kWarps; w++) t.merge(s_ds[w], s_dc[w]);
-      a.dpart[parity * nblk + blockIdx.x] = DeadPart{t.s, t.c};
-    }
-    dacc = Neu();
-  };
-  auto grid_dead_total = [&](int parity) {
-    Neu t;
-    for (uint32_t k = 0; k < nblk; k++) {
-      const double *p = &a.dpart[parity * nblk + k].s;
-      t.merge(__ldcg(p), __ldcg(p + 1));
-    }
-    return t.s + t.c;
-  };
   if (a.teleport) block_dead_partial(0);
   if (!grid_sync(ctl, epoch, &s_err)) return;
 
   uint32_t cnt[3];
 #pragma unroll
   for (int bb = 0; bb < 3; bb++) cnt[bb] = df && !a.start_full ? ldcg(&ctl->tail[0][bb]) : 0u;
-  double D = a.teleport ? grid_dead_total(0) : 0.0;
-  double D_prev = a.D_ref;
+  long long Dn = 0;
+  double Dd = 0.0;
+  if (a.teleport) Dn = grid_dead_total(0, &Dd);
+  R tele_prev = a.teleport ? tele_of(a.D_ref_n, a.D_ref_d) : (R)0;
   bool ever_full = !df || a.start_full;
   uint32_t iters = 0;
   bool converged = false;
-  double last = 0.0;
+  unsigned long long last_key = 0;
   const uint32_t dense_at = a.n / kDenseDiv;
 
   // ------------------------------------------------------------- iterations
   for (int it = 0; it < a.max_iter; it++) {
-    Iter I;
-    I.it = (uint32_t)it;
-    I.D = D;
-    if (df && a.teleport && !ever_full && a.alpha_over_n * fabs(D - D_prev) > a.ftol) {
+    Iter<F32> I;
+    I.tele = a.teleport ? tele_of(Dn, Dd) : (R)0;
+    if (df && a.teleport && !ever_full && Num<F32>::delta(I.tele, tele_prev) > a.ftol) {
+      // the teleport term of every vertex moved by more than tau_f: all of V is affected
       ever_full = true;
       if (blockIdx.x == 0 && tid == 0) ctl->full_from = (uint32_t)it + 1;
     }
-    D_prev = D;
+    tele_prev = I.tele;
     I.full = ever_full;
     const int par = it & 1;
     const R *Rin = par ? a.R1 : a.R0;
@@ -388,88 +515,13 @@ __global__ void __launch_bounds__(kRankBlock) k_rank(const RankArgs<F32> a) {
     const uint32_t slot = (uint32_t)it + 1;
     B my_max = 0;
 
-    // block bin: one block per vertex, taken dynamically
-    for (;;) {
-      if (tid == 0) s_idx = atomicAdd(&ctl->blk_next[it], 1u);
-      __syncthreads();
-      const uint32_t idx = s_idx;
-      __syncthreads();
-      if (idx >= c2) break;
-      const uint32_t v = ldcg(L2 + idx);
-      if (dense && ldcg(a.stamp + v) > (uint16_t)it) continue;
-      const uint2 d = __ldg(&a.in_rd[v]);
-      const uint32_t *cols = a.in_col + d.x;
-      C sum = (C)0;
-      for (uint32_t j = tid * 4; j < d.y; j += kRankBlock * 4) {
-        uint4 q = __ldg(reinterpret_cast<const uint4 *>(cols + j));
-        sum += gather4(Cin, q, min(4u, d.y - j));
-      }
-      sum = warp_sum(sum);
-      if (lane == 0) s_part[wib] = sum;
-      __syncthreads();
-      if (tid == 0) {
-        C tot = (C)0;
-        for (int w = 0; w < kWarps; w++) tot += s_part[w];
-        B dr = finish_vertex(a, Rin, Rout, Cout, v, tot, I, dacc);
-        my_max = dr > my_max ? dr : my_max;
-        my_v++;
-        my_e += d.y;
-        s_expand = expand && dr > ftol && first_expansion(a.xbits, v);
-      }
-      __syncthreads();
-      if (s_expand) {
-        const uint2 od = __ldg(&a.out_rd[v]);
-        my_app += warp_mark_range(a, a.out_col + od.x, od.y, wib * 32, kRankBlock, slot, cnt, lane);
-        if (tid == 0) {
-          my_xv++;
-          my_xe += od.y;
-        }
-      }
-    }
-
-    // warp bin: one warp per vertex
-    for (uint32_t i = gwarp; i < c1; i += nwarps) {
-      const uint32_t v = ldcg(L1 + i);
-      if (dense && ldcg(a.stamp + v) > (uint16_t)it) continue;
-      const uint2 d = __ldg(&a.in_rd[v]);
-      const uint32_t *cols = a.in_col + d.x;
-      C sum = (C)0;
-      for (uint32_t j = lane * 4; j < d.y; j += 128) {
-        uint4 q = __ldg(reinterpret_cast<const uint4 *>(cols + j));
-        sum += gather4(Cin, q, min(4u, d.y - j));
-      }
-      sum = warp_sum(sum);
-      int exp_now = 0;
-      if (lane == 0) {
-        B dr = finish_vertex(a, Rin, Rout, Cout, v, sum, I, dacc);
-        my_max = dr > my_max ? dr : my_max;
-        my_v++;
-        my_e += d.y;
-        exp_now = expand && dr > ftol && first_expansion(a.xbits, v);
-      }
-      exp_now = __shfl_sync(kFull, exp_now, 0);
-      if (exp_now) {
-        const uint2 od = __ldg(&a.out_rd[v]);
-        my_app += warp_mark_range(a, a.out_col + od.x, od.y, 0, 32, slot, cnt, lane);
-        if (lane == 0) {
-          my_xv++;
-          my_xe += od.y;
-        }
-      }
-    }
-
     // thread bin: one thread per vertex
     if (!expand) {
       for (uint32_t i = gtid; i < c0; i += nthreads) {
         const uint32_t v = ldcg(L0 + i);
         const uint2 d = __ldg(&a.in_rd[v]);
-        const uint32_t *cols = a.in_col + d.x;
-        C sum = (C)0;
-        for (uint32_t j = 0; j < d.y; j += 4) {
-          uint4 q = __ldg(reinterpret_cast<const uint4 *>(cols + j));
-          sum += gather4(Cin, q, min(4u, d.y - j));
-        }
-        B dr = finish_vertex(a, Rin, Rout, Cout, v, sum, I, dacc);
+        C sum = row_sum_thread(Cin, a.in_col + d.x, d.y, pol_cols, pol_c);
+        B dr = finish_vertex(a, Rin, Rout, Cout, v, sum, I, dacc, pol_c);
         my_max = dr > my_max ? dr : my_max;
         my_v++;
         my_e += d.y;
@@ -487,17 +539,12 @@ __global__ void __launch_bounds__(kRankBlock) k_rank(const RankArgs<F32> a) {
           const uint32_t v = ldcg(L0 + i);
           if (!dense || ldcg(a.stamp + v) <= (uint16_t)it) {
             const uint2 d = __ldg(&a.in_rd[v]);
-            const uint32_t *cols = a.in_col + d.x;
-            C sum = (C)0;
-            for (uint32_t j = 0; j < d.y; j += 4) {
-              uint4 q = __ldg(reinterpret_cast<const uint4 *>(cols + j));
-              sum += gather4(Cin, q, min(4u, d.y - j));
-            }
-            B dr = finish_vertex(a, Rin, Rout, Cout, v, sum, I, dacc);
+            C sum = row_sum_thread(Cin, a.in_col + d.x, d.y, pol_cols, pol_c);
+            B dr = finish_vertex(a, Rin, Rout, Cout, v, sum, I, dacc, pol_c);
             my_max = dr > my_max ? dr : my_max;
             my_v++;
             my_e += d.y;
-            if (dr > ftol && first_expansion(a.xbits, v)) {
+            if (dr > a.ftol && first_expansion(a.xbits, v)) {
               push = 1;
               s_q[qp][atomicAdd(&s_qn[qp], 1u)] = v;
             }
@@ -519,34 +566,112 @@ __global__ void __launch_bounds__(kRankBlock) k_rank(const RankArgs<F32> a) {
       }
     }
 
-    // block reductions: L-inf (and dead-end mass) of this iteration
-    {
-      double m = from_bits(my_max);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(kFull, m, o));
-      if (lane == 0) s_dmax[wib] = m;
+    // warp bin: one warp per vertex
+    for (uint32_t i = gwarp; i < c1; i += nwarps) {
+      const uint32_t v = ldcg(L1 + i);
+      if (dense && ldcg(a.stamp + v) > (uint16_t)it) continue;
+      const uint2 d = __ldg(&a.in_rd[v]);
+      const uint32_t *cols = a.in_col + d.x;
+      C sum = (C)0;
+      for (uint32_t j = lane * 4; j < d.y; j += 128) {
+        uint4 q = ld_cols(cols + j, pol_cols);
+        sum += gather4(Cin, q, min(4u, d.y - j), pol_c);
+      }
+      sum = warp_sum(sum);
+      int exp_now = 0;
+      if (lane == 0) {
+        B dr = finish_vertex(a, Rin, Rout, Cout, v, sum, I, dacc, pol_c);
+        my_max = dr > my_max ? dr : my_max;
+        my_v++;
+        my_e += d.y;
+        exp_now = expand && dr > a.ftol && first_expansion(a.xbits, v);
+      }
+      exp_now = __shfl_sync(kFull, exp_now, 0);
+      if (exp_now) {
+        const uint2 od = __ldg(&a.out_rd[v]);
+        my_app += warp_mark_range(a, a.out_col + od.x, od.y, 0, 32, slot, cnt, lane);
+        if (lane == 0) {
+          my_xv++;
+          my_xe += od.y;
+        }
+      }
+    }
+
+    // block bin: one block per vertex, taken dynamically (last, so blocks that finish
+    // their share of the other bins early take the hubs)
+    for (;;) {
+      if (tid == 0) s_idx = atomicAdd(&ctl->blk_next[it], 1u);
+      __syncthreads();
+      const uint32_t idx = s_idx;
+      __syncthreads();
+      if (idx >= c2) break;
+      const uint32_t v = ldcg(L2 + idx);
+      if (dense && ldcg(a.stamp + v) > (uint16_t)it) continue;
+      const uint2 d = __ldg(&a.in_rd[v]);
+      const uint32_t *cols = a.in_col + d.x;
+      C sum = (C)0;
+      for (uint32_t j = tid * 4; j < d.y; j += kRankBlock * 4) {
+        uint4 q = ld_cols(cols + j, pol_cols);
+        sum += gather4(Cin, q, min(4u, d.y - j), pol_c);
+      }
+      sum = warp_sum(sum);
+      if (lane == 0) s_part[wib] = sum;
       __syncthreads();
       if (tid == 0) {
-        double bm = 0.0;
-        for (int w = 0; w < kWarps; w++) bm = fmax(bm, s_dmax[w]);
-        if (bm > 0.0) atomicMax(&ctl->dR_bits[it], (unsigned long long)__double_as_longlong(bm));
+        C tot = (C)0;
+        for (int w = 0; w < kWarps; w++) tot += s_part[w];
+        B dr = finish_vertex(a, Rin, Rout, Cout, v, tot, I, dacc, pol_c);
+        my_max = dr > my_max ? dr : my_max;
+        my_v++;
+        my_e += d.y;
+        s_expand = expand && dr > a.ftol && first_expansion(a.xbits, v);
+      }
+      __syncthreads();
+      if (s_expand) {
+        const uint2 od = __ldg(&a.out_rd[v]);
+        my_app += warp_mark_range(a, a.out_col + od.x, od.y, wib * 32, kRankBlock, slot, cnt, lane);
+        if (tid == 0) {
+          my_xv++;
+          my_xe += od.y;
+        }
+      }
+    }
+
+    // block reductions: L-inf (and dead-end mass) of this iteration
+    {
+      unsigned long long m = Num<F32>::key(my_max);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(kFull, m, o));
+      if (lane == 0) s_key[wib] = m;
+      __syncthreads();
+      if (tid == 0) {
+        unsigned long long bm = 0;
+        for (int w = 0; w < kWarps; w++) bm = max(bm, s_key[w]);
+        if (bm) atomicMax(&ctl->dR_bits[it], bm);
       }
     }
     if (a.teleport) block_dead_partial((it + 1) & 1);
     if (!grid_sync(ctl, epoch, &s_err)) return;
 
-    const double dR = __longlong_as_double((long long)__ldcg(&ctl->dR_bits[it]));
+    const unsigned long long dR = __ldcg(&ctl->dR_bits[it]);
     if (df && !I.full) {
 #pragma unroll
       for (int bb = 0; bb < 3; bb++) cnt[bb] += ldcg(&ctl->tail[slot][bb]);
     }
     if (a.teleport) {
-      double part = grid_dead_total((it + 1) & 1);
-      D = I.full ? part : D + part;
+      double pd = 0.0;
+      long long pn = grid_dead_total((it + 1) & 1, &pd);
+      if (I.full) {
+        Dn = pn;
+        Dd = pd;
+      } else {
+        Dn += pn;
+        Dd += pd;
+      }
     }
     iters = (uint32_t)it + 1;
-    last = dR;
-    if (dR <= a.tol) {
+    last_key = dR;
+    if (dR <= a.tol_key) {
       converged = true;
       break;
     }
@@ -585,17 +710,16 @@ __global__ void __launch_bounds__(kRankBlock) k_rank(const RankArgs<F32> a) {
     unsigned long long *dst[5] = {&ctl->vproc, &ctl->eproc, &ctl->expv, &ctl->expe, &ctl->appended};
 #pragma unroll
     for (int k = 0; k < 5; k++) {
-      unsigned long long x = vals[k];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+      unsigned long long x = warp_sum(vals[k]);
       if (lane == 0 && x) atomicAdd(dst[k], x);
     }
   }
   if (blockIdx.x == 0 && tid == 0) {
     ctl->iterations = iters;
     ctl->converged = converged ? 1u : 0u;
-    ctl->last_delta = last;
-    ctl->D_final = D;
+    ctl->last_key = last_key;
+    ctl->D_final = Dd;
+    ctl->D_final_n = Dn;
     for (int bb = 0; bb < 3; bb++) ctl->final_cnt[bb] = cnt[bb];
   }
 }
@@ -607,6 +731,8 @@ __global__ void __launch_bounds__(kRankBlock) k_rank(const RankArgs<F32> a) {
     cudaError_t e_ = (call);                                \
     if (e_ != cudaSuccess) return cuda_fail(g, e_, #call);  \
   } while (0)
+
+static constexpr double kOne62 = 4611686018427387904.0;  // 2^62
 
 template <bool F32>
 static cudaError_t grid_blocks(int sm_count, int *blocks) {
@@ -634,6 +760,7 @@ template <bool F32>
 static pr_status launch(Graph *g, RankMode mode, bool start_full) {
   using S = Store<F32>;
   RankArgs<F32> a{};
+  const double n = (double)g->n, alpha = g->p.alpha;
   a.n = g->n;
   a.in_rd = g->in.rd;
   a.in_col = g->in.col;
@@ -661,13 +788,24 @@ static pr_status launch(Graph *g, RankMode mode, bool start_full) {
   a.dead = g->dead;
   a.n_dead = g->teleport ? g->n_dead : 0;
   a.dpart = g->dpart;
-  a.base = (1.0 - g->p.alpha) / (double)g->n;
+  if constexpr (F32) {
+    a.base = (float)((1.0 - alpha) / n);
+    a.init = (float)(1.0 / n);
+    float ft = (float)g->p.frontier_tol;
+    std::memcpy(&a.ftol, &ft, 4);
+    double tl = g->p.tol;
+    std::memcpy(&a.tol_key, &tl, 8);
+    a.tele_d = alpha / n;
+  } else {
+    a.base = std::llrint((1.0 - alpha) / n * kOne62);
+    a.init = std::llrint(1.0 / n * kOne62);
+    a.ftol = (unsigned long long)std::floor(std::min(g->p.frontier_tol * kOne62, 9.0e18));
+    a.tol_key = (unsigned long long)std::floor(std::min(g->p.tol * kOne62, 9.0e18));
+    a.tele_frac = (unsigned long long)(alpha / n * 18446744073709551616.0);  // < 2^64 since alpha < 1
+  }
+  a.D_ref_n = g->D_ref_n;
+  a.D_ref_d = g->D_ref;
   a.teleport = g->teleport ? 1 : 0;
-  a.tele = g->teleport ? g->p.alpha / (double)g->n : 0.0;
-  a.alpha_over_n = g->p.alpha / (double)g->n;
-  a.D_ref = g->D_ref;
-  a.tol = g->p.tol;
-  a.ftol = g->p.frontier_tol;
   a.max_iter = g->p.max_iter;
   a.mode = (int)mode;
   a.start_full = start_full ? 1 : 0;
@@ -707,9 +845,15 @@ pr_status rank_run(Graph *g, RankMode mode, pr_stats *stats) {
   g->n_pend_src = 0;
   g->n_pend_tgt = 0;
   g->pend_all = false;
-  if (g->teleport) g->D_ref = h.D_final;
+  if (g->teleport) {
+    g->D_ref = h.D_final;
+    g->D_ref_n = h.D_final_n;
+  }
   if (stats) {
     const double vb = g->f32 ? 24.0 : 36.0, eb = g->f32 ? 8.0 : 12.0;
+    double last = 0.0;
+    if (g->f32) std::memcpy(&last, &h.last_key, 8);
+    else last = (double)h.last_key / kOne62;
     stats->iterations = (int32_t)h.iterations;
     stats->converged = (int32_t)h.converged;
     stats->affected_final =
@@ -718,7 +862,7 @@ pr_status rank_run(Graph *g, RankMode mode, pr_stats *stats) {
     stats->edges_processed = (int64_t)h.eproc;
     stats->bytes_algorithmic = vb * (double)h.vproc + eb * (double)h.eproc + 8.0 * (double)h.expv +
                                4.0 * (double)h.expe + 4.0 * (double)h.appended;
-    stats->last_delta = h.last_delta;
+    stats->last_delta = last;
     stats->ms_apply = g->ms_apply;
     stats->ms_rank = ms;
   }
@@ -733,7 +877,7 @@ __global__ void k_set_ranks(const double *in, uint32_t n, const typename Store<F
   using S = Store<F32>;
   uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= n) return;
-  typename S::R r = (typename S::R)in[v];
+  typename S::R r = S::from_double(in[v]);
   typename S::C c = S::contrib(r, adeg[v]);
   R0[v] = r;
   R1[v] = r;
@@ -741,49 +885,72 @@ __global__ void k_set_ranks(const double *in, uint32_t n, const typename Store<F
   C1[v] = c;
 }
 
-template <class R>
-__global__ void k_get_ranks(const R *Rv, uint32_t n, double *out) {
+template <bool F32>
+__global__ void k_get_ranks(const typename Store<F32>::R *Rv, uint32_t n, double *out) {
   uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v < n) out[v] = (double)Rv[v];
+  if (v < n) out[v] = Store<F32>::to_double(Rv[v]);
 }
 
-__global__ void k_dead_mass(const uint32_t *dead, uint32_t n_dead, const double *R, double *out) {
-  // one block; plain sums per thread, then an ordered combine
-  __shared__ double s[256];
-  double acc = 0.0;
-  for (uint32_t k = threadIdx.x; k < n_dead; k += 256) acc += R[dead[k]];
-  s[threadIdx.x] = acc;
+// Dead-end mass of the current ranks: exact in 64-bit mode, plain per-thread sums and an
+// ordered combine in FP32 mode.  One block.
+template <bool F32>
+__global__ void k_dead_mass(const uint32_t *dead, uint32_t n_dead, const typename Store<F32>::R *Rv, double *out_d,
+                            long long *out_n) {
+  __shared__ double sd[256];
+  __shared__ long long sn[256];
+  double ad = 0.0;
+  long long an = 0;
+  for (uint32_t k = threadIdx.x; k < n_dead; k += 256) {
+    if constexpr (F32) ad += (double)Rv[dead[k]];
+    else an += Rv[dead[k]];
+  }
+  sd[threadIdx.x] = ad;
+  sn[threadIdx.x] = an;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int i = 0; i < 256; i++) t += s[i];
-    *out = t;
+    double td = 0.0;
+    long long tn = 0;
+    for (int i = 0; i < 256; i++) {
+      td += sd[i];
+      tn += sn[i];
+    }
+    *out_d = td;
+    *out_n = tn;
   }
 }
 
 pr_status rank_set(Graph *g, const double *in_d) {
   unsigned grid = (g->n + 255) / 256;
-  if (g->f32)
-    k_set_ranks<true><<<grid, 256, 0, g->st>>>(in_d, g->n, (const float *)g->adeg, (float *)g->R[0],
-                                               (float *)g->R[1], (float *)g->C[0], (float *)g->C[1]);
-  else
-    k_set_ranks<false><<<grid, 256, 0, g->st>>>(in_d, g->n, (const double *)g->adeg, (double *)g->R[0],
-                                                (double *)g->R[1], (long long *)g->C[0], (long long *)g->C[1]);
+  if (g->f32) {
+    using S = Store<true>;
+    k_set_ranks<true><<<grid, 256, 0, g->st>>>(in_d, g->n, (const S::A *)g->adeg, (S::R *)g->R[0], (S::R *)g->R[1],
+                                               (S::C *)g->C[0], (S::C *)g->C[1]);
+  } else {
+    using S = Store<false>;
+    k_set_ranks<false><<<grid, 256, 0, g->st>>>(in_d, g->n, (const S::A *)g->adeg, (S::R *)g->R[0],
+                                                (S::R *)g->R[1], (S::C *)g->C[0], (S::C *)g->C[1]);
+  }
   count_launch();
   CK(cudaGetLastError());
   if (g->teleport) {
     pr_status rc = graph_refresh_dead(g);
     if (rc != PR_OK) return rc;
-    double *dm = nullptr;
-    CK(cudaMalloc((void **)&dm, sizeof(double)));
-    k_dead_mass<<<1, 256, 0, g->st>>>(g->dead, g->n_dead, in_d, dm);
+    struct {
+      double d;
+      long long n;
+    } *dm = nullptr, hm{};
+    CK(cudaMalloc((void **)&dm, sizeof(*dm)));
+    if (g->f32)
+      k_dead_mass<true><<<1, 256, 0, g->st>>>(g->dead, g->n_dead, (const float *)g->R[0], &dm->d, &dm->n);
+    else
+      k_dead_mass<false><<<1, 256, 0, g->st>>>(g->dead, g->n_dead, (const long long *)g->R[0], &dm->d, &dm->n);
     count_launch();
-    double D = 0.0;
-    cudaError_t e = cudaMemcpyAsync(&D, dm, sizeof(double), cudaMemcpyDeviceToHost, g->st);
+    cudaError_t e = cudaMemcpyAsync(&hm, dm, sizeof(hm), cudaMemcpyDeviceToHost, g->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
     cudaFree(dm);
     if (e != cudaSuccess) return cuda_fail(g, e, "dead-end mass");
-    g->D_ref = D;
+    g->D_ref = hm.d;
+    g->D_ref_n = hm.n;
   }
   CK(cudaStreamSynchronize(g->st));
   return PR_OK;
@@ -792,9 +959,9 @@ pr_status rank_set(Graph *g, const double *in_d) {
 pr_status rank_get(Graph *g, double *out_d) {
   unsigned grid = (g->n + 255) / 256;
   if (g->f32)
-    k_get_ranks<float><<<grid, 256, 0, g->st>>>((const float *)g->R[0], g->n, out_d);
+    k_get_ranks<true><<<grid, 256, 0, g->st>>>((const float *)g->R[0], g->n, out_d);
   else
-    k_get_ranks<double><<<grid, 256, 0, g->st>>>((const double *)g->R[0], g->n, out_d);
+    k_get_ranks<false><<<grid, 256, 0, g->st>>>((const long long *)g->R[0], g->n, out_d);
   count_launch();
   CK(cudaGetLastError());
   return PR_OK;

@@ -324,11 +324,13 @@ def test_df_max_iter_zero_marks_only(prdf):
     _, aff, _ = oracle.df_sync(G, H, ed, ei, R_or, oracle.Params(max_iter=0))
     with prdf.Graph(g.n, g.src, g.dst, p) as dg:
         dg.set_ranks(R_or)
+        before = dg.ranks().copy()
+        assert np.max(np.abs(before - R_or)) <= 1e-18
         dg.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
         st = dg.frontier()
         assert st.iterations == 0
         assert sorted(dg.affected().tolist()) == sorted(np.nonzero(aff)[0].tolist())
-        assert np.array_equal(dg.ranks(), R_or)
+        assert np.array_equal(dg.ranks(), before)
 
 
 def test_df_deterministic(prdf):
