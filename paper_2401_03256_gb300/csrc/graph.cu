@@ -352,7 +352,8 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(uint2 *rd, uint32_t *ca
       cap[r] = move_cap(new_len);
       atomicAdd(garbage, (unsigned long long)cap_r);
     }
-    if (!hook.is_out && degree_bin(len, hook.bin_lo, hook.bin_hi) != degree_bin(new_len, hook.bin_lo, hook.bin_hi))
+    if (!hook.is_out && (degree_bin(len, hook.bin_lo, hook.bin_hi) != degree_bin(new_len, hook.bin_lo, hook.bin_hi) ||
+                         (new_len > hook.bin_lo && (len + kChunk - 1) / kChunk != (new_len + kChunk - 1) / kChunk)))
       actl->bins_changed = 1;
     if (hook.is_out) {
       using S = Store<F32>;
@@ -409,6 +410,20 @@ __global__ void k_bin_flags(const uint2 *rd, uint32_t n, uint32_t lo, uint32_t h
   uint32_t len = rd[v].y;
   int b = len <= lo ? 0 : (len <= hi ? 1 : 2);
   flags[v] = b == bin;
+}
+
+// Chunks per long-row vertex of the degree-binned order (bins 1 and 2).
+__global__ void k_chunk_counts(const uint32_t *big, uint32_t nb, const uint2 *rd, uint32_t *cnt) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nb) cnt[i] = (rd[big[i]].y + kChunk - 1) / kChunk;
+  else if (i == nb) cnt[i] = 0;
+}
+
+__global__ void k_chunk_emit(const uint32_t *big, uint32_t nb, const uint2 *rd, const uint32_t *start, uint2 *chunks) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nb) return;
+  uint32_t v = big[i], c = (rd[v].y + kChunk - 1) / kChunk, s = start[i];
+  for (uint32_t k = 0; k < c; k++) chunks[s + k] = make_uint2(v, k * kChunk);
 }
 
 __global__ void k_dead_flags(const uint2 *rd, uint32_t n, uint32_t *flags) {
@@ -548,6 +563,8 @@ pr_status graph_build(Graph *g, uint64_t m_in, const uint32_t *src_d, const uint
   CK(cudaMemsetAsync(g->xbits, 0, 4ull * words, st));
   CK(dalloc(&g->stamp, n));
   CK(cudaMemsetAsync(g->stamp, 0xFF, 2ull * n, st));
+  CK(dalloc(&g->chunk_done, n));
+  CK(cudaMemsetAsync(g->chunk_done, 0, 4ull * n, st));
   for (int i = 0; i < 3; i++) CK(dalloc(&g->list[i], n));
   CK(dalloc(&g->ident, n));
   CK(dalloc(&g->dead, n));
@@ -829,6 +846,32 @@ pr_status graph_refresh_ident(Graph *g) {
     g->ident_cnt[bin] = c;
     base += c;
   }
+  // chunk list of the long rows (bins 1 and 2), in bin order
+  const uint32_t nb = g->ident_cnt[1] + g->ident_cnt[2];
+  const uint32_t *big = g->ident + g->ident_cnt[0];
+  k_chunk_counts<<<grid_for((uint64_t)nb + 1), 256, 0, st>>>(big, nb, g->in.rd, g->gen_tmp);
+  count_launch();
+  exclusive_scan_u32(g->gen_tmp, g->gen_tmp2, (uint64_t)nb + 1, g->scan_tmp, st);
+  uint32_t total = 0;
+  CK(cudaMemcpyAsync(&total, g->gen_tmp2 + nb, 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (total > g->chunk_cap) {
+    cudaFree(g->chunks);
+    cudaFree(g->partials);
+    g->chunks = nullptr;
+    g->partials = nullptr;
+    g->chunk_cap = 0;
+    uint64_t cap = (uint64_t)total + total / 4 + 1024;
+    CK(dalloc(&g->chunks, cap));
+    CK(cudaMalloc(&g->partials, 8 * cap));
+    g->chunk_cap = cap;
+  }
+  if (nb) {
+    k_chunk_emit<<<grid_for(nb), 256, 0, st>>>(big, nb, g->in.rd, g->gen_tmp2, g->chunks);
+    count_launch();
+  }
+  CK(cudaGetLastError());
+  g->n_chunks = total;
   g->ident_dirty = false;
   return PR_OK;
 }
@@ -864,6 +907,9 @@ void graph_free(Graph *g) {
   cudaFree(g->bitmap);
   cudaFree(g->xbits);
   cudaFree(g->stamp);
+  cudaFree(g->chunks);
+  cudaFree(g->partials);
+  cudaFree(g->chunk_done);
   for (int i = 0; i < 3; i++) cudaFree(g->list[i]);
   cudaFree(g->ident);
   cudaFree(g->dead);

@@ -18,6 +18,7 @@ constexpr int kMaxIterLimit = 1000;       // hard cap on max_iter (control array
 constexpr uint64_t kSentinel = ~0ull;     // key of a dropped pair
 constexpr int kRankBlock = 256;           // threads per block of the rank kernel
 constexpr uint32_t kSmallSort = 4096;     // largest key count sorted by one block
+constexpr uint32_t kChunk = 512;          // edges per chunk of a long row in full and dense sweeps
 
 // ----------------------------------------------------------------- device helpers ---
 
@@ -121,6 +122,7 @@ struct RankCtl {
   unsigned long long dR_bits[kMaxIterLimit + 1];  // per-iteration L-inf (bits of a non-negative double)
   uint32_t tail[kMaxIterLimit + 2][4];            // per-iteration appends per bin ([0] = initial marks)
   uint32_t blk_next[kMaxIterLimit + 1];           // dynamic index into the block bin
+  uint32_t chunk_next[kMaxIterLimit + 1];         // dynamic index into the chunk list
   unsigned long long vproc, eproc, expv, expe, appended;
 };
 

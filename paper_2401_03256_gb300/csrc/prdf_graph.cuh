@@ -41,6 +41,11 @@ struct Graph {
   uint32_t *ident = nullptr;         // all vertices grouped by bin (for full sweeps)
   uint32_t ident_cnt[3] = {0, 0, 0};
   bool ident_dirty = true;
+  uint2 *chunks = nullptr;           // {vertex, first edge} of the kChunk-edge pieces of rows in bins 1-2
+  uint32_t n_chunks = 0;
+  uint64_t chunk_cap = 0;
+  void *partials = nullptr;          // one contribution-typed partial sum per chunk
+  uint32_t *chunk_done = nullptr;    // per vertex: chunks finished in this iteration (0 between)
   uint32_t *dead = nullptr;          // vertices with out-degree 0 (teleport mode)
   uint32_t n_dead = 0;
   bool dead_dirty = true;

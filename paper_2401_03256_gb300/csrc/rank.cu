@@ -47,6 +47,9 @@ constexpr int kWarps = kRankBlock / 32;
 constexpr uint32_t kFull = 0xffffffffu;
 constexpr uint32_t kDenseDiv = 16;  // dense iteration once affected > n / kDenseDiv
 constexpr uint16_t kNoStamp = 0xFFFF;
+#ifndef PRDF_RANK_MIN_BLOCKS
+#define PRDF_RANK_MIN_BLOCKS 1  // resident blocks per SM the register budget must allow
+#endif
 
 // Per-mode arithmetic of the kernel.  Rank changes are compared as "delta bits"
 // (non-negative values that order like unsigned integers) and reduced to an L-inf key
@@ -94,6 +97,10 @@ struct RankArgs {
   uint32_t *list0, *list1, *list2;
   const uint32_t *ident;
   uint32_t id_cnt0, id_cnt1, id_cnt2;
+  const uint2 *chunks;   // {vertex, first edge} of the long rows' chunks, bin order
+  uint32_t n_chunks;
+  typename S::C *partials;
+  uint32_t *chunk_done;
   const uint32_t *pend_src;
   uint32_t n_pend_src;
   const uint32_t *pend_tgt;
@@ -344,13 +351,11 @@ __device__ __forceinline__ typename Num<F32>::B finish_vertex(const RankArgs<F32
 }
 
 template <bool F32>
-__global__ void __launch_bounds__(kRankBlock) k_rank(const RankArgs<F32> a) {
+__global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const RankArgs<F32> a) {
   using S = Store<F32>;
   using R = typename S::R;
   using C = typename S::C;
   using B = typename Num<F32>::B;
-  __shared__ uint32_t s_q[2][kRankBlock];
-  __shared__ uint32_t s_qn[2];
   __shared__ uint32_t s_idx, s_err;
   __shared__ C s_part[kWarps];
   __shared__ unsigned long long s_key[kWarps];
@@ -368,7 +373,6 @@ __global__ void __launch_bounds__(kRankBlock) k_rank(const RankArgs<F32> a) {
   const unsigned long long pol_cols = l2_evict_first();
   const unsigned long long pol_c = l2_evict_last();
   unsigned long long my_v = 0, my_e = 0, my_xv = 0, my_xe = 0, my_app = 0;
-  if (tid < 2) s_qn[tid] = 0;
 
   // dead-end mass: per-block partials (double-buffered by parity) and their grid total
   Mass<F32> dacc;
@@ -515,47 +519,30 @@ __global__ void __launch_bounds__(kRankBlock) k_rank(const RankArgs<F32> a) {
     const uint32_t slot = (uint32_t)it + 1;
     B my_max = 0;
 
-    // thread bin: one thread per vertex
-    if (!expand) {
-      for (uint32_t i = gtid; i < c0; i += nthreads) {
-        const uint32_t v = ldcg(L0 + i);
-        const uint2 d = __ldg(&a.in_rd[v]);
-        C sum = row_sum_thread(Cin, a.in_col + d.x, d.y, pol_cols, pol_c);
-        B dr = finish_vertex(a, Rin, Rout, Cout, v, sum, I, dacc, pol_c);
-        my_max = dr > my_max ? dr : my_max;
-        my_v++;
-        my_e += d.y;
-      }
-    } else {
-      // rounds of one vertex per thread; vertices to expand are queued in shared memory
-      // and their out-rows marked by whole warps (counter and queue double-buffered by
-      // round parity, one block barrier per round)
-      uint32_t round = 0;
-      for (uint32_t b0 = blockIdx.x * kRankBlock; b0 < c0; b0 += nthreads, round++) {
-        const uint32_t qp = round & 1;
-        const uint32_t i = b0 + tid;
-        int push = 0;
-        if (i < c0) {
-          const uint32_t v = ldcg(L0 + i);
-          if (!dense || ldcg(a.stamp + v) <= (uint16_t)it) {
-            const uint2 d = __ldg(&a.in_rd[v]);
-            C sum = row_sum_thread(Cin, a.in_col + d.x, d.y, pol_cols, pol_c);
-            B dr = finish_vertex(a, Rin, Rout, Cout, v, sum, I, dacc, pol_c);
-            my_max = dr > my_max ? dr : my_max;
-            my_v++;
-            my_e += d.y;
-            if (dr > a.ftol && first_expansion(a.xbits, v)) {
-              push = 1;
-              s_q[qp][atomicAdd(&s_qn[qp], 1u)] = v;
-            }
-          }
+    // thread bin: one thread per vertex, 32 consecutive list entries per warp; vertices to
+    // expand are handed to the whole warp by ballot
+    for (uint32_t b0 = gwarp * 32; b0 < c0; b0 += nwarps * 32) {
+      const uint32_t i = b0 + lane;
+      int push = 0;
+      uint32_t v = 0;
+      if (i < c0) {
+        v = ldcg(L0 + i);
+        if (!dense || ldcg(a.stamp + v) <= (uint16_t)it) {
+          const uint2 d = __ldg(&a.in_rd[v]);
+          C sum = row_sum_thread(Cin, a.in_col + d.x, d.y, pol_cols, pol_c);
+          B dr = finish_vertex(a, Rin, Rout, Cout, v, sum, I, dacc, pol_c);
+          my_max = dr > my_max ? dr : my_max;
+          my_v++;
+          my_e += d.y;
+          push = expand && dr > a.ftol && first_expansion(a.xbits, v);
         }
-        const uint32_t qn = __syncthreads_count(push);
-        // every push of this round is in; the counter is next used two rounds later,
-        // after the next round's barrier, which thread 0 reaches only after this reset
-        if (tid == 0) s_qn[qp] = 0;
-        for (uint32_t k = wib; k < qn; k += kWarps) {
-          const uint32_t x = s_q[qp][k];
+      }
+      if (expand) {
+        uint32_t mask = __ballot_sync(kFull, push);
+        while (mask) {
+          const uint32_t src = __ffs(mask) - 1;
+          mask &= mask - 1;
+          const uint32_t x = __shfl_sync(kFull, v, src);
           const uint2 od = __ldg(&a.out_rd[x]);
           my_app += warp_mark_range(a, a.out_col + od.x, od.y, 0, 32, slot, cnt, lane);
           if (lane == 0) {
@@ -566,73 +553,141 @@ __global__ void __launch_bounds__(kRankBlock) k_rank(const RankArgs<F32> a) {
       }
     }
 
-    // warp bin: one warp per vertex
-    for (uint32_t i = gwarp; i < c1; i += nwarps) {
-      const uint32_t v = ldcg(L1 + i);
-      if (dense && ldcg(a.stamp + v) > (uint16_t)it) continue;
-      const uint2 d = __ldg(&a.in_rd[v]);
-      const uint32_t *cols = a.in_col + d.x;
-      C sum = (C)0;
-      for (uint32_t j = lane * 4; j < d.y; j += 128) {
-        uint4 q = ld_cols(cols + j, pol_cols);
-        sum += gather4(Cin, q, min(4u, d.y - j), pol_c);
-      }
-      sum = warp_sum(sum);
-      int exp_now = 0;
-      if (lane == 0) {
-        B dr = finish_vertex(a, Rin, Rout, Cout, v, sum, I, dacc, pol_c);
-        my_max = dr > my_max ? dr : my_max;
-        my_v++;
-        my_e += d.y;
-        exp_now = expand && dr > a.ftol && first_expansion(a.xbits, v);
-      }
-      exp_now = __shfl_sync(kFull, exp_now, 0);
-      if (exp_now) {
-        const uint2 od = __ldg(&a.out_rd[v]);
-        my_app += warp_mark_range(a, a.out_col + od.x, od.y, 0, 32, slot, cnt, lane);
-        if (lane == 0) {
-          my_xv++;
-          my_xe += od.y;
+    if (I.full || dense) {
+      // long rows as kChunk-edge chunks dealt round-robin to warps (a hub's consecutive
+      // chunks land on different warps); a row split into several chunks is finished by
+      // the warp that completes its last chunk, which adds the partial sums in chunk order
+      C *part = a.partials;
+      {
+        for (uint32_t k = gwarp; k < a.n_chunks; k += nwarps) {
+          const uint2 ch = __ldg(&a.chunks[k]);
+          const uint32_t v = ch.x;
+          if (dense && ldcg(a.stamp + v) > (uint16_t)it) continue;
+          const uint2 d = __ldg(&a.in_rd[v]);
+          const uint32_t len = min(kChunk, d.y - ch.y);
+          const uint32_t *cols = a.in_col + d.x + ch.y;
+          uint4 q[4];
+#pragma unroll
+          for (int r = 0; r < 4; r++) {
+            const uint32_t j = 4 * (lane + 32 * r);
+            if (j < len) q[r] = ld_cols(cols + j, pol_cols);
+          }
+          C sum = (C)0;
+#pragma unroll
+          for (int r = 0; r < 4; r++) {
+            const uint32_t j = 4 * (lane + 32 * r);
+            if (j < len) sum += gather4(Cin, q[r], min(4u, len - j), pol_c);
+          }
+          sum = warp_sum(sum);
+          const uint32_t nch = (d.y + kChunk - 1) / kChunk;
+          int finish = 1;
+          if (nch > 1) {
+            // publish this chunk's partial; the last of the row's chunks adds them up
+            uint32_t old = 0;
+            if (lane == 0) {
+              part[k] = sum;
+              __threadfence();
+              old = atomicAdd(&a.chunk_done[v], 1u);
+            }
+            old = __shfl_sync(kFull, old, 0);
+            finish = old == nch - 1;
+            if (finish) {
+              __threadfence();
+              const uint32_t first = k - ch.y / kChunk;
+              C tot = (C)0;
+              for (uint32_t c = lane; c < nch; c += 32) tot += ldcg(part + first + c);
+              // lane order then a fixed shuffle tree: the same sum whichever warp finishes
+              sum = warp_sum(tot);
+              if (lane == 0) a.chunk_done[v] = 0;
+            }
+          }
+          if (finish) {
+            int exp_now = 0;
+            if (lane == 0) {
+              B dr = finish_vertex(a, Rin, Rout, Cout, v, sum, I, dacc, pol_c);
+              my_max = dr > my_max ? dr : my_max;
+              my_v++;
+              my_e += d.y;
+              exp_now = expand && dr > a.ftol && first_expansion(a.xbits, v);
+            }
+            exp_now = __shfl_sync(kFull, exp_now, 0);
+            if (exp_now) {
+              const uint2 od = __ldg(&a.out_rd[v]);
+              my_app += warp_mark_range(a, a.out_col + od.x, od.y, 0, 32, slot, cnt, lane);
+              if (lane == 0) {
+                my_xv++;
+                my_xe += od.y;
+              }
+            }
+          }
         }
       }
-    }
+    } else {
+      // sparse: warp bin, one warp per vertex
+      for (uint32_t i = gwarp; i < c1; i += nwarps) {
+        const uint32_t v = ldcg(L1 + i);
+        const uint2 d = __ldg(&a.in_rd[v]);
+        const uint32_t *cols = a.in_col + d.x;
+        C sum = (C)0;
+        for (uint32_t j = lane * 4; j < d.y; j += 128) {
+          uint4 q = ld_cols(cols + j, pol_cols);
+          sum += gather4(Cin, q, min(4u, d.y - j), pol_c);
+        }
+        sum = warp_sum(sum);
+        int exp_now = 0;
+        if (lane == 0) {
+          B dr = finish_vertex(a, Rin, Rout, Cout, v, sum, I, dacc, pol_c);
+          my_max = dr > my_max ? dr : my_max;
+          my_v++;
+          my_e += d.y;
+          exp_now = expand && dr > a.ftol && first_expansion(a.xbits, v);
+        }
+        exp_now = __shfl_sync(kFull, exp_now, 0);
+        if (exp_now) {
+          const uint2 od = __ldg(&a.out_rd[v]);
+          my_app += warp_mark_range(a, a.out_col + od.x, od.y, 0, 32, slot, cnt, lane);
+          if (lane == 0) {
+            my_xv++;
+            my_xe += od.y;
+          }
+        }
+      }
 
-    // block bin: one block per vertex, taken dynamically (last, so blocks that finish
-    // their share of the other bins early take the hubs)
-    for (;;) {
-      if (tid == 0) s_idx = atomicAdd(&ctl->blk_next[it], 1u);
-      __syncthreads();
-      const uint32_t idx = s_idx;
-      __syncthreads();
-      if (idx >= c2) break;
-      const uint32_t v = ldcg(L2 + idx);
-      if (dense && ldcg(a.stamp + v) > (uint16_t)it) continue;
-      const uint2 d = __ldg(&a.in_rd[v]);
-      const uint32_t *cols = a.in_col + d.x;
-      C sum = (C)0;
-      for (uint32_t j = tid * 4; j < d.y; j += kRankBlock * 4) {
-        uint4 q = ld_cols(cols + j, pol_cols);
-        sum += gather4(Cin, q, min(4u, d.y - j), pol_c);
-      }
-      sum = warp_sum(sum);
-      if (lane == 0) s_part[wib] = sum;
-      __syncthreads();
-      if (tid == 0) {
-        C tot = (C)0;
-        for (int w = 0; w < kWarps; w++) tot += s_part[w];
-        B dr = finish_vertex(a, Rin, Rout, Cout, v, tot, I, dacc, pol_c);
-        my_max = dr > my_max ? dr : my_max;
-        my_v++;
-        my_e += d.y;
-        s_expand = expand && dr > a.ftol && first_expansion(a.xbits, v);
-      }
-      __syncthreads();
-      if (s_expand) {
-        const uint2 od = __ldg(&a.out_rd[v]);
-        my_app += warp_mark_range(a, a.out_col + od.x, od.y, wib * 32, kRankBlock, slot, cnt, lane);
+      // sparse: block bin, one block per vertex, taken dynamically
+      for (;;) {
+        if (tid == 0) s_idx = atomicAdd(&ctl->blk_next[it], 1u);
+        __syncthreads();
+        const uint32_t idx = s_idx;
+        __syncthreads();
+        if (idx >= c2) break;
+        const uint32_t v = ldcg(L2 + idx);
+        const uint2 d = __ldg(&a.in_rd[v]);
+        const uint32_t *cols = a.in_col + d.x;
+        C sum = (C)0;
+        for (uint32_t j = tid * 4; j < d.y; j += kRankBlock * 4) {
+          uint4 q = ld_cols(cols + j, pol_cols);
+          sum += gather4(Cin, q, min(4u, d.y - j), pol_c);
+        }
+        sum = warp_sum(sum);
+        if (lane == 0) s_part[wib] = sum;
+        __syncthreads();
         if (tid == 0) {
-          my_xv++;
-          my_xe += od.y;
+          C tot = (C)0;
+          for (int w = 0; w < kWarps; w++) tot += s_part[w];
+          B dr = finish_vertex(a, Rin, Rout, Cout, v, tot, I, dacc, pol_c);
+          my_max = dr > my_max ? dr : my_max;
+          my_v++;
+          my_e += d.y;
+          s_expand = expand && dr > a.ftol && first_expansion(a.xbits, v);
+        }
+        __syncthreads();
+        if (s_expand) {
+          const uint2 od = __ldg(&a.out_rd[v]);
+          my_app += warp_mark_range(a, a.out_col + od.x, od.y, wib * 32, kRankBlock, slot, cnt, lane);
+          if (tid == 0) {
+            my_xv++;
+            my_xe += od.y;
+          }
         }
       }
     }
@@ -781,6 +836,10 @@ static pr_status launch(Graph *g, RankMode mode, bool start_full) {
   a.id_cnt0 = g->ident_cnt[0];
   a.id_cnt1 = g->ident_cnt[1];
   a.id_cnt2 = g->ident_cnt[2];
+  a.chunks = g->chunks;
+  a.n_chunks = g->n_chunks;
+  a.partials = (typename S::C *)g->partials;
+  a.chunk_done = g->chunk_done;
   a.pend_src = g->pend_src;
   a.n_pend_src = g->n_pend_src;
   a.pend_tgt = g->pend_tgt;
