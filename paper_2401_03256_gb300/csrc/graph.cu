@@ -352,8 +352,9 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(uint2 *rd, uint32_t *ca
       cap[r] = move_cap(new_len);
       atomicAdd(garbage, (unsigned long long)cap_r);
     }
-    if (!hook.is_out && (degree_bin(len, hook.bin_lo, hook.bin_hi) != degree_bin(new_len, hook.bin_lo, hook.bin_hi) ||
-                         (new_len > hook.bin_lo && (len + kChunk - 1) / kChunk != (new_len + kChunk - 1) / kChunk)))
+    if (!hook.is_out && (sweep_tier(len, hook.bin_lo) != sweep_tier(new_len, hook.bin_lo) ||
+                         (sweep_tier(new_len, hook.bin_lo) == 2 &&
+                          (len + kChunk - 1) / kChunk != (new_len + kChunk - 1) / kChunk)))
       actl->bins_changed = 1;
     if (hook.is_out) {
       using S = Store<F32>;
@@ -404,15 +405,13 @@ __global__ void k_pack_rows(const uint2 *rd, uint32_t n, const uint32_t *col, co
   for (uint32_t j = lane; j < d.y; j += 32) packed[o + j] = col[d.x + j];
 }
 
-__global__ void k_bin_flags(const uint2 *rd, uint32_t n, uint32_t lo, uint32_t hi, int bin, uint32_t *flags) {
+__global__ void k_bin_flags(const uint2 *rd, uint32_t n, uint32_t lo, int bin, uint32_t *flags) {
   uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= n) return;
-  uint32_t len = rd[v].y;
-  int b = len <= lo ? 0 : (len <= hi ? 1 : 2);
-  flags[v] = b == bin;
+  flags[v] = sweep_tier(rd[v].y, lo) == bin;
 }
 
-// Chunks per long-row vertex of the degree-binned order (bins 1 and 2).
+// Chunks per long-row vertex (tier 2 of the sweep order).
 __global__ void k_chunk_counts(const uint32_t *big, uint32_t nb, const uint2 *rd, uint32_t *cnt) {
   uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < nb) cnt[i] = (rd[big[i]].y + kChunk - 1) / kChunk;
@@ -836,8 +835,8 @@ pr_status graph_refresh_ident(Graph *g) {
   uint32_t *cnt = (uint32_t *)&g->actl->n_seg_out;  // reuse a device word
   uint32_t base = 0;
   for (int bin = 0; bin < 3; bin++) {
-    k_bin_flags<<<grid_for(n), 256, 0, st>>>(g->in.rd, n, (uint32_t)g->p.bin_lo, (uint32_t)g->p.bin_hi, bin,
-                                            g->gen_tmp); count_launch();
+    k_bin_flags<<<grid_for(n), 256, 0, st>>>(g->in.rd, n, (uint32_t)g->p.bin_lo, bin, g->gen_tmp);
+    count_launch();
     exclusive_scan_u32(g->gen_tmp, g->gen_tmp2, n, g->scan_tmp, st);
     k_compact_ids<<<grid_for(n), 256, 0, st>>>(g->gen_tmp, g->gen_tmp2, n, g->ident + base, cnt); count_launch();
     uint32_t c = 0;
@@ -846,9 +845,9 @@ pr_status graph_refresh_ident(Graph *g) {
     g->ident_cnt[bin] = c;
     base += c;
   }
-  // chunk list of the long rows (bins 1 and 2), in bin order
-  const uint32_t nb = g->ident_cnt[1] + g->ident_cnt[2];
-  const uint32_t *big = g->ident + g->ident_cnt[0];
+  // chunk list of the long rows (tier 2), in sweep order
+  const uint32_t nb = g->ident_cnt[2];
+  const uint32_t *big = g->ident + g->ident_cnt[0] + g->ident_cnt[1];
   k_chunk_counts<<<grid_for((uint64_t)nb + 1), 256, 0, st>>>(big, nb, g->in.rd, g->gen_tmp);
   count_launch();
   exclusive_scan_u32(g->gen_tmp, g->gen_tmp2, (uint64_t)nb + 1, g->scan_tmp, st);

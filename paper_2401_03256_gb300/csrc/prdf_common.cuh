@@ -19,6 +19,13 @@ constexpr uint64_t kSentinel = ~0ull;     // key of a dropped pair
 constexpr int kRankBlock = 256;           // threads per block of the rank kernel
 constexpr uint32_t kSmallSort = 4096;     // largest key count sorted by one block
 constexpr uint32_t kChunk = 512;          // edges per chunk of a long row in full and dense sweeps
+constexpr uint32_t kGroupMax = 64;        // full/dense sweeps: rows up to this length use 8-lane groups
+
+// Tier of an in-degree in the full/dense sweep order: 0 = one thread (<= lo), 1 = an
+// 8-lane group (<= max(lo, kGroupMax)), 2 = kChunk-edge chunks taken by whole warps.
+__host__ __device__ inline int sweep_tier(uint32_t d, uint32_t lo) {
+  return d <= lo ? 0 : (d <= (lo > kGroupMax ? lo : kGroupMax) ? 1 : 2);
+}
 
 // ----------------------------------------------------------------- device helpers ---
 

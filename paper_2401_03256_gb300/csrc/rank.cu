@@ -48,7 +48,7 @@ constexpr uint32_t kFull = 0xffffffffu;
 constexpr uint32_t kDenseDiv = 16;  // dense iteration once affected > n / kDenseDiv
 constexpr uint16_t kNoStamp = 0xFFFF;
 #ifndef PRDF_RANK_MIN_BLOCKS
-#define PRDF_RANK_MIN_BLOCKS 1  // resident blocks per SM the register budget must allow
+#define PRDF_RANK_MIN_BLOCKS 4  // resident blocks per SM the register budget must allow
 #endif
 
 // Per-mode arithmetic of the kernel.  Rank changes are compared as "delta bits"
@@ -281,19 +281,19 @@ __device__ __forceinline__ C gather4(const C *Cv, uint4 q, uint32_t valid, unsig
   return s;
 }
 
-// Sum of C over one whole row by one thread: runs of 16 columns, all loads of a run in
+// Sum of C over one whole row by one thread: runs of 8 columns, all loads of a run in
 // flight together.
 template <class C>
 __device__ __forceinline__ C row_sum_thread(const C *Cv, const uint32_t *cols, uint32_t len,
                                             unsigned long long pol_cols, unsigned long long pol_c) {
   C sum = (C)0;
-  for (uint32_t j0 = 0; j0 < len; j0 += 16) {
-    uint4 q[4];
+  for (uint32_t j0 = 0; j0 < len; j0 += 8) {
+    uint4 q[2];
 #pragma unroll
-    for (int k = 0; k < 4; k++)
+    for (int k = 0; k < 2; k++)
       if (j0 + 4 * k < len) q[k] = ld_cols(cols + j0 + 4 * k, pol_cols);
 #pragma unroll
-    for (int k = 0; k < 4; k++)
+    for (int k = 0; k < 2; k++)
       if (j0 + 4 * k < len) sum += gather4(Cv, q[k], min(4u, len - j0 - 4 * k), pol_c);
   }
   return sum;
@@ -370,9 +370,9 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
   RankCtl *ctl = a.ctl;
   uint32_t epoch = 0;
   const bool df = a.mode == kModeDF;
-  const unsigned long long pol_cols = l2_evict_first();
-  const unsigned long long pol_c = l2_evict_last();
-  unsigned long long my_v = 0, my_e = 0, my_xv = 0, my_xe = 0, my_app = 0;
+#define pol_cols l2_evict_first()
+#define pol_c l2_evict_last()
+  uint32_t my_v = 0, my_e = 0, my_xv = 0, my_xe = 0, my_app = 0;  // per-thread, folded at the end
 
   // dead-end mass: per-block partials (double-buffered by parity) and their grid total
   Mass<F32> dacc;
@@ -554,6 +554,56 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
     }
 
     if (I.full || dense) {
+      // tier 1: rows of lo < len <= kGroupMax by 8-lane groups, four vertices per warp
+      const uint32_t grp = lane >> 3, gl = lane & 7;
+      for (uint32_t b0 = gwarp * 4; b0 < c1; b0 += nwarps * 4) {
+        const uint32_t i = b0 + grp;
+        const bool have = i < c1;
+        uint32_t v = have ? ldcg(L1 + i) : 0u;
+        const bool act = have && (!dense || ldcg(a.stamp + v) <= (uint16_t)it);
+        C sum = (C)0;
+        uint2 d = make_uint2(0, 0);
+        if (act) {
+          d = __ldg(&a.in_rd[v]);
+          const uint32_t *cols = a.in_col + d.x;
+          uint4 q[2];
+#pragma unroll
+          for (int r = 0; r < 2; r++) {
+            const uint32_t j = 4 * (gl + 8 * r);
+            if (j < d.y) q[r] = ld_cols(cols + j, pol_cols);
+          }
+#pragma unroll
+          for (int r = 0; r < 2; r++) {
+            const uint32_t j = 4 * (gl + 8 * r);
+            if (j < d.y) sum += gather4(Cin, q[r], min(4u, d.y - j), pol_c);
+          }
+        }
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
+        int push = 0;
+        if (act && gl == 0) {
+          B dr = finish_vertex(a, Rin, Rout, Cout, v, sum, I, dacc, pol_c);
+          my_max = dr > my_max ? dr : my_max;
+          my_v++;
+          my_e += d.y;
+          push = expand && dr > a.ftol && first_expansion(a.xbits, v);
+        }
+        if (expand) {
+          uint32_t mask = __ballot_sync(kFull, push);
+          while (mask) {
+            const uint32_t src = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const uint32_t x = __shfl_sync(kFull, v, src);
+            const uint2 od = __ldg(&a.out_rd[x]);
+            my_app += warp_mark_range(a, a.out_col + od.x, od.y, 0, 32, slot, cnt, lane);
+            if (lane == 0) {
+              my_xv++;
+              my_xe += od.y;
+            }
+          }
+        }
+      }
+
       // long rows as kChunk-edge chunks dealt round-robin to warps (a hub's consecutive
       // chunks land on different warps); a row split into several chunks is finished by
       // the warp that completes its last chunk, which adds the partial sums in chunk order
@@ -664,9 +714,18 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
         const uint2 d = __ldg(&a.in_rd[v]);
         const uint32_t *cols = a.in_col + d.x;
         C sum = (C)0;
-        for (uint32_t j = tid * 4; j < d.y; j += kRankBlock * 4) {
-          uint4 q = ld_cols(cols + j, pol_cols);
-          sum += gather4(Cin, q, min(4u, d.y - j), pol_c);
+        for (uint32_t j0 = tid * 4; j0 < d.y; j0 += kRankBlock * 16) {
+          uint4 q[4];
+#pragma unroll
+          for (int r = 0; r < 4; r++) {
+            const uint32_t j = j0 + r * kRankBlock * 4;
+            if (j < d.y) q[r] = ld_cols(cols + j, pol_cols);
+          }
+#pragma unroll
+          for (int r = 0; r < 4; r++) {
+            const uint32_t j = j0 + r * kRankBlock * 4;
+            if (j < d.y) sum += gather4(Cin, q[r], min(4u, d.y - j), pol_c);
+          }
         }
         sum = warp_sum(sum);
         if (lane == 0) s_part[wib] = sum;
@@ -761,7 +820,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
   }
   // counters
   {
-    unsigned long long vals[5] = {my_v, my_e, my_xv, my_xe, my_app};
+    unsigned long long vals[5] = {my_v, my_e, my_xv, my_xe, my_app};  // widened before the warp sums
     unsigned long long *dst[5] = {&ctl->vproc, &ctl->eproc, &ctl->expv, &ctl->expe, &ctl->appended};
 #pragma unroll
     for (int k = 0; k < 5; k++) {
@@ -778,6 +837,9 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
     for (int bb = 0; bb < 3; bb++) ctl->final_cnt[bb] = cnt[bb];
   }
 }
+
+#undef pol_cols
+#undef pol_c
 
 // ------------------------------------------------------------------ host side ---
 
