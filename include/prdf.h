@@ -57,7 +57,7 @@ typedef struct {
     int32_t max_iter;     /* MAX_ITERATIONS; 500 (Section 5.1.2); at most 1000 */
     int32_t precision;    /* pr_precision: rank and contribution storage (FP64 or FP32) */
     int32_t dead_end;     /* pr_deadend */
-    int32_t bin_lo;       /* in-degree <= bin_lo: one thread per vertex (0 = default 16) */
+    int32_t bin_lo;       /* in-degree <= bin_lo: one thread per vertex (0 = default 8) */
     int32_t bin_hi;       /* in-degree >  bin_hi: one block per vertex (0 = default 4096) */
     int32_t reserved;     /* must be 0 */
 } pr_params;

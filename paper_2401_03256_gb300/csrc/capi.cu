@@ -82,7 +82,7 @@ void pr_params_default(pr_params *p) {
   p->max_iter = 500;
   p->precision = PR_F64;
   p->dead_end = PR_DEADEND_SELFLOOP;
-  p->bin_lo = 16;
+  p->bin_lo = 8;
   p->bin_hi = 4096;
   p->reserved = 0;
 }
@@ -117,7 +117,7 @@ pr_status pr_graph_create(uint32_t n, int64_t m, const uint32_t *src, const uint
   pr_params p;
   if (params) p = *params; else pr_params_default(&p);
   if (p.bin_lo == 0 && p.bin_hi == 0) {
-    p.bin_lo = 16;
+    p.bin_lo = 8;
     p.bin_hi = 4096;
   }
   std::string why;
