@@ -140,6 +140,13 @@ __global__ void k_init_rank(const uint2 *out_rd, uint32_t n, double alpha, typen
 
 // ---- batch update ----
 
+// Chunk items of the tier-2 rows; chunk c of a row covers edges [c kChunk, (c+1) kChunk).
+__device__ __forceinline__ uint4 chunk_item(uint32_t v, uint2 d, uint32_t c, uint32_t nch, uint32_t number) {
+  uint32_t len = min(kChunk, d.y - c * kChunk);
+  return make_uint4(v, d.x + c * kChunk, len | (c << 10) | (nch > 1 ? 0x80000000u : 0u), number);
+}
+
+
 __device__ __forceinline__ bool row_has(const uint2 *rd, const uint32_t *col, uint32_t u, uint32_t v) {
   uint2 d = rd[u];
   const uint32_t *c = col + d.x;
@@ -270,6 +277,8 @@ struct RowHook {
   uint32_t *pend_src, *pend_tgt;
   uint32_t pend_cap;
   uint32_t bin_lo, bin_hi;
+  uint4 *items;               // in-rows: sweep items to patch (tier and chunk count unchanged)
+  const uint32_t *item_pos;
 };
 
 __device__ __forceinline__ int degree_bin(uint32_t d, uint32_t lo, uint32_t hi) {
@@ -354,8 +363,10 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(uint2 *rd, uint32_t *ca
     }
     if (!hook.is_out && (sweep_tier(len, hook.bin_lo) != sweep_tier(new_len, hook.bin_lo) ||
                          (sweep_tier(new_len, hook.bin_lo) == 2 &&
-                          (len + kChunk - 1) / kChunk != (new_len + kChunk - 1) / kChunk)))
+                          (len + kChunk - 1) / kChunk != (new_len + kChunk - 1) / kChunk))) {
       actl->bins_changed = 1;
+      s_ok = 0;  // the sweep items are rebuilt after this update; nothing to patch
+    }
     if (hook.is_out) {
       using S = Store<F32>;
       typename S::A a = S::factor(hook.alpha, new_len);
@@ -366,6 +377,21 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(uint2 *rd, uint32_t *ca
       if ((len == 0) != (new_len == 0)) actl->dead_changed = 1;
       uint32_t p = atomicAdd(&actl->n_pend_src, 1u);
       if (p < hook.pend_cap) hook.pend_src[p] = r;
+    }
+  }
+  if (!hook.is_out) {
+    // keep the sweep items of this in-row current (start and length)
+    __syncthreads();
+    if (s_ok) {
+      const uint2 nd = make_uint2(s_dest, new_len);
+      const uint32_t pos = hook.item_pos[r];
+      if (sweep_tier(new_len, hook.bin_lo) < 2) {
+        if (tid == 0) hook.items[pos] = make_uint4(r, nd.x, nd.y, 0u);
+      } else {
+        const uint32_t nch = (new_len + kChunk - 1) / kChunk;
+        const uint32_t number0 = hook.items[pos].w;
+        for (uint32_t c = tid; c < nch; c += kMergeThreads) hook.items[pos + c] = chunk_item(r, nd, c, nch, number0 + c);
+      }
     }
   }
 }
@@ -418,11 +444,25 @@ __global__ void k_chunk_counts(const uint32_t *big, uint32_t nb, const uint2 *rd
   else if (i == nb) cnt[i] = 0;
 }
 
-__global__ void k_chunk_emit(const uint32_t *big, uint32_t nb, const uint2 *rd, const uint32_t *start, uint2 *chunks) {
+__global__ void k_items_simple(const uint32_t *ident, uint32_t cnt, const uint2 *rd, uint4 *items,
+                               uint32_t *item_pos) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= cnt) return;
+  uint32_t v = ident[i];
+  uint2 d = rd[v];
+  items[i] = make_uint4(v, d.x, d.y, 0u);
+  item_pos[v] = i;
+}
+
+__global__ void k_items_chunks(const uint32_t *big, uint32_t nb, const uint2 *rd, const uint32_t *start,
+                               uint32_t base, uint4 *items, uint32_t *item_pos) {
   uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nb) return;
-  uint32_t v = big[i], c = (rd[v].y + kChunk - 1) / kChunk, s = start[i];
-  for (uint32_t k = 0; k < c; k++) chunks[s + k] = make_uint2(v, k * kChunk);
+  uint32_t v = big[i];
+  uint2 d = rd[v];
+  uint32_t nch = (d.y + kChunk - 1) / kChunk, s = start[i];
+  for (uint32_t c = 0; c < nch; c++) items[base + s + c] = chunk_item(v, d, c, nch, s + c);
+  item_pos[v] = base + s;
 }
 
 __global__ void k_dead_flags(const uint2 *rd, uint32_t n, uint32_t *flags) {
@@ -564,6 +604,7 @@ pr_status graph_build(Graph *g, uint64_t m_in, const uint32_t *src_d, const uint
   CK(cudaMemsetAsync(g->stamp, 0xFF, 2ull * n, st));
   CK(dalloc(&g->chunk_done, n));
   CK(cudaMemsetAsync(g->chunk_done, 0, 4ull * n, st));
+  CK(dalloc(&g->item_pos, n));
   for (int i = 0; i < 3; i++) CK(dalloc(&g->list[i], n));
   CK(dalloc(&g->ident, n));
   CK(dalloc(&g->dead, n));
@@ -754,8 +795,9 @@ pr_status graph_apply(Graph *g, uint64_t nd, const uint32_t *ds, const uint32_t 
   if (g->f32) {
     using S = Store<true>;
     RowHook<true> ho{true, g->p.alpha, (S::A *)g->adeg, (S::R *)g->R[0], (S::C *)g->C[0], (S::C *)g->C[1],
-                     g->pend_src, g->pend_tgt, g->pend_cap, lo, hi_b};
-    RowHook<true> hin{false, g->p.alpha, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, lo, hi_b};
+                     g->pend_src, g->pend_tgt, g->pend_cap, lo, hi_b, nullptr, nullptr};
+    RowHook<true> hin{false, g->p.alpha, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, lo, hi_b,
+                      g->items, g->item_pos};
     k_merge<true><<<K, kMergeThreads, 0, st>>>(g->out.rd, g->out.cap, g->out.col, co, b, seg_o, &dctl->n_seg_out,
                                                tp_o, &dctl->tail_out, &dctl->garbage_out, g->big, &dctl->big_cursor,
                                                g->out.col_cap, g->big_cap, dctl, ho);
@@ -767,8 +809,9 @@ pr_status graph_apply(Graph *g, uint64_t nd, const uint32_t *ds, const uint32_t 
   } else {
     using S = Store<false>;
     RowHook<false> ho{true, g->p.alpha, (S::A *)g->adeg, (S::R *)g->R[0], (S::C *)g->C[0], (S::C *)g->C[1],
-                      g->pend_src, g->pend_tgt, g->pend_cap, lo, hi_b};
-    RowHook<false> hin{false, g->p.alpha, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, lo, hi_b};
+                      g->pend_src, g->pend_tgt, g->pend_cap, lo, hi_b, nullptr, nullptr};
+    RowHook<false> hin{false, g->p.alpha, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, lo, hi_b,
+                       g->items, g->item_pos};
     k_merge<false><<<K, kMergeThreads, 0, st>>>(g->out.rd, g->out.cap, g->out.col, co, b, seg_o, &dctl->n_seg_out,
                                                 tp_o, &dctl->tail_out, &dctl->garbage_out, g->big, &dctl->big_cursor,
                                                 g->out.col_cap, g->big_cap, dctl, ho);
@@ -845,32 +888,43 @@ pr_status graph_refresh_ident(Graph *g) {
     g->ident_cnt[bin] = c;
     base += c;
   }
-  // chunk list of the long rows (tier 2), in sweep order
+  // sweep items: tier 0 and 1 one per vertex, tier-2 rows as kChunk-edge chunks
+  const uint32_t c01 = g->ident_cnt[0] + g->ident_cnt[1];
   const uint32_t nb = g->ident_cnt[2];
-  const uint32_t *big = g->ident + g->ident_cnt[0] + g->ident_cnt[1];
+  const uint32_t *big = g->ident + c01;
   k_chunk_counts<<<grid_for((uint64_t)nb + 1), 256, 0, st>>>(big, nb, g->in.rd, g->gen_tmp);
   count_launch();
   exclusive_scan_u32(g->gen_tmp, g->gen_tmp2, (uint64_t)nb + 1, g->scan_tmp, st);
   uint32_t total = 0;
   CK(cudaMemcpyAsync(&total, g->gen_tmp2 + nb, 4, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  if (total > g->chunk_cap) {
-    cudaFree(g->chunks);
+  if ((uint64_t)c01 + total > g->items_cap) {
+    cudaFree(g->items);
+    cudaFree(g->items_cmp);
     cudaFree(g->partials);
-    g->chunks = nullptr;
+    g->items = g->items_cmp = nullptr;
     g->partials = nullptr;
-    g->chunk_cap = 0;
-    uint64_t cap = (uint64_t)total + total / 4 + 1024;
-    CK(dalloc(&g->chunks, cap));
-    CK(cudaMalloc(&g->partials, 8 * cap));
-    g->chunk_cap = cap;
+    g->items_cap = g->chunk_cap = 0;
+    uint64_t chunks = (uint64_t)total + total / 4 + 1024;
+    uint64_t cap = (uint64_t)n + chunks;
+    CK(dalloc(&g->items, cap));
+    CK(dalloc(&g->items_cmp, cap));
+    CK(cudaMalloc(&g->partials, 8 * chunks));
+    g->items_cap = cap;
+    g->chunk_cap = chunks;
+  }
+  if (c01) {
+    k_items_simple<<<grid_for(c01), 256, 0, st>>>(g->ident, c01, g->in.rd, g->items, g->item_pos);
+    count_launch();
   }
   if (nb) {
-    k_chunk_emit<<<grid_for(nb), 256, 0, st>>>(big, nb, g->in.rd, g->gen_tmp2, g->chunks);
+    k_items_chunks<<<grid_for(nb), 256, 0, st>>>(big, nb, g->in.rd, g->gen_tmp2, c01, g->items, g->item_pos);
     count_launch();
   }
   CK(cudaGetLastError());
-  g->n_chunks = total;
+  g->item_cnt[0] = g->ident_cnt[0];
+  g->item_cnt[1] = g->ident_cnt[1];
+  g->item_cnt[2] = total;
   g->ident_dirty = false;
   return PR_OK;
 }
@@ -906,7 +960,9 @@ void graph_free(Graph *g) {
   cudaFree(g->bitmap);
   cudaFree(g->xbits);
   cudaFree(g->stamp);
-  cudaFree(g->chunks);
+  cudaFree(g->items);
+  cudaFree(g->items_cmp);
+  cudaFree(g->item_pos);
   cudaFree(g->partials);
   cudaFree(g->chunk_done);
   for (int i = 0; i < 3; i++) cudaFree(g->list[i]);

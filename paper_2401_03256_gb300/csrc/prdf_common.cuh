@@ -129,7 +129,7 @@ struct RankCtl {
   unsigned long long dR_bits[kMaxIterLimit + 1];  // per-iteration L-inf (bits of a non-negative double)
   uint32_t tail[kMaxIterLimit + 2][4];            // per-iteration appends per bin ([0] = initial marks)
   uint32_t blk_next[kMaxIterLimit + 1];           // dynamic index into the block bin
-  uint32_t chunk_next[kMaxIterLimit + 1];         // dynamic index into the chunk list
+  uint32_t cmp[kMaxIterLimit + 1][4];             // affected items per tier after a dense compaction
   unsigned long long vproc, eproc, expv, expe, appended;
 };
 

@@ -41,8 +41,14 @@ struct Graph {
   uint32_t *ident = nullptr;         // all vertices grouped by bin (for full sweeps)
   uint32_t ident_cnt[3] = {0, 0, 0};
   bool ident_dirty = true;
-  uint2 *chunks = nullptr;           // {vertex, first edge} of the kChunk-edge pieces of rows in bins 1-2
-  uint32_t n_chunks = 0;
+  // Sweep items (16 B each) in tier order: tier 0 and 1 items {v, start, len, 0}, then the
+  // kChunk-edge chunks of tier-2 rows {v, start of chunk, len | index in row << 10 |
+  // several-chunks flag << 31, chunk number}.  items_cmp holds the affected subset during
+  // dense Dynamic Frontier iterations.
+  uint4 *items = nullptr, *items_cmp = nullptr;
+  uint64_t items_cap = 0;
+  uint32_t item_cnt[3] = {0, 0, 0};  // tier-0 items, tier-1 items, chunks
+  uint32_t *item_pos = nullptr;      // per vertex: index of its (first) item
   uint64_t chunk_cap = 0;
   void *partials = nullptr;          // one contribution-typed partial sum per chunk
   uint32_t *chunk_done = nullptr;    // per vertex: chunks finished in this iteration (0 between)

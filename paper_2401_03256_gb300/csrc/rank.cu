@@ -95,10 +95,9 @@ struct RankArgs {
   uint32_t *xbits;   // out-row already scanned in this call
   uint16_t *stamp;   // iteration a vertex joins (kNoStamp = not affected)
   uint32_t *list0, *list1, *list2;
-  const uint32_t *ident;
-  uint32_t id_cnt0, id_cnt1, id_cnt2;
-  const uint2 *chunks;   // {vertex, first edge} of the long rows' chunks, bin order
-  uint32_t n_chunks;
+  const uint4 *items;    // sweep items in tier order (see the graph handle)
+  uint4 *items_cmp;      // affected items, compacted in dense iterations
+  uint32_t it_c0, it_c1, it_c2;
   typename S::C *partials;
   uint32_t *chunk_done;
   const uint32_t *pend_src;
@@ -326,21 +325,18 @@ struct Iter {
   typename Store<F32>::R tele;  // alpha D / n in the rank representation
 };
 
-// Rank of v from its in-edge sum; writes the new rank and contribution; returns the
-// delta bits of |r - R[v]|.
+// Rank of v from its in-edge sum, given R[v] and A[v] loaded beforehand; writes the new
+// rank and contribution; returns the delta bits of |r - R[v]|.
 template <bool F32>
-__device__ __forceinline__ typename Num<F32>::B finish_vertex(const RankArgs<F32> &a,
-                                                              const typename Store<F32>::R *Rin,
-                                                              typename Store<F32>::R *Rout,
+__device__ __forceinline__ typename Num<F32>::B finish_vertex(const RankArgs<F32> &a, typename Store<F32>::R *Rout,
                                                               typename Store<F32>::C *Cout, uint32_t v,
-                                                              typename Store<F32>::C sum, const Iter<F32> &I,
+                                                              typename Store<F32>::C sum, typename Store<F32>::R rold,
+                                                              typename Store<F32>::A ad, const Iter<F32> &I,
                                                               Mass<F32> &dacc, unsigned long long pol_c) {
   using S = Store<F32>;
   using R = typename S::R;
   R r = a.base + sum;
   if (a.teleport) r += I.tele;
-  const R rold = ldcg(Rin + v);
-  const typename S::A ad = __ldg(a.adeg + v);
   Rout[v] = r;
   st_keep(Cout + v, S::contrib(r, ad), pol_c);
   if (a.teleport && ad == (typename S::A)0) {
@@ -349,6 +345,8 @@ __device__ __forceinline__ typename Num<F32>::B finish_vertex(const RankArgs<F32
   }
   return Num<F32>::delta(r, rold);
 }
+
+__device__ __forceinline__ uint4 ldcg(const uint4 *p) { return __ldcg(p); }
 
 template <bool F32>
 __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const RankArgs<F32> a) {
@@ -479,6 +477,8 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
   bool converged = false;
   unsigned long long last_key = 0;
   const uint32_t dense_at = a.n / kDenseDiv;
+  uint32_t cmp_total = 0xFFFFFFFFu;  // affected count at the last compaction (none yet)
+  uint32_t cmp_n[3] = {0, 0, 0};
 
   // ------------------------------------------------------------- iterations
   for (int it = 0; it < a.max_iter; it++) {
@@ -496,105 +496,198 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
     const C *Cin = par ? a.C1 : a.C0;
     R *Rout = par ? a.R0 : a.R1;
     C *Cout = par ? a.C0 : a.C1;
-    // dense: walk all vertices in bin order, skip those not yet affected in iteration it
+    // dense: once the affected lists are large, iterate over the sweep items of the affected
+    // vertices (compacted from all items whenever the affected set grew), in tier order
     const bool dense = !I.full && (cnt[0] + cnt[1] + cnt[2] > dense_at);
-    const uint32_t *L0, *L1, *L2;
-    uint32_t c0, c1, c2;
-    if (I.full || dense) {
-      L0 = a.ident;
-      c0 = a.id_cnt0;
-      L1 = a.ident + a.id_cnt0;
-      c1 = a.id_cnt1;
-      L2 = a.ident + a.id_cnt0 + a.id_cnt1;
-      c2 = a.id_cnt2;
-    } else {
-      L0 = a.list0;
-      c0 = cnt[0];
-      L1 = a.list1;
-      c1 = cnt[1];
-      L2 = a.list2;
-      c2 = cnt[2];
-    }
     const bool expand = df && !I.full;
     const uint32_t slot = (uint32_t)it + 1;
     B my_max = 0;
 
-    // thread bin: one thread per vertex, 32 consecutive list entries per warp; vertices to
-    // expand are handed to the whole warp by ballot
-    for (uint32_t b0 = gwarp * 32; b0 < c0; b0 += nwarps * 32) {
-      const uint32_t i = b0 + lane;
-      int push = 0;
-      uint32_t v = 0;
-      if (i < c0) {
-        v = ldcg(L0 + i);
-        if (!dense || ldcg(a.stamp + v) <= (uint16_t)it) {
-          const uint2 d = __ldg(&a.in_rd[v]);
-          C sum = row_sum_thread(Cin, a.in_col + d.x, d.y, pol_cols, pol_c);
-          B dr = finish_vertex(a, Rin, Rout, Cout, v, sum, I, dacc, pol_c);
-          my_max = dr > my_max ? dr : my_max;
-          my_v++;
-          my_e += d.y;
-          push = expand && dr > a.ftol && first_expansion(a.xbits, v);
+    auto expand_lanes = [&](int push, uint32_t v) {
+      uint32_t mask = __ballot_sync(kFull, push);
+      while (mask) {
+        const uint32_t src = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const uint32_t x = __shfl_sync(kFull, v, src);
+        const uint2 od = __ldg(&a.out_rd[x]);
+        my_app += warp_mark_range(a, a.out_col + od.x, od.y, 0, 32, slot, cnt, lane);
+        if (lane == 0) {
+          my_xv++;
+          my_xe += od.y;
         }
       }
-      if (expand) {
-        uint32_t mask = __ballot_sync(kFull, push);
-        while (mask) {
-          const uint32_t src = __ffs(mask) - 1;
-          mask &= mask - 1;
-          const uint32_t x = __shfl_sync(kFull, v, src);
-          const uint2 od = __ldg(&a.out_rd[x]);
-          my_app += warp_mark_range(a, a.out_col + od.x, od.y, 0, 32, slot, cnt, lane);
-          if (lane == 0) {
-            my_xv++;
-            my_xe += od.y;
-          }
-        }
-      }
-    }
+    };
 
     if (I.full || dense) {
-      // tier 1: rows of lo < len <= kGroupMax by 8-lane groups, four vertices per warp
-      const uint32_t grp = lane >> 3, gl = lane & 7;
-      for (uint32_t b0 = gwarp * 4; b0 < c1; b0 += nwarps * 4) {
-        const uint32_t i = b0 + grp;
-        const bool have = i < c1;
-        uint32_t v = have ? ldcg(L1 + i) : 0u;
-        const bool act = have && (!dense || ldcg(a.stamp + v) <= (uint16_t)it);
-        C sum = (C)0;
-        uint2 d = make_uint2(0, 0);
-        if (act) {
-          d = __ldg(&a.in_rd[v]);
-          const uint32_t *cols = a.in_col + d.x;
-          uint4 q[2];
+      const uint32_t off1 = a.it_c0, off2 = a.it_c0 + a.it_c1;
+      const uint4 *T = a.items;
+      uint32_t n0 = a.it_c0, n1 = a.it_c1, n2 = a.it_c2;
+      if (dense) {
+        const uint32_t total = cnt[0] + cnt[1] + cnt[2];
+        if (total != cmp_total) {
+          // keep the items of vertices stamped <= it; warp-aggregated appends keep runs of
+          // up to 32 items in tier order
+          const uint32_t segs[3][2] = {{0u, a.it_c0}, {off1, a.it_c1}, {off2, a.it_c2}};
 #pragma unroll
-          for (int r = 0; r < 2; r++) {
-            const uint32_t j = 4 * (gl + 8 * r);
-            if (j < d.y) q[r] = ld_cols(cols + j, pol_cols);
+          for (int t = 0; t < 3; t++) {
+            const uint32_t base = segs[t][0], cntt = segs[t][1];
+            for (uint32_t b0 = gwarp * 32; b0 < cntt; b0 += nwarps * 32) {
+              const uint32_t i = b0 + lane;
+              uint4 item = make_uint4(0, 0, 0, 0);
+              bool keep = false;
+              if (i < cntt) {
+                item = __ldg(a.items + base + i);
+                keep = ldcg(a.stamp + item.x) <= (uint16_t)it;
+              }
+              const uint32_t mask = __ballot_sync(kFull, keep);
+              if (mask) {
+                const uint32_t leader = __ffs(mask) - 1;
+                uint32_t at = 0;
+                if (lane == leader) at = atomicAdd(&ctl->cmp[slot][t], (uint32_t)__popc(mask));
+                at = __shfl_sync(kFull, at, leader);
+                if (keep) a.items_cmp[base + at + __popc(mask & lanemask_lt())] = item;
+              }
+            }
           }
+          if (!grid_sync(ctl, epoch, &s_err)) return;
 #pragma unroll
-          for (int r = 0; r < 2; r++) {
-            const uint32_t j = 4 * (gl + 8 * r);
-            if (j < d.y) sum += gather4(Cin, q[r], min(4u, d.y - j), pol_c);
-          }
+          for (int t = 0; t < 3; t++) cmp_n[t] = ldcg(&ctl->cmp[slot][t]);
+          cmp_total = total;
         }
-#pragma unroll
-        for (int o = 4; o > 0; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
+        T = a.items_cmp;
+        n0 = cmp_n[0];
+        n1 = cmp_n[1];
+        n2 = cmp_n[2];
+      }
+
+      // tier 0: one thread per vertex, 32 consecutive items per warp
+      for (uint32_t b0 = gwarp * 32; b0 < n0; b0 += nwarps * 32) {
+        const uint32_t i = b0 + lane;
         int push = 0;
-        if (act && gl == 0) {
-          B dr = finish_vertex(a, Rin, Rout, Cout, v, sum, I, dacc, pol_c);
+        uint32_t v = 0;
+        if (i < n0) {
+          const uint4 item = ldcg(T + i);
+          v = item.x;
+          const R rold = ldcg(Rin + v);
+          const typename S::A ad = __ldg(a.adeg + v);
+          C sum = row_sum_thread(Cin, a.in_col + item.y, item.z, pol_cols, pol_c);
+          B dr = finish_vertex(a, Rout, Cout, v, sum, rold, ad, I, dacc, pol_c);
           my_max = dr > my_max ? dr : my_max;
           my_v++;
-          my_e += d.y;
+          my_e += item.z;
           push = expand && dr > a.ftol && first_expansion(a.xbits, v);
         }
-        if (expand) {
-          uint32_t mask = __ballot_sync(kFull, push);
-          while (mask) {
-            const uint32_t src = __ffs(mask) - 1;
-            mask &= mask - 1;
-            const uint32_t x = __shfl_sync(kFull, v, src);
-            const uint2 od = __ldg(&a.out_rd[x]);
+        if (expand) expand_lanes(push, v);
+      }
+
+      // tier 1: rows of lo < len <= kGroupMax by 8-lane groups, four vertices per warp
+      {
+        const uint32_t grp = lane >> 3, gl = lane & 7;
+        for (uint32_t b0 = gwarp * 4; b0 < n1; b0 += nwarps * 4) {
+          const uint32_t i = b0 + grp;
+          const bool act = i < n1;
+          uint4 item = make_uint4(0, 0, 0, 0);
+          R rold = (R)0;
+          typename S::A ad = (typename S::A)0;
+          C sum = (C)0;
+          if (act) {
+            item = ldcg(T + off1 + i);
+            if (gl == 0) {
+              rold = ldcg(Rin + item.x);
+              ad = __ldg(a.adeg + item.x);
+            }
+            const uint32_t *cols = a.in_col + item.y;
+            uint4 q[2];
+#pragma unroll
+            for (int r = 0; r < 2; r++) {
+              const uint32_t j = 4 * (gl + 8 * r);
+              if (j < item.z) q[r] = ld_cols(cols + j, pol_cols);
+            }
+#pragma unroll
+            for (int r = 0; r < 2; r++) {
+              const uint32_t j = 4 * (gl + 8 * r);
+              if (j < item.z) sum += gather4(Cin, q[r], min(4u, item.z - j), pol_c);
+            }
+          }
+#pragma unroll
+          for (int o = 4; o > 0; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
+          int push = 0;
+          if (act && gl == 0) {
+            B dr = finish_vertex(a, Rout, Cout, item.x, sum, rold, ad, I, dacc, pol_c);
+            my_max = dr > my_max ? dr : my_max;
+            my_v++;
+            my_e += item.z;
+            push = expand && dr > a.ftol && first_expansion(a.xbits, item.x);
+          }
+          if (expand) expand_lanes(push, item.x);
+        }
+      }
+
+      // tier 2: kChunk-edge chunks dealt round-robin to warps (a hub's consecutive chunks
+      // land on different warps); a row split into several chunks is finished by the warp
+      // that completes its last chunk, which adds the partial sums in chunk order
+      C *part = a.partials;
+      for (uint32_t k = gwarp; k < n2; k += nwarps) {
+        const uint4 ch = ldcg(T + off2 + k);
+        const uint32_t v = ch.x;
+        const uint32_t len = ch.z & 0x3FFu;
+        const bool multi = (ch.z >> 31) != 0;
+        R rold = (R)0;
+        typename S::A ad = (typename S::A)0;
+        uint32_t deg = len;
+        if (lane == 0) {
+          rold = ldcg(Rin + v);
+          ad = __ldg(a.adeg + v);
+          if (multi) deg = __ldg(&a.in_rd[v]).y;
+        }
+        const uint32_t *cols = a.in_col + ch.y;
+        uint4 q[4];
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+          const uint32_t j = 4 * (lane + 32 * r);
+          if (j < len) q[r] = ld_cols(cols + j, pol_cols);
+        }
+        C sum = (C)0;
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+          const uint32_t j = 4 * (lane + 32 * r);
+          if (j < len) sum += gather4(Cin, q[r], min(4u, len - j), pol_c);
+        }
+        sum = warp_sum(sum);
+        int finish = 1;
+        if (multi) {
+          // publish this chunk's partial; the last of the row's chunks adds them up
+          const uint32_t nch = (__shfl_sync(kFull, deg, 0) + kChunk - 1) / kChunk;
+          uint32_t old = 0;
+          if (lane == 0) {
+            part[ch.w] = sum;
+            __threadfence();
+            old = atomicAdd(&a.chunk_done[v], 1u);
+          }
+          old = __shfl_sync(kFull, old, 0);
+          finish = old == nch - 1;
+          if (finish) {
+            __threadfence();
+            const uint32_t first = ch.w - ((ch.z >> 10) & 0x1FFFFFu);
+            C tot = (C)0;
+            for (uint32_t c = lane; c < nch; c += 32) tot += ldcg(part + first + c);
+            // lane order then a fixed shuffle tree: the same sum whichever warp finishes
+            sum = warp_sum(tot);
+            if (lane == 0) a.chunk_done[v] = 0;
+          }
+        }
+        if (finish) {
+          int exp_now = 0;
+          if (lane == 0) {
+            B dr = finish_vertex(a, Rout, Cout, v, sum, rold, ad, I, dacc, pol_c);
+            my_max = dr > my_max ? dr : my_max;
+            my_v++;
+            my_e += deg;
+            exp_now = expand && dr > a.ftol && first_expansion(a.xbits, v);
+          }
+          exp_now = __shfl_sync(kFull, exp_now, 0);
+          if (exp_now) {
+            const uint2 od = __ldg(&a.out_rd[v]);
             my_app += warp_mark_range(a, a.out_col + od.x, od.y, 0, 32, slot, cnt, lane);
             if (lane == 0) {
               my_xv++;
@@ -603,79 +696,30 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
           }
         }
       }
-
-      // long rows as kChunk-edge chunks dealt round-robin to warps (a hub's consecutive
-      // chunks land on different warps); a row split into several chunks is finished by
-      // the warp that completes its last chunk, which adds the partial sums in chunk order
-      C *part = a.partials;
-      {
-        for (uint32_t k = gwarp; k < a.n_chunks; k += nwarps) {
-          const uint2 ch = __ldg(&a.chunks[k]);
-          const uint32_t v = ch.x;
-          if (dense && ldcg(a.stamp + v) > (uint16_t)it) continue;
-          const uint2 d = __ldg(&a.in_rd[v]);
-          const uint32_t len = min(kChunk, d.y - ch.y);
-          const uint32_t *cols = a.in_col + d.x + ch.y;
-          uint4 q[4];
-#pragma unroll
-          for (int r = 0; r < 4; r++) {
-            const uint32_t j = 4 * (lane + 32 * r);
-            if (j < len) q[r] = ld_cols(cols + j, pol_cols);
-          }
-          C sum = (C)0;
-#pragma unroll
-          for (int r = 0; r < 4; r++) {
-            const uint32_t j = 4 * (lane + 32 * r);
-            if (j < len) sum += gather4(Cin, q[r], min(4u, len - j), pol_c);
-          }
-          sum = warp_sum(sum);
-          const uint32_t nch = (d.y + kChunk - 1) / kChunk;
-          int finish = 1;
-          if (nch > 1) {
-            // publish this chunk's partial; the last of the row's chunks adds them up
-            uint32_t old = 0;
-            if (lane == 0) {
-              part[k] = sum;
-              __threadfence();
-              old = atomicAdd(&a.chunk_done[v], 1u);
-            }
-            old = __shfl_sync(kFull, old, 0);
-            finish = old == nch - 1;
-            if (finish) {
-              __threadfence();
-              const uint32_t first = k - ch.y / kChunk;
-              C tot = (C)0;
-              for (uint32_t c = lane; c < nch; c += 32) tot += ldcg(part + first + c);
-              // lane order then a fixed shuffle tree: the same sum whichever warp finishes
-              sum = warp_sum(tot);
-              if (lane == 0) a.chunk_done[v] = 0;
-            }
-          }
-          if (finish) {
-            int exp_now = 0;
-            if (lane == 0) {
-              B dr = finish_vertex(a, Rin, Rout, Cout, v, sum, I, dacc, pol_c);
-              my_max = dr > my_max ? dr : my_max;
-              my_v++;
-              my_e += d.y;
-              exp_now = expand && dr > a.ftol && first_expansion(a.xbits, v);
-            }
-            exp_now = __shfl_sync(kFull, exp_now, 0);
-            if (exp_now) {
-              const uint2 od = __ldg(&a.out_rd[v]);
-              my_app += warp_mark_range(a, a.out_col + od.x, od.y, 0, 32, slot, cnt, lane);
-              if (lane == 0) {
-                my_xv++;
-                my_xe += od.y;
-              }
-            }
-          }
-        }
-      }
     } else {
+      // sparse: thread bin, one thread per vertex, 32 consecutive list entries per warp
+      for (uint32_t b0 = gwarp * 32; b0 < cnt[0]; b0 += nwarps * 32) {
+        const uint32_t i = b0 + lane;
+        int push = 0;
+        uint32_t v = 0;
+        if (i < cnt[0]) {
+          v = ldcg(a.list0 + i);
+          const R rold = ldcg(Rin + v);
+          const typename S::A ad = __ldg(a.adeg + v);
+          const uint2 d = __ldg(&a.in_rd[v]);
+          C sum = row_sum_thread(Cin, a.in_col + d.x, d.y, pol_cols, pol_c);
+          B dr = finish_vertex(a, Rout, Cout, v, sum, rold, ad, I, dacc, pol_c);
+          my_max = dr > my_max ? dr : my_max;
+          my_v++;
+          my_e += d.y;
+          push = expand && dr > a.ftol && first_expansion(a.xbits, v);
+        }
+        if (expand) expand_lanes(push, v);
+      }
+
       // sparse: warp bin, one warp per vertex
-      for (uint32_t i = gwarp; i < c1; i += nwarps) {
-        const uint32_t v = ldcg(L1 + i);
+      for (uint32_t i = gwarp; i < cnt[1]; i += nwarps) {
+        const uint32_t v = ldcg(a.list1 + i);
         const uint2 d = __ldg(&a.in_rd[v]);
         const uint32_t *cols = a.in_col + d.x;
         C sum = (C)0;
@@ -686,7 +730,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
         sum = warp_sum(sum);
         int exp_now = 0;
         if (lane == 0) {
-          B dr = finish_vertex(a, Rin, Rout, Cout, v, sum, I, dacc, pol_c);
+          B dr = finish_vertex(a, Rout, Cout, v, sum, ldcg(Rin + v), __ldg(a.adeg + v), I, dacc, pol_c);
           my_max = dr > my_max ? dr : my_max;
           my_v++;
           my_e += d.y;
@@ -709,8 +753,8 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
         __syncthreads();
         const uint32_t idx = s_idx;
         __syncthreads();
-        if (idx >= c2) break;
-        const uint32_t v = ldcg(L2 + idx);
+        if (idx >= cnt[2]) break;
+        const uint32_t v = ldcg(a.list2 + idx);
         const uint2 d = __ldg(&a.in_rd[v]);
         const uint32_t *cols = a.in_col + d.x;
         C sum = (C)0;
@@ -733,7 +777,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
         if (tid == 0) {
           C tot = (C)0;
           for (int w = 0; w < kWarps; w++) tot += s_part[w];
-          B dr = finish_vertex(a, Rin, Rout, Cout, v, tot, I, dacc, pol_c);
+          B dr = finish_vertex(a, Rout, Cout, v, tot, ldcg(Rin + v), __ldg(a.adeg + v), I, dacc, pol_c);
           my_max = dr > my_max ? dr : my_max;
           my_v++;
           my_e += d.y;
@@ -894,12 +938,11 @@ static pr_status launch(Graph *g, RankMode mode, bool start_full) {
   a.list0 = g->list[0];
   a.list1 = g->list[1];
   a.list2 = g->list[2];
-  a.ident = g->ident;
-  a.id_cnt0 = g->ident_cnt[0];
-  a.id_cnt1 = g->ident_cnt[1];
-  a.id_cnt2 = g->ident_cnt[2];
-  a.chunks = g->chunks;
-  a.n_chunks = g->n_chunks;
+  a.items = g->items;
+  a.items_cmp = g->items_cmp;
+  a.it_c0 = g->item_cnt[0];
+  a.it_c1 = g->item_cnt[1];
+  a.it_c2 = g->item_cnt[2];
   a.partials = (typename S::C *)g->partials;
   a.chunk_done = g->chunk_done;
   a.pend_src = g->pend_src;
