@@ -264,9 +264,12 @@ __device__ __forceinline__ uint32_t warp_mark_range(const RankArgs<F32> &a, cons
   return newly_total;
 }
 
-// True the first time v asks (per call): its out-row is then scanned by the caller.
+// True the first time v asks (per call): its out-row is then scanned by the caller.  A
+// plain read first, so a vertex that keeps changing costs one load per iteration, not an
+// atomic.
 __device__ __forceinline__ bool first_expansion(uint32_t *xbits, uint32_t v) {
   uint32_t bit = 1u << (v & 31);
+  if (__ldcg(xbits + (v >> 5)) & bit) return false;
   return !(atomicOr(xbits + (v >> 5), bit) & bit);
 }
 
