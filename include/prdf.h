@@ -135,6 +135,14 @@ pr_status pr_get_csr(pr_graph *g, int32_t dir, uint64_t *offs, uint32_t *cols);
  * into a host array of capacity cap; *count receives the total number. */
 pr_status pr_get_affected(pr_graph *g, uint32_t *out, int64_t cap, int64_t *count);
 
+/* Trace of the last rank call (Static, Naive-dynamic or Dynamic Frontier), from the device
+ * clock: phase_ms = initial marking (phase 0); for each iteration i < *count (at most cap
+ * entries written): iter_ms[i] its duration, affected[i] the vertices it covered, kind[i]
+ * 0 = affected lists, 1 = compacted sweep items reused, 2 = sweep items compacted in this
+ * iteration, 3 = all vertices.  Any of the output arrays may be NULL (host memory). */
+pr_status pr_get_trace(const pr_graph *g, int32_t cap, double *phase_ms, double *iter_ms, int64_t *affected,
+                       int32_t *kind, int32_t *count);
+
 /* Number of CUDA kernels this library has launched in this process (all handles),
  * for accounting of device work.  Never fails. */
 uint64_t pr_kernel_launches(void);

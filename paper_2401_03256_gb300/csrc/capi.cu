@@ -100,6 +100,22 @@ const char *pr_status_string(pr_status s) {
   return "unknown status";
 }
 
+pr_status pr_get_trace(const pr_graph *h, int32_t cap, double *phase_ms, double *iter_ms, int64_t *affected,
+                       int32_t *kind, int32_t *count) {
+  if (!h) return invalid(nullptr, "graph is NULL");
+  const Graph &g = h->g;
+  if (cap < 0) return PR_ERR_INVALID_ARG;
+  const int32_t k = g.trace_ms.empty() ? 0 : (int32_t)g.trace_ms.size() - 1;
+  if (count) *count = k;
+  if (phase_ms) *phase_ms = g.trace_ms.empty() ? 0.0 : g.trace_ms[0];
+  for (int32_t i = 0; i < k && i < cap; i++) {
+    if (iter_ms) iter_ms[i] = g.trace_ms[i + 1];
+    if (affected) affected[i] = g.trace_aff[i];
+    if (kind) kind[i] = g.trace_kind[i];
+  }
+  return PR_OK;
+}
+
 uint64_t pr_kernel_launches(void) { return prdf::g_launches.load(std::memory_order_relaxed); }
 
 const char *pr_last_error(const pr_graph *h) { return h ? h->g.err.c_str() : g_create_err.c_str(); }

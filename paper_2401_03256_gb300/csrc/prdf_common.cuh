@@ -131,6 +131,11 @@ struct RankCtl {
   uint32_t blk_next[kMaxIterLimit + 1];           // dynamic index into the block bin
   uint32_t cmp[kMaxIterLimit + 1][4];             // affected items per tier after a dense compaction
   unsigned long long vproc, eproc, expv, expe, appended;
+  // trace (written by block 0): %globaltimer at kernel start, after phase 0 and after each
+  // iteration's barrier; affected vertices at the start of each iteration; iteration kind
+  unsigned long long t_ns[kMaxIterLimit + 2];
+  uint32_t it_aff[kMaxIterLimit + 1];
+  uint8_t it_kind[kMaxIterLimit + 1];  // 0 sparse, 1 dense (reused items), 2 dense (compacted), 3 full
 };
 
 // Per-block Neumaier partials of the dead-end mass, double-buffered by iteration parity.

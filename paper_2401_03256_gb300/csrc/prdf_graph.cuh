@@ -2,6 +2,7 @@
 #pragma once
 
 #include <string>
+#include <vector>
 
 #include "prdf_common.cuh"
 #include "../../include/prdf.h"
@@ -78,6 +79,9 @@ struct Graph {
   uint32_t *gen_tmp2 = nullptr;
   uint32_t *scan_tmp = nullptr;      // block sums of scans over n
   double ms_apply = 0.0;
+  std::vector<double> trace_ms;      // last rank call: phase 0, then each iteration (device clock)
+  std::vector<int64_t> trace_aff;    // affected vertices at the start of each iteration
+  std::vector<int32_t> trace_kind;   // 0 sparse, 1 dense, 2 dense after compaction, 3 all vertices
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::string err;
 };

@@ -157,14 +157,26 @@ __device__ __forceinline__ uint4 ld_cols(const uint32_t *p, unsigned long long p
                : "l"(p), "l"(pol));
   return r;
 }
+// Contribution gathers.  C of the iteration's input parity is not written during the
+// iteration, and the grid barrier's acquire orders every block after all writes of the
+// previous iteration, so the gathers may be served by L1 (hub contributions are gathered
+// by many rows of the same SM); PRDF_GATHER_L2_ONLY=1 keeps them at L2.
+#ifndef PRDF_GATHER_L2_ONLY
+#define PRDF_GATHER_L2_ONLY 0
+#endif
+#if PRDF_GATHER_L2_ONLY
+#define PRDF_GATHER_COP "cg"
+#else
+#define PRDF_GATHER_COP "ca"
+#endif
 __device__ __forceinline__ long long ld_keep(const long long *p, unsigned long long pol) {
   long long r;
-  asm("ld.global.cg.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(r) : "l"(p), "l"(pol));
+  asm("ld.global." PRDF_GATHER_COP ".L2::cache_hint.b64 %0, [%1], %2;" : "=l"(r) : "l"(p), "l"(pol));
   return r;
 }
 __device__ __forceinline__ float ld_keep(const float *p, unsigned long long pol) {
   float r;
-  asm("ld.global.cg.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(r) : "l"(p), "l"(pol));
+  asm("ld.global." PRDF_GATHER_COP ".L2::cache_hint.f32 %0, [%1], %2;" : "=f"(r) : "l"(p), "l"(pol));
   return r;
 }
 __device__ __forceinline__ void st_keep(long long *p, long long v, unsigned long long pol) {
@@ -436,6 +448,8 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
     else return S::contrib(Dn, a.tele_frac);
   };
 
+  if (blockIdx.x == 0 && tid == 0) ctl->t_ns[0] = globaltimer_ns();
+
   // ---------------------------------------------------------------- phase 0
   if (a.mode == kModeStatic) {
     const R r = a.init;
@@ -467,6 +481,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
   }
   if (a.teleport) block_dead_partial(0);
   if (!grid_sync(ctl, epoch, &s_err)) return;
+  if (blockIdx.x == 0 && tid == 0) ctl->t_ns[1] = globaltimer_ns();
 
   uint32_t cnt[3];
 #pragma unroll
@@ -505,6 +520,10 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
     const bool expand = df && !I.full;
     const uint32_t slot = (uint32_t)it + 1;
     B my_max = 0;
+    if (blockIdx.x == 0 && tid == 0) {
+      ctl->it_aff[it] = I.full ? a.n : cnt[0] + cnt[1] + cnt[2];
+      ctl->it_kind[it] = I.full ? 3 : (dense ? (cnt[0] + cnt[1] + cnt[2] != cmp_total ? 2 : 1) : 0);
+    }
 
     auto expand_lanes = [&](int push, uint32_t v) {
       uint32_t mask = __ballot_sync(kFull, push);
@@ -832,6 +851,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
     }
     iters = (uint32_t)it + 1;
     last_key = dR;
+    if (blockIdx.x == 0 && tid == 0) ctl->t_ns[it + 2] = globaltimer_ns();
     if (dR <= a.tol_key) {
       converged = true;
       break;
@@ -1006,6 +1026,23 @@ pr_status rank_run(Graph *g, RankMode mode, pr_stats *stats) {
   }
   float ms = 0.f;
   CK(cudaEventElapsedTime(&ms, g->ev0, g->ev1));
+  {
+    const uint32_t k = h.iterations;
+    CK(cudaMemcpyAsync(g->ctl_h->t_ns, g->ctl->t_ns, sizeof(unsigned long long) * (k + 2), cudaMemcpyDeviceToHost,
+                       g->st));
+    CK(cudaMemcpyAsync(g->ctl_h->it_aff, g->ctl->it_aff, sizeof(uint32_t) * (k + 1), cudaMemcpyDeviceToHost, g->st));
+    CK(cudaMemcpyAsync(g->ctl_h->it_kind, g->ctl->it_kind, k + 1, cudaMemcpyDeviceToHost, g->st));
+    CK(cudaStreamSynchronize(g->st));
+    g->trace_ms.assign(k + 1, 0.0);
+    g->trace_aff.assign(k, 0);
+    g->trace_kind.assign(k, 0);
+    g->trace_ms[0] = (double)(h.t_ns[1] - h.t_ns[0]) * 1e-6;  // phase 0 (marking)
+    for (uint32_t i = 0; i < k; i++) {
+      g->trace_ms[i + 1] = (double)(h.t_ns[i + 2] - h.t_ns[i + 1]) * 1e-6;
+      g->trace_aff[i] = h.it_aff[i];
+      g->trace_kind[i] = h.it_kind[i];
+    }
+  }
   const bool full = mode != kModeDF || start_full || h.full_from != 0;
   g->last_full = full;
   for (int b = 0; b < 3; b++) g->last_list_cnt[b] = mode == kModeDF ? h.final_cnt[b] : 0;

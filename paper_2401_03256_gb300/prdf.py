@@ -31,7 +31,7 @@ PR_DEADEND_TELEPORT = 1
 EXPORTED = (
     "pr_params_default", "pr_graph_create", "pr_graph_destroy", "pr_apply_batch", "pr_static",
     "pr_naive_dynamic", "pr_dynamic_frontier", "pr_get_ranks", "pr_set_ranks", "pr_graph_info",
-    "pr_get_csr", "pr_get_affected", "pr_kernel_launches", "pr_last_error", "pr_status_string",
+    "pr_get_csr", "pr_get_affected", "pr_get_trace", "pr_kernel_launches", "pr_last_error", "pr_status_string",
 )
 
 
@@ -91,6 +91,8 @@ def load(path: str = LIB_PATH):
     lib.pr_get_csr.argtypes = [vp, i32, vp, vp]
     lib.pr_get_affected.restype = ctypes.c_int
     lib.pr_get_affected.argtypes = [vp, vp, i64, ctypes.POINTER(i64)]
+    lib.pr_get_trace.restype = ctypes.c_int
+    lib.pr_get_trace.argtypes = [vp, i32, vp, vp, vp, vp, ctypes.POINTER(i32)]
     lib.pr_kernel_launches.restype = ctypes.c_uint64
     lib.pr_kernel_launches.argtypes = []
     lib.pr_last_error.restype = ctypes.c_char_p
@@ -224,6 +226,21 @@ def pr_get_csr(h: int, direction: int):
     return off, col[:m]
 
 
+def pr_get_trace(h: int) -> dict:
+    """Device-clock trace of the last rank call: phase-0 ms and per-iteration ms, affected
+    counts and kinds (0 lists, 1 dense reused, 2 dense compacted, 3 all vertices)."""
+    cnt = ctypes.c_int32()
+    _check(load().pr_get_trace(h, 0, None, None, None, None, ctypes.byref(cnt)), h)
+    k = cnt.value
+    ph = ctypes.c_double()
+    ms = np.zeros(max(k, 1), np.float64)
+    aff = np.zeros(max(k, 1), np.int64)
+    kind = np.zeros(max(k, 1), np.int32)
+    _check(load().pr_get_trace(h, k, ctypes.byref(ph), ms.ctypes.data, aff.ctypes.data, kind.ctypes.data,
+                               ctypes.byref(cnt)), h)
+    return {"phase_ms": ph.value, "iter_ms": ms[:k], "affected": aff[:k], "kind": kind[:k]}
+
+
 def pr_kernel_launches() -> int:
     """Kernels launched by libprdf.so in this process so far."""
     return int(load().pr_kernel_launches())
@@ -267,6 +284,9 @@ class Graph:
 
     def affected(self):
         return pr_get_affected(self.h)
+
+    def trace(self):
+        return pr_get_trace(self.h)
 
     def info(self):
         return pr_graph_info(self.h)
