@@ -605,6 +605,8 @@ pr_status graph_build(Graph *g, uint64_t m_in, const uint32_t *src_d, const uint
   CK(dalloc(&g->chunk_done, n));
   CK(cudaMemsetAsync(g->chunk_done, 0, 4ull * n, st));
   CK(dalloc(&g->item_pos, n));
+  CK(dalloc(&g->hub_v, n));
+  CK(dalloc(&g->hub_base, n));
   for (int i = 0; i < 3; i++) CK(dalloc(&g->list[i], n));
   CK(dalloc(&g->ident, n));
   CK(dalloc(&g->dead, n));
@@ -963,6 +965,8 @@ void graph_free(Graph *g) {
   cudaFree(g->items);
   cudaFree(g->items_cmp);
   cudaFree(g->item_pos);
+  cudaFree(g->hub_v);
+  cudaFree(g->hub_base);
   cudaFree(g->partials);
   cudaFree(g->chunk_done);
   for (int i = 0; i < 3; i++) cudaFree(g->list[i]);

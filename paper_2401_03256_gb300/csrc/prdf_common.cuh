@@ -130,6 +130,7 @@ struct RankCtl {
   uint32_t tail[kMaxIterLimit + 2][4];            // per-iteration appends per bin ([0] = initial marks)
   uint32_t blk_next[kMaxIterLimit + 1];           // dynamic index into the block bin
   uint32_t cmp[kMaxIterLimit + 1][4];             // affected items per tier after a dense compaction
+  unsigned long long hubq[kMaxIterLimit + 2];     // per slot: queued long out-rows << 32 | their chunks
   unsigned long long vproc, eproc, expv, expe, appended;
   // trace (written by block 0): %globaltimer at kernel start, after phase 0 and after each
   // iteration's barrier; affected vertices at the start of each iteration; iteration kind

@@ -53,6 +53,8 @@ struct Graph {
   uint64_t chunk_cap = 0;
   void *partials = nullptr;          // one contribution-typed partial sum per chunk
   uint32_t *chunk_done = nullptr;    // per vertex: chunks finished in this iteration (0 between)
+  uint32_t *hub_v = nullptr;         // long out-rows queued for cooperative marking (per slot)
+  uint32_t *hub_base = nullptr;      // their first chunk number (ascending)
   uint32_t *dead = nullptr;          // vertices with out-degree 0 (teleport mode)
   uint32_t n_dead = 0;
   bool dead_dirty = true;

@@ -47,6 +47,7 @@ constexpr int kWarps = kRankBlock / 32;
 constexpr uint32_t kFull = 0xffffffffu;
 constexpr uint32_t kDenseDiv = 16;  // dense iteration once affected > n / kDenseDiv
 constexpr uint16_t kNoStamp = 0xFFFF;
+constexpr uint32_t kInlineOut = 128;  // longer out-rows are marked by the whole grid (hub queue)
 #ifndef PRDF_RANK_MIN_BLOCKS
 #define PRDF_RANK_MIN_BLOCKS 4  // resident blocks per SM the register budget must allow
 #endif
@@ -100,6 +101,7 @@ struct RankArgs {
   uint32_t it_c0, it_c1, it_c2;
   typename S::C *partials;
   uint32_t *chunk_done;
+  uint32_t *hub_v, *hub_base;  // hub queue of the current slot
   const uint32_t *pend_src;
   uint32_t n_pend_src;
   const uint32_t *pend_tgt;
@@ -159,10 +161,10 @@ __device__ __forceinline__ uint4 ld_cols(const uint32_t *p, unsigned long long p
 }
 // Contribution gathers.  C of the iteration's input parity is not written during the
 // iteration, and the grid barrier's acquire orders every block after all writes of the
-// previous iteration, so the gathers may be served by L1 (hub contributions are gathered
-// by many rows of the same SM); PRDF_GATHER_L2_ONLY=1 keeps them at L2.
+// previous iteration, so the gathers may be served by L1 (PRDF_GATHER_L2_ONLY=0); measured
+// slower on GB300 than keeping them at L2 (the default).
 #ifndef PRDF_GATHER_L2_ONLY
-#define PRDF_GATHER_L2_ONLY 0
+#define PRDF_GATHER_L2_ONLY 1
 #endif
 #if PRDF_GATHER_L2_ONLY
 #define PRDF_GATHER_COP "cg"
@@ -283,6 +285,46 @@ __device__ __forceinline__ bool first_expansion(uint32_t *xbits, uint32_t v) {
   uint32_t bit = 1u << (v & 31);
   if (__ldcg(xbits + (v >> 5)) & bit) return false;
   return !(atomicOr(xbits + (v >> 5), bit) & bit);
+}
+
+// Marks the out-neighbours of v for iteration `slot`: short out-rows by the calling warp,
+// long ones queued for the cooperative pass that follows the iteration's barrier (entry
+// index and chunk base are reserved by one 64-bit atomic, so bases ascend with the index).
+// Called by a whole warp; returns the vertices this warp newly marked.
+template <bool F32>
+__device__ __forceinline__ uint32_t expand_vertex(const RankArgs<F32> &a, uint32_t v, uint2 od, uint32_t slot,
+                                                  const uint32_t cnt[3], uint32_t lane) {
+  if (od.y <= kInlineOut) return warp_mark_range(a, a.out_col + od.x, od.y, 0, 32, slot, cnt, lane);
+  if (lane == 0) {
+    const uint32_t nch = (od.y + kChunk - 1) / kChunk;
+    const unsigned long long old = atomicAdd(&a.ctl->hubq[slot], (1ull << 32) | nch);
+    const uint32_t e = (uint32_t)(old >> 32);
+    a.hub_v[e] = v;
+    a.hub_base[e] = (uint32_t)old;
+  }
+  return 0;
+}
+
+// The cooperative pass over the queued long out-rows of `slot`: kChunk-entry chunks
+// dealt round-robin to all warps of the grid.
+template <bool F32>
+__device__ uint32_t hub_pass(const RankArgs<F32> &a, uint32_t slot, const uint32_t cnt[3], uint32_t lane,
+                             uint32_t gwarp, uint32_t nwarps) {
+  const unsigned long long hq = __ldcg(&a.ctl->hubq[slot]);
+  const uint32_t ne = (uint32_t)(hq >> 32), K = (uint32_t)hq;
+  uint32_t newly = 0;
+  for (uint32_t k = gwarp; k < K; k += nwarps) {
+    uint32_t lo = 0, hi = ne;
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (__ldcg(a.hub_base + mid) <= k) lo = mid; else hi = mid;
+    }
+    const uint32_t v = __ldcg(a.hub_v + lo), c = k - __ldcg(a.hub_base + lo);
+    const uint2 od = __ldg(&a.out_rd[v]);
+    const uint32_t start = c * kChunk;
+    newly += warp_mark_range(a, a.out_col + od.x + start, min(kChunk, od.y - start), 0, 32, slot, cnt, lane);
+  }
+  return newly;
 }
 
 template <class C>
@@ -471,7 +513,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
     for (uint32_t k = gwarp; k < a.n_pend_src; k += nwarps) {
       uint32_t u = __ldg(a.pend_src + k);
       uint2 od = __ldg(&a.out_rd[u]);
-      my_app += warp_mark_range(a, a.out_col + od.x, od.y, 0, 32, 0, zero_cnt, lane);
+      my_app += expand_vertex(a, u, od, 0, zero_cnt, lane);
     }
     // deleted targets, 32 per warp round
     for (uint32_t k0 = gwarp * 32; k0 < a.n_pend_tgt; k0 += nwarps * 32) {
@@ -481,6 +523,10 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
   }
   if (a.teleport) block_dead_partial(0);
   if (!grid_sync(ctl, epoch, &s_err)) return;
+  if (df && __ldcg(&ctl->hubq[0]) != 0) {
+    my_app += hub_pass(a, 0, zero_cnt, lane, gwarp, nwarps);
+    if (!grid_sync(ctl, epoch, &s_err)) return;
+  }
   if (blockIdx.x == 0 && tid == 0) ctl->t_ns[1] = globaltimer_ns();
 
   uint32_t cnt[3];
@@ -532,7 +578,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
         mask &= mask - 1;
         const uint32_t x = __shfl_sync(kFull, v, src);
         const uint2 od = __ldg(&a.out_rd[x]);
-        my_app += warp_mark_range(a, a.out_col + od.x, od.y, 0, 32, slot, cnt, lane);
+        my_app += expand_vertex(a, x, od, slot, cnt, lane);
         if (lane == 0) {
           my_xv++;
           my_xe += od.y;
@@ -710,7 +756,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
           exp_now = __shfl_sync(kFull, exp_now, 0);
           if (exp_now) {
             const uint2 od = __ldg(&a.out_rd[v]);
-            my_app += warp_mark_range(a, a.out_col + od.x, od.y, 0, 32, slot, cnt, lane);
+            my_app += expand_vertex(a, v, od, slot, cnt, lane);
             if (lane == 0) {
               my_xv++;
               my_xe += od.y;
@@ -761,7 +807,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
         exp_now = __shfl_sync(kFull, exp_now, 0);
         if (exp_now) {
           const uint2 od = __ldg(&a.out_rd[v]);
-          my_app += warp_mark_range(a, a.out_col + od.x, od.y, 0, 32, slot, cnt, lane);
+          my_app += expand_vertex(a, v, od, slot, cnt, lane);
           if (lane == 0) {
             my_xv++;
             my_xe += od.y;
@@ -808,7 +854,11 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
         __syncthreads();
         if (s_expand) {
           const uint2 od = __ldg(&a.out_rd[v]);
-          my_app += warp_mark_range(a, a.out_col + od.x, od.y, wib * 32, kRankBlock, slot, cnt, lane);
+          if (od.y <= kInlineOut) {
+            my_app += warp_mark_range(a, a.out_col + od.x, od.y, wib * 32, kRankBlock, slot, cnt, lane);
+          } else if (wib == 0) {
+            my_app += expand_vertex(a, v, od, slot, cnt, lane);
+          }
           if (tid == 0) {
             my_xv++;
             my_xe += od.y;
@@ -832,6 +882,10 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
     }
     if (a.teleport) block_dead_partial((it + 1) & 1);
     if (!grid_sync(ctl, epoch, &s_err)) return;
+    if (expand && __ldcg(&ctl->hubq[slot]) != 0) {
+      my_app += hub_pass(a, slot, cnt, lane, gwarp, nwarps);
+      if (!grid_sync(ctl, epoch, &s_err)) return;
+    }
 
     const unsigned long long dR = __ldcg(&ctl->dR_bits[it]);
     if (df && !I.full) {
@@ -968,6 +1022,8 @@ static pr_status launch(Graph *g, RankMode mode, bool start_full) {
   a.it_c2 = g->item_cnt[2];
   a.partials = (typename S::C *)g->partials;
   a.chunk_done = g->chunk_done;
+  a.hub_v = g->hub_v;
+  a.hub_base = g->hub_base;
   a.pend_src = g->pend_src;
   a.n_pend_src = g->n_pend_src;
   a.pend_tgt = g->pend_tgt;
