@@ -359,6 +359,106 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------- batched form ----
+
+def run_batched(args, rank: int, world: int, local_rank: int):
+    """Batched form (config 4): 256 independent R-MAT graphs (scales uniform in 10..18, edge
+    factor 8), each with its own 80/20 batch of f ~ log-uniform [1e-4, 1e-2] of its edges;
+    one pr_apply_batch for all graphs and one Dynamic Frontier launch (CUDA-graph replay,
+    autotuned bins), FP32 ranks.  Compared with the same updates as 256 standalone handles
+    called one after another.  value = ms per batched update (apply + DF)."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2401_03256_gb300 import build as libbuild
+
+    libbuild.build()
+    from paper_2401_03256_gb300 import prdf
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    rng = np.random.default_rng(1 + rank)
+    G = args.graphs
+    scales = rng.integers(10, 19, G)
+    gs = [synth.rmat(int(s), 8, seed=1000 * (1 + rank) + i) for i, s in enumerate(scales)]
+    fr = np.exp(rng.uniform(np.log(1e-4), np.log(1e-2), G))
+    firsts = np.cumsum([0] + [g.n for g in gs])
+    src = np.concatenate([g.src.astype(np.uint64) + firsts[i] for i, g in enumerate(gs)]).astype(np.uint32)
+    dst = np.concatenate([g.dst.astype(np.uint64) + firsts[i] for i, g in enumerate(gs)]).astype(np.uint32)
+    params = prdf.pr_params_default()
+    params.precision = prdf.PR_F32 if args.precision != "fp64" else prdf.PR_F64
+    W, K = args.warmup, args.steps
+    streams = [synth.BatchStream(g, seed=77 + i) for i, g in enumerate(gs)]
+    steps = []
+    for _ in range(W + K):
+        bs = [s.next(float(fr[i])) for i, s in enumerate(streams)]
+        off = lambda a, i: (a.astype(np.uint64) + firsts[i]).astype(np.uint32)
+        comb = [np.concatenate([off(getattr(b, k), i) for i, b in enumerate(bs)])
+                for k in ("del_src", "del_dst", "ins_src", "ins_dst")]
+        steps.append((bs, comb))
+    stream = torch.cuda.Stream(device=dev)
+    res = {}
+    with torch.cuda.stream(stream):
+        B = prdf.Graph.batched([g.n for g in gs], src, dst, params, stream.cuda_stream)
+        tune = B.autotune(6)
+        B.set_graph_launch(True)
+        B.static()
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+        times, dfms, apms, iters = [], [], [], []
+        l0 = None
+        for i in range(W + K):
+            if i == W:
+                torch.cuda.synchronize(dev)
+                l0 = prdf.pr_kernel_launches()
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            t = time.perf_counter()
+            B.apply(*steps[i][1])
+            st = B.frontier()
+            torch.cuda.synchronize(dev)
+            if i >= W:
+                times.append((time.perf_counter() - t) * 1e3)
+                dfms.append(st.ms_rank)
+                apms.append(st.ms_apply)
+                iters.append(max(c.iterations for c in B.component_stats()))
+        launches = prdf.pr_kernel_launches() - l0
+        B.close()
+        # the same updates, one standalone handle per graph, called one after another
+        As = [prdf.Graph(g.n, g.src, g.dst, params, stream.cuda_stream) for g in gs]
+        for A in As:
+            A.static()
+        seq = []
+        for i in range(W + K):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            t = time.perf_counter()
+            for j, A in enumerate(As):
+                b = steps[i][0][j]
+                A.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+                A.frontier()
+            torch.cuda.synchronize(dev)
+            if i >= W:
+                seq.append((time.perf_counter() - t) * 1e3)
+        for A in As:
+            A.close()
+    value = statistics.median(times)
+    line = {
+        "metric": "batched form: ms per update of all graphs (apply + Dynamic Frontier, one launch)",
+        "value": value, "unit": "ms", "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": value,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision != "fp64" else "i64", "data": "synthetic",
+        "config": {"workload": f"{G} R-MAT graphs, scales U{{10..18}}, edge factor 8, own 80/20 batch of "
+                               f"f ~ logU[1e-4, 1e-2] each", "vertices": int(firsts[-1]), "edges": int(src.size),
+                   "precision": args.precision, "launch": "CUDA graph replay", "tuning": tune.as_dict()},
+        "df_ms_median": statistics.median(dfms), "apply_ms_median": statistics.median(apms),
+        "max_graph_iterations": max(iters), "sequential_ms_median": statistics.median(seq),
+        "speedup_vs_sequential": statistics.median(seq) / value, "gpu_launches": launches,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+
+
 # -------------------------------------------------------- reference arm ----
 
 def run_reference(args, rank: int, world: int):
@@ -414,6 +514,9 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-timeout", type=float, default=600.0)
+    ap.add_argument("--config", choices=["plain", "batched"], default="plain",
+                    help="plain: the headline workload (R-MAT s22 sweep); batched: the batched form")
+    ap.add_argument("--graphs", type=int, default=256, help="graphs of the batched form")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -422,6 +525,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.config == "batched":
+        run_batched(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

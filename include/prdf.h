@@ -88,6 +88,45 @@ void pr_params_default(pr_params *params);
 pr_status pr_graph_create(uint32_t n, int64_t m, const uint32_t *src, const uint32_t *dst,
                           const pr_params *params, void *cuda_stream, pr_graph **out);
 
+/* Batched form: ncomp (1..1024) independent graphs in one handle, updated together.
+ * Vertex ids are global: graph c owns [first_c, first_c + comp_n[c]) with
+ * first_c = comp_n[0] + ... + comp_n[c-1] (each comp_n[c] >= 1).  src/dst hold the edges of
+ * all graphs in global ids; an edge (or later a batch pair) joining two graphs is rejected
+ * with PR_ERR_INVALID_ARG.  pr_apply_batch takes one combined batch for all graphs, and each
+ * rank call runs every graph in one persistent launch: graph c uses its own (1 - alpha)/n_c
+ * and starting rank 1/n_c (Eq. 1 per graph) and its own convergence test, and stops
+ * updating once converged, so its ranks are those of a run of graph c alone.  Self-loop
+ * dead-end mode only.  Per-graph results: pr_get_component_stats. */
+pr_status pr_graph_create_batched(int32_t ncomp, const uint32_t *comp_n, int64_t m, const uint32_t *src,
+                                  const uint32_t *dst, const pr_params *params, void *cuda_stream, pr_graph **out);
+
+/* Per-graph statistics of the last rank call of a batched handle (ncomp entries, host):
+ * iterations, converged, affected_final, last_delta; ms_rank is the whole launch. */
+pr_status pr_get_component_stats(const pr_graph *g, pr_stats *stats, int32_t ncomp);
+
+/* Work distribution of the rank kernel (results do not depend on it): in-degree thresholds
+ * of the thread and block bins, the dense-iteration divisor (an iteration sweeps the
+ * compacted affected set once it exceeds n / dense_div vertices) and the resident blocks per
+ * SM of the persistent launch.  ms is the time the autotuner measured (0 otherwise). */
+typedef struct {
+    int32_t bin_lo, bin_hi, dense_div, blocks_per_sm;
+    double ms;
+} pr_tuning;
+
+/* Sets the tuning (rebuilds the degree-tiered sweep order if bin_lo changes). */
+pr_status pr_set_tuning(pr_graph *g, const pr_tuning *t);
+pr_status pr_get_tuning(const pr_graph *g, pr_tuning *t);
+
+/* Autotuner: times sweep_iters-iteration Naive-dynamic sweeps of this graph for each
+ * candidate bin_lo (4, 8, 16, 32) and blocks per SM, keeps the fastest, restores the ranks
+ * and pending marks, and returns the choice in *chosen (may be NULL). */
+pr_status pr_autotune(pr_graph *g, int32_t sweep_iters, pr_tuning *chosen);
+
+/* enable != 0: rank calls replay one CUDA graph (control-block reset + the cooperative
+ * persistent kernel), captured on first use; only the kernel's arguments change between
+ * replays. */
+pr_status pr_set_graph_launch(pr_graph *g, int32_t enable);
+
 /* Frees all device memory of the handle.  NULL is accepted. */
 pr_status pr_graph_destroy(pr_graph *g);
 

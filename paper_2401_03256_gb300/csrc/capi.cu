@@ -73,6 +73,8 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 extern "C" {
 
+static pr_status ensure_stage(pr_graph *h);
+
 void pr_params_default(pr_params *p) {
   if (!p) return;
   std::memset(p, 0, sizeof(*p));
@@ -120,8 +122,133 @@ uint64_t pr_kernel_launches(void) { return prdf::g_launches.load(std::memory_ord
 
 const char *pr_last_error(const pr_graph *h) { return h ? h->g.err.c_str() : g_create_err.c_str(); }
 
+static pr_status create_impl(uint32_t n, int64_t m, const uint32_t *src, const uint32_t *dst, const pr_params *params,
+                             void *cuda_stream, const std::vector<uint32_t> *comp_n, pr_graph **out);
+
 pr_status pr_graph_create(uint32_t n, int64_t m, const uint32_t *src, const uint32_t *dst, const pr_params *params,
                           void *cuda_stream, pr_graph **out) {
+  return create_impl(n, m, src, dst, params, cuda_stream, nullptr, out);
+}
+
+pr_status pr_graph_create_batched(int32_t ncomp, const uint32_t *comp_n, int64_t m, const uint32_t *src,
+                                  const uint32_t *dst, const pr_params *params, void *cuda_stream, pr_graph **out) {
+  if (!out) return invalid(nullptr, "out is NULL");
+  *out = nullptr;
+  if (ncomp < 1 || ncomp > (int32_t)prdf::kMaxComponents || !comp_n)
+    return invalid(nullptr, "ncomp must be in [1, 1024] with comp_n given");
+  std::vector<uint32_t> cn(comp_n, comp_n + ncomp);
+  uint64_t total = 0;
+  for (uint32_t x : cn) {
+    if (x == 0) return invalid(nullptr, "every graph needs at least one vertex");
+    total += x;
+  }
+  if (total > 0xFFFFFFFFull) return invalid(nullptr, "more than 2^32 - 1 vertices in all");
+  pr_params p;
+  if (params) p = *params; else pr_params_default(&p);
+  if (p.dead_end == PR_DEADEND_TELEPORT && ncomp > 1)
+    return invalid(nullptr, "batched handles use self-loops for dead ends");
+  return create_impl((uint32_t)total, m, src, dst, &p, cuda_stream, ncomp > 1 ? &cn : nullptr, out);
+}
+
+pr_status pr_get_component_stats(const pr_graph *h, pr_stats *stats, int32_t ncomp) {
+  if (!h) return invalid(nullptr, "graph is NULL");
+  if (!stats || ncomp != (int32_t)h->g.ncomp) return PR_ERR_INVALID_ARG;
+  if (h->g.ncomp == 1) return PR_ERR_INVALID_ARG;
+  for (int32_t c = 0; c < ncomp; c++) stats[c] = h->g.comp_stats[c];
+  return PR_OK;
+}
+
+pr_status pr_set_tuning(pr_graph *h, const pr_tuning *t) {
+  if (!h) return invalid(nullptr, "graph is NULL");
+  Graph &g = h->g;
+  if (!t || t->bin_lo < 1 || t->bin_hi < t->bin_lo || t->dense_div < 1 || t->blocks_per_sm < 1 ||
+      t->blocks_per_sm * g.sm_count > g.rank_grid_max)
+    return invalid(&g, "need 1 <= bin_lo <= bin_hi, dense_div >= 1, blocks_per_sm within the resident limit");
+  DeviceGuard dg(g.device);
+  if (t->bin_lo != g.p.bin_lo) g.ident_dirty = true;
+  g.p.bin_lo = t->bin_lo;
+  g.p.bin_hi = t->bin_hi;
+  g.dense_div = (uint32_t)t->dense_div;
+  g.rank_grid = t->blocks_per_sm * g.sm_count;
+  return prdf::graph_refresh_ident(&g);
+}
+
+pr_status pr_get_tuning(const pr_graph *h, pr_tuning *t) {
+  if (!h || !t) return invalid(nullptr, "NULL argument");
+  const Graph &g = h->g;
+  t->bin_lo = g.p.bin_lo;
+  t->bin_hi = g.p.bin_hi;
+  t->dense_div = (int32_t)g.dense_div;
+  t->blocks_per_sm = g.rank_grid / g.sm_count;
+  t->ms = 0.0;
+  return PR_OK;
+}
+
+pr_status pr_set_graph_launch(pr_graph *h, int32_t enable) {
+  if (!h) return invalid(nullptr, "graph is NULL");
+  h->g.use_graph = enable != 0;
+  return PR_OK;
+}
+
+// Autotuner: times Naive-dynamic sweeps of sweep_iters iterations (the full-sweep cost the
+// thresholds steer) for every candidate bin_lo x blocks-per-SM, keeps the fastest, and
+// restores the ranks.  Results do not depend on the choice.
+pr_status pr_autotune(pr_graph *h, int32_t sweep_iters, pr_tuning *chosen) {
+  if (!h) return invalid(nullptr, "graph is NULL");
+  Graph &g = h->g;
+  if (sweep_iters < 1 || sweep_iters > 100) return invalid(&g, "sweep_iters must be in [1, 100]");
+  DeviceGuard dg(g.device);
+  pr_status rc = ensure_stage(h);
+  if (rc != PR_OK) return rc;
+  if ((rc = prdf::rank_get(&g, h->stage)) != PR_OK) return rc;
+  const int32_t keep_iter = g.p.max_iter;
+  const uint32_t keep_pend_src = g.n_pend_src, keep_pend_tgt = g.n_pend_tgt;
+  const bool keep_all = g.pend_all;
+  const double keep_apply = g.ms_apply;
+  pr_tuning cur{};
+  pr_get_tuning(h, &cur);
+  pr_tuning best = cur;
+  best.ms = 1e30;
+  const int32_t los[] = {4, 8, 16, 32};
+  const int per_sm_max = std::max(1, g.rank_grid_max / g.sm_count);
+  g.p.max_iter = sweep_iters;
+  for (int32_t lo : los) {
+    for (int bps = std::max(1, per_sm_max - 2); bps <= per_sm_max; bps++) {
+      pr_tuning t = cur;
+      t.bin_lo = lo;
+      t.bin_hi = std::max(cur.bin_hi, lo);
+      t.blocks_per_sm = bps;
+      if ((rc = pr_set_tuning(h, &t)) != PR_OK) break;
+      pr_stats st;
+      double ms = 1e30;
+      for (int rep = 0; rep < 2 && rc == PR_OK; rep++) {  // best of two
+        g.n_pend_src = 0;
+        g.n_pend_tgt = 0;
+        if ((rc = prdf::rank_run(&g, prdf::kModeNaive, &st)) == PR_OK) ms = std::min(ms, st.ms_rank);
+        if (rc == PR_OK) rc = prdf::rank_set(&g, h->stage);
+      }
+      if (rc != PR_OK) break;
+      if (ms < best.ms) {
+        best = t;
+        best.ms = ms;
+      }
+    }
+    if (rc != PR_OK) break;
+  }
+  g.p.max_iter = keep_iter;
+  g.n_pend_src = keep_pend_src;
+  g.n_pend_tgt = keep_pend_tgt;
+  g.pend_all = keep_all;
+  g.ms_apply = keep_apply;
+  if (rc != PR_OK) return rc;
+  if ((rc = pr_set_tuning(h, &best)) != PR_OK) return rc;
+  if ((rc = prdf::rank_set(&g, h->stage)) != PR_OK) return rc;
+  if (chosen) *chosen = best;
+  return PR_OK;
+}
+
+static pr_status create_impl(uint32_t n, int64_t m, const uint32_t *src, const uint32_t *dst, const pr_params *params,
+                             void *cuda_stream, const std::vector<uint32_t> *comp_n, pr_graph **out) {
   if (!out) return invalid(nullptr, "out is NULL");
   *out = nullptr;
   if (n == 0) return invalid(nullptr, "n must be >= 1");
@@ -170,6 +297,7 @@ pr_status pr_graph_create(uint32_t n, int64_t m, const uint32_t *src, const uint
     }
     rc = prdf::graph_build(&g, (uint64_t)m, sd, dd);
     if (rc != PR_OK) break;
+    if (comp_n && (rc = prdf::components_setup(&g, *comp_n)) != PR_OK) break;
     rc = prdf::rank_setup(&g);
   } while (0);
   if (tmp) {

@@ -169,7 +169,7 @@ __device__ __forceinline__ bool sorted_has(const uint64_t *a, uint64_t n, uint64
 
 __global__ void k_batch_keys(const uint32_t *ds, const uint32_t *dd, uint64_t nd, const uint32_t *is,
                              const uint32_t *id, uint64_t ni, uint32_t n, int b, uint64_t *kd, uint64_t *ki,
-                             ApplyCtl *actl) {
+                             const uint16_t *comp, ApplyCtl *actl) {
   uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nd + ni) return;
   uint64_t u, v;
@@ -177,6 +177,9 @@ __global__ void k_batch_keys(const uint32_t *ds, const uint32_t *dd, uint64_t nd
   uint64_t key;
   if (u >= n || v >= n) {
     atomicOr(&actl->bad_id, 1u);
+    key = kSentinel;
+  } else if (comp && comp[u] != comp[v]) {
+    atomicOr(&actl->bad_comp, 1u);
     key = kSentinel;
   } else {
     key = u == v ? kSentinel : ((u << b) | v);
@@ -712,7 +715,7 @@ pr_status graph_apply(Graph *g, uint64_t nd, const uint32_t *ds, const uint32_t 
   h.tail_in = g->in.used;
   CK(cudaMemcpyAsync(g->actl, &h, sizeof(ApplyCtl), cudaMemcpyHostToDevice, st));
 
-  k_batch_keys<<<grid_for(N), 256, 0, st>>>(ds, dd, nd, is, id, ni, g->n, b, s.kd, s.ki, g->actl); count_launch();
+  k_batch_keys<<<grid_for(N), 256, 0, st>>>(ds, dd, nd, is, id, ni, g->n, b, s.kd, s.ki, g->comp, g->actl); count_launch();
   uint64_t *kd = sort_u64(s.kd, s.tmp, nd, 2 * b, s.radix_hist, s.scan_tmp, st);
   uint64_t *ki = sort_u64(s.ki, s.tmp2, ni, 2 * b, s.radix_hist, s.scan_tmp, st);
   k_filter<<<grid_for(N), 256, 0, st>>>(kd, nd, ki, ni, g->out.rd, g->out.col, b, s.flags); count_launch();
@@ -726,6 +729,10 @@ pr_status graph_apply(Graph *g, uint64_t nd, const uint32_t *ds, const uint32_t 
   if (h.bad_id) {
     g->err = "vertex id out of range";
     return PR_ERR_VERTEX_RANGE;
+  }
+  if (h.bad_comp) {
+    g->err = "a pair joins two different graphs of a batched handle";
+    return PR_ERR_INVALID_ARG;
   }
   const uint32_t K = h.n_eff;
   const uint32_t K_del = h.n_eff_del;
@@ -947,6 +954,105 @@ pr_status graph_refresh_dead(Graph *g) {
   return PR_OK;
 }
 
+__global__ void k_fill_comp(uint16_t *comp, uint32_t first, uint32_t count, uint16_t c) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) comp[first + i] = c;
+}
+
+// One thread per vertex: flags an out-edge that leaves the vertex's graph.
+__global__ void k_check_comp(const uint2 *rd, const uint32_t *col, const uint16_t *comp, uint32_t n, uint32_t *bad) {
+  uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= n) return;
+  uint2 d = rd[u];
+  for (uint32_t j = 0; j < d.y; j++)
+    if (comp[col[d.x + j]] != comp[u]) {
+      atomicOr(bad, 1u);
+      return;
+    }
+}
+
+template <bool F32>
+__global__ void k_init_comp_rank(const uint16_t *comp, uint32_t n, const typename Store<F32>::R *init,
+                                 const typename Store<F32>::A *adeg, typename Store<F32>::R *R0,
+                                 typename Store<F32>::R *R1, typename Store<F32>::C *C0, typename Store<F32>::C *C1) {
+  using S = Store<F32>;
+  uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  typename S::R r = init[comp[v]];
+  typename S::C c = S::contrib(r, adeg[v]);
+  R0[v] = r;
+  R1[v] = r;
+  C0[v] = c;
+  C1[v] = c;
+}
+
+template <bool F32>
+__global__ void k_comp_consts(const uint32_t *first, uint32_t ncomp, double alpha, typename Store<F32>::R *base,
+                              typename Store<F32>::R *init) {
+  using S = Store<F32>;
+  uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncomp) return;
+  double nc = (double)(first[c + 1] - first[c]);
+  base[c] = S::from_double((1.0 - alpha) / nc);
+  init[c] = S::from_double(1.0 / nc);
+}
+
+pr_status components_setup(Graph *g, const std::vector<uint32_t> &comp_n) {
+  const uint32_t n = g->n, nc = (uint32_t)comp_n.size();
+  cudaStream_t st = g->st;
+  g->ncomp = nc;
+  g->comp_first.assign(nc + 1, 0);
+  for (uint32_t c = 0; c < nc; c++) g->comp_first[c + 1] = g->comp_first[c] + comp_n[c];
+  CK(dalloc(&g->comp, n));
+  for (uint32_t c = 0; c < nc; c++) {
+    k_fill_comp<<<grid_for(comp_n[c]), 256, 0, st>>>(g->comp, g->comp_first[c], comp_n[c], (uint16_t)c);
+    count_launch();
+  }
+  uint32_t *bad = nullptr, *first_d = nullptr;
+  CK(dalloc(&bad, 1));
+  CK(dalloc(&first_d, nc + 1));
+  CK(cudaMemsetAsync(bad, 0, 4, st));
+  CK(cudaMemcpyAsync(first_d, g->comp_first.data(), 4ull * (nc + 1), cudaMemcpyHostToDevice, st));
+  k_check_comp<<<grid_for(n), 256, 0, st>>>(g->out.rd, g->out.col, g->comp, n, bad);
+  count_launch();
+  uint32_t hbad = 0;
+  CK(cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  cudaFree(bad);
+  if (hbad) {
+    cudaFree(first_d);
+    g->err = "an edge joins two different graphs of a batched handle";
+    return PR_ERR_INVALID_ARG;
+  }
+  CK(cudaMalloc(&g->comp_base, 8ull * nc));
+  CK(cudaMalloc(&g->comp_init, 8ull * nc));
+  CK(dalloc(&g->dRc, 3ull * nc));
+  CK(dalloc(&g->comp_out, 4ull * nc));
+  CK(dalloc(&g->comp_last, nc));
+  if (g->f32) {
+    using S = Store<true>;
+    k_comp_consts<true><<<grid_for(nc), 256, 0, st>>>(first_d, nc, g->p.alpha, (S::R *)g->comp_base, (S::R *)g->comp_init);
+    count_launch();
+    k_init_comp_rank<true><<<grid_for(n), 256, 0, st>>>(g->comp, n, (const S::R *)g->comp_init, (const S::A *)g->adeg,
+                                                        (S::R *)g->R[0], (S::R *)g->R[1], (S::C *)g->C[0],
+                                                        (S::C *)g->C[1]);
+  } else {
+    using S = Store<false>;
+    k_comp_consts<false><<<grid_for(nc), 256, 0, st>>>(first_d, nc, g->p.alpha, (S::R *)g->comp_base,
+                                                       (S::R *)g->comp_init);
+    count_launch();
+    k_init_comp_rank<false><<<grid_for(n), 256, 0, st>>>(g->comp, n, (const S::R *)g->comp_init,
+                                                         (const S::A *)g->adeg, (S::R *)g->R[0], (S::R *)g->R[1],
+                                                         (S::C *)g->C[0], (S::C *)g->C[1]);
+  }
+  count_launch();
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  cudaFree(first_d);
+  g->comp_stats.assign(nc, pr_stats{});
+  return PR_OK;
+}
+
 void graph_free(Graph *g) {
   Adj *adjs[2] = {&g->out, &g->in};
   for (Adj *A : adjs) {
@@ -967,6 +1073,12 @@ void graph_free(Graph *g) {
   cudaFree(g->item_pos);
   cudaFree(g->hub_v);
   cudaFree(g->hub_base);
+  cudaFree(g->comp);
+  cudaFree(g->comp_base);
+  cudaFree(g->comp_init);
+  cudaFree(g->dRc);
+  cudaFree(g->comp_out);
+  cudaFree(g->comp_last);
   cudaFree(g->partials);
   cudaFree(g->chunk_done);
   for (int i = 0; i < 3; i++) cudaFree(g->list[i]);
@@ -987,6 +1099,8 @@ void graph_free(Graph *g) {
   cudaFree(g->gen_tmp);
   cudaFree(g->gen_tmp2);
   cudaFree(g->scan_tmp);
+  if (g->cg_exec) cudaGraphExecDestroy(g->cg_exec);
+  if (g->cg) cudaGraphDestroy(g->cg);
   if (g->ev0) cudaEventDestroy(g->ev0);
   if (g->ev1) cudaEventDestroy(g->ev1);
 }

@@ -20,6 +20,7 @@ constexpr int kRankBlock = 256;           // threads per block of the rank kerne
 constexpr uint32_t kSmallSort = 4096;     // largest key count sorted by one block
 constexpr uint32_t kChunk = 512;          // edges per chunk of a long row in full and dense sweeps
 constexpr uint32_t kGroupMax = 64;        // full/dense sweeps: rows up to this length use 8-lane groups
+constexpr uint32_t kMaxComponents = 1024; // graphs in one batched handle
 
 // Tier of an in-degree in the full/dense sweep order: 0 = one thread (<= lo), 1 = an
 // 8-lane group (<= max(lo, kGroupMax)), 2 = kChunk-edge chunks taken by whole warps.
@@ -173,7 +174,7 @@ struct ApplyCtl {
   uint32_t n_eff_del;                       // effective deletions among n_eff
   uint32_t overflow;                        // a merge found no room (graph left unchanged rows)
   uint32_t bins_changed;                    // an in-degree crossed a bin threshold
-  uint32_t pad2;
+  uint32_t bad_comp;                        // a pair joins two graphs of a batched handle
   unsigned long long big_cursor;            // global scratch cursor for long rows
 };
 

@@ -70,6 +70,14 @@ struct Graph {
   RankCtl *ctl_h = nullptr;          // pinned host mirror
   DeadPart *dpart = nullptr;         // [2][rank_grid]
   int rank_grid = 0;                 // cooperative grid of the rank kernel
+  int rank_grid_max = 0;             // most blocks that can be co-resident
+  // CUDA-graph launch of rank calls (pr_set_graph_launch): captured once, kernel arguments
+  // updated in place before every replay
+  bool use_graph = false;
+  cudaGraph_t cg = nullptr;
+  cudaGraphExec_t cg_exec = nullptr;
+  cudaGraphNode_t cg_kernel = nullptr;
+  bool cg_f32 = false;
   uint32_t last_list_cnt[3] = {0, 0, 0};
   bool last_full = false;
 
@@ -81,6 +89,17 @@ struct Graph {
   uint32_t *gen_tmp2 = nullptr;
   uint32_t *scan_tmp = nullptr;      // block sums of scans over n
   double ms_apply = 0.0;
+  // batched form: ncomp independent graphs; graph c owns vertices [comp_first[c], comp_first[c+1])
+  uint32_t ncomp = 1;
+  std::vector<uint32_t> comp_first;
+  uint16_t *comp = nullptr;          // [n] graph of each vertex (ncomp > 1)
+  void *comp_base = nullptr;         // [ncomp] (1 - alpha) / n_c, rank representation
+  void *comp_init = nullptr;         // [ncomp] 1 / n_c
+  unsigned long long *dRc = nullptr; // [3][ncomp]
+  uint32_t *comp_out = nullptr;      // [ncomp][4]
+  unsigned long long *comp_last = nullptr;
+  std::vector<pr_stats> comp_stats;  // per graph, from the last rank call
+  uint32_t dense_div = 16;           // dense iterations once affected > n / dense_div
   std::vector<double> trace_ms;      // last rank call: phase 0, then each iteration (device clock)
   std::vector<int64_t> trace_aff;    // affected vertices at the start of each iteration
   std::vector<int32_t> trace_kind;   // 0 sparse, 1 dense, 2 dense after compaction, 3 all vertices
@@ -107,5 +126,6 @@ pr_status rank_init_contrib(Graph *g);  // C = R * adeg for all v, both parities
 pr_status rank_set(Graph *g, const double *in_d);
 pr_status rank_get(Graph *g, double *out_d);
 pr_status rank_dead_mass(Graph *g, double *D);
+pr_status components_setup(Graph *g, const std::vector<uint32_t> &comp_n);  // after graph_build
 
 }  // namespace prdf

@@ -102,6 +102,14 @@ struct RankArgs {
   typename S::C *partials;
   uint32_t *chunk_done;
   uint32_t *hub_v, *hub_base;  // hub queue of the current slot
+  // batched form (ncomp > 1): component of each vertex and per-component constants
+  uint32_t ncomp;
+  const uint16_t *comp;
+  const R *comp_base, *comp_init;
+  unsigned long long *dRc;        // [3][ncomp] per-component L-inf keys, rotating by iteration
+  uint32_t *comp_out;             // [ncomp][4] iterations, converged, affected
+  unsigned long long *comp_last;  // [ncomp] last L-inf key
+  uint32_t dense_div;
   const uint32_t *pend_src;
   uint32_t n_pend_src;
   const uint32_t *pend_tgt;
@@ -389,10 +397,11 @@ __device__ __forceinline__ typename Num<F32>::B finish_vertex(const RankArgs<F32
                                                               typename Store<F32>::C *Cout, uint32_t v,
                                                               typename Store<F32>::C sum, typename Store<F32>::R rold,
                                                               typename Store<F32>::A ad, const Iter<F32> &I,
-                                                              Mass<F32> &dacc, unsigned long long pol_c) {
+                                                              Mass<F32> &dacc, unsigned long long pol_c,
+                                                              typename Store<F32>::R base) {
   using S = Store<F32>;
   using R = typename S::R;
-  R r = a.base + sum;
+  R r = base + sum;
   if (a.teleport) r += I.tele;
   Rout[v] = r;
   st_keep(Cout + v, S::contrib(r, ad), pol_c);
@@ -425,6 +434,21 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
   RankCtl *ctl = a.ctl;
   uint32_t epoch = 0;
   const bool df = a.mode == kModeDF;
+  // per-component state (batched form), identical in every block
+  const bool multi = a.ncomp > 1;
+  const uint32_t nc = a.ncomp;
+  extern __shared__ unsigned long long dsm[];
+  unsigned long long *s_kmax = dsm;                         // block max key / counter per component
+  R *s_base = reinterpret_cast<R *>(dsm + nc);              // (1 - alpha) / n_c
+  uint16_t *s_iters = reinterpret_cast<uint16_t *>(dsm + 2 * nc);
+  uint8_t *s_active = reinterpret_cast<uint8_t *>(s_iters + nc);
+  for (uint32_t c = tid; c < nc; c += kRankBlock) {
+    s_kmax[c] = 0;
+    s_base[c] = multi ? a.comp_base[c] : a.base;
+    s_iters[c] = 0;
+    s_active[c] = 1;
+  }
+  auto live = [&](uint32_t v) -> bool { return !multi || s_active[__ldg(a.comp + v)]; };
 #define pol_cols l2_evict_first()
 #define pol_c l2_evict_last()
   uint32_t my_v = 0, my_e = 0, my_xv = 0, my_xe = 0, my_app = 0;  // per-thread, folded at the end
@@ -494,8 +518,8 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
 
   // ---------------------------------------------------------------- phase 0
   if (a.mode == kModeStatic) {
-    const R r = a.init;
     for (uint32_t v = gtid; v < a.n; v += nthreads) {
+      const R r = multi ? a.comp_init[__ldg(a.comp + v)] : a.init;
       C c = S::contrib(r, __ldg(a.adeg + v));
       a.R0[v] = r;
       a.R1[v] = r;
@@ -503,7 +527,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
       a.C1[v] = c;
     }
     if (a.teleport)
-      for (uint32_t k = gtid; k < a.n_dead; k += nthreads) dacc.add(r);
+      for (uint32_t k = gtid; k < a.n_dead; k += nthreads) dacc.add(a.init);
   } else if (a.teleport) {
     for (uint32_t k = gtid; k < a.n_dead; k += nthreads) dacc.add(ldcg(a.R0 + __ldg(a.dead + k)));
   }
@@ -540,7 +564,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
   uint32_t iters = 0;
   bool converged = false;
   unsigned long long last_key = 0;
-  const uint32_t dense_at = a.n / kDenseDiv;
+  const uint32_t dense_at = a.n / a.dense_div;
   uint32_t cmp_total = 0xFFFFFFFFu;  // affected count at the last compaction (none yet)
   uint32_t cmp_n[3] = {0, 0, 0};
 
@@ -584,6 +608,15 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
           my_xe += od.y;
         }
       }
+    };
+
+    // rank of v from its in-sum; notes |change| in the (per-component) L-inf max
+    auto finish_at = [&](uint32_t v, C sum, R rold, typename S::A ad) -> B {
+      const uint32_t c = multi ? (uint32_t)__ldg(a.comp + v) : 0u;
+      const B dr = finish_vertex(a, Rout, Cout, v, sum, rold, ad, I, dacc, pol_c, multi ? s_base[c] : a.base);
+      if (multi) atomicMax(&s_kmax[c], Num<F32>::key(dr));
+      else my_max = dr > my_max ? dr : my_max;
+      return dr;
     };
 
     if (I.full || dense) {
@@ -633,14 +666,13 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
         const uint32_t i = b0 + lane;
         int push = 0;
         uint32_t v = 0;
-        if (i < n0) {
+        if (i < n0 && live(ldcg(T + i).x)) {
           const uint4 item = ldcg(T + i);
           v = item.x;
           const R rold = ldcg(Rin + v);
           const typename S::A ad = __ldg(a.adeg + v);
           C sum = row_sum_thread(Cin, a.in_col + item.y, item.z, pol_cols, pol_c);
-          B dr = finish_vertex(a, Rout, Cout, v, sum, rold, ad, I, dacc, pol_c);
-          my_max = dr > my_max ? dr : my_max;
+          B dr = finish_at(v, sum, rold, ad);
           my_v++;
           my_e += item.z;
           push = expand && dr > a.ftol && first_expansion(a.xbits, v);
@@ -653,7 +685,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
         const uint32_t grp = lane >> 3, gl = lane & 7;
         for (uint32_t b0 = gwarp * 4; b0 < n1; b0 += nwarps * 4) {
           const uint32_t i = b0 + grp;
-          const bool act = i < n1;
+          const bool act = i < n1 && live(ldcg(T + off1 + i).x);
           uint4 item = make_uint4(0, 0, 0, 0);
           R rold = (R)0;
           typename S::A ad = (typename S::A)0;
@@ -681,8 +713,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
           for (int o = 4; o > 0; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
           int push = 0;
           if (act && gl == 0) {
-            B dr = finish_vertex(a, Rout, Cout, item.x, sum, rold, ad, I, dacc, pol_c);
-            my_max = dr > my_max ? dr : my_max;
+            B dr = finish_at(item.x, sum, rold, ad);
             my_v++;
             my_e += item.z;
             push = expand && dr > a.ftol && first_expansion(a.xbits, item.x);
@@ -698,6 +729,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
       for (uint32_t k = gwarp; k < n2; k += nwarps) {
         const uint4 ch = ldcg(T + off2 + k);
         const uint32_t v = ch.x;
+        if (!live(v)) continue;
         const uint32_t len = ch.z & 0x3FFu;
         const bool multi = (ch.z >> 31) != 0;
         R rold = (R)0;
@@ -747,8 +779,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
         if (finish) {
           int exp_now = 0;
           if (lane == 0) {
-            B dr = finish_vertex(a, Rout, Cout, v, sum, rold, ad, I, dacc, pol_c);
-            my_max = dr > my_max ? dr : my_max;
+            B dr = finish_at(v, sum, rold, ad);
             my_v++;
             my_e += deg;
             exp_now = expand && dr > a.ftol && first_expansion(a.xbits, v);
@@ -770,14 +801,13 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
         const uint32_t i = b0 + lane;
         int push = 0;
         uint32_t v = 0;
-        if (i < cnt[0]) {
+        if (i < cnt[0] && live(ldcg(a.list0 + i))) {
           v = ldcg(a.list0 + i);
           const R rold = ldcg(Rin + v);
           const typename S::A ad = __ldg(a.adeg + v);
           const uint2 d = __ldg(&a.in_rd[v]);
           C sum = row_sum_thread(Cin, a.in_col + d.x, d.y, pol_cols, pol_c);
-          B dr = finish_vertex(a, Rout, Cout, v, sum, rold, ad, I, dacc, pol_c);
-          my_max = dr > my_max ? dr : my_max;
+          B dr = finish_at(v, sum, rold, ad);
           my_v++;
           my_e += d.y;
           push = expand && dr > a.ftol && first_expansion(a.xbits, v);
@@ -788,6 +818,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
       // sparse: warp bin, one warp per vertex
       for (uint32_t i = gwarp; i < cnt[1]; i += nwarps) {
         const uint32_t v = ldcg(a.list1 + i);
+        if (!live(v)) continue;
         const uint2 d = __ldg(&a.in_rd[v]);
         const uint32_t *cols = a.in_col + d.x;
         C sum = (C)0;
@@ -798,8 +829,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
         sum = warp_sum(sum);
         int exp_now = 0;
         if (lane == 0) {
-          B dr = finish_vertex(a, Rout, Cout, v, sum, ldcg(Rin + v), __ldg(a.adeg + v), I, dacc, pol_c);
-          my_max = dr > my_max ? dr : my_max;
+          B dr = finish_at(v, sum, ldcg(Rin + v), __ldg(a.adeg + v));
           my_v++;
           my_e += d.y;
           exp_now = expand && dr > a.ftol && first_expansion(a.xbits, v);
@@ -823,6 +853,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
         __syncthreads();
         if (idx >= cnt[2]) break;
         const uint32_t v = ldcg(a.list2 + idx);
+        if (!live(v)) continue;
         const uint2 d = __ldg(&a.in_rd[v]);
         const uint32_t *cols = a.in_col + d.x;
         C sum = (C)0;
@@ -845,8 +876,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
         if (tid == 0) {
           C tot = (C)0;
           for (int w = 0; w < kWarps; w++) tot += s_part[w];
-          B dr = finish_vertex(a, Rout, Cout, v, tot, ldcg(Rin + v), __ldg(a.adeg + v), I, dacc, pol_c);
-          my_max = dr > my_max ? dr : my_max;
+          B dr = finish_at(v, tot, ldcg(Rin + v), __ldg(a.adeg + v));
           my_v++;
           my_e += d.y;
           s_expand = expand && dr > a.ftol && first_expansion(a.xbits, v);
@@ -868,7 +898,16 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
     }
 
     // block reductions: L-inf (and dead-end mass) of this iteration
-    {
+    if (multi) {
+      __syncthreads();
+      unsigned long long *cur = a.dRc + (uint64_t)(it % 3) * nc;
+      unsigned long long *nxt = a.dRc + (uint64_t)((it + 1) % 3) * nc;
+      for (uint32_t c = tid; c < nc; c += kRankBlock) {
+        if (s_kmax[c]) atomicMax(cur + c, s_kmax[c]);
+        s_kmax[c] = 0;
+        if (blockIdx.x == 0) nxt[c] = 0;  // last read two iterations ago, before the previous barrier
+      }
+    } else {
       unsigned long long m = Num<F32>::key(my_max);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(kFull, m, o));
@@ -887,7 +926,38 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
       if (!grid_sync(ctl, epoch, &s_err)) return;
     }
 
-    const unsigned long long dR = __ldcg(&ctl->dR_bits[it]);
+    unsigned long long dR = __ldcg(&ctl->dR_bits[it]);
+    int any_active = 1;
+    if (multi) {
+      // every block applies the same per-component convergence decisions
+      const unsigned long long *cur = a.dRc + (uint64_t)(it % 3) * nc;
+      int act = 0;
+      unsigned long long mx = 0;
+      for (uint32_t c = tid; c < nc; c += kRankBlock) {
+        if (!s_active[c]) continue;
+        const unsigned long long k = __ldcg(cur + c);
+        mx = k > mx ? k : mx;
+        s_iters[c] = (uint16_t)(it + 1);
+        const bool done = k <= a.tol_key;
+        if (done || it + 1 == a.max_iter) {
+          s_active[c] = 0;
+          if (blockIdx.x == 0) {
+            a.comp_out[4 * c + 0] = (uint32_t)it + 1;
+            a.comp_out[4 * c + 1] = done ? 1u : 0u;
+            a.comp_last[c] = k;
+          }
+        } else {
+          act = 1;
+        }
+      }
+      any_active = __syncthreads_or(act);
+      if (blockIdx.x == 0) {
+        // combined L-inf of this iteration for the call's stats
+        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(kFull, mx, o));
+        if (lane == 0 && mx) atomicMax(&ctl->dR_bits[it], mx);
+      }
+      dR = any_active ? a.tol_key + 1 : 0;  // stop when no component is still iterating
+    }
     if (df && !I.full) {
 #pragma unroll
       for (int bb = 0; bb < 3; bb++) cnt[bb] += ldcg(&ctl->tail[slot][bb]);
@@ -913,30 +983,37 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
   }
 
   // -------------------------------------------------------------- writeback
-  const int fp = iters & 1;
-  const R *Rf = fp ? a.R1 : a.R0;
-  const C *Cf = fp ? a.C1 : a.C0;
-  R *Ro = fp ? a.R0 : a.R1;
-  C *Co = fp ? a.C0 : a.C1;
-  if (ever_full) {
-    for (uint32_t v = gtid; v < a.n; v += nthreads) {
-      Ro[v] = ldcg(Rf + v);
-      Co[v] = ldcg(Cf + v);
-    }
-  }
+  // the final values of a vertex are in parity (its component's iterations) & 1; copy them
+  // to the other parity so both hold the current ranks
+  auto copy_final = [&](uint32_t v) {
+    const uint32_t k = multi ? s_iters[__ldg(a.comp + v)] : iters;
+    const bool fp = k & 1;
+    const R *Rf = fp ? a.R1 : a.R0;
+    const C *Cf = fp ? a.C1 : a.C0;
+    R *Ro = fp ? a.R0 : a.R1;
+    C *Co = fp ? a.C0 : a.C1;
+    Ro[v] = ldcg(Rf + v);
+    Co[v] = ldcg(Cf + v);
+  };
+  __syncthreads();
+  if (ever_full)
+    for (uint32_t v = gtid; v < a.n; v += nthreads) copy_final(v);
   if (df) {
     const uint32_t *lists[3] = {a.list0, a.list1, a.list2};
     for (int bb = 0; bb < 3; bb++) {
       for (uint32_t k = gtid; k < cnt[bb]; k += nthreads) {
         const uint32_t v = ldcg(lists[bb] + k);
-        if (!ever_full) {
-          Ro[v] = ldcg(Rf + v);
-          Co[v] = ldcg(Cf + v);
-        }
+        if (!ever_full) copy_final(v);
+        if (multi) atomicAdd(&s_kmax[__ldg(a.comp + v)], 1ull);
         a.bitmap[v >> 5] = 0u;
         a.xbits[v >> 5] = 0u;
         a.stamp[v] = kNoStamp;
       }
+    }
+    if (multi) {
+      __syncthreads();
+      for (uint32_t c = tid; c < nc; c += kRankBlock)
+        if (s_kmax[c]) atomicAdd(&a.comp_out[4 * c + 2], (uint32_t)s_kmax[c]);
     }
   }
   // counters
@@ -972,10 +1049,13 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
 
 static constexpr double kOne62 = 4611686018427387904.0;  // 2^62
 
+// Dynamic shared memory of k_rank: per-component max key, base, iteration count, active flag.
+static size_t rank_smem(uint32_t ncomp) { return ((size_t)ncomp * 19 + 15) & ~(size_t)15; }
+
 template <bool F32>
-static cudaError_t grid_blocks(int sm_count, int *blocks) {
+static cudaError_t grid_blocks(int sm_count, size_t smem, int *blocks) {
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rank<F32>, kRankBlock, 0);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rank<F32>, kRankBlock, smem);
   if (e != cudaSuccess) return e;
   per_sm = std::max(1, std::min(per_sm, 4));
   *blocks = per_sm * sm_count;
@@ -984,8 +1064,10 @@ static cudaError_t grid_blocks(int sm_count, int *blocks) {
 
 pr_status rank_setup(Graph *g) {
   int blocks = 0;
-  CK(g->f32 ? grid_blocks<true>(g->sm_count, &blocks) : grid_blocks<false>(g->sm_count, &blocks));
+  const size_t smem = rank_smem(g->ncomp);
+  CK(g->f32 ? grid_blocks<true>(g->sm_count, smem, &blocks) : grid_blocks<false>(g->sm_count, smem, &blocks));
   g->rank_grid = blocks;
+  g->rank_grid_max = blocks;
   CK(cudaMalloc((void **)&g->ctl, sizeof(RankCtl)));
   CK(cudaMallocHost((void **)&g->ctl_h, sizeof(RankCtl)));
   CK(cudaMalloc((void **)&g->dpart, sizeof(DeadPart) * 2 * (size_t)blocks));
@@ -1055,8 +1137,58 @@ static pr_status launch(Graph *g, RankMode mode, bool start_full) {
   a.bin_lo = (uint32_t)g->p.bin_lo;
   a.bin_hi = (uint32_t)g->p.bin_hi;
   a.ctl = g->ctl;
+  a.ncomp = g->ncomp;
+  a.comp = g->comp;
+  a.comp_base = (const typename S::R *)g->comp_base;
+  a.comp_init = (const typename S::R *)g->comp_init;
+  a.dRc = g->dRc;
+  a.comp_out = g->comp_out;
+  a.comp_last = g->comp_last;
+  a.dense_div = g->dense_div;
   void *args[] = {(void *)&a};
-  CK(cudaLaunchCooperativeKernel((const void *)k_rank<F32>, dim3(g->rank_grid), dim3(kRankBlock), args, 0, g->st));
+  if (!g->use_graph) {
+    CK(cudaLaunchCooperativeKernel((const void *)k_rank<F32>, dim3(g->rank_grid), dim3(kRankBlock), args,
+                                   rank_smem(g->ncomp), g->st));
+    count_launch();
+    return PR_OK;
+  }
+  // CUDA-graph launch: the control-block reset, the event records and the cooperative
+  // kernel are captured once; later calls only replace the kernel's arguments and replay
+  cudaKernelNodeParams kp{};
+  kp.func = (void *)k_rank<F32>;
+  kp.gridDim = dim3(g->rank_grid);
+  kp.blockDim = dim3(kRankBlock);
+  kp.sharedMemBytes = (unsigned)rank_smem(g->ncomp);
+  kp.kernelParams = args;
+  if (g->cg_exec && (g->cg_f32 != F32)) {
+    cudaGraphExecDestroy(g->cg_exec);
+    cudaGraphDestroy(g->cg);
+    g->cg_exec = nullptr;
+  }
+  if (!g->cg_exec) {
+    cudaGraph_t graph = nullptr;
+    CK(cudaGraphCreate(&graph, 0));
+    cudaGraphNode_t reset = nullptr, kern = nullptr;
+    cudaMemsetParams mp{};
+    mp.dst = g->ctl;
+    mp.value = 0;
+    mp.elementSize = 1;
+    mp.width = sizeof(RankCtl);
+    mp.height = 1;
+    mp.pitch = sizeof(RankCtl);
+    CK(cudaGraphAddMemsetNode(&reset, graph, nullptr, 0, &mp));
+    CK(cudaGraphAddKernelNode(&kern, graph, &reset, 1, &kp));
+    cudaLaunchAttributeValue coop{};
+    coop.cooperative = 1;
+    CK(cudaGraphKernelNodeSetAttribute(kern, cudaLaunchAttributeCooperative, &coop));
+    CK(cudaGraphInstantiate(&g->cg_exec, graph, 0));
+    g->cg = graph;
+    g->cg_kernel = kern;
+    g->cg_f32 = F32;
+  } else {
+    CK(cudaGraphExecKernelNodeSetParams(g->cg_exec, g->cg_kernel, &kp));
+  }
+  CK(cudaGraphLaunch(g->cg_exec, g->st));
   count_launch();
   return PR_OK;
 }
@@ -1066,7 +1198,12 @@ pr_status rank_run(Graph *g, RankMode mode, pr_stats *stats) {
   const bool start_full = mode == kModeDF && g->pend_all;
   if (g->teleport && (rc = graph_refresh_dead(g)) != PR_OK) return rc;
   if ((rc = graph_refresh_ident(g)) != PR_OK) return rc;
-  CK(cudaMemsetAsync(g->ctl, 0, sizeof(RankCtl), g->st));
+  if (!g->use_graph) CK(cudaMemsetAsync(g->ctl, 0, sizeof(RankCtl), g->st));
+  if (g->ncomp > 1) {
+    CK(cudaMemsetAsync(g->dRc, 0, 3ull * g->ncomp * sizeof(unsigned long long), g->st));
+    CK(cudaMemsetAsync(g->comp_out, 0, 16ull * g->ncomp, g->st));
+    CK(cudaMemsetAsync(g->comp_last, 0, 8ull * g->ncomp, g->st));
+  }
   CK(cudaEventRecord(g->ev0, g->st));
   rc = g->f32 ? launch<true>(g, mode, start_full) : launch<false>(g, mode, start_full);
   if (rc != PR_OK) return rc;
@@ -1109,13 +1246,34 @@ pr_status rank_run(Graph *g, RankMode mode, pr_stats *stats) {
     g->D_ref = h.D_final;
     g->D_ref_n = h.D_final_n;
   }
+  bool all_conv = h.converged != 0;
+  if (g->ncomp > 1) {
+    std::vector<uint32_t> co(4ull * g->ncomp);
+    std::vector<unsigned long long> cl(g->ncomp);
+    CK(cudaMemcpyAsync(co.data(), g->comp_out, 16ull * g->ncomp, cudaMemcpyDeviceToHost, g->st));
+    CK(cudaMemcpyAsync(cl.data(), g->comp_last, 8ull * g->ncomp, cudaMemcpyDeviceToHost, g->st));
+    CK(cudaStreamSynchronize(g->st));
+    all_conv = true;
+    for (uint32_t c = 0; c < g->ncomp; c++) {
+      pr_stats &cs = g->comp_stats[c];
+      std::memset(&cs, 0, sizeof(cs));
+      cs.iterations = (int32_t)co[4 * c];
+      cs.converged = (int32_t)co[4 * c + 1];
+      const int64_t nc = (int64_t)g->comp_first[c + 1] - g->comp_first[c];
+      cs.affected_final = full ? nc : (int64_t)co[4 * c + 2];
+      if (g->f32) std::memcpy(&cs.last_delta, &cl[c], 8);
+      else cs.last_delta = (double)cl[c] / kOne62;
+      cs.ms_rank = ms;
+      all_conv = all_conv && cs.converged;
+    }
+  }
   if (stats) {
     const double vb = g->f32 ? 24.0 : 36.0, eb = g->f32 ? 8.0 : 12.0;
     double last = 0.0;
     if (g->f32) std::memcpy(&last, &h.last_key, 8);
     else last = (double)h.last_key / kOne62;
     stats->iterations = (int32_t)h.iterations;
-    stats->converged = (int32_t)h.converged;
+    stats->converged = all_conv ? 1 : 0;
     stats->affected_final =
         full ? (int64_t)g->n : (int64_t)h.final_cnt[0] + h.final_cnt[1] + h.final_cnt[2];
     stats->vertices_processed = (int64_t)h.vproc;

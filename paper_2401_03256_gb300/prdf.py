@@ -32,6 +32,8 @@ EXPORTED = (
     "pr_params_default", "pr_graph_create", "pr_graph_destroy", "pr_apply_batch", "pr_static",
     "pr_naive_dynamic", "pr_dynamic_frontier", "pr_get_ranks", "pr_set_ranks", "pr_graph_info",
     "pr_get_csr", "pr_get_affected", "pr_get_trace", "pr_kernel_launches", "pr_last_error", "pr_status_string",
+    "pr_graph_create_batched", "pr_get_component_stats", "pr_set_tuning", "pr_get_tuning", "pr_autotune",
+    "pr_set_graph_launch",
 )
 
 
@@ -46,6 +48,14 @@ class pr_stats(ctypes.Structure):
                 ("affected_final", ctypes.c_int64), ("vertices_processed", ctypes.c_int64),
                 ("edges_processed", ctypes.c_int64), ("bytes_algorithmic", ctypes.c_double),
                 ("last_delta", ctypes.c_double), ("ms_apply", ctypes.c_double), ("ms_rank", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class pr_tuning(ctypes.Structure):
+    _fields_ = [("bin_lo", ctypes.c_int32), ("bin_hi", ctypes.c_int32), ("dense_div", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -91,6 +101,18 @@ def load(path: str = LIB_PATH):
     lib.pr_get_csr.argtypes = [vp, i32, vp, vp]
     lib.pr_get_affected.restype = ctypes.c_int
     lib.pr_get_affected.argtypes = [vp, vp, i64, ctypes.POINTER(i64)]
+    lib.pr_graph_create_batched.restype = ctypes.c_int
+    lib.pr_graph_create_batched.argtypes = [i32, vp, i64, vp, vp, ctypes.POINTER(pr_params), vp, ctypes.POINTER(vp)]
+    lib.pr_get_component_stats.restype = ctypes.c_int
+    lib.pr_get_component_stats.argtypes = [vp, ctypes.POINTER(pr_stats), i32]
+    lib.pr_set_tuning.restype = ctypes.c_int
+    lib.pr_set_tuning.argtypes = [vp, ctypes.POINTER(pr_tuning)]
+    lib.pr_get_tuning.restype = ctypes.c_int
+    lib.pr_get_tuning.argtypes = [vp, ctypes.POINTER(pr_tuning)]
+    lib.pr_autotune.restype = ctypes.c_int
+    lib.pr_autotune.argtypes = [vp, i32, ctypes.POINTER(pr_tuning)]
+    lib.pr_set_graph_launch.restype = ctypes.c_int
+    lib.pr_set_graph_launch.argtypes = [vp, i32]
     lib.pr_get_trace.restype = ctypes.c_int
     lib.pr_get_trace.argtypes = [vp, i32, vp, vp, vp, vp, ctypes.POINTER(i32)]
     lib.pr_kernel_launches.restype = ctypes.c_uint64
@@ -153,6 +175,50 @@ def pr_graph_create(n: int, src, dst, params: pr_params | None = None, stream: i
                                 stream, ctypes.byref(h))
     _check(st, None)
     return h.value
+
+
+def pr_graph_create_batched(comp_n, src, dst, params: pr_params | None = None, stream: int | None = None) -> int:
+    """Batched handle of len(comp_n) graphs; src/dst use global ids (graph c owns
+    [sum(comp_n[:c]), sum(comp_n[:c+1])))."""
+    cn = np.ascontiguousarray(np.asarray(comp_n, dtype=np.uint32))
+    src, dst = _u32(src), _u32(dst)
+    ps, ms = _ptr(src)
+    pd, md = _ptr(dst)
+    if ms != md:
+        raise ValueError("src and dst differ in length")
+    h = ctypes.c_void_p()
+    st = load().pr_graph_create_batched(cn.shape[0], cn.ctypes.data, ms, ps, pd,
+                                        ctypes.byref(params) if params is not None else None, stream,
+                                        ctypes.byref(h))
+    _check(st, None)
+    return h.value
+
+
+def pr_get_component_stats(h: int, ncomp: int):
+    arr = (pr_stats * ncomp)()
+    _check(load().pr_get_component_stats(h, arr, ncomp), h)
+    return [arr[i] for i in range(ncomp)]
+
+
+def pr_set_tuning(h: int, bin_lo: int, bin_hi: int, dense_div: int, blocks_per_sm: int) -> None:
+    t = pr_tuning(bin_lo, bin_hi, dense_div, blocks_per_sm, 0.0)
+    _check(load().pr_set_tuning(h, ctypes.byref(t)), h)
+
+
+def pr_get_tuning(h: int) -> pr_tuning:
+    t = pr_tuning()
+    _check(load().pr_get_tuning(h, ctypes.byref(t)), h)
+    return t
+
+
+def pr_autotune(h: int, sweep_iters: int = 8) -> pr_tuning:
+    t = pr_tuning()
+    _check(load().pr_autotune(h, sweep_iters, ctypes.byref(t)), h)
+    return t
+
+
+def pr_set_graph_launch(h: int, enable: bool) -> None:
+    _check(load().pr_set_graph_launch(h, 1 if enable else 0), h)
 
 
 def pr_graph_destroy(h: int) -> None:
@@ -256,10 +322,34 @@ def pr_get_affected(h: int) -> np.ndarray:
 
 
 class Graph:
-    """Owning wrapper of a handle: ``with Graph(n, src, dst) as g: g.static()``."""
+    """Owning wrapper of a handle: ``with Graph(n, src, dst) as g: g.static()``.
+    ``Graph.batched(comp_n, src, dst)`` builds a batched handle."""
 
-    def __init__(self, n: int, src, dst, params: pr_params | None = None, stream: int | None = None):
-        self.h = pr_graph_create(n, src, dst, params, stream)
+    def __init__(self, n: int, src, dst, params: pr_params | None = None, stream: int | None = None,
+                 _handle: int | None = None):
+        self.h = _handle if _handle is not None else pr_graph_create(n, src, dst, params, stream)
+        self.ncomp = 1
+
+    @classmethod
+    def batched(cls, comp_n, src, dst, params: pr_params | None = None, stream: int | None = None) -> "Graph":
+        g = cls(0, None, None, _handle=pr_graph_create_batched(comp_n, src, dst, params, stream))
+        g.ncomp = len(comp_n)
+        return g
+
+    def component_stats(self):
+        return pr_get_component_stats(self.h, self.ncomp)
+
+    def autotune(self, sweep_iters: int = 8) -> pr_tuning:
+        return pr_autotune(self.h, sweep_iters)
+
+    def tuning(self) -> pr_tuning:
+        return pr_get_tuning(self.h)
+
+    def set_tuning(self, bin_lo: int, bin_hi: int, dense_div: int, blocks_per_sm: int):
+        pr_set_tuning(self.h, bin_lo, bin_hi, dense_div, blocks_per_sm)
+
+    def set_graph_launch(self, enable: bool):
+        pr_set_graph_launch(self.h, enable)
 
     def apply(self, del_src, del_dst, ins_src, ins_dst):
         pr_apply_batch(self.h, del_src, del_dst, ins_src, ins_dst)

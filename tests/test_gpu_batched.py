@@ -1,0 +1,199 @@
+"""Batched form: many independent graphs in one handle, one launch per rank call.
+
+Each graph of a batched handle must give the ranks of a run of that graph alone: the same
+values as a standalone handle (bit for bit in 64-bit mode, whose sums are exact) and the
+oracle's within the usual L-inf bound, with its own iteration count.
+"""
+import numpy as np
+import pytest
+
+import __graft_entry__
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-9
+TOL32 = 1e-6
+
+
+@pytest.fixture(scope="module")
+def prdf():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    __graft_entry__.build()
+    from paper_2401_03256_gb300 import prdf as mod
+
+    mod.load()
+    return mod
+
+
+def _graphs(seed=0):
+    rng = np.random.default_rng(seed)
+    gs = [synth.rmat(int(s), 8, seed=100 + i) for i, s in enumerate(rng.integers(6, 12, 9))]
+    n = 17
+    gs.append(synth.from_pairs(n, [(i, (i + 1) % n) for i in range(n)], "cycle"))
+    gs.append(synth.from_pairs(21, [(i, 0) for i in range(1, 21)], "star"))
+    gs.append(synth.from_pairs(3, [], "empty"))
+    return gs
+
+
+def _union(gs):
+    firsts = np.cumsum([0] + [g.n for g in gs])
+    src = np.concatenate([g.src.astype(np.uint64) + firsts[i] for i, g in enumerate(gs)]).astype(np.uint32)
+    dst = np.concatenate([g.dst.astype(np.uint64) + firsts[i] for i, g in enumerate(gs)]).astype(np.uint32)
+    return firsts, src, dst
+
+
+def _params(prdf, **kw):
+    p = prdf.pr_params_default()
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+@pytest.mark.parametrize("graph_launch", [False, True])
+def test_batched_static_equals_standalone_and_oracle(prdf, graph_launch):
+    gs = _graphs()
+    firsts, src, dst = _union(gs)
+    with prdf.Graph.batched([g.n for g in gs], src, dst) as B:
+        B.set_graph_launch(graph_launch)
+        st = B.static()
+        R = B.ranks()
+        cs = B.component_stats()
+        assert st.converged and st.iterations == max(c.iterations for c in cs)
+        for i, g in enumerate(gs):
+            part = R[firsts[i]:firsts[i + 1]]
+            with prdf.Graph(g.n, g.src, g.dst) as A:
+                sa = A.static()
+                assert np.array_equal(A.ranks(), part), g.name
+                assert cs[i].iterations == sa.iterations and cs[i].converged
+            G = oracle.Graph.build(g.n, g.src, g.dst)
+            Ro, so = oracle.static_pr(G)
+            assert np.max(np.abs(part - Ro)) <= TOL64
+            assert abs(cs[i].iterations - so.iterations) <= 1
+
+
+def test_batched_apply_and_frontier(prdf):
+    gs = _graphs(1)
+    firsts, src, dst = _union(gs)
+    streams = [synth.BatchStream(g, seed=7 + i) for i, g in enumerate(gs)]
+    Gs = [oracle.Graph.build(g.n, g.src, g.dst) for g in gs]
+    Rs = [oracle.static_pr(G)[0] for G in Gs]
+    U = oracle.Graph.build(int(firsts[-1]), src, dst)
+    with prdf.Graph.batched([g.n for g in gs], src, dst) as B:
+        B.set_ranks(np.concatenate(Rs))
+        for t in range(3):
+            bs = [s.next(1e-2) for s in streams]
+            off = lambda a, i: (a.astype(np.uint64) + firsts[i]).astype(np.uint32)
+            ds = np.concatenate([off(b.del_src, i) for i, b in enumerate(bs)])
+            dd = np.concatenate([off(b.del_dst, i) for i, b in enumerate(bs)])
+            is_ = np.concatenate([off(b.ins_src, i) for i, b in enumerate(bs)])
+            id_ = np.concatenate([off(b.ins_dst, i) for i, b in enumerate(bs)])
+            B.set_ranks(np.concatenate(Rs))
+            B.apply(ds, dd, is_, id_)
+            U, _, _ = U.apply(ds, dd, is_, id_)
+            for d in (0, 1):
+                off_b, col_b = B.csr(d)
+                off_u, col_u = U.csr(d)
+                assert np.array_equal(off_b, off_u) and np.array_equal(col_b, col_u)
+            B.frontier()
+            R = B.ranks()
+            cs = B.component_stats()
+            for i, b in enumerate(bs):
+                H, ed, ei = Gs[i].apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+                Rn, aff, so = oracle.df_sync(Gs[i], H, ed, ei, Rs[i])
+                part = R[firsts[i]:firsts[i + 1]]
+                assert np.max(np.abs(part - Rn)) <= TOL64, gs[i].name
+                assert abs(cs[i].iterations - so.iterations) <= 1
+                assert abs(cs[i].affected_final - so.affected_final) <= max(2, 0.01 * so.affected_final)
+                Gs[i], Rs[i] = H, Rn
+
+
+def test_batched_df_equals_standalone_bitwise(prdf):
+    gs = _graphs(2)
+    firsts, src, dst = _union(gs)
+    bs = [synth.BatchStream(g, seed=3 + i).next(1e-2) for i, g in enumerate(gs)]
+    off = lambda a, i: (a.astype(np.uint64) + firsts[i]).astype(np.uint32)
+    with prdf.Graph.batched([g.n for g in gs], src, dst) as B:
+        B.static()
+        R0 = B.ranks().copy()
+        B.apply(np.concatenate([off(b.del_src, i) for i, b in enumerate(bs)]),
+                np.concatenate([off(b.del_dst, i) for i, b in enumerate(bs)]),
+                np.concatenate([off(b.ins_src, i) for i, b in enumerate(bs)]),
+                np.concatenate([off(b.ins_dst, i) for i, b in enumerate(bs)]))
+        B.frontier()
+        R = B.ranks()
+        cs = B.component_stats()
+    for i, g in enumerate(gs):
+        with prdf.Graph(g.n, g.src, g.dst) as A:
+            A.set_ranks(R0[firsts[i]:firsts[i + 1]])
+            b = bs[i]
+            A.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+            sa = A.frontier()
+            assert np.array_equal(A.ranks(), R[firsts[i]:firsts[i + 1]]), g.name
+            assert sa.iterations == cs[i].iterations
+
+
+def test_batched_rejects_cross_graph_pairs(prdf):
+    gs = _graphs(3)[:3]
+    firsts, src, dst = _union(gs)
+    with pytest.raises(prdf.PrdfError) as e:
+        prdf.Graph.batched([g.n for g in gs], np.append(src, 0), np.append(dst, firsts[1]))
+    assert e.value.status == prdf.PR_ERR_INVALID_ARG
+    with prdf.Graph.batched([g.n for g in gs], src, dst) as B:
+        before = B.csr(0)
+        with pytest.raises(prdf.PrdfError) as e:
+            B.apply([], [], [0], [int(firsts[2])])
+        assert e.value.status == prdf.PR_ERR_INVALID_ARG
+        after = B.csr(0)
+        assert np.array_equal(before[1], after[1])
+
+
+def test_batched_fp32(prdf):
+    gs = _graphs(4)
+    firsts, src, dst = _union(gs)
+    p = _params(prdf, precision=prdf.PR_F32)
+    with prdf.Graph.batched([g.n for g in gs], src, dst, p) as B:
+        B.static()
+        R = B.ranks()
+    for i, g in enumerate(gs):
+        Ro, _ = oracle.static_pr(oracle.Graph.build(g.n, g.src, g.dst))
+        assert np.max(np.abs(R[firsts[i]:firsts[i + 1]] - Ro)) <= TOL32
+
+
+def test_autotune_keeps_ranks_and_pending_marks(prdf):
+    g = synth.rmat(13, 8, seed=5)
+    G = oracle.Graph.build(g.n, g.src, g.dst)
+    R0, _ = oracle.static_pr(G)
+    b = synth.BatchStream(g, seed=5).next(1e-3)
+    H, ed, ei = G.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+    Rdf, _, _ = oracle.df_sync(G, H, ed, ei, R0)
+    with prdf.Graph(g.n, g.src, g.dst) as A:
+        A.set_ranks(R0)
+        A.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+        before = A.ranks().copy()
+        t = A.autotune(4)
+        assert t.bin_lo in (4, 8, 16, 32) and t.blocks_per_sm >= 1 and t.ms > 0
+        assert np.array_equal(A.ranks(), before)
+        cur = A.tuning()
+        assert (cur.bin_lo, cur.blocks_per_sm) == (t.bin_lo, t.blocks_per_sm)
+        A.frontier()  # pending marks of the batch survive the autotuner
+        assert np.max(np.abs(A.ranks() - Rdf)) <= TOL64
+
+
+@pytest.mark.parametrize("lo,bps", [(1, 1), (4, 2), (32, 3)])
+def test_results_do_not_depend_on_tuning(prdf, lo, bps):
+    g = synth.rmat(13, 8, seed=9)
+    b = synth.BatchStream(g, seed=9).next(1e-3)
+    out = []
+    for tune in (None, (lo, max(lo, 64), 4, bps)):
+        with prdf.Graph(g.n, g.src, g.dst) as A:
+            if tune:
+                A.set_tuning(*tune)
+            A.static()
+            A.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+            A.frontier()
+            out.append(A.ranks().copy())
+    assert np.array_equal(out[0], out[1])
