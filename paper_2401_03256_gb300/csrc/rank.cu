@@ -567,6 +567,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
   const uint32_t dense_at = a.n / a.dense_div;
   uint32_t cmp_total = 0xFFFFFFFFu;  // affected count at the last compaction (none yet)
   uint32_t cmp_n[3] = {0, 0, 0};
+  uint32_t deact = 0, cmp_deact = 0;  // iterations in which some graph stopped (batched form)
 
   // ------------------------------------------------------------- iterations
   for (int it = 0; it < a.max_iter; it++) {
@@ -625,7 +626,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
       uint32_t n0 = a.it_c0, n1 = a.it_c1, n2 = a.it_c2;
       if (dense) {
         const uint32_t total = cnt[0] + cnt[1] + cnt[2];
-        if (total != cmp_total) {
+        if (total != cmp_total || deact != cmp_deact) {
           // keep the items of vertices stamped <= it; warp-aggregated appends keep runs of
           // up to 32 items in tier order
           const uint32_t segs[3][2] = {{0u, a.it_c0}, {off1, a.it_c1}, {off2, a.it_c2}};
@@ -638,7 +639,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
               bool keep = false;
               if (i < cntt) {
                 item = __ldg(a.items + base + i);
-                keep = ldcg(a.stamp + item.x) <= (uint16_t)it;
+                keep = ldcg(a.stamp + item.x) <= (uint16_t)it && live(item.x);
               }
               const uint32_t mask = __ballot_sync(kFull, keep);
               if (mask) {
@@ -654,6 +655,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
 #pragma unroll
           for (int t = 0; t < 3; t++) cmp_n[t] = ldcg(&ctl->cmp[slot][t]);
           cmp_total = total;
+          cmp_deact = deact;
         }
         T = a.items_cmp;
         n0 = cmp_n[0];
@@ -931,7 +933,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
     if (multi) {
       // every block applies the same per-component convergence decisions
       const unsigned long long *cur = a.dRc + (uint64_t)(it % 3) * nc;
-      int act = 0;
+      int act = 0, stopped = 0;
       unsigned long long mx = 0;
       for (uint32_t c = tid; c < nc; c += kRankBlock) {
         if (!s_active[c]) continue;
@@ -941,6 +943,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
         const bool done = k <= a.tol_key;
         if (done || it + 1 == a.max_iter) {
           s_active[c] = 0;
+          stopped = 1;
           if (blockIdx.x == 0) {
             a.comp_out[4 * c + 0] = (uint32_t)it + 1;
             a.comp_out[4 * c + 1] = done ? 1u : 0u;
@@ -951,6 +954,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
         }
       }
       any_active = __syncthreads_or(act);
+      if (__syncthreads_or(stopped)) deact++;
       if (blockIdx.x == 0) {
         // combined L-inf of this iteration for the call's stats
         for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(kFull, mx, o));

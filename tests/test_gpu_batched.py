@@ -119,6 +119,8 @@ def test_batched_df_equals_standalone_bitwise(prdf):
     with prdf.Graph.batched([g.n for g in gs], src, dst) as B:
         B.static()
         R0 = B.ranks().copy()
+        B.set_ranks(R0)  # both sides start from the same doubles (a rank near 1 does not
+        #                  survive the double round trip of its 2^-62 value bit for bit)
         B.apply(np.concatenate([off(b.del_src, i) for i, b in enumerate(bs)]),
                 np.concatenate([off(b.del_dst, i) for i, b in enumerate(bs)]),
                 np.concatenate([off(b.ins_src, i) for i, b in enumerate(bs)]),
