@@ -459,6 +459,97 @@ def run_batched(args, rank: int, world: int, local_rank: int):
         print(json.dumps(line))
 
 
+# ------------------------------------------------------------- serving form ----
+
+def run_serving(args, rank: int, world: int, local_rank: int):
+    """Serving form (config 5): 8 resident R-MAT graphs (scales 18, 18, 19, 20, 21, 22, 23,
+    24, edge factor 16, FP32 ranks), Poisson arrivals at --rate requests/s for --duration s,
+    target graph uniform, batch f ~ log-uniform [1e-7, 1e-3] of that graph's edges (80/20,
+    drawn against the resident graph), admission by slots and free HBM, continuous batching
+    of each graph's queue.  value = p99 latency (submit -> ranks updated) in ms."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2401_03256_gb300 import build as libbuild
+
+    libbuild.build()
+    from paper_2401_03256_gb300 import prdf
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    scales = [int(x) for x in args.serve_scales.split(",")]
+    rng = np.random.default_rng(1 + rank)
+    gs = [synth.rmat(s, 16, seed=500 + 10 * rank + i) for i, s in enumerate(scales)]
+    params = prdf.pr_params_default()
+    params.precision = prdf.PR_F32 if args.precision != "fp64" else prdf.PR_F64
+    streams = [torch.cuda.Stream(device=dev) for _ in gs]
+    hs = [prdf.Graph(g.n, g.src, g.dst, params, s.cuda_stream) for g, s in zip(gs, streams)]
+    for h in hs:
+        h.static()
+    bstreams = [synth.BatchStream(g, seed=900 + i) for i, g in enumerate(gs)]
+    nreq = int(args.rate * args.duration)
+    warm = 4 * len(gs)
+    targets = rng.integers(0, len(gs), nreq + warm)
+    fr = np.exp(rng.uniform(np.log(1e-7), np.log(1e-3), nreq + warm))
+    batches = [bstreams[t].next(float(f), apply=False) for t, f in zip(targets, fr)]
+    gaps = rng.exponential(1.0 / args.rate, nreq)
+    srv = prdf.Server(slots=args.slots, max_coalesce=args.coalesce, hbm_reserve_bytes=1 << 30)
+    idx = [srv.add(h) for h in hs]
+    for k in range(warm):  # warm-up, untimed
+        b = batches[k]
+        srv.submit(idx[targets[k]], b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+    srv.drain()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    l0 = prdf.pr_kernel_launches()
+    tickets = []
+    t0 = time.perf_counter()
+    due = t0
+    for k in range(nreq):
+        due += gaps[k]
+        while True:
+            now = time.perf_counter()
+            if now >= due:
+                break
+            if due - now > 2e-4:
+                time.sleep((due - now) * 0.5)
+        b = batches[warm + k]
+        tickets.append(srv.submit(idx[targets[warm + k]], b.del_src, b.del_dst, b.ins_src, b.ins_dst))
+    t_submitted = time.perf_counter()
+    info = srv.drain()
+    t_end = time.perf_counter()
+    clk = clocks.stop()
+    launches = prdf.pr_kernel_launches() - l0
+    res = [srv.wait(t) for t in tickets]
+    srv.close()
+    lat = np.array([r.t_done_ms - r.t_submit_ms for r in res])
+    ok = sum(1 for r in res if r.status == prdf.PR_OK)
+    span_ms = max(r.t_done_ms for r in res) - min(r.t_submit_ms for r in res)
+    pairs = [int(batches[warm + k].size) for k in range(nreq)]
+    line = {
+        "metric": "serving p50/p99 ms", "value": float(np.percentile(lat, 99)), "unit": "ms",
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
+        "updates_per_s": nreq / (span_ms * 1e-3), "offered_rate_per_s": args.rate,
+        "achieved_submit_rate_per_s": nreq / (t_submitted - t0), "requests": nreq, "ok": ok,
+        "coalesced_mean": float(np.mean([r.coalesced for r in res])),
+        "waited_for_memory": info.waited_for_memory, "wall_s": t_end - t0,
+        "n_gpus": world, "steps": nreq, "warmup": warm, "ms_per_step": span_ms / nreq,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision != "fp64" else "i64", "data": "synthetic",
+        "config": {"workload": f"{len(gs)} resident R-MAT graphs scales {scales}, edge factor 16, Poisson "
+                               f"{args.rate:g}/s, f ~ logU[1e-7, 1e-3], 80/20", "slots": args.slots,
+                   "max_coalesce": args.coalesce, "batch_pairs_mean": float(np.mean(pairs)),
+                   "vertices": int(sum(g.n for g in gs))},
+        "gpu_launches": launches, "clocks": clk,
+    }
+    for h in hs:
+        h.close()
+    if rank == 0:
+        print(json.dumps(line))
+
+
 # -------------------------------------------------------- reference arm ----
 
 def run_reference(args, rank: int, world: int):
@@ -515,14 +606,19 @@ def main():
                     help="default fp64 for the plain workload, fp32 for the batched form")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-timeout", type=float, default=600.0)
-    ap.add_argument("--config", choices=["plain", "batched"], default="plain",
-                    help="plain: the headline workload (R-MAT s22 sweep); batched: the batched form")
+    ap.add_argument("--config", choices=["plain", "batched", "serving"], default="plain",
+                    help="plain: the headline workload (R-MAT s22 sweep); batched / serving: those forms")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serving: Poisson arrivals per second")
+    ap.add_argument("--duration", type=float, default=2.0, help="serving: seconds of arrivals")
+    ap.add_argument("--slots", type=int, default=4, help="serving: concurrent updates")
+    ap.add_argument("--coalesce", type=int, default=64, help="serving: requests per coalesced update")
+    ap.add_argument("--serve-scales", default="18,18,19,20,21,22,23,24", help="serving: R-MAT scales")
     ap.add_argument("--graphs", type=int, default=256, help="graphs of the batched form")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.precision is None:
-        args.precision = "fp32" if args.config == "batched" else "fp64"
+        args.precision = "fp32" if args.config in ("batched", "serving") else "fp64"
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
@@ -530,6 +626,8 @@ def main():
         run_reference(args, rank, world)
     elif args.config == "batched":
         run_batched(args, rank, world, local_rank)
+    elif args.config == "serving":
+        run_serving(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

@@ -186,6 +186,57 @@ pr_status pr_get_trace(const pr_graph *g, int32_t cap, double *phase_ms, double 
  * for accounting of device work.  Never fails. */
 uint64_t pr_kernel_launches(void);
 
+/* ---------------------------------------------------------------- serving form ----
+ * A request loop over several resident graphs.  Each attached graph gets a FIFO and one
+ * worker, so it has a single writer and its requests run in submission order; requests of
+ * different graphs run concurrently on their graphs' streams (create each graph with its
+ * own stream for overlap).  A request is admitted when one of `slots` device slots is free
+ * and free device memory (cudaMemGetInfo) covers hbm_reserve_bytes plus the request's
+ * estimate; an idle device always admits one request.  Attaching a graph sizes its
+ * persistent launch to 1/slots of the resident blocks so concurrent launches fit together.
+ * An update = pr_apply_batch of each coalesced request in order + one pr_dynamic_frontier;
+ * results carry host-clock times in ms since the server was created.  While attached, a
+ * graph must not be used directly. */
+typedef struct pr_server pr_server;
+
+typedef struct {
+    int32_t slots;               /* concurrent updates on the device (1..64) */
+    int32_t max_coalesce;        /* queued requests of one graph served by one update (>= 1):
+                                    their batches are applied in order, then one Dynamic
+                                    Frontier call covers them all (pending marks accumulate) */
+    uint64_t hbm_reserve_bytes;  /* device memory to keep free */
+} pr_server_config;
+
+typedef struct {
+    uint64_t ticket;
+    int32_t graph;               /* index from pr_server_add_graph */
+    int32_t status;              /* pr_status of the request */
+    double t_submit_ms, t_start_ms, t_done_ms;
+    int32_t coalesced;           /* requests served by the same update (1 = alone) */
+    int32_t reserved;
+    pr_stats stats;              /* of the pr_dynamic_frontier that served it */
+} pr_request_result;
+
+typedef struct {
+    int64_t submitted, completed, waited_for_memory;
+    double elapsed_ms;
+} pr_server_info;
+
+void pr_server_config_default(pr_server_config *cfg); /* 4 slots, coalesce up to 64, 1 GiB reserve */
+pr_status pr_server_create(const pr_server_config *cfg, pr_server **out);
+/* Attaches g (caller keeps ownership; destroy the server before the graph). */
+pr_status pr_server_add_graph(pr_server *s, pr_graph *g, int32_t *index);
+/* Queues one batch for graph `graph` (host arrays, copied); returns at once with a ticket. */
+pr_status pr_server_submit(pr_server *s, int32_t graph, int64_t n_del, const uint32_t *del_src,
+                           const uint32_t *del_dst, int64_t n_ins, const uint32_t *ins_src, const uint32_t *ins_dst,
+                           uint64_t *ticket);
+/* Blocks until the request has finished and copies its result. */
+pr_status pr_server_wait(pr_server *s, uint64_t ticket, pr_request_result *out);
+/* Blocks until every submitted request has finished; info may be NULL. */
+pr_status pr_server_drain(pr_server *s, pr_server_info *info);
+/* Finishes queued requests, joins the workers and frees the server (not the graphs). */
+pr_status pr_server_destroy(pr_server *s);
+
 /* Message of the last failed call on g (or of the last failed pr_graph_create if g is NULL). */
 const char *pr_last_error(const pr_graph *g);
 

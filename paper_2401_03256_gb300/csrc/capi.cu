@@ -12,10 +12,6 @@
 
 #include "prdf_graph.cuh"
 
-struct pr_graph {
-  prdf::Graph g;
-  double *stage = nullptr;  // n doubles for host <-> device rank copies
-};
 
 namespace {
 

@@ -129,3 +129,9 @@ pr_status rank_dead_mass(Graph *g, double *D);
 pr_status components_setup(Graph *g, const std::vector<uint32_t> &comp_n);  // after graph_build
 
 }  // namespace prdf
+
+// The opaque handle of the C ABI.
+struct pr_graph {
+  prdf::Graph g;
+  double *stage = nullptr;  // n doubles for host <-> device rank copies
+};

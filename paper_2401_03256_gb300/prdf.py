@@ -33,7 +33,8 @@ EXPORTED = (
     "pr_naive_dynamic", "pr_dynamic_frontier", "pr_get_ranks", "pr_set_ranks", "pr_graph_info",
     "pr_get_csr", "pr_get_affected", "pr_get_trace", "pr_kernel_launches", "pr_last_error", "pr_status_string",
     "pr_graph_create_batched", "pr_get_component_stats", "pr_set_tuning", "pr_get_tuning", "pr_autotune",
-    "pr_set_graph_launch",
+    "pr_set_graph_launch", "pr_server_config_default", "pr_server_create", "pr_server_add_graph",
+    "pr_server_submit", "pr_server_wait", "pr_server_drain", "pr_server_destroy",
 )
 
 
@@ -59,6 +60,21 @@ class pr_tuning(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class pr_server_config(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("max_coalesce", ctypes.c_int32), ("hbm_reserve_bytes", ctypes.c_uint64)]
+
+
+class pr_request_result(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("graph", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("t_submit_ms", ctypes.c_double), ("t_start_ms", ctypes.c_double), ("t_done_ms", ctypes.c_double),
+                ("coalesced", ctypes.c_int32), ("reserved", ctypes.c_int32), ("stats", pr_stats)]
+
+
+class pr_server_info(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("waited_for_memory", ctypes.c_int64), ("elapsed_ms", ctypes.c_double)]
 
 
 class PrdfError(RuntimeError):
@@ -113,6 +129,20 @@ def load(path: str = LIB_PATH):
     lib.pr_autotune.argtypes = [vp, i32, ctypes.POINTER(pr_tuning)]
     lib.pr_set_graph_launch.restype = ctypes.c_int
     lib.pr_set_graph_launch.argtypes = [vp, i32]
+    lib.pr_server_config_default.restype = None
+    lib.pr_server_config_default.argtypes = [ctypes.POINTER(pr_server_config)]
+    lib.pr_server_create.restype = ctypes.c_int
+    lib.pr_server_create.argtypes = [ctypes.POINTER(pr_server_config), ctypes.POINTER(vp)]
+    lib.pr_server_add_graph.restype = ctypes.c_int
+    lib.pr_server_add_graph.argtypes = [vp, vp, ctypes.POINTER(i32)]
+    lib.pr_server_submit.restype = ctypes.c_int
+    lib.pr_server_submit.argtypes = [vp, i32, i64, vp, vp, i64, vp, vp, ctypes.POINTER(ctypes.c_uint64)]
+    lib.pr_server_wait.restype = ctypes.c_int
+    lib.pr_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(pr_request_result)]
+    lib.pr_server_drain.restype = ctypes.c_int
+    lib.pr_server_drain.argtypes = [vp, ctypes.POINTER(pr_server_info)]
+    lib.pr_server_destroy.restype = ctypes.c_int
+    lib.pr_server_destroy.argtypes = [vp]
     lib.pr_get_trace.restype = ctypes.c_int
     lib.pr_get_trace.argtypes = [vp, i32, vp, vp, vp, vp, ctypes.POINTER(i32)]
     lib.pr_kernel_launches.restype = ctypes.c_uint64
@@ -384,6 +414,67 @@ class Graph:
     def close(self):
         if getattr(self, "h", None):
             pr_graph_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pr_server_config_default() -> pr_server_config:
+    c = pr_server_config()
+    load().pr_server_config_default(ctypes.byref(c))
+    return c
+
+
+class Server:
+    """Serving form: ``srv = Server(slots=4); gi = srv.add(graph); t = srv.submit(gi, batch...)``.
+    Attached graphs must outlive the server and are not used directly while attached."""
+
+    def __init__(self, slots: int = 4, max_coalesce: int = 64, hbm_reserve_bytes: int = 1 << 30):
+        c = pr_server_config(slots, max_coalesce, hbm_reserve_bytes)
+        h = ctypes.c_void_p()
+        _check(load().pr_server_create(ctypes.byref(c), ctypes.byref(h)), None)
+        self.h = h.value
+
+    def add(self, graph: "Graph") -> int:
+        idx = ctypes.c_int32()
+        _check(load().pr_server_add_graph(self.h, graph.h, ctypes.byref(idx)), None)
+        return idx.value
+
+    def submit(self, gi: int, del_src, del_dst, ins_src, ins_dst) -> int:
+        del_src, del_dst, ins_src, ins_dst = _u32(del_src), _u32(del_dst), _u32(ins_src), _u32(ins_dst)
+        a, na = _ptr(del_src)
+        b, nb = _ptr(del_dst)
+        c, nc = _ptr(ins_src)
+        d, nd = _ptr(ins_dst)
+        if na != nb or nc != nd:
+            raise ValueError("source and target arrays differ in length")
+        t = ctypes.c_uint64()
+        _check(load().pr_server_submit(self.h, gi, na, a, b, nc, c, d, ctypes.byref(t)), None)
+        return t.value
+
+    def wait(self, ticket: int) -> pr_request_result:
+        r = pr_request_result()
+        _check(load().pr_server_wait(self.h, ticket, ctypes.byref(r)), None)
+        return r
+
+    def drain(self) -> pr_server_info:
+        info = pr_server_info()
+        _check(load().pr_server_drain(self.h, ctypes.byref(info)), None)
+        return info
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().pr_server_destroy(self.h)
             self.h = None
 
     def __enter__(self):
