@@ -140,6 +140,21 @@ pr_status pr_graph_destroy(pr_graph *g);
 pr_status pr_apply_batch(pr_graph *g, int64_t n_del, const uint32_t *del_src, const uint32_t *del_dst,
                          int64_t n_ins, const uint32_t *ins_src, const uint32_t *ins_dst);
 
+#define PR_MAX_BATCHES 65536
+
+/* Applies n_batches batch updates one after another (Section 3.2 applied per batch) in one
+ * pass: the graph afterwards is exactly the one that n_batches pr_apply_batch calls would
+ * give.  Batch k deletes the pairs del_src/del_dst[del_off[k] .. del_off[k+1]) and inserts
+ * ins_src/ins_dst[ins_off[k] .. ins_off[k+1]); del_off and ins_off are host arrays of
+ * n_batches + 1 non-decreasing entries starting at 0 (PR_ERR_INVALID_ARG otherwise, and
+ * for n_batches > PR_MAX_BATCHES or more than 2^31 pairs in all).  Only the net change
+ * between the graph before the first batch and after the last becomes pending marks: an
+ * edge deleted by one batch and inserted again by a later one marks nothing.  Pair arrays
+ * may be host or device memory. */
+pr_status pr_apply_batches(pr_graph *g, int32_t n_batches, const int64_t *del_off, const uint32_t *del_src,
+                           const uint32_t *del_dst, const int64_t *ins_off, const uint32_t *ins_src,
+                           const uint32_t *ins_dst);
+
 /* Static PageRank (Section 3.1, Eq. 1): ranks restart at 1/n; every vertex is updated
  * each iteration until the L-inf change is <= tol or max_iter iterations ran.
  * stats may be NULL. */
@@ -194,7 +209,8 @@ uint64_t pr_kernel_launches(void);
  * and free device memory (cudaMemGetInfo) covers hbm_reserve_bytes plus the request's
  * estimate; an idle device always admits one request.  Attaching a graph sizes its
  * persistent launch to 1/slots of the resident blocks so concurrent launches fit together.
- * An update = pr_apply_batch of each coalesced request in order + one pr_dynamic_frontier;
+ * An update = one pr_apply_batches over the coalesced requests in submission order + one
+ * pr_dynamic_frontier;
  * results carry host-clock times in ms since the server was created.  While attached, a
  * graph must not be used directly. */
 typedef struct pr_server pr_server;
@@ -202,8 +218,9 @@ typedef struct pr_server pr_server;
 typedef struct {
     int32_t slots;               /* concurrent updates on the device (1..64) */
     int32_t max_coalesce;        /* queued requests of one graph served by one update (>= 1):
-                                    their batches are applied in order, then one Dynamic
-                                    Frontier call covers them all (pending marks accumulate) */
+                                    their batches are applied in order by one
+                                    pr_apply_batches, then one Dynamic Frontier call covers
+                                    the net change */
     uint64_t hbm_reserve_bytes;  /* device memory to keep free */
 } pr_server_config;
 

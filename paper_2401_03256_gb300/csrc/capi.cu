@@ -322,11 +322,11 @@ pr_status pr_graph_destroy(pr_graph *h) {
   return PR_OK;
 }
 
-pr_status pr_apply_batch(pr_graph *h, int64_t n_del, const uint32_t *del_src, const uint32_t *del_dst,
-                         int64_t n_ins, const uint32_t *ins_src, const uint32_t *ins_dst) {
-  if (!h) return invalid(nullptr, "graph is NULL");
+// Shared by pr_apply_batch (nb = 1, no offsets) and pr_apply_batches.
+static pr_status apply_impl(pr_graph *h, int32_t nb, const int64_t *del_off, const int64_t *ins_off, int64_t n_del,
+                            const uint32_t *del_src, const uint32_t *del_dst, int64_t n_ins, const uint32_t *ins_src,
+                            const uint32_t *ins_dst) {
   Graph &g = h->g;
-  if (n_del < 0 || n_ins < 0) return invalid(&g, "negative batch size");
   if ((n_del > 0 && (!del_src || !del_dst)) || (n_ins > 0 && (!ins_src || !ins_dst)))
     return invalid(&g, "batch array is NULL");
   const uint64_t N = (uint64_t)n_del + (uint64_t)n_ins;
@@ -346,7 +346,26 @@ pr_status pr_apply_batch(pr_graph *h, int64_t n_del, const uint32_t *del_src, co
   }
   pr_status rc = prdf::apply_scratch(&g, N);
   if (rc != PR_OK) return rc;
+  std::vector<uint32_t> off_h;
+  if (nb > 1) {
+    prdf::ApplyScratch &s = g.sc;
+    if (nb > s.boff_cap) {
+      cudaFree(s.boff);
+      s.boff = nullptr;
+      s.boff_cap = 0;
+      cudaError_t e = cudaMalloc(&s.boff, sizeof(uint32_t) * 2 * ((uint64_t)nb + 1));
+      if (e != cudaSuccess) return prdf::cuda_fail(&g, e, "batch offsets");
+      s.boff_cap = nb;
+    }
+    off_h.resize(2 * ((size_t)nb + 1));
+    for (int32_t k = 0; k <= nb; k++) {
+      off_h[k] = (uint32_t)del_off[k];
+      off_h[nb + 1 + k] = (uint32_t)ins_off[k];
+    }
+  }
   cudaError_t e = cudaEventRecord(g.ev0, g.st);
+  if (e == cudaSuccess && nb > 1)
+    e = cudaMemcpyAsync(g.sc.boff, off_h.data(), sizeof(uint32_t) * off_h.size(), cudaMemcpyHostToDevice, g.st);
   const uint32_t *dev[4];
   uint32_t *stage = g.sc.pairs;
   for (int k = 0; k < 4 && e == cudaSuccess; k++) {
@@ -359,7 +378,9 @@ pr_status pr_apply_batch(pr_graph *h, int64_t n_del, const uint32_t *del_src, co
     stage += len[k];
   }
   if (e != cudaSuccess) return prdf::cuda_fail(&g, e, "upload batch");
-  rc = prdf::graph_apply(&g, (uint64_t)n_del, dev[0], dev[1], (uint64_t)n_ins, dev[2], dev[3]);
+  // graph_apply synchronises the stream before it returns, so off_h outlives its copy
+  rc = prdf::graph_apply(&g, (uint64_t)n_del, dev[0], dev[1], (uint64_t)n_ins, dev[2], dev[3], nb > 1 ? nb : 1,
+                         nb > 1 ? g.sc.boff : nullptr);
   if (rc != PR_OK) return rc;
   e = cudaEventRecord(g.ev1, g.st);
   if (e == cudaSuccess) e = cudaEventSynchronize(g.ev1);
@@ -368,6 +389,30 @@ pr_status pr_apply_batch(pr_graph *h, int64_t n_del, const uint32_t *del_src, co
   if (e != cudaSuccess) return prdf::cuda_fail(&g, e, "apply timing");
   g.ms_apply += ms;
   return PR_OK;
+}
+
+pr_status pr_apply_batch(pr_graph *h, int64_t n_del, const uint32_t *del_src, const uint32_t *del_dst,
+                         int64_t n_ins, const uint32_t *ins_src, const uint32_t *ins_dst) {
+  if (!h) return invalid(nullptr, "graph is NULL");
+  if (n_del < 0 || n_ins < 0) return invalid(&h->g, "negative batch size");
+  return apply_impl(h, 1, nullptr, nullptr, n_del, del_src, del_dst, n_ins, ins_src, ins_dst);
+}
+
+pr_status pr_apply_batches(pr_graph *h, int32_t n_batches, const int64_t *del_off, const uint32_t *del_src,
+                           const uint32_t *del_dst, const int64_t *ins_off, const uint32_t *ins_src,
+                           const uint32_t *ins_dst) {
+  if (!h) return invalid(nullptr, "graph is NULL");
+  Graph &g = h->g;
+  if (n_batches < 0 || n_batches > PR_MAX_BATCHES) return invalid(&g, "batch count out of range");
+  if (n_batches == 0) return PR_OK;
+  if (!del_off || !ins_off) return invalid(&g, "offset array is NULL");
+  if (del_off[0] != 0 || ins_off[0] != 0) return invalid(&g, "offsets must start at 0");
+  for (int32_t k = 0; k < n_batches; k++)
+    if (del_off[k + 1] < del_off[k] || ins_off[k + 1] < ins_off[k]) return invalid(&g, "offsets must not decrease");
+  if (del_off[n_batches] + ins_off[n_batches] > (int64_t)(1ull << 31))
+    return invalid(&g, "batch too large (more than 2^31 pairs)");
+  return apply_impl(h, n_batches, del_off, ins_off, del_off[n_batches], del_src, del_dst, ins_off[n_batches], ins_src,
+                    ins_dst);
 }
 
 static pr_status run(pr_graph *h, prdf::RankMode mode, pr_stats *stats) {

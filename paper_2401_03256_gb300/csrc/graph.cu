@@ -5,10 +5,11 @@
 // Section 3.1 / 5.1.4 add a self-loop to every vertex (kept fixed across updates).
 //
 // Update pipeline (all on the handle's stream):
-//   keys (u << b | v) of the requested pairs -> sort -> filter to the effective changes
-//   (drop self pairs, duplicates, deletions of absent edges, deletions that are
-//   re-inserted, insertions of present edges) -> tagged change list sorted by (u, v)
-//   and a transposed copy sorted by (v, u) -> segments = touched rows -> one block
+//   keys (u << b | v) of the requested pairs in sequence order -> stable sort -> the last
+//   request on each edge decides its state, and the edges whose state changes are the
+//   effective changes (self pairs, duplicates, deletions of absent edges, deletions that
+//   are re-inserted and insertions of present edges drop out) -> tagged change list in
+//   (u, v) order and a transposed copy sorted by (v, u) -> segments = touched rows -> one block
 //   per touched row merges the row with its changes, in place if the row's slots
 //   suffice, else into freshly allocated tail slots.  The out-row merge also refreshes
 //   the row's contribution alpha R[u] / |out(u)| and records the pending marks
@@ -167,13 +168,39 @@ __device__ __forceinline__ bool sorted_has(const uint64_t *a, uint64_t n, uint64
   return lo < n && a[lo] == x;
 }
 
-__global__ void k_batch_keys(const uint32_t *ds, const uint32_t *dd, uint64_t nd, const uint32_t *is,
-                             const uint32_t *id, uint64_t ni, uint32_t n, int b, uint64_t *kd, uint64_t *ki,
-                             const uint16_t *comp, ApplyCtl *actl) {
+// Batch k of a sequence holding op x of one kind: the last k with off[k] <= x.
+__device__ __forceinline__ uint32_t batch_of(const uint32_t *off, int nb, uint64_t x) {
+  uint32_t lo = 0, hi = (uint32_t)nb;  // off[0] = 0 <= x
+  while (hi - lo > 1) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (off[mid] <= x) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Keys (u << b | v) of a sequence of batches, each request written at its place in the
+// order D_0, I_0, D_1, I_1, ... (deletions before insertions inside a batch, Section 3.2),
+// with the payload (place << 1) | is_insertion.  off = [del offsets (nb + 1), ins offsets
+// (nb + 1)], or null for a single batch.
+__global__ void k_seq_keys(const uint32_t *ds, const uint32_t *dd, uint64_t nd, const uint32_t *is,
+                           const uint32_t *id, uint64_t ni, int nb, const uint32_t *off, uint32_t n, int b,
+                           uint64_t *keys, uint32_t *vals, const uint16_t *comp, ApplyCtl *actl) {
   uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nd + ni) return;
-  uint64_t u, v;
-  if (i < nd) { u = ds[i]; v = dd[i]; } else { u = is[i - nd]; v = id[i - nd]; }
+  uint64_t u, v, at;
+  uint32_t kind;
+  if (i < nd) {
+    u = ds[i];
+    v = dd[i];
+    kind = 0;
+    at = off ? off[nb + 1 + batch_of(off, nb, i)] + i : i;
+  } else {
+    const uint64_t j = i - nd;
+    u = is[j];
+    v = id[j];
+    kind = 1;
+    at = off ? off[batch_of(off + nb + 1, nb, j) + 1] + j : nd + j;
+  }
   uint64_t key;
   if (u >= n || v >= n) {
     atomicOr(&actl->bad_id, 1u);
@@ -184,48 +211,43 @@ __global__ void k_batch_keys(const uint32_t *ds, const uint32_t *dd, uint64_t nd
   } else {
     key = u == v ? kSentinel : ((u << b) | v);
   }
-  if (i < nd) kd[i] = key; else ki[i - nd] = key;
+  keys[at] = key;
+  vals[at] = (uint32_t)(at << 1) | kind;
 }
 
-// flags[i] = 1 for an effective change: deletions (i < nd) of present edges not also
-// inserted, insertions of absent edges; duplicates and self pairs never.
-__global__ void k_filter(const uint64_t *kd, uint64_t nd, const uint64_t *ki, uint64_t ni, const uint2 *rd,
-                         const uint32_t *col, int b, uint32_t *flags) {
+// After the stable sort every key's requests sit together in sequence order, so the last
+// one fixes the edge's final state; flags[i] = 1 where that state differs from the graph's
+// (an effective deletion or insertion).  Self pairs and repeated requests never count.
+__global__ void k_last_op(const uint64_t *keys, const uint32_t *vals, uint64_t N, const uint2 *rd,
+                          const uint32_t *col, int b, uint32_t *flags) {
   uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nd + ni) return;
-  const uint64_t mask = (1ull << b) - 1;
+  if (i >= N) return;
+  const uint64_t k = keys[i];
   uint32_t keep = 0;
-  if (i < nd) {
-    uint64_t k = kd[i];
-    if (k != kSentinel && (i == 0 || kd[i - 1] != k))
-      keep = row_has(rd, col, (uint32_t)(k >> b), (uint32_t)(k & mask)) && !sorted_has(ki, ni, k);
-  } else {
-    uint64_t j = i - nd, k = ki[j];
-    if (k != kSentinel && (j == 0 || ki[j - 1] != k))
-      keep = !row_has(rd, col, (uint32_t)(k >> b), (uint32_t)(k & mask));
+  if (k != kSentinel && (i + 1 == N || keys[i + 1] != k)) {
+    const bool fin = vals[i] & 1u;
+    const bool was = row_has(rd, col, (uint32_t)(k >> b), (uint32_t)(k & ((1ull << b) - 1)));
+    keep = fin != was;
   }
   flags[i] = keep;
 }
 
-// Tagged change keys: (key << 1) | is_insertion, in row-major (u, v) and transposed (v, u) form.
-__global__ void k_emit_changes(const uint64_t *kd, uint64_t nd, const uint64_t *ki, uint64_t ni,
-                               const uint32_t *flags, const uint32_t *pos, int b, uint64_t *chg, uint64_t *chg_t,
-                               ApplyCtl *actl) {
+// Tagged change keys: (key << 1) | is_insertion, in row-major (u, v) order and a
+// transposed (v, u) copy.
+__global__ void k_emit_changes(const uint64_t *keys, const uint32_t *vals, uint64_t N, const uint32_t *flags,
+                               const uint32_t *pos, int b, uint64_t *chg, uint64_t *chg_t, ApplyCtl *actl) {
   uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  uint64_t N = nd + ni;
   if (i >= N) return;
   if (flags[i]) {
-    uint64_t k = i < nd ? kd[i] : ki[i - nd];
-    uint64_t tag = i < nd ? 0 : 1;
-    uint64_t mask = (1ull << b) - 1;
-    uint64_t kt = ((k & mask) << b) | (k >> b);
+    const uint64_t k = keys[i];
+    const uint64_t tag = vals[i] & 1u;
+    const uint64_t mask = (1ull << b) - 1;
+    const uint64_t kt = ((k & mask) << b) | (k >> b);
     chg[pos[i]] = (k << 1) | tag;
     chg_t[pos[i]] = (kt << 1) | tag;
+    if (!tag) atomicAdd(&actl->n_eff_del, 1u);
   }
-  if (i == N - 1) {
-    actl->n_eff = pos[i] + flags[i];
-    actl->n_eff_del = nd < N ? pos[nd] : pos[i] + flags[i];
-  }
+  if (i == N - 1) actl->n_eff = pos[i] + flags[i];
 }
 
 __device__ __forceinline__ uint32_t chg_row(uint64_t c, int b) { return (uint32_t)((c >> 1) >> b); }
@@ -642,13 +664,18 @@ pr_status apply_scratch(Graph *g, uint64_t N) {
   ApplyScratch &s = g->sc;
   if (N <= s.cap && s.pairs) return PR_OK;
   uint64_t cap = std::max<uint64_t>(N, 4096);
-  cudaFree(s.pairs); cudaFree(s.kd); cudaFree(s.ki); cudaFree(s.tmp); cudaFree(s.tmp2);
+  uint32_t *boff = s.boff;
+  const int32_t boff_cap = s.boff_cap;
+  cudaFree(s.pairs); cudaFree(s.kd); cudaFree(s.vals); cudaFree(s.vals2); cudaFree(s.tmp); cudaFree(s.tmp2);
   cudaFree(s.chg); cudaFree(s.chg_t); cudaFree(s.flags); cudaFree(s.pos); cudaFree(s.seg);
   cudaFree(s.tagpref); cudaFree(s.radix_hist); cudaFree(s.scan_tmp);
   s = ApplyScratch{};
+  s.boff = boff;
+  s.boff_cap = boff_cap;
   CK(dalloc(&s.pairs, 2 * cap));
   CK(dalloc(&s.kd, cap));
-  CK(dalloc(&s.ki, cap));
+  CK(dalloc(&s.vals, cap));
+  CK(dalloc(&s.vals2, cap));
   CK(dalloc(&s.tmp, cap));
   CK(dalloc(&s.tmp2, cap));
   CK(dalloc(&s.chg, cap));
@@ -697,7 +724,7 @@ static pr_status repack_adj(Graph *g, Adj &A, uint64_t reserve) {
 }
 
 pr_status graph_apply(Graph *g, uint64_t nd, const uint32_t *ds, const uint32_t *dd, uint64_t ni, const uint32_t *is,
-                      const uint32_t *id) {
+                      const uint32_t *id, int nb, const uint32_t *off) {
   const uint64_t N = nd + ni;
   if (N == 0) return PR_OK;
   cudaStream_t st = g->st;
@@ -715,14 +742,14 @@ pr_status graph_apply(Graph *g, uint64_t nd, const uint32_t *ds, const uint32_t 
   h.tail_in = g->in.used;
   CK(cudaMemcpyAsync(g->actl, &h, sizeof(ApplyCtl), cudaMemcpyHostToDevice, st));
 
-  k_batch_keys<<<grid_for(N), 256, 0, st>>>(ds, dd, nd, is, id, ni, g->n, b, s.kd, s.ki, g->comp, g->actl); count_launch();
-  uint64_t *kd = sort_u64(s.kd, s.tmp, nd, 2 * b, s.radix_hist, s.scan_tmp, st);
-  uint64_t *ki = sort_u64(s.ki, s.tmp2, ni, 2 * b, s.radix_hist, s.scan_tmp, st);
-  k_filter<<<grid_for(N), 256, 0, st>>>(kd, nd, ki, ni, g->out.rd, g->out.col, b, s.flags); count_launch();
+  k_seq_keys<<<grid_for(N), 256, 0, st>>>(ds, dd, nd, is, id, ni, nb, off, g->n, b, s.kd, s.vals, g->comp,
+                                          g->actl); count_launch();
+  uint64_t *keys = s.kd;
+  uint32_t *vals = s.vals;
+  sort_u64_kv(&keys, &vals, s.tmp, s.vals2, N, 2 * b, s.radix_hist, s.scan_tmp, st);
+  k_last_op<<<grid_for(N), 256, 0, st>>>(keys, vals, N, g->out.rd, g->out.col, b, s.flags); count_launch();
   exclusive_scan_u32(s.flags, s.pos, N, s.scan_tmp, st);
-  uint64_t *chg = kd == s.kd ? s.tmp : s.kd;     // free buffers after the sorts
-  uint64_t *chg_t = ki == s.ki ? s.tmp2 : s.ki;
-  k_emit_changes<<<grid_for(N), 256, 0, st>>>(kd, nd, ki, ni, s.flags, s.pos, b, s.chg, s.chg_t, g->actl); count_launch();
+  k_emit_changes<<<grid_for(N), 256, 0, st>>>(keys, vals, N, s.flags, s.pos, b, s.chg, s.chg_t, g->actl); count_launch();
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(&h, g->actl, sizeof(ApplyCtl), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -738,8 +765,10 @@ pr_status graph_apply(Graph *g, uint64_t nd, const uint32_t *ds, const uint32_t 
   const uint32_t K_del = h.n_eff_del;
   if (K == 0) return PR_OK;
 
-  uint64_t *co = sort_u64(s.chg, chg, K, kbits, s.radix_hist, s.scan_tmp, st);
-  uint64_t *ci = sort_u64(s.chg_t, chg_t, K, kbits, s.radix_hist, s.scan_tmp, st);
+  // the change list is already in (u, v) order (one entry per key); only the transposed
+  // copy needs a sort
+  uint64_t *co = s.chg;
+  uint64_t *ci = sort_u64(s.chg_t, s.tmp2, K, kbits, s.radix_hist, s.scan_tmp, st);
   uint32_t *seg_o = s.seg, *seg_i = s.seg + (s.cap + 2);
   uint32_t *tp_o = s.tagpref, *tp_i = s.tagpref + (s.cap + 2);
   ApplyCtl *dctl = g->actl;
@@ -1090,7 +1119,8 @@ void graph_free(Graph *g) {
   if (g->ctl_h) cudaFreeHost(g->ctl_h);
   cudaFree(g->dpart);
   ApplyScratch &s = g->sc;
-  cudaFree(s.pairs); cudaFree(s.kd); cudaFree(s.ki); cudaFree(s.tmp); cudaFree(s.tmp2);
+  cudaFree(s.pairs); cudaFree(s.kd); cudaFree(s.vals); cudaFree(s.vals2); cudaFree(s.tmp); cudaFree(s.tmp2);
+  cudaFree(s.boff);
   cudaFree(s.chg); cudaFree(s.chg_t); cudaFree(s.flags); cudaFree(s.pos); cudaFree(s.seg);
   cudaFree(s.tagpref); cudaFree(s.radix_hist); cudaFree(s.scan_tmp);
   cudaFree(g->actl);

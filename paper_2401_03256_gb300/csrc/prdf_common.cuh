@@ -149,7 +149,7 @@ struct DeadPart {
 struct ApplyScratch {
   uint64_t cap = 0;             // capacity in pairs
   uint32_t *pairs = nullptr;    // 4 * cap: del_src, del_dst, ins_src, ins_dst
-  uint64_t *kd = nullptr, *ki = nullptr, *tmp = nullptr, *tmp2 = nullptr;  // keys [2 cap] each
+  uint64_t *kd = nullptr, *tmp = nullptr, *tmp2 = nullptr;  // keys [cap] each
   uint64_t *chg = nullptr, *chg_t = nullptr;   // tagged change lists [2 cap]
   uint32_t *flags = nullptr, *pos = nullptr;   // [2 cap + 1]
   uint32_t *seg = nullptr;                      // segment starts [2 cap + 1]
@@ -158,6 +158,9 @@ struct ApplyScratch {
   uint64_t radix_hist_cap = 0;
   uint32_t *scan_tmp = nullptr;                 // scan block sums
   uint64_t scan_tmp_cap = 0;
+  uint32_t *vals = nullptr, *vals2 = nullptr;   // (place << 1) | is_insertion [cap], sorted with the keys
+  uint32_t *boff = nullptr;                     // batch offsets of a sequence [2 (boff_cap + 1)]
+  int32_t boff_cap = 0;
 };
 
 // Device-side counters of a batch update (one struct, read back once).
@@ -191,6 +194,11 @@ void exclusive_scan_u32(const uint32_t *in, uint32_t *out, uint64_t n, uint32_t 
 size_t radix_hist_words(uint64_t n);
 uint64_t *sort_u64(uint64_t *keys, uint64_t *alt, uint64_t n, int bits, uint32_t *hist,
                    uint32_t *scan_tmp, cudaStream_t st);
+
+// Stable sort of n (key, value) pairs by the key's low `bits` bits; *keys / *vals point at
+// the result afterwards (the inputs or the alternates).
+void sort_u64_kv(uint64_t **keys, uint32_t **vals, uint64_t *alt_k, uint32_t *alt_v, uint64_t n, int bits,
+                 uint32_t *hist, uint32_t *scan_tmp, cudaStream_t st);
 
 int bits_for(uint32_t n);  // bits needed for ids in [0, n), at least 1
 

@@ -109,8 +109,10 @@ struct Graph {
 
 // graph.cu
 pr_status graph_build(Graph *g, uint64_t m_in, const uint32_t *src_d, const uint32_t *dst_d);
+// Applies nb batches in sequence (nb = 1: one batch).  off_d = device copy of the del and
+// ins offsets ([nb + 1] each, del first), or null for a single batch.
 pr_status graph_apply(Graph *g, uint64_t nd, const uint32_t *ds_d, const uint32_t *dd_d, uint64_t ni,
-                      const uint32_t *is_d, const uint32_t *id_d);
+                      const uint32_t *is_d, const uint32_t *id_d, int nb, const uint32_t *off_d);
 pr_status apply_scratch(Graph *g, uint64_t N);
 pr_status graph_export(Graph *g, int dir, uint64_t *offs_h, uint32_t *cols_h);
 pr_status graph_refresh_ident(Graph *g);

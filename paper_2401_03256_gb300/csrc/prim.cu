@@ -1,6 +1,8 @@
 // prim.cu - data-parallel primitives used by graph construction and batch updates:
 // an exclusive scan of uint32 values and a stable LSD radix sort of 64-bit keys
 // (one-block bitonic sort for small inputs).
+#include <utility>
+
 #include "prdf_common.cuh"
 
 namespace prdf {
@@ -175,6 +177,117 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(const uint64_t 
       out[gbase[d] + wcnt[warp][d] + local[r]] = k[r];
     }
   }
+}
+
+// Key-value variants: equal keys keep the order of their values (the values enter in
+// ascending order), so a stable sort by key is also a sort by (key, value).
+__global__ void __launch_bounds__(1024) k_block_sort_kv(uint64_t *keys, uint32_t *vals, uint32_t n) {
+  __shared__ uint64_t sk[kSmallSort / 2];
+  __shared__ uint32_t sv[kSmallSort / 2];
+  uint32_t p = 2;
+  while (p < n) p <<= 1;
+  for (uint32_t i = threadIdx.x; i < p; i += blockDim.x) {
+    sk[i] = i < n ? keys[i] : kSentinel;
+    sv[i] = i < n ? vals[i] : 0xFFFFFFFFu;
+  }
+  __syncthreads();
+  for (uint32_t k = 2; k <= p; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = threadIdx.x; i < p; i += blockDim.x) {
+        uint32_t l = i ^ j;
+        if (l > i) {
+          uint64_t a = sk[i], b = sk[l];
+          uint32_t va = sv[i], vb = sv[l];
+          bool gt = a > b || (a == b && va > vb);
+          bool up = (i & k) == 0;
+          if (gt == up) {
+            sk[i] = b;
+            sk[l] = a;
+            sv[i] = vb;
+            sv[l] = va;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+    keys[i] = sk[i];
+    vals[i] = sv[i];
+  }
+}
+
+__global__ void __launch_bounds__(kRadixThreads) k_radix_scatter_kv(const uint64_t *keys, const uint32_t *vals,
+                                                                    uint64_t *out, uint32_t *vout, uint64_t n,
+                                                                    int shift, const uint32_t *hist,
+                                                                    uint32_t nblocks) {
+  __shared__ uint32_t wcnt[kRadixWarps][256];
+  __shared__ uint32_t gbase[256];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int w = 0; w < kRadixWarps; w++) wcnt[w][threadIdx.x] = 0;
+  gbase[threadIdx.x] = hist[(uint64_t)threadIdx.x * nblocks + blockIdx.x];
+  __syncthreads();
+  const uint64_t base = (uint64_t)blockIdx.x * kRadixTile + (uint64_t)warp * kWarpKeys;
+  uint64_t k[kRadixItems];
+  uint32_t local[kRadixItems];
+#pragma unroll
+  for (int r = 0; r < kRadixItems; r++) {
+    uint64_t idx = base + (uint64_t)r * 32 + lane;
+    bool valid = idx < n;
+    k[r] = valid ? keys[idx] : 0ull;
+    uint32_t d = valid ? (uint32_t)((k[r] >> shift) & 0xFF) : 0xFFFFu;
+    uint32_t peers = __match_any_sync(0xffffffffu, d);
+    uint32_t rank = __popc(peers & lanemask_lt());
+    uint32_t b = valid ? wcnt[warp][d] : 0u;
+    __syncwarp();
+    if (valid && rank == 0) wcnt[warp][d] = b + __popc(peers);
+    __syncwarp();
+    local[r] = b + rank;
+  }
+  __syncthreads();
+  {
+    uint32_t run = 0;
+    for (int w = 0; w < kRadixWarps; w++) {
+      uint32_t c = wcnt[w][threadIdx.x];
+      wcnt[w][threadIdx.x] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kRadixItems; r++) {
+    uint64_t idx = base + (uint64_t)r * 32 + lane;
+    if (idx < n) {
+      uint32_t d = (uint32_t)((k[r] >> shift) & 0xFF);
+      uint32_t at = gbase[d] + wcnt[warp][d] + local[r];
+      out[at] = k[r];
+      vout[at] = vals[idx];
+    }
+  }
+}
+
+void sort_u64_kv(uint64_t **keys, uint32_t **vals, uint64_t *alt_k, uint32_t *alt_v, uint64_t n, int bits,
+                 uint32_t *hist, uint32_t *scan_tmp, cudaStream_t st) {
+  if (n < 2) return;
+  if (n <= kSmallSort / 2) {
+    k_block_sort_kv<<<1, 1024, 0, st>>>(*keys, *vals, (uint32_t)n);
+    count_launch();
+    return;
+  }
+  const uint32_t nblocks = (uint32_t)((n + kRadixTile - 1) / kRadixTile);
+  uint64_t *sk = *keys, *dk = alt_k;
+  uint32_t *sv = *vals, *dv = alt_v;
+  for (int shift = 0; shift < bits; shift += 8) {
+    k_radix_hist<<<nblocks, kRadixThreads, 0, st>>>(sk, n, shift, hist, nblocks);
+    count_launch();
+    exclusive_scan_u32(hist, hist, (uint64_t)256 * nblocks, scan_tmp, st);
+    k_radix_scatter_kv<<<nblocks, kRadixThreads, 0, st>>>(sk, sv, dk, dv, n, shift, hist, nblocks);
+    count_launch();
+    std::swap(sk, dk);
+    std::swap(sv, dv);
+  }
+  *keys = sk;
+  *vals = sv;
 }
 
 size_t radix_hist_words(uint64_t n) {

@@ -8,8 +8,8 @@
 // streams.  Each graph's persistent rank launch is sized to 1/slots of the blocks that can
 // be resident, so the cooperative kernels of concurrent requests always fit on the device
 // together.  Continuous batching: when a graph's worker gets a slot it takes the requests
-// queued for that graph by then (up to max_coalesce), applies their batches in order and
-// runs one pr_dynamic_frontier for all of them (pending marks accumulate across applies);
+// queued for that graph by then (up to max_coalesce), applies their batches in order with
+// one pr_apply_batches and runs one pr_dynamic_frontier over the net change;
 // each result records submit, start and completion times (host clock) and the stats.
 #include <algorithm>
 #include <chrono>
@@ -66,6 +66,28 @@ uint64_t request_estimate(const pr_graph *h, uint64_t pairs) {
   return 128ull * pairs + cols / 8 + (16ull << 20);
 }
 
+// The group's batches concatenated in submission order, applied by one pr_apply_batches.
+pr_status apply_group(pr_graph *h, const std::vector<Request> &group) {
+  const size_t nb = group.size();
+  std::vector<int64_t> doff(nb + 1, 0), ioff(nb + 1, 0);
+  for (size_t k = 0; k < nb; k++) {
+    doff[k + 1] = doff[k] + (int64_t)group[k].del_src.size();
+    ioff[k + 1] = ioff[k] + (int64_t)group[k].ins_src.size();
+  }
+  std::vector<uint32_t> ds, dd, is, id;
+  ds.reserve(doff[nb]);
+  dd.reserve(doff[nb]);
+  is.reserve(ioff[nb]);
+  id.reserve(ioff[nb]);
+  for (const Request &rq : group) {
+    ds.insert(ds.end(), rq.del_src.begin(), rq.del_src.end());
+    dd.insert(dd.end(), rq.del_dst.begin(), rq.del_dst.end());
+    is.insert(is.end(), rq.ins_src.begin(), rq.ins_src.end());
+    id.insert(id.end(), rq.ins_dst.begin(), rq.ins_dst.end());
+  }
+  return pr_apply_batches(h, (int32_t)nb, doff.data(), ds.data(), dd.data(), ioff.data(), is.data(), id.data());
+}
+
 void worker_loop(pr_server *s, int32_t gi) {
   pr_graph *h = s->graphs[gi];
   for (;;) {
@@ -110,11 +132,27 @@ void worker_loop(pr_server *s, int32_t gi) {
     if (dev != h->g.device) cudaSetDevice(h->g.device);
     std::vector<pr_status> st(group.size(), PR_OK);
     bool any = false;
-    for (size_t k = 0; k < group.size(); k++) {
-      const Request &rq = group[k];
-      st[k] = pr_apply_batch(h, (int64_t)rq.del_src.size(), rq.del_src.data(), rq.del_dst.data(),
+    if (group.size() == 1) {
+      const Request &rq = group[0];
+      st[0] = pr_apply_batch(h, (int64_t)rq.del_src.size(), rq.del_src.data(), rq.del_dst.data(),
                              (int64_t)rq.ins_src.size(), rq.ins_src.data(), rq.ins_dst.data());
-      any = any || st[k] == PR_OK;
+      any = st[0] == PR_OK;
+    } else {
+      // one sequence apply for the whole group; if it is rejected (the graph is then
+      // unchanged), each request is applied alone so that only the bad ones fail
+      pr_status all = apply_group(h, group);
+      if (all == PR_OK) {
+        any = true;
+      } else if (all == PR_ERR_VERTEX_RANGE || all == PR_ERR_INVALID_ARG) {
+        for (size_t k = 0; k < group.size(); k++) {
+          const Request &rq = group[k];
+          st[k] = pr_apply_batch(h, (int64_t)rq.del_src.size(), rq.del_src.data(), rq.del_dst.data(),
+                                 (int64_t)rq.ins_src.size(), rq.ins_src.data(), rq.ins_dst.data());
+          any = any || st[k] == PR_OK;
+        }
+      } else {
+        std::fill(st.begin(), st.end(), all);
+      }
     }
     pr_stats stats{};
     pr_status df = any ? pr_dynamic_frontier(h, &stats) : PR_OK;
@@ -158,7 +196,7 @@ pr_status pr_server_create(const pr_server_config *cfg, pr_server **out) {
   *out = nullptr;
   pr_server_config c;
   if (cfg) c = *cfg; else pr_server_config_default(&c);
-  if (c.slots < 1 || c.slots > 64 || c.max_coalesce < 1) return PR_ERR_INVALID_ARG;
+  if (c.slots < 1 || c.slots > 64 || c.max_coalesce < 1 || c.max_coalesce > PR_MAX_BATCHES) return PR_ERR_INVALID_ARG;
   pr_server *s = new (std::nothrow) pr_server;
   if (!s) return PR_ERR_OUT_OF_MEMORY;
   s->cfg = c;

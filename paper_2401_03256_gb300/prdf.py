@@ -29,7 +29,7 @@ PR_DEADEND_SELFLOOP = 0
 PR_DEADEND_TELEPORT = 1
 
 EXPORTED = (
-    "pr_params_default", "pr_graph_create", "pr_graph_destroy", "pr_apply_batch", "pr_static",
+    "pr_params_default", "pr_graph_create", "pr_graph_destroy", "pr_apply_batch", "pr_apply_batches", "pr_static",
     "pr_naive_dynamic", "pr_dynamic_frontier", "pr_get_ranks", "pr_set_ranks", "pr_graph_info",
     "pr_get_csr", "pr_get_affected", "pr_get_trace", "pr_kernel_launches", "pr_last_error", "pr_status_string",
     "pr_graph_create_batched", "pr_get_component_stats", "pr_set_tuning", "pr_get_tuning", "pr_autotune",
@@ -103,6 +103,8 @@ def load(path: str = LIB_PATH):
     lib.pr_graph_destroy.argtypes = [vp]
     lib.pr_apply_batch.restype = ctypes.c_int
     lib.pr_apply_batch.argtypes = [vp, i64, vp, vp, i64, vp, vp]
+    lib.pr_apply_batches.restype = ctypes.c_int
+    lib.pr_apply_batches.argtypes = [vp, ctypes.c_int32, vp, vp, vp, vp, vp, vp]
     for name in ("pr_static", "pr_naive_dynamic", "pr_dynamic_frontier"):
         f = getattr(lib, name)
         f.restype = ctypes.c_int
@@ -266,6 +268,28 @@ def pr_apply_batch(h: int, del_src, del_dst, ins_src, ins_dst) -> None:
     _check(load().pr_apply_batch(h, na, a, b, nc, c, d), h)
 
 
+def pr_apply_batches(h: int, batches) -> None:
+    """batches: a sequence of (del_src, del_dst, ins_src, ins_dst) host arrays, applied in
+    order by one library call."""
+    parts = [[], [], [], []]
+    doff, ioff = [0], [0]
+    for bt in batches:
+        arrs = [np.asarray(x, dtype=np.uint32).ravel() for x in bt]
+        if arrs[0].size != arrs[1].size or arrs[2].size != arrs[3].size:
+            raise ValueError("source and target arrays differ in length")
+        for k in range(4):
+            parts[k].append(arrs[k])
+        doff.append(doff[-1] + arrs[0].size)
+        ioff.append(ioff[-1] + arrs[2].size)
+    if not doff[1:]:
+        return
+    cat = [np.ascontiguousarray(np.concatenate(p) if p else np.zeros(0, np.uint32), dtype=np.uint32) for p in parts]
+    do = np.asarray(doff, dtype=np.int64)
+    io = np.asarray(ioff, dtype=np.int64)
+    _check(load().pr_apply_batches(h, len(doff) - 1, do.ctypes.data, cat[0].ctypes.data, cat[1].ctypes.data,
+                                   io.ctypes.data, cat[2].ctypes.data, cat[3].ctypes.data), h)
+
+
 def _rank(fn, h: int) -> pr_stats:
     s = pr_stats()
     _check(fn(h, ctypes.byref(s)), h)
@@ -383,6 +407,9 @@ class Graph:
 
     def apply(self, del_src, del_dst, ins_src, ins_dst):
         pr_apply_batch(self.h, del_src, del_dst, ins_src, ins_dst)
+
+    def apply_batches(self, batches):
+        pr_apply_batches(self.h, batches)
 
     def static(self) -> pr_stats:
         return pr_static(self.h)
