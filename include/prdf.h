@@ -201,6 +201,40 @@ pr_status pr_get_trace(const pr_graph *g, int32_t cap, double *phase_ms, double 
  * for accounting of device work.  Never fails. */
 uint64_t pr_kernel_launches(void);
 
+/* ------------------------------------------------------ allocation-free Static PageRank ----
+ * The paper has no counterpart to this entry point; it exists for callers that must not
+ * allocate device memory: code that draws all of its device memory from a host
+ * application's own pool or budget, latency-critical code that cannot afford the implicit
+ * device-wide synchronisation of cudaMalloc / cudaFree, and plugins that are handed device
+ * buffers but not the right to allocate.  Everything else in this library allocates.
+ *
+ * Static PageRank (Eq. 1, iterated from 1/n until the L-inf change is <= params->tol or
+ * params->max_iter iterations ran) of a graph given as an in-edge CSR in device memory:
+ * in_off[0..n] (non-decreasing from 0 to m) and in_col[0..m) = the sources u of the edges
+ * (u, v) of row v, in the layout pr_get_csr(g, 1, ...) exports.  Every vertex needs an
+ * out-edge (the self-loops of Section 3.1 give one).  The n ranks are written to `ranks`
+ * (device memory); the work runs on cuda_stream and the call returns when it is done.
+ * params may be NULL (defaults); it must ask for PR_F64 and PR_DEADEND_SELFLOOP.  stats
+ * may be NULL; its timing fields stay 0.  Arithmetic is plain FP64, so the ranks agree
+ * with pr_static's within the usual L-inf tolerance, not bit for bit.
+ *
+ * No device memory is allocated.  Working memory is one fixed array of
+ * PR_NOALLOC_SCRATCH_BYTES inside this library, held on every device that loads the
+ * library until the process exits; hence n <= PR_NOALLOC_MAX_VERTICES, and larger n is
+ * rejected with PR_ERR_CAPACITY before any device work.  The first call on a device looks
+ * up that array's device address (with that device current), so make the first call on
+ * each device before any stream capture begins.  All calls on a device share the array:
+ * calls whose work overlaps on the GPU (several host threads, or several streams) race and
+ * must be serialised by the caller.  A call clears what it needs cleared at its start.
+ * Errors: PR_ERR_INVALID_ARG (NULL or host pointers, pointers on another device than the
+ * current one, bad params, malformed offsets, a vertex with no out-edge),
+ * PR_ERR_VERTEX_RANGE (a column id >= n), PR_ERR_CUDA; ranks are written only after the
+ * CSR has passed these checks. */
+#define PR_NOALLOC_MAX_VERTICES (1u << 18)
+#define PR_NOALLOC_SCRATCH_BYTES (256u + 20u * PR_NOALLOC_MAX_VERTICES)
+pr_status pr_static_noalloc(uint32_t n, int64_t m, const uint64_t *in_off, const uint32_t *in_col,
+                            const pr_params *params, void *cuda_stream, double *ranks, pr_stats *stats);
+
 /* ---------------------------------------------------------------- serving form ----
  * A request loop over several resident graphs.  Each attached graph gets a FIFO and one
  * worker, so it has a single writer and its requests run in submission order; requests of

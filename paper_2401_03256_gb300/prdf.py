@@ -34,8 +34,10 @@ EXPORTED = (
     "pr_get_csr", "pr_get_affected", "pr_get_trace", "pr_kernel_launches", "pr_last_error", "pr_status_string",
     "pr_graph_create_batched", "pr_get_component_stats", "pr_set_tuning", "pr_get_tuning", "pr_autotune",
     "pr_set_graph_launch", "pr_server_config_default", "pr_server_create", "pr_server_add_graph",
-    "pr_server_submit", "pr_server_wait", "pr_server_drain", "pr_server_destroy",
+    "pr_server_submit", "pr_server_wait", "pr_server_drain", "pr_server_destroy", "pr_static_noalloc",
 )
+
+PR_NOALLOC_MAX_VERTICES = 1 << 18
 
 
 class pr_params(ctypes.Structure):
@@ -103,6 +105,8 @@ def load(path: str = LIB_PATH):
     lib.pr_graph_destroy.argtypes = [vp]
     lib.pr_apply_batch.restype = ctypes.c_int
     lib.pr_apply_batch.argtypes = [vp, i64, vp, vp, i64, vp, vp]
+    lib.pr_static_noalloc.restype = ctypes.c_int
+    lib.pr_static_noalloc.argtypes = [ctypes.c_uint32, i64, vp, vp, vp, vp, vp, vp]
     lib.pr_apply_batches.restype = ctypes.c_int
     lib.pr_apply_batches.argtypes = [vp, ctypes.c_int32, vp, vp, vp, vp, vp, vp]
     for name in ("pr_static", "pr_naive_dynamic", "pr_dynamic_frontier"):
@@ -288,6 +292,20 @@ def pr_apply_batches(h: int, batches) -> None:
     io = np.asarray(ioff, dtype=np.int64)
     _check(load().pr_apply_batches(h, len(doff) - 1, do.ctypes.data, cat[0].ctypes.data, cat[1].ctypes.data,
                                    io.ctypes.data, cat[2].ctypes.data, cat[3].ctypes.data), h)
+
+
+def pr_static_noalloc(n: int, in_off, in_col, ranks, params: pr_params | None = None,
+                      stream: int | None = None) -> pr_stats:
+    """Allocation-free Static PageRank of an in-edge CSR held in device memory (torch
+    tensors: in_off int64 [n + 1], in_col int32 [m], ranks float64 [n], all on the current
+    device); the library allocates no device memory for it."""
+    s = pr_stats()
+    st = load().pr_static_noalloc(n, int(in_col.numel()), in_off.data_ptr(), in_col.data_ptr(),
+                                  ctypes.byref(params) if params is not None else None, stream,
+                                  ranks.data_ptr(), ctypes.byref(s))
+    if st != PR_OK:
+        raise PrdfError(st, load().pr_status_string(st).decode())
+    return s
 
 
 def _rank(fn, h: int) -> pr_stats:
