@@ -550,6 +550,130 @@ def run_serving(args, rank: int, world: int, local_rank: int):
         print(json.dumps(line))
 
 
+# ----------------------------------------------------------- precision form ----
+
+def run_precision(args, rank: int, world: int, local_rank: int):
+    """Precision form (config 3): FP32 ranks and contributions with FP64 compensated
+    reductions, on a Kronecker (R-MAT initiator 0.57/0.19/0.19/0.05) scale-24 graph with
+    edge factor 16 and on a 4900 x 4900 directed grid with 1% random long-range arcs;
+    80/20 batches of 1e-5 and 1e-3 |E|.  Every update is run twice, by an FP32 handle and by
+    an FP64 handle of the same graph from the same previous ranks, and the L-inf distance of
+    the two results is the FP32 error (the FP64 path is the one held to the oracle at
+    1e-9).  value = geometric mean of the FP32 Dynamic Frontier times."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2401_03256_gb300 import build as libbuild
+
+    libbuild.build()
+    from paper_2401_03256_gb300 import prdf
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    fracs = [1e-5, 1e-3]
+    shapes = [("kronecker s24 ef16", lambda: synth.rmat(24, 16, seed=11 + rank)),
+              ("grid 4900x4900 + 1% long-range", lambda: synth.grid(4900, 4900, 0.01, seed=12 + rank))]
+    W, K = args.warmup, args.steps
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    out = {}
+    dfs = []
+    launches = 0
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    t_start = time.perf_counter()
+    for name, make in shapes:
+        g = make()
+        p32 = prdf.pr_params_default()
+        p32.precision = prdf.PR_F32
+        p64 = prdf.pr_params_default()
+        with torch.cuda.stream(stream):
+            A = prdf.Graph(g.n, g.src, g.dst, p32, stream.cuda_stream)
+            B = prdf.Graph(g.n, g.src, g.dst, p64, stream.cuda_stream)
+            n, m = A.info()
+            st32 = A.static()
+            st64 = B.static()
+            R32 = torch.empty(n, dtype=torch.float64, device=dev)
+            R64 = torch.empty(n, dtype=torch.float64, device=dev)
+            Rp = torch.empty(n, dtype=torch.float64, device=dev)
+            A.ranks(R32)
+            B.ranks(R64)
+            static_err = float((R32 - R64).abs().max())
+            A.set_ranks(R64)  # both chains start from the same FP64 ranks
+            bs = synth.BatchStream(g, seed=13 + rank)
+            rec = {f: {"df": [], "naive": [], "static": [], "apply": [], "err": [], "it": [], "it64": [],
+                       "aff": [], "bytes": [], "df64": []} for f in fracs}
+            l0 = prdf.pr_kernel_launches()
+            for i in range(W + K):
+                for f in fracs:
+                    b = bs.next(f)
+                    B.ranks(Rp)
+                    A.set_ranks(Rp)
+                    A.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+                    B.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+                    flush.zero_()
+                    s32 = A.frontier()
+                    flush.zero_()
+                    s64 = B.frontier()
+                    A.ranks(R32)
+                    B.ranks(R64)
+                    err = float((R32 - R64).abs().max())
+                    A.set_ranks(Rp)
+                    flush.zero_()
+                    sn = A.naive()
+                    flush.zero_()
+                    ss = A.static()
+                    if i >= W:
+                        r = rec[f]
+                        r["df"].append(s32.ms_rank)
+                        r["df64"].append(s64.ms_rank)
+                        r["apply"].append(s32.ms_apply)
+                        r["naive"].append(sn.ms_rank)
+                        r["static"].append(ss.ms_rank)
+                        r["err"].append(err)
+                        r["it"].append(s32.iterations)
+                        r["it64"].append(s64.iterations)
+                        r["aff"].append(s32.affected_final)
+                        r["bytes"].append(s32.bytes_algorithmic)
+            torch.cuda.synchronize(dev)
+            launches += prdf.pr_kernel_launches() - l0
+            A.close()
+            B.close()
+        mean = lambda xs: sum(xs) / len(xs)
+        per = {}
+        for f in fracs:
+            r = rec[f]
+            dfs.append(mean(r["df"]))
+            per[f"{f:g}"] = {
+                "df_ms": mean(r["df"]), "df_fp64_ms": mean(r["df64"]), "naive_ms": mean(r["naive"]),
+                "static_ms": mean(r["static"]), "apply_ms": mean(r["apply"]),
+                "speedup_vs_static": mean(r["static"]) / mean(r["df"]),
+                "speedup_vs_naive": mean(r["naive"]) / mean(r["df"]),
+                "df_gbs": sum(r["bytes"]) / (sum(r["df"]) * 1e-3) / 1e9,
+                "linf_err_vs_fp64_max": max(r["err"]), "df_iterations": mean(r["it"]),
+                "df_fp64_iterations": mean(r["it64"]), "df_affected": mean(r["aff"]),
+            }
+        out[name] = {"n": n, "m_with_self_loops": m, "static_linf_err_vs_fp64": static_err,
+                     "static_fp32_ms": st32.ms_rank, "static_fp64_ms": st64.ms_rank, "per_frac": per}
+        del g
+    t_end = time.perf_counter()
+    clk = clocks.stop()
+    value = geomean(dfs)
+    line = {
+        "metric": "precision form: FP32 Dynamic Frontier update ms (geomean over shapes and batch sizes)",
+        "value": value, "unit": "ms", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": (t_end - t_start) * 1e3 / (K + W), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "Kronecker s24 ef16 and 4900x4900 grid + 1% long-range, 80/20 batches 1e-5 and "
+                               "1e-3 |E|, FP32 ranks/contributions, FP64 compensated reductions",
+                   "l2": "flushed (256 MB write) before every timed call", "error_reference": "FP64 path, same inputs"},
+        "shapes": out, "gpu_launches": launches, "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+
+
 # -------------------------------------------------------- reference arm ----
 
 def run_reference(args, rank: int, world: int):
@@ -606,8 +730,9 @@ def main():
                     help="default fp64 for the plain workload, fp32 for the batched form")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-timeout", type=float, default=600.0)
-    ap.add_argument("--config", choices=["plain", "batched", "serving"], default="plain",
-                    help="plain: the headline workload (R-MAT s22 sweep); batched / serving: those forms")
+    ap.add_argument("--config", choices=["plain", "precision", "batched", "serving"], default="plain",
+                    help="plain: the headline workload (R-MAT s22 sweep); precision / batched / serving: "
+                         "those forms")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: Poisson arrivals per second")
     ap.add_argument("--duration", type=float, default=2.0, help="serving: seconds of arrivals")
     ap.add_argument("--slots", type=int, default=4, help="serving: concurrent updates")
@@ -624,6 +749,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.config == "precision":
+        run_precision(args, rank, world, local_rank)
     elif args.config == "batched":
         run_batched(args, rank, world, local_rank)
     elif args.config == "serving":

@@ -193,7 +193,8 @@ pr_status pr_get_affected(pr_graph *g, uint32_t *out, int64_t cap, int64_t *coun
  * clock: phase_ms = initial marking (phase 0); for each iteration i < *count (at most cap
  * entries written): iter_ms[i] its duration, affected[i] the vertices it covered, kind[i]
  * 0 = affected lists, 1 = compacted sweep items reused, 2 = sweep items compacted in this
- * iteration, 3 = all vertices.  Any of the output arrays may be NULL (host memory). */
+ * iteration, 3 = all vertices, 4 = all sweep items scanned, those of vertices stamped later
+ * skipped.  Any of the output arrays may be NULL (host memory). */
 pr_status pr_get_trace(const pr_graph *g, int32_t cap, double *phase_ms, double *iter_ms, int64_t *affected,
                        int32_t *kind, int32_t *count);
 

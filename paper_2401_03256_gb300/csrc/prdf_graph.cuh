@@ -78,6 +78,7 @@ struct Graph {
   cudaGraphExec_t cg_exec = nullptr;
   cudaGraphNode_t cg_kernel = nullptr;
   bool cg_f32 = false;
+  bool cg_df = false;
   uint32_t last_list_cnt[3] = {0, 0, 0};
   bool last_full = false;
 

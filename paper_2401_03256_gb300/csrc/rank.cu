@@ -20,8 +20,9 @@
 //             anything new.  One grid barrier per iteration; all blocks read the same
 //             L-inf value and stop together when it is <= tau.
 //             Sparse iterations walk the affected lists; once they hold more than
-//             n / kDenseDiv vertices an iteration walks all vertices in bin order and
-//             skips those whose stamp is later than i (same set, better locality).
+//             n / dense_div vertices an iteration walks the sweep items of the affected
+//             vertices in tier order (same set, better locality); marks made in dense
+//             iterations are buffered per warp and appended to list 0 in runs.
 //   writeback the final parity is copied to the other for every affected vertex (both
 //             parities hold the current ranks between calls) and the per-call marks are
 //             cleared.
@@ -45,7 +46,6 @@ namespace prdf {
 constexpr uint64_t kBarrierTimeoutNs = 4000000000ull;  // 4 s
 constexpr int kWarps = kRankBlock / 32;
 constexpr uint32_t kFull = 0xffffffffu;
-constexpr uint32_t kDenseDiv = 16;  // dense iteration once affected > n / kDenseDiv
 constexpr uint16_t kNoStamp = 0xFFFF;
 constexpr uint32_t kInlineOut = 128;  // longer out-rows are marked by the whole grid (hub queue)
 #ifndef PRDF_RANK_MIN_BLOCKS
@@ -239,22 +239,80 @@ __device__ __forceinline__ int bin_of(uint32_t deg, uint32_t lo, uint32_t hi) {
   return deg <= lo ? 0 : (deg <= hi ? 1 : 2);
 }
 
-// Appends, per bin, the lanes' newly marked vertices with one atomic per bin and warp.
+// Newly marked vertices are buffered per warp in shared memory, one run per bin, and
+// appended to the bin's list with one global atomic per run rather than one per marking
+// round (the list tails are contended by every warp of the grid).  Every buffer is flushed
+// before the grid barrier after which the tails are read.  In dense iterations all marks
+// go to list 0 and the in-degree lookup for the bin is skipped: later iterations are dense
+// too (the affected set only grows) and sweep the sweep items, and the writeback only
+// needs every affected vertex in some list.
+constexpr uint32_t kMarkBuf = 64;
+struct WarpBuf {
+  uint32_t *buf;   // [3][kMarkBuf] entries of this warp's shared memory
+  uint32_t n[3];   // entries held per bin (the same in every lane)
+  bool dense;
+};
+
 template <bool F32>
-__device__ __forceinline__ void warp_append(const RankArgs<F32> &a, int bin, uint32_t w, uint32_t slot,
-                                            const uint32_t cnt[3], uint32_t lane) {
-  uint32_t *lists[3] = {a.list0, a.list1, a.list2};
+__device__ __forceinline__ void flush_bin(const RankArgs<F32> &a, int bb, uint32_t slot, const uint32_t cnt[3],
+                                          uint32_t lane, WarpBuf &wb) {
+  __syncwarp();
+  const uint32_t k = wb.n[bb];
+  if (k) {
+    uint32_t *lists[3] = {a.list0, a.list1, a.list2};
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(&a.ctl->tail[slot][bb], k);
+    base = __shfl_sync(kFull, base, 0);
+    for (uint32_t i = lane; i < k; i += 32) lists[bb][cnt[bb] + base + i] = wb.buf[bb * kMarkBuf + i];
+  }
+  __syncwarp();
+  wb.n[bb] = 0;
+}
+
+template <bool F32>
+__device__ __forceinline__ void flush_marks(const RankArgs<F32> &a, uint32_t slot, const uint32_t cnt[3],
+                                            uint32_t lane, WarpBuf &wb) {
 #pragma unroll
-  for (int bb = 0; bb < 3; bb++) {
-    uint32_t mask = __ballot_sync(kFull, bin == bb);
+  for (int bb = 0; bb < 3; bb++) flush_bin(a, bb, slot, cnt, lane, wb);
+}
+
+// Appends w where fresh to its bin's run in the warp's buffer.  Called by a whole warp.
+template <bool F32>
+__device__ __forceinline__ void append_mark(const RankArgs<F32> &a, bool fresh, uint32_t w, uint32_t slot,
+                                            const uint32_t cnt[3], uint32_t lane, WarpBuf &wb) {
+  int bin = -1;
+  if (fresh) bin = wb.dense ? 0 : bin_of(__ldg(&a.in_rd[w]).y, a.bin_lo, a.bin_hi);
+  const int nb = wb.dense ? 1 : 3;
+  for (int bb = 0; bb < nb; bb++) {
+    const uint32_t mask = __ballot_sync(kFull, bin == bb);
     if (mask) {
-      uint32_t leader = __ffs(mask) - 1;
-      uint32_t base = 0;
-      if (lane == leader) base = atomicAdd(&a.ctl->tail[slot][bb], (uint32_t)__popc(mask));
-      base = __shfl_sync(kFull, base, leader);
-      if (bin == bb) lists[bb][cnt[bb] + base + __popc(mask & lanemask_lt())] = w;
+      if (wb.n[bb] + __popc(mask) > kMarkBuf) flush_bin(a, bb, slot, cnt, lane, wb);
+      if (bin == bb) wb.buf[bb * kMarkBuf + wb.n[bb] + __popc(mask & lanemask_lt())] = w;
+      wb.n[bb] += __popc(mask);
     }
   }
+}
+
+// Marks w (where valid) for iteration `slot`: a plain read of the bitmap first, then the
+// atomic; a newly marked vertex is stamped and appended through the warp's buffer.  Called
+// by a whole warp; returns 1 where this lane marked a new vertex.
+template <bool F32>
+__device__ __forceinline__ uint32_t mark_one(const RankArgs<F32> &a, bool valid, uint32_t w, uint32_t slot,
+                                             const uint32_t cnt[3], uint32_t lane, WarpBuf &wb) {
+  bool fresh = false;
+  if (valid) {
+    uint32_t bit = 1u << (w & 31);
+    uint32_t *word = a.bitmap + (w >> 5);
+    if (!(ldcg(word) & bit)) {
+      uint32_t old = atomicOr(word, bit);
+      if (!(old & bit)) {
+        fresh = true;
+        a.stamp[w] = (uint16_t)slot;
+      }
+    }
+  }
+  append_mark(a, fresh, w, slot, cnt, lane, wb);
+  return fresh ? 1u : 0u;
 }
 
 // Marks cols[first + 32 k + lane] (k = 0, 1, ...; stride `stride`), stamping newly marked
@@ -262,28 +320,51 @@ __device__ __forceinline__ void warp_append(const RankArgs<F32> &a, int bin, uin
 template <bool F32>
 __device__ __forceinline__ uint32_t warp_mark_range(const RankArgs<F32> &a, const uint32_t *cols, uint32_t len,
                                                     uint32_t first, uint32_t stride, uint32_t slot,
-                                                    const uint32_t cnt[3], uint32_t lane) {
+                                                    const uint32_t cnt[3], uint32_t lane, WarpBuf &wb) {
   uint32_t newly_total = 0;
   for (uint32_t j0 = first; j0 < len; j0 += stride) {
-    uint32_t j = j0 + lane;
-    int bin = -1;
-    uint32_t w = 0;
-    if (j < len) {
-      w = __ldg(cols + j);
-      uint32_t bit = 1u << (w & 31);
-      uint32_t *word = a.bitmap + (w >> 5);
-      if (!(ldcg(word) & bit)) {
-        uint32_t old = atomicOr(word, bit);
-        if (!(old & bit)) {
-          bin = bin_of(__ldg(&a.in_rd[w]).y, a.bin_lo, a.bin_hi);
-          a.stamp[w] = (uint16_t)slot;
-        }
-      }
-    }
-    newly_total += bin >= 0;
-    warp_append(a, bin, w, slot, cnt, lane);
+    const uint32_t j = j0 + lane;
+    const bool valid = j < len;
+    newly_total += mark_one(a, valid, valid ? __ldg(cols + j) : 0u, slot, cnt, lane, wb);
   }
   return newly_total;
+}
+
+// Short out-rows (at most kThreadOut entries; a row starts 16-byte aligned and its slots
+// come in whole groups of four): every lane in `mine` marks its own row.  The bitmap words
+// of all its entries are read together and the atomics for the clear bits are issued
+// together, so a row costs two dependent round trips rather than a pair per entry; the
+// stamps and warp-aggregated appends follow entry by entry.  Called by a whole warp.
+constexpr uint32_t kThreadOut = 8;
+template <bool F32>
+__device__ __forceinline__ uint32_t lane_mark_rows(const RankArgs<F32> &a, bool mine, uint2 od, uint32_t slot,
+                                                   const uint32_t cnt[3], uint32_t lane, WarpBuf &wb) {
+  const uint32_t len = mine ? od.y : 0u;
+  const uint32_t rounds = __reduce_max_sync(kFull, len);
+  uint4 q0 = make_uint4(0, 0, 0, 0), q1 = q0;
+  if (len > 0) q0 = __ldg(reinterpret_cast<const uint4 *>(a.out_col + od.x));
+  if (len > 4) q1 = __ldg(reinterpret_cast<const uint4 *>(a.out_col + od.x + 4));
+  const uint32_t w[kThreadOut] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+  uint32_t word[kThreadOut];
+#pragma unroll
+  for (uint32_t k = 0; k < kThreadOut; k++) word[k] = k < len ? ldcg(a.bitmap + (w[k] >> 5)) : ~0u;
+  uint32_t fresh = 0;  // bit k: entry k newly marked by this lane
+#pragma unroll
+  for (uint32_t k = 0; k < kThreadOut; k++) {
+    const uint32_t bit = 1u << (w[k] & 31);
+    if (!(word[k] & bit) && !(atomicOr(a.bitmap + (w[k] >> 5), bit) & bit)) fresh |= 1u << k;
+  }
+  uint32_t newly = 0;
+#pragma unroll
+  for (uint32_t k = 0; k < kThreadOut; k++) {
+    if (k < rounds) {
+      const bool f = (fresh >> k) & 1u;
+      if (f) a.stamp[w[k]] = (uint16_t)slot;
+      append_mark(a, f, w[k], slot, cnt, lane, wb);
+      newly += f ? 1u : 0u;
+    }
+  }
+  return newly;
 }
 
 // True the first time v asks (per call): its out-row is then scanned by the caller.  A
@@ -294,6 +375,13 @@ __device__ __forceinline__ bool first_expansion(uint32_t *xbits, uint32_t v) {
   if (__ldcg(xbits + (v >> 5)) & bit) return false;
   return !(atomicOr(xbits + (v >> 5), bit) & bit);
 }
+// The same with the word read beforehand (issued with the row's loads, so the test adds no
+// round trip); the atomic still decides, so a stale word only costs an atomic.
+__device__ __forceinline__ bool first_expansion_pre(uint32_t *xbits, uint32_t v, uint32_t word) {
+  uint32_t bit = 1u << (v & 31);
+  if (word & bit) return false;
+  return !(atomicOr(xbits + (v >> 5), bit) & bit);
+}
 
 // Marks the out-neighbours of v for iteration `slot`: short out-rows by the calling warp,
 // long ones queued for the cooperative pass that follows the iteration's barrier (entry
@@ -301,8 +389,8 @@ __device__ __forceinline__ bool first_expansion(uint32_t *xbits, uint32_t v) {
 // Called by a whole warp; returns the vertices this warp newly marked.
 template <bool F32>
 __device__ __forceinline__ uint32_t expand_vertex(const RankArgs<F32> &a, uint32_t v, uint2 od, uint32_t slot,
-                                                  const uint32_t cnt[3], uint32_t lane) {
-  if (od.y <= kInlineOut) return warp_mark_range(a, a.out_col + od.x, od.y, 0, 32, slot, cnt, lane);
+                                                  const uint32_t cnt[3], uint32_t lane, WarpBuf &wb) {
+  if (od.y <= kInlineOut) return warp_mark_range(a, a.out_col + od.x, od.y, 0, 32, slot, cnt, lane, wb);
   if (lane == 0) {
     const uint32_t nch = (od.y + kChunk - 1) / kChunk;
     const unsigned long long old = atomicAdd(&a.ctl->hubq[slot], (1ull << 32) | nch);
@@ -317,7 +405,7 @@ __device__ __forceinline__ uint32_t expand_vertex(const RankArgs<F32> &a, uint32
 // dealt round-robin to all warps of the grid.
 template <bool F32>
 __device__ uint32_t hub_pass(const RankArgs<F32> &a, uint32_t slot, const uint32_t cnt[3], uint32_t lane,
-                             uint32_t gwarp, uint32_t nwarps) {
+                             uint32_t gwarp, uint32_t nwarps, WarpBuf &wb) {
   const unsigned long long hq = __ldcg(&a.ctl->hubq[slot]);
   const uint32_t ne = (uint32_t)(hq >> 32), K = (uint32_t)hq;
   uint32_t newly = 0;
@@ -330,7 +418,7 @@ __device__ uint32_t hub_pass(const RankArgs<F32> &a, uint32_t slot, const uint32
     const uint32_t v = __ldcg(a.hub_v + lo), c = k - __ldcg(a.hub_base + lo);
     const uint2 od = __ldg(&a.out_rd[v]);
     const uint32_t start = c * kChunk;
-    newly += warp_mark_range(a, a.out_col + od.x + start, min(kChunk, od.y - start), 0, 32, slot, cnt, lane);
+    newly += warp_mark_range(a, a.out_col + od.x + start, min(kChunk, od.y - start), 0, 32, slot, cnt, lane, wb);
   }
   return newly;
 }
@@ -414,7 +502,288 @@ __device__ __forceinline__ typename Num<F32>::B finish_vertex(const RankArgs<F32
 
 __device__ __forceinline__ uint4 ldcg(const uint4 *p) { return __ldcg(p); }
 
+// Frontier expansion of the lanes' vertices that changed by more than tau_f (push):
+// short out-rows by their own lanes together, longer ones by the whole warp (or the hub
+// queue) one at a time.  Out of line: it runs only when some lane of the warp expands, and
+// keeping its registers out of the sweep loops keeps those loops free of spills.  Called
+// by a whole warp.
+struct ExpandOut {
+  uint32_t app, xv, xe;  // vertices appended; vertices and out-edges expanded (this lane)
+};
 template <bool F32>
+__device__ __noinline__ ExpandOut expand_lanes(const RankArgs<F32> &a, int push, uint32_t v, uint32_t slot,
+                                               uint32_t c0, uint32_t c1, uint32_t c2, WarpBuf *wbp) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t cnt[3] = {c0, c1, c2};
+  WarpBuf wb = *wbp;
+  ExpandOut o{0u, 0u, 0u};
+  uint2 od = make_uint2(0, 0);
+  if (push) od = __ldg(&a.out_rd[v]);
+  const bool mine = push && od.y <= kThreadOut;
+  if (__any_sync(kFull, mine)) o.app += lane_mark_rows(a, mine, od, slot, cnt, lane, wb);
+  if (mine) {
+    o.xv++;
+    o.xe += od.y;
+  }
+  uint32_t mask = __ballot_sync(kFull, push && !mine);
+  while (mask) {
+    const uint32_t src = __ffs(mask) - 1;
+    mask &= mask - 1;
+    const uint32_t x = __shfl_sync(kFull, v, src);
+    const uint2 ox = make_uint2(__shfl_sync(kFull, od.x, src), __shfl_sync(kFull, od.y, src));
+    o.app += expand_vertex(a, x, ox, slot, cnt, lane, wb);
+    if (lane == 0) {
+      o.xv++;
+      o.xe += ox.y;
+    }
+  }
+  *wbp = wb;
+  return o;
+}
+
+// One vertex's out-row (hub rows queued), by the whole warp; out of line like expand_lanes.
+template <bool F32>
+__device__ __noinline__ ExpandOut expand_one(const RankArgs<F32> &a, uint32_t v, uint32_t slot, uint32_t c0,
+                                             uint32_t c1, uint32_t c2, WarpBuf *wbp) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t cnt[3] = {c0, c1, c2};
+  WarpBuf wb = *wbp;
+  const uint2 od = __ldg(&a.out_rd[v]);
+  ExpandOut o{expand_vertex(a, v, od, slot, cnt, lane, wb), 0u, 0u};
+  if (lane == 0) {
+    o.xv = 1;
+    o.xe = od.y;
+  }
+  *wbp = wb;
+  return o;
+}
+
+// In/out state of an out-of-line sweep of the sweep items (full and dense iterations).
+template <bool F32>
+struct SweepIo {
+  const typename Store<F32>::R *Rin;
+  const typename Store<F32>::C *Cin;
+  typename Store<F32>::R *Rout;
+  typename Store<F32>::C *Cout;
+  const uint4 *T;
+  uint32_t n0, n1, n2, off1, off2;
+  uint32_t it, slot;
+  uint32_t cnt[3];
+  bool scan_all, expand;
+  Iter<F32> I;
+  const typename Store<F32>::R *s_base;
+  unsigned long long *s_kmax;
+  const uint8_t *s_active;
+  WarpBuf *wb;
+  Mass<F32> dacc;
+  typename Num<F32>::B my_max;
+  uint32_t my_v = 0, my_e = 0, my_xv = 0, my_xe = 0, my_app = 0;
+};
+
+// The three tiers of a full or dense iteration.
+template <bool F32, bool DF>
+__device__ __forceinline__ void sweep_tiers(const RankArgs<F32> &a, SweepIo<F32> &io) {
+  using S = Store<F32>;
+  using R = typename S::R;
+  using C = typename S::C;
+  using B = typename Num<F32>::B;
+  const uint32_t tid = threadIdx.x, lane = tid & 31;
+  const uint32_t nwarps = (gridDim.x * kRankBlock) >> 5, gwarp = (blockIdx.x * kRankBlock + tid) >> 5;
+  const bool multi = a.ncomp > 1;
+  const R *Rin = io.Rin;
+  const C *Cin = io.Cin;
+  R *Rout = io.Rout;
+  C *Cout = io.Cout;
+  const uint4 *T = io.T;
+  const uint32_t n0 = io.n0, n1 = io.n1, n2 = io.n2, off1 = io.off1, off2 = io.off2;
+  const uint32_t it = io.it, slot = io.slot;
+  const uint32_t cnt[3] = {io.cnt[0], io.cnt[1], io.cnt[2]};
+  const bool scan_all = io.scan_all;
+  const bool expand = DF && io.expand;
+  const Iter<F32> I = io.I;
+  Mass<F32> dacc = io.dacc;
+  WarpBuf wb = *io.wb;
+  B my_max = io.my_max;
+  uint32_t my_v = 0, my_e = 0, my_xv = 0, my_xe = 0, my_app = 0;
+  const unsigned long long pol_cols = l2_evict_first(), pol_c = l2_evict_last();
+
+  auto live = [&](uint32_t v) -> bool { return !multi || io.s_active[__ldg(a.comp + v)]; };
+  auto take = [&](uint32_t v) -> bool {
+    return live(v) && (!scan_all || ldcg(a.stamp + v) <= (uint16_t)it);
+  };
+  auto finish_at = [&](uint32_t v, C sum, R rold, typename S::A ad) -> B {
+    const uint32_t c = multi ? (uint32_t)__ldg(a.comp + v) : 0u;
+    const B dr = finish_vertex(a, Rout, Cout, v, sum, rold, ad, I, dacc, pol_c, multi ? io.s_base[c] : a.base);
+    if (multi) atomicMax(&io.s_kmax[c], Num<F32>::key(dr));
+    else my_max = dr > my_max ? dr : my_max;
+    return dr;
+  };
+  auto expand_if = [&](int push, uint32_t v) {
+    if (__any_sync(kFull, push)) {
+      const ExpandOut o = expand_lanes(a, push, v, slot, cnt[0], cnt[1], cnt[2], &wb);
+      my_app += o.app;
+      my_xv += o.xv;
+      my_xe += o.xe;
+    }
+  };
+
+    // tier 0: one thread per vertex, 32 consecutive items per warp
+    for (uint32_t b0 = gwarp * 32; b0 < n0; b0 += nwarps * 32) {
+      const uint32_t i = b0 + lane;
+      int push = 0;
+      uint32_t v = 0;
+      if (i < n0 && take(ldcg(T + i).x)) {
+        const uint4 item = ldcg(T + i);
+        v = item.x;
+        const R rold = ldcg(Rin + v);
+        const typename S::A ad = __ldg(a.adeg + v);
+        const uint32_t xw = expand ? __ldcg(a.xbits + (v >> 5)) : 0u;
+        C sum = row_sum_thread(Cin, a.in_col + item.y, item.z, pol_cols, pol_c);
+        B dr = finish_at(v, sum, rold, ad);
+        my_v++;
+        my_e += item.z;
+        push = expand && dr > a.ftol && first_expansion_pre(a.xbits, v, xw);
+      }
+      if constexpr (DF) {
+        if (expand) expand_if(push, v);
+      }
+    }
+
+    // tier 1: rows of lo < len <= kGroupMax by 8-lane groups, four vertices per warp
+    {
+      const uint32_t grp = lane >> 3, gl = lane & 7;
+      for (uint32_t b0 = gwarp * 4; b0 < n1; b0 += nwarps * 4) {
+        const uint32_t i = b0 + grp;
+        const bool act = i < n1 && take(ldcg(T + off1 + i).x);
+        uint32_t xw = 0;
+        uint4 item = make_uint4(0, 0, 0, 0);
+        R rold = (R)0;
+        typename S::A ad = (typename S::A)0;
+        C sum = (C)0;
+        if (act) {
+          item = ldcg(T + off1 + i);
+          if (gl == 0) {
+            rold = ldcg(Rin + item.x);
+            ad = __ldg(a.adeg + item.x);
+            if (expand) xw = __ldcg(a.xbits + (item.x >> 5));
+          }
+          const uint32_t *cols = a.in_col + item.y;
+          uint4 q[2];
+#pragma unroll
+          for (int r = 0; r < 2; r++) {
+            const uint32_t j = 4 * (gl + 8 * r);
+            if (j < item.z) q[r] = ld_cols(cols + j, pol_cols);
+          }
+#pragma unroll
+          for (int r = 0; r < 2; r++) {
+            const uint32_t j = 4 * (gl + 8 * r);
+            if (j < item.z) sum += gather4(Cin, q[r], min(4u, item.z - j), pol_c);
+          }
+        }
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
+        int push = 0;
+        if (act && gl == 0) {
+          B dr = finish_at(item.x, sum, rold, ad);
+          my_v++;
+          my_e += item.z;
+          push = expand && dr > a.ftol && first_expansion_pre(a.xbits, item.x, xw);
+        }
+        if constexpr (DF) {
+          if (expand) expand_if(push, item.x);
+        }
+      }
+    }
+
+    // tier 2: kChunk-edge chunks dealt round-robin to warps (a hub's consecutive chunks
+    // land on different warps); a row split into several chunks is finished by the warp
+    // that completes its last chunk, which adds the partial sums in chunk order
+    C *part = a.partials;
+    for (uint32_t k = gwarp; k < n2; k += nwarps) {
+      const uint4 ch = ldcg(T + off2 + k);
+      const uint32_t v = ch.x;
+      if (!take(v)) continue;
+      const uint32_t len = ch.z & 0x3FFu;
+      const bool multi = (ch.z >> 31) != 0;
+      R rold = (R)0;
+      typename S::A ad = (typename S::A)0;
+      uint32_t deg = len, xw = 0;
+      if (lane == 0) {
+        rold = ldcg(Rin + v);
+        ad = __ldg(a.adeg + v);
+        if (multi) deg = __ldg(&a.in_rd[v]).y;
+        if (expand) xw = __ldcg(a.xbits + (v >> 5));
+      }
+      const uint32_t *cols = a.in_col + ch.y;
+      uint4 q[4];
+#pragma unroll
+      for (int r = 0; r < 4; r++) {
+        const uint32_t j = 4 * (lane + 32 * r);
+        if (j < len) q[r] = ld_cols(cols + j, pol_cols);
+      }
+      C sum = (C)0;
+#pragma unroll
+      for (int r = 0; r < 4; r++) {
+        const uint32_t j = 4 * (lane + 32 * r);
+        if (j < len) sum += gather4(Cin, q[r], min(4u, len - j), pol_c);
+      }
+      sum = warp_sum(sum);
+      int finish = 1;
+      if (multi) {
+        // publish this chunk's partial; the last of the row's chunks adds them up
+        const uint32_t nch = (__shfl_sync(kFull, deg, 0) + kChunk - 1) / kChunk;
+        uint32_t old = 0;
+        if (lane == 0) {
+          part[ch.w] = sum;
+          __threadfence();
+          old = atomicAdd(&a.chunk_done[v], 1u);
+        }
+        old = __shfl_sync(kFull, old, 0);
+        finish = old == nch - 1;
+        if (finish) {
+          __threadfence();
+          const uint32_t first = ch.w - ((ch.z >> 10) & 0x1FFFFFu);
+          C tot = (C)0;
+          for (uint32_t c = lane; c < nch; c += 32) tot += ldcg(part + first + c);
+          // lane order then a fixed shuffle tree: the same sum whichever warp finishes
+          sum = warp_sum(tot);
+          if (lane == 0) a.chunk_done[v] = 0;
+        }
+      }
+      if (finish) {
+        int exp_now = 0;
+        if (lane == 0) {
+          B dr = finish_at(v, sum, rold, ad);
+          my_v++;
+          my_e += deg;
+          exp_now = expand && dr > a.ftol && first_expansion_pre(a.xbits, v, xw);
+        }
+        if constexpr (DF) {
+          exp_now = __shfl_sync(kFull, exp_now, 0);
+          if (exp_now) {
+            const ExpandOut o = expand_one(a, v, slot, cnt[0], cnt[1], cnt[2], &wb);
+            my_app += o.app;
+            my_xv += o.xv;
+            my_xe += o.xe;
+          }
+        }
+      }
+    }
+
+  io.my_max = my_max;
+  io.dacc = dacc;
+  *io.wb = wb;
+  io.my_v = my_v;
+  io.my_e = my_e;
+  io.my_xv = my_xv;
+  io.my_xe = my_xe;
+  io.my_app = my_app;
+}
+
+
+// DF: compiled for Dynamic Frontier calls (marking and frontier expansion); Static and
+// Naive-dynamic use the instance without them, which needs fewer registers.
+template <bool F32, bool DF>
 __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const RankArgs<F32> a) {
   using S = Store<F32>;
   using R = typename S::R;
@@ -425,6 +794,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
   __shared__ unsigned long long s_key[kWarps];
   __shared__ double s_ds[kWarps], s_dc[kWarps];
   __shared__ int s_expand;
+  __shared__ uint32_t s_mbuf[kWarps][3 * kMarkBuf];
 
   const uint32_t tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
   const uint32_t nblk = gridDim.x;
@@ -433,7 +803,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
   const uint32_t nwarps = nthreads >> 5, gwarp = gtid >> 5;
   RankCtl *ctl = a.ctl;
   uint32_t epoch = 0;
-  const bool df = a.mode == kModeDF;
+  constexpr bool df = DF;
   // per-component state (batched form), identical in every block
   const bool multi = a.ncomp > 1;
   const uint32_t nc = a.ncomp;
@@ -532,23 +902,26 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
     for (uint32_t k = gtid; k < a.n_dead; k += nthreads) dacc.add(ldcg(a.R0 + __ldg(a.dead + k)));
   }
   const uint32_t zero_cnt[3] = {0, 0, 0};
+  WarpBuf wb{s_mbuf[wib], {0u, 0u, 0u}, false};
   if (df && !a.start_full) {
     // sources: mark G^t.out(u), one warp per source
     for (uint32_t k = gwarp; k < a.n_pend_src; k += nwarps) {
       uint32_t u = __ldg(a.pend_src + k);
       uint2 od = __ldg(&a.out_rd[u]);
-      my_app += expand_vertex(a, u, od, 0, zero_cnt, lane);
+      my_app += expand_vertex(a, u, od, 0, zero_cnt, lane, wb);
     }
     // deleted targets, 32 per warp round
     for (uint32_t k0 = gwarp * 32; k0 < a.n_pend_tgt; k0 += nwarps * 32) {
       uint32_t cnt_left = min(32u, a.n_pend_tgt - k0);
-      my_app += warp_mark_range(a, a.pend_tgt + k0, cnt_left, 0, 32, 0, zero_cnt, lane);
+      my_app += warp_mark_range(a, a.pend_tgt + k0, cnt_left, 0, 32, 0, zero_cnt, lane, wb);
     }
   }
+  flush_marks(a, 0u, zero_cnt, lane, wb);
   if (a.teleport) block_dead_partial(0);
   if (!grid_sync(ctl, epoch, &s_err)) return;
   if (df && __ldcg(&ctl->hubq[0]) != 0) {
-    my_app += hub_pass(a, 0, zero_cnt, lane, gwarp, nwarps);
+    my_app += hub_pass(a, 0, zero_cnt, lane, gwarp, nwarps, wb);
+    flush_marks(a, 0u, zero_cnt, lane, wb);
     if (!grid_sync(ctl, epoch, &s_err)) return;
   }
   if (blockIdx.x == 0 && tid == 0) ctl->t_ns[1] = globaltimer_ns();
@@ -566,6 +939,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
   unsigned long long last_key = 0;
   const uint32_t dense_at = a.n / a.dense_div;
   uint32_t cmp_total = 0xFFFFFFFFu;  // affected count at the last compaction (none yet)
+  uint32_t prev_total = 0xFFFFFFFFu; // affected count at the start of the previous iteration
   uint32_t cmp_n[3] = {0, 0, 0};
   uint32_t deact = 0, cmp_deact = 0;  // iterations in which some graph stopped (batched form)
 
@@ -588,26 +962,31 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
     // dense: once the affected lists are large, iterate over the sweep items of the affected
     // vertices (compacted from all items whenever the affected set grew), in tier order
     const bool dense = !I.full && (cnt[0] + cnt[1] + cnt[2] > dense_at);
+    // dense iterations sweep the compacted items of the affected vertices, compacted again
+    // when the set changed; a set that is large (over n / 4) and still growing by more than
+    // 1/16 per iteration is instead swept through all items, skipping vertices stamped later
+    // than it
+    const uint32_t total_now = cnt[0] + cnt[1] + cnt[2];
+    const bool scan_all = dense && total_now != cmp_total && total_now > a.n / 4 &&
+                          (prev_total == 0xFFFFFFFFu || total_now - prev_total > total_now / 16);
+    prev_total = total_now;
     const bool expand = df && !I.full;
     const uint32_t slot = (uint32_t)it + 1;
     B my_max = 0;
     if (blockIdx.x == 0 && tid == 0) {
       ctl->it_aff[it] = I.full ? a.n : cnt[0] + cnt[1] + cnt[2];
-      ctl->it_kind[it] = I.full ? 3 : (dense ? (cnt[0] + cnt[1] + cnt[2] != cmp_total ? 2 : 1) : 0);
+      ctl->it_kind[it] =
+          I.full ? 3 : (scan_all ? 4 : (dense ? (cnt[0] + cnt[1] + cnt[2] != cmp_total ? 2 : 1) : 0));
     }
 
-    auto expand_lanes = [&](int push, uint32_t v) {
-      uint32_t mask = __ballot_sync(kFull, push);
-      while (mask) {
-        const uint32_t src = __ffs(mask) - 1;
-        mask &= mask - 1;
-        const uint32_t x = __shfl_sync(kFull, v, src);
-        const uint2 od = __ldg(&a.out_rd[x]);
-        my_app += expand_vertex(a, x, od, slot, cnt, lane);
-        if (lane == 0) {
-          my_xv++;
-          my_xe += od.y;
-        }
+    wb.dense = dense;
+
+    auto expand_if = [&](int push, uint32_t v) {
+      if (__any_sync(kFull, push)) {
+        const ExpandOut o = expand_lanes(a, push, v, slot, cnt[0], cnt[1], cnt[2], &wb);
+        my_app += o.app;
+        my_xv += o.xv;
+        my_xe += o.xe;
       }
     };
 
@@ -624,7 +1003,10 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
       const uint32_t off1 = a.it_c0, off2 = a.it_c0 + a.it_c1;
       const uint4 *T = a.items;
       uint32_t n0 = a.it_c0, n1 = a.it_c1, n2 = a.it_c2;
-      if (dense) {
+      auto take = [&](uint32_t v) -> bool {
+        return live(v) && (!scan_all || ldcg(a.stamp + v) <= (uint16_t)it);
+      };
+      if (dense && !scan_all) {
         const uint32_t total = cnt[0] + cnt[1] + cnt[2];
         if (total != cmp_total || deact != cmp_deact) {
           // keep the items of vertices stamped <= it; warp-aggregated appends keep runs of
@@ -663,140 +1045,39 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
         n2 = cmp_n[2];
       }
 
-      // tier 0: one thread per vertex, 32 consecutive items per warp
-      for (uint32_t b0 = gwarp * 32; b0 < n0; b0 += nwarps * 32) {
-        const uint32_t i = b0 + lane;
-        int push = 0;
-        uint32_t v = 0;
-        if (i < n0 && live(ldcg(T + i).x)) {
-          const uint4 item = ldcg(T + i);
-          v = item.x;
-          const R rold = ldcg(Rin + v);
-          const typename S::A ad = __ldg(a.adeg + v);
-          C sum = row_sum_thread(Cin, a.in_col + item.y, item.z, pol_cols, pol_c);
-          B dr = finish_at(v, sum, rold, ad);
-          my_v++;
-          my_e += item.z;
-          push = expand && dr > a.ftol && first_expansion(a.xbits, v);
-        }
-        if (expand) expand_lanes(push, v);
-      }
-
-      // tier 1: rows of lo < len <= kGroupMax by 8-lane groups, four vertices per warp
-      {
-        const uint32_t grp = lane >> 3, gl = lane & 7;
-        for (uint32_t b0 = gwarp * 4; b0 < n1; b0 += nwarps * 4) {
-          const uint32_t i = b0 + grp;
-          const bool act = i < n1 && live(ldcg(T + off1 + i).x);
-          uint4 item = make_uint4(0, 0, 0, 0);
-          R rold = (R)0;
-          typename S::A ad = (typename S::A)0;
-          C sum = (C)0;
-          if (act) {
-            item = ldcg(T + off1 + i);
-            if (gl == 0) {
-              rold = ldcg(Rin + item.x);
-              ad = __ldg(a.adeg + item.x);
-            }
-            const uint32_t *cols = a.in_col + item.y;
-            uint4 q[2];
-#pragma unroll
-            for (int r = 0; r < 2; r++) {
-              const uint32_t j = 4 * (gl + 8 * r);
-              if (j < item.z) q[r] = ld_cols(cols + j, pol_cols);
-            }
-#pragma unroll
-            for (int r = 0; r < 2; r++) {
-              const uint32_t j = 4 * (gl + 8 * r);
-              if (j < item.z) sum += gather4(Cin, q[r], min(4u, item.z - j), pol_c);
-            }
-          }
-#pragma unroll
-          for (int o = 4; o > 0; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
-          int push = 0;
-          if (act && gl == 0) {
-            B dr = finish_at(item.x, sum, rold, ad);
-            my_v++;
-            my_e += item.z;
-            push = expand && dr > a.ftol && first_expansion(a.xbits, item.x);
-          }
-          if (expand) expand_lanes(push, item.x);
-        }
-      }
-
-      // tier 2: kChunk-edge chunks dealt round-robin to warps (a hub's consecutive chunks
-      // land on different warps); a row split into several chunks is finished by the warp
-      // that completes its last chunk, which adds the partial sums in chunk order
-      C *part = a.partials;
-      for (uint32_t k = gwarp; k < n2; k += nwarps) {
-        const uint4 ch = ldcg(T + off2 + k);
-        const uint32_t v = ch.x;
-        if (!live(v)) continue;
-        const uint32_t len = ch.z & 0x3FFu;
-        const bool multi = (ch.z >> 31) != 0;
-        R rold = (R)0;
-        typename S::A ad = (typename S::A)0;
-        uint32_t deg = len;
-        if (lane == 0) {
-          rold = ldcg(Rin + v);
-          ad = __ldg(a.adeg + v);
-          if (multi) deg = __ldg(&a.in_rd[v]).y;
-        }
-        const uint32_t *cols = a.in_col + ch.y;
-        uint4 q[4];
-#pragma unroll
-        for (int r = 0; r < 4; r++) {
-          const uint32_t j = 4 * (lane + 32 * r);
-          if (j < len) q[r] = ld_cols(cols + j, pol_cols);
-        }
-        C sum = (C)0;
-#pragma unroll
-        for (int r = 0; r < 4; r++) {
-          const uint32_t j = 4 * (lane + 32 * r);
-          if (j < len) sum += gather4(Cin, q[r], min(4u, len - j), pol_c);
-        }
-        sum = warp_sum(sum);
-        int finish = 1;
-        if (multi) {
-          // publish this chunk's partial; the last of the row's chunks adds them up
-          const uint32_t nch = (__shfl_sync(kFull, deg, 0) + kChunk - 1) / kChunk;
-          uint32_t old = 0;
-          if (lane == 0) {
-            part[ch.w] = sum;
-            __threadfence();
-            old = atomicAdd(&a.chunk_done[v], 1u);
-          }
-          old = __shfl_sync(kFull, old, 0);
-          finish = old == nch - 1;
-          if (finish) {
-            __threadfence();
-            const uint32_t first = ch.w - ((ch.z >> 10) & 0x1FFFFFu);
-            C tot = (C)0;
-            for (uint32_t c = lane; c < nch; c += 32) tot += ldcg(part + first + c);
-            // lane order then a fixed shuffle tree: the same sum whichever warp finishes
-            sum = warp_sum(tot);
-            if (lane == 0) a.chunk_done[v] = 0;
-          }
-        }
-        if (finish) {
-          int exp_now = 0;
-          if (lane == 0) {
-            B dr = finish_at(v, sum, rold, ad);
-            my_v++;
-            my_e += deg;
-            exp_now = expand && dr > a.ftol && first_expansion(a.xbits, v);
-          }
-          exp_now = __shfl_sync(kFull, exp_now, 0);
-          if (exp_now) {
-            const uint2 od = __ldg(&a.out_rd[v]);
-            my_app += expand_vertex(a, v, od, slot, cnt, lane);
-            if (lane == 0) {
-              my_xv++;
-              my_xe += od.y;
-            }
-          }
-        }
-      }
+      SweepIo<F32> io;
+      io.Rin = Rin;
+      io.Cin = Cin;
+      io.Rout = Rout;
+      io.Cout = Cout;
+      io.T = T;
+      io.n0 = n0;
+      io.n1 = n1;
+      io.n2 = n2;
+      io.off1 = off1;
+      io.off2 = off2;
+      io.it = (uint32_t)it;
+      io.slot = slot;
+      io.cnt[0] = cnt[0];
+      io.cnt[1] = cnt[1];
+      io.cnt[2] = cnt[2];
+      io.scan_all = scan_all;
+      io.expand = expand;
+      io.I = I;
+      io.s_base = s_base;
+      io.s_kmax = s_kmax;
+      io.s_active = s_active;
+      io.wb = &wb;
+      io.dacc = dacc;
+      io.my_max = my_max;
+      sweep_tiers<F32, DF>(a, io);
+      my_max = io.my_max;
+      dacc = io.dacc;
+      my_v += io.my_v;
+      my_e += io.my_e;
+      my_xv += io.my_xv;
+      my_xe += io.my_xe;
+      my_app += io.my_app;
     } else {
       // sparse: thread bin, one thread per vertex, 32 consecutive list entries per warp
       for (uint32_t b0 = gwarp * 32; b0 < cnt[0]; b0 += nwarps * 32) {
@@ -814,7 +1095,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
           my_e += d.y;
           push = expand && dr > a.ftol && first_expansion(a.xbits, v);
         }
-        if (expand) expand_lanes(push, v);
+        if (expand) expand_if(push, v);
       }
 
       // sparse: warp bin, one warp per vertex
@@ -838,12 +1119,10 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
         }
         exp_now = __shfl_sync(kFull, exp_now, 0);
         if (exp_now) {
-          const uint2 od = __ldg(&a.out_rd[v]);
-          my_app += expand_vertex(a, v, od, slot, cnt, lane);
-          if (lane == 0) {
-            my_xv++;
-            my_xe += od.y;
-          }
+          const ExpandOut o = expand_one(a, v, slot, cnt[0], cnt[1], cnt[2], &wb);
+          my_app += o.app;
+          my_xv += o.xv;
+          my_xe += o.xe;
         }
       }
 
@@ -887,9 +1166,9 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
         if (s_expand) {
           const uint2 od = __ldg(&a.out_rd[v]);
           if (od.y <= kInlineOut) {
-            my_app += warp_mark_range(a, a.out_col + od.x, od.y, wib * 32, kRankBlock, slot, cnt, lane);
+            my_app += warp_mark_range(a, a.out_col + od.x, od.y, wib * 32, kRankBlock, slot, cnt, lane, wb);
           } else if (wib == 0) {
-            my_app += expand_vertex(a, v, od, slot, cnt, lane);
+            my_app += expand_vertex(a, v, od, slot, cnt, lane, wb);
           }
           if (tid == 0) {
             my_xv++;
@@ -898,6 +1177,8 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
         }
       }
     }
+
+    if (expand) flush_marks(a, slot, cnt, lane, wb);
 
     // block reductions: L-inf (and dead-end mass) of this iteration
     if (multi) {
@@ -924,7 +1205,8 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
     if (a.teleport) block_dead_partial((it + 1) & 1);
     if (!grid_sync(ctl, epoch, &s_err)) return;
     if (expand && __ldcg(&ctl->hubq[slot]) != 0) {
-      my_app += hub_pass(a, slot, cnt, lane, gwarp, nwarps);
+      my_app += hub_pass(a, slot, cnt, lane, gwarp, nwarps, wb);
+      flush_marks(a, slot, cnt, lane, wb);
       if (!grid_sync(ctl, epoch, &s_err)) return;
     }
 
@@ -1059,8 +1341,12 @@ static size_t rank_smem(uint32_t ncomp) { return ((size_t)ncomp * 19 + 15) & ~(s
 template <bool F32>
 static cudaError_t grid_blocks(int sm_count, size_t smem, int *blocks) {
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rank<F32>, kRankBlock, smem);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rank<F32, false>, kRankBlock, smem);
   if (e != cudaSuccess) return e;
+  int per_sm_df = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_df, k_rank<F32, true>, kRankBlock, smem);
+  if (e != cudaSuccess) return e;
+  per_sm = std::min(per_sm, per_sm_df);
   per_sm = std::max(1, std::min(per_sm, 4));
   *blocks = per_sm * sm_count;
   return cudaSuccess;
@@ -1150,8 +1436,9 @@ static pr_status launch(Graph *g, RankMode mode, bool start_full) {
   a.comp_last = g->comp_last;
   a.dense_div = g->dense_div;
   void *args[] = {(void *)&a};
+  const void *fn = mode == kModeDF ? (const void *)k_rank<F32, true> : (const void *)k_rank<F32, false>;
   if (!g->use_graph) {
-    CK(cudaLaunchCooperativeKernel((const void *)k_rank<F32>, dim3(g->rank_grid), dim3(kRankBlock), args,
+    CK(cudaLaunchCooperativeKernel(fn, dim3(g->rank_grid), dim3(kRankBlock), args,
                                    rank_smem(g->ncomp), g->st));
     count_launch();
     return PR_OK;
@@ -1159,12 +1446,12 @@ static pr_status launch(Graph *g, RankMode mode, bool start_full) {
   // CUDA-graph launch: the control-block reset, the event records and the cooperative
   // kernel are captured once; later calls only replace the kernel's arguments and replay
   cudaKernelNodeParams kp{};
-  kp.func = (void *)k_rank<F32>;
+  kp.func = const_cast<void *>(fn);
   kp.gridDim = dim3(g->rank_grid);
   kp.blockDim = dim3(kRankBlock);
   kp.sharedMemBytes = (unsigned)rank_smem(g->ncomp);
   kp.kernelParams = args;
-  if (g->cg_exec && (g->cg_f32 != F32)) {
+  if (g->cg_exec && (g->cg_f32 != F32 || g->cg_df != (mode == kModeDF))) {
     cudaGraphExecDestroy(g->cg_exec);
     cudaGraphDestroy(g->cg);
     g->cg_exec = nullptr;
@@ -1189,6 +1476,7 @@ static pr_status launch(Graph *g, RankMode mode, bool start_full) {
     g->cg = graph;
     g->cg_kernel = kern;
     g->cg_f32 = F32;
+    g->cg_df = mode == kModeDF;
   } else {
     CK(cudaGraphExecKernelNodeSetParams(g->cg_exec, g->cg_kernel, &kp));
   }
