@@ -735,8 +735,8 @@ def main():
                          "those forms")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: Poisson arrivals per second")
     ap.add_argument("--duration", type=float, default=2.0, help="serving: seconds of arrivals")
-    ap.add_argument("--slots", type=int, default=4, help="serving: concurrent updates")
-    ap.add_argument("--coalesce", type=int, default=64, help="serving: requests per coalesced update")
+    ap.add_argument("--slots", type=int, default=2, help="serving: concurrent updates")
+    ap.add_argument("--coalesce", type=int, default=256, help="serving: requests per coalesced update")
     ap.add_argument("--serve-scales", default="18,18,19,20,21,22,23,24", help="serving: R-MAT scales")
     ap.add_argument("--graphs", type=int, default=256, help="graphs of the batched form")
     args = ap.parse_args()

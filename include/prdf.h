@@ -274,7 +274,7 @@ typedef struct {
     double elapsed_ms;
 } pr_server_info;
 
-void pr_server_config_default(pr_server_config *cfg); /* 4 slots, coalesce up to 64, 1 GiB reserve */
+void pr_server_config_default(pr_server_config *cfg); /* 2 slots, coalesce up to 256, 1 GiB reserve */
 pr_status pr_server_create(const pr_server_config *cfg, pr_server **out);
 /* Attaches g (caller keeps ownership; destroy the server before the graph). */
 pr_status pr_server_add_graph(pr_server *s, pr_graph *g, int32_t *index);

@@ -186,8 +186,8 @@ extern "C" {
 void pr_server_config_default(pr_server_config *c) {
   if (!c) return;
   std::memset(c, 0, sizeof(*c));
-  c->slots = 4;
-  c->max_coalesce = 64;
+  c->slots = 2;
+  c->max_coalesce = 256;
   c->hbm_reserve_bytes = 1ull << 30;
 }
 

@@ -481,10 +481,10 @@ def pr_server_config_default() -> pr_server_config:
 
 
 class Server:
-    """Serving form: ``srv = Server(slots=4); gi = srv.add(graph); t = srv.submit(gi, batch...)``.
+    """Serving form: ``srv = Server(slots=2); gi = srv.add(graph); t = srv.submit(gi, batch...)``.
     Attached graphs must outlive the server and are not used directly while attached."""
 
-    def __init__(self, slots: int = 4, max_coalesce: int = 64, hbm_reserve_bytes: int = 1 << 30):
+    def __init__(self, slots: int = 2, max_coalesce: int = 256, hbm_reserve_bytes: int = 1 << 30):
         c = pr_server_config(slots, max_coalesce, hbm_reserve_bytes)
         h = ctypes.c_void_p()
         _check(load().pr_server_create(ctypes.byref(c), ctypes.byref(h)), None)
