@@ -106,10 +106,14 @@ pr_status pr_get_component_stats(const pr_graph *g, pr_stats *stats, int32_t nco
 
 /* Work distribution of the rank kernel (results do not depend on it): in-degree thresholds
  * of the thread and block bins, the dense-iteration divisor (an iteration sweeps the
- * compacted affected set once it exceeds n / dense_div vertices) and the resident blocks per
- * SM of the persistent launch.  ms is the time the autotuner measured (0 otherwise). */
+ * compacted affected set once it exceeds n / dense_div vertices), the resident blocks per
+ * SM of the persistent launch, and df_split (1, the default: a Dynamic Frontier call on a
+ * single-graph handle in self-loop mode continues in a lean kernel without marking code
+ * once its affected set has settled, going back to the marking kernel if a vertex needs
+ * expanding; 0: one launch).  ms is the time the autotuner measured (0 otherwise). */
 typedef struct {
     int32_t bin_lo, bin_hi, dense_div, blocks_per_sm;
+    int32_t df_split, reserved;
     double ms;
 } pr_tuning;
 
@@ -194,7 +198,8 @@ pr_status pr_get_affected(pr_graph *g, uint32_t *out, int64_t cap, int64_t *coun
  * entries written): iter_ms[i] its duration, affected[i] the vertices it covered, kind[i]
  * 0 = affected lists, 1 = compacted sweep items reused, 2 = sweep items compacted in this
  * iteration, 3 = all vertices, 4 = all sweep items scanned, those of vertices stamped later
- * skipped.  Any of the output arrays may be NULL (host memory). */
+ * skipped, 5 = compacted items swept by the continuation kernel of a split call.  Any of
+ * the output arrays may be NULL (host memory). */
 pr_status pr_get_trace(const pr_graph *g, int32_t cap, double *phase_ms, double *iter_ms, int64_t *affected,
                        int32_t *kind, int32_t *count);
 

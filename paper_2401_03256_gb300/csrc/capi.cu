@@ -158,7 +158,7 @@ pr_status pr_set_tuning(pr_graph *h, const pr_tuning *t) {
   if (!h) return invalid(nullptr, "graph is NULL");
   Graph &g = h->g;
   if (!t || t->bin_lo < 1 || t->bin_hi < t->bin_lo || t->dense_div < 1 || t->blocks_per_sm < 1 ||
-      t->blocks_per_sm * g.sm_count > g.rank_grid_max)
+      t->blocks_per_sm * g.sm_count > g.rank_grid_max || (t->df_split != 0 && t->df_split != 1))
     return invalid(&g, "need 1 <= bin_lo <= bin_hi, dense_div >= 1, blocks_per_sm within the resident limit");
   DeviceGuard dg(g.device);
   if (t->bin_lo != g.p.bin_lo) g.ident_dirty = true;
@@ -166,6 +166,7 @@ pr_status pr_set_tuning(pr_graph *h, const pr_tuning *t) {
   g.p.bin_hi = t->bin_hi;
   g.dense_div = (uint32_t)t->dense_div;
   g.rank_grid = t->blocks_per_sm * g.sm_count;
+  g.split_df = t->df_split != 0;
   return prdf::graph_refresh_ident(&g);
 }
 
@@ -176,6 +177,8 @@ pr_status pr_get_tuning(const pr_graph *h, pr_tuning *t) {
   t->bin_hi = g.p.bin_hi;
   t->dense_div = (int32_t)g.dense_div;
   t->blocks_per_sm = g.rank_grid / g.sm_count;
+  t->df_split = g.split_df ? 1 : 0;
+  t->reserved = 0;
   t->ms = 0.0;
   return PR_OK;
 }

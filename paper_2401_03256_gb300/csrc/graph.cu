@@ -633,6 +633,7 @@ pr_status graph_build(Graph *g, uint64_t m_in, const uint32_t *src_d, const uint
   CK(dalloc(&g->hub_v, n));
   CK(dalloc(&g->hub_base, n));
   for (int i = 0; i < 3; i++) CK(dalloc(&g->list[i], n));
+  CK(dalloc(&g->xlist, n));
   CK(dalloc(&g->ident, n));
   CK(dalloc(&g->dead, n));
   CK(dalloc(&g->gen_tmp, (uint64_t)n + 2));
@@ -1111,6 +1112,7 @@ void graph_free(Graph *g) {
   cudaFree(g->partials);
   cudaFree(g->chunk_done);
   for (int i = 0; i < 3; i++) cudaFree(g->list[i]);
+  cudaFree(g->xlist);
   cudaFree(g->ident);
   cudaFree(g->dead);
   cudaFree(g->pend_src);

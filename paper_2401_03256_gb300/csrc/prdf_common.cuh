@@ -122,6 +122,8 @@ struct RankCtl {
   uint32_t iterations;
   uint32_t converged;
   uint32_t full_from;                             // iteration from which all of V is affected (+1; 0 = never)
+  uint32_t status;                                // split calls: what the last launch left to do
+  uint32_t next_it;                               // split calls: iteration the next launch starts with
   uint32_t final_cnt[3];                          // affected-list lengths at the end (Dynamic Frontier)
   uint32_t pad;
   unsigned long long last_key;                    // L-inf change of the last iteration (see Num<>::key)
@@ -133,6 +135,8 @@ struct RankCtl {
   uint32_t cmp[kMaxIterLimit + 1][4];             // affected items per tier after a dense compaction
   unsigned long long hubq[kMaxIterLimit + 2];     // per slot: queued long out-rows << 32 | their chunks
   unsigned long long vproc, eproc, expv, expe, appended;
+  uint32_t save_cnt[3], save_cmp[3], save_cmp_total;  // split calls: lists and compaction at the handoff
+  uint32_t xcnt;                                      // split calls: vertices recorded for expansion
   // trace (written by block 0): %globaltimer at kernel start, after phase 0 and after each
   // iteration's barrier; affected vertices at the start of each iteration; iteration kind
   unsigned long long t_ns[kMaxIterLimit + 2];

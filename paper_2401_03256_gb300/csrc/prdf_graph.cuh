@@ -39,6 +39,7 @@ struct Graph {
   uint32_t *xbits = nullptr;         // out-row scanned in this call, all zero between calls
   uint16_t *stamp = nullptr;         // iteration a vertex joins the affected set, 0xFFFF between calls
   uint32_t *list[3] = {nullptr, nullptr, nullptr};  // affected vertices by in-degree bin
+  uint32_t *xlist = nullptr;         // vertices a continuation launch recorded for expansion
   uint32_t *ident = nullptr;         // all vertices grouped by bin (for full sweeps)
   uint32_t ident_cnt[3] = {0, 0, 0};
   bool ident_dirty = true;
@@ -101,6 +102,7 @@ struct Graph {
   unsigned long long *comp_last = nullptr;
   std::vector<pr_stats> comp_stats;  // per graph, from the last rank call
   uint32_t dense_div = 16;           // dense iterations once affected > n / dense_div
+  bool split_df = true;              // Dynamic Frontier calls may continue in k_rank_cont
   std::vector<double> trace_ms;      // last rank call: phase 0, then each iteration (device clock)
   std::vector<int64_t> trace_aff;    // affected vertices at the start of each iteration
   std::vector<int32_t> trace_kind;   // 0 sparse, 1 dense, 2 dense after compaction, 3 all vertices

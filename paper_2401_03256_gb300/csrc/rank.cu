@@ -47,6 +47,11 @@ constexpr uint64_t kBarrierTimeoutNs = 4000000000ull;  // 4 s
 constexpr int kWarps = kRankBlock / 32;
 constexpr uint32_t kFull = 0xffffffffu;
 constexpr uint16_t kNoStamp = 0xFFFF;
+// RankCtl::status after a launch of a split call
+constexpr uint32_t kStatusDone = 1;     // the call is complete (writeback done)
+constexpr uint32_t kStatusHandoff = 2;  // continue in k_rank_cont from next_it
+constexpr uint32_t kStatusCont = 3;     // the continuation finished the iterations: k_df_finish
+constexpr uint32_t kStatusExpand = 4;   // resume the marking kernel at next_it
 constexpr uint32_t kInlineOut = 128;  // longer out-rows are marked by the whole grid (hub queue)
 #ifndef PRDF_RANK_MIN_BLOCKS
 #define PRDF_RANK_MIN_BLOCKS 4  // resident blocks per SM the register budget must allow
@@ -131,6 +136,13 @@ struct RankArgs {
   int start_full;  // Dynamic Frontier with every vertex affected from iteration 0
   uint32_t bin_lo, bin_hi;
   RankCtl *ctl;
+  // split Dynamic Frontier calls (single graph, self-loop mode): once the affected set has
+  // settled the call continues in k_rank_cont; a Dynamic Frontier launch resumes it when
+  // the continuation finds vertices to expand
+  int split;              // this call may hand off to the continuation
+  int resume;             // this launch resumes a call at iteration it0
+  int it0;
+  uint32_t *xlist;        // vertices to expand, recorded by the continuation (n)
 };
 
 // Neumaier's compensated summation (Neumaier 1974), for the FP32 mode's dead-end mass.
@@ -558,6 +570,21 @@ __device__ __noinline__ ExpandOut expand_one(const RankArgs<F32> &a, uint32_t v,
   return o;
 }
 
+// A continuation launch found vertices whose out-rows must now be scanned (their first
+// change above tau_f): they are listed for the Dynamic Frontier launch that resumes the
+// call.  Rare, so a plain warp-aggregated append.
+template <bool F32>
+__device__ __forceinline__ void record_expansion(const RankArgs<F32> &a, bool push, uint32_t v, uint32_t lane) {
+  const uint32_t mask = __ballot_sync(kFull, push);
+  if (mask) {
+    const uint32_t leader = __ffs(mask) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(&a.ctl->xcnt, (uint32_t)__popc(mask));
+    base = __shfl_sync(kFull, base, leader);
+    if (push) a.xlist[base + __popc(mask & lanemask_lt())] = v;
+  }
+}
+
 // In/out state of an out-of-line sweep of the sweep items (full and dense iterations).
 template <bool F32>
 struct SweepIo {
@@ -581,8 +608,11 @@ struct SweepIo {
 };
 
 // The three tiers of a full or dense iteration.
-template <bool F32, bool DF>
+// MODE: 0 full sweeps (Static, Naive-dynamic), 1 Dynamic Frontier (expands in place),
+// 2 continuation of a Dynamic Frontier call (only records the vertices to expand).
+template <bool F32, int MODE>
 __device__ __forceinline__ void sweep_tiers(const RankArgs<F32> &a, SweepIo<F32> &io) {
+  constexpr bool DF = MODE == 1, CONT = MODE == 2;
   using S = Store<F32>;
   using R = typename S::R;
   using C = typename S::C;
@@ -599,7 +629,7 @@ __device__ __forceinline__ void sweep_tiers(const RankArgs<F32> &a, SweepIo<F32>
   const uint32_t it = io.it, slot = io.slot;
   const uint32_t cnt[3] = {io.cnt[0], io.cnt[1], io.cnt[2]};
   const bool scan_all = io.scan_all;
-  const bool expand = DF && io.expand;
+  const bool expand = (DF || CONT) && io.expand;
   const Iter<F32> I = io.I;
   Mass<F32> dacc = io.dacc;
   WarpBuf wb = *io.wb;
@@ -647,6 +677,7 @@ __device__ __forceinline__ void sweep_tiers(const RankArgs<F32> &a, SweepIo<F32>
       if constexpr (DF) {
         if (expand) expand_if(push, v);
       }
+      if constexpr (CONT) record_expansion(a, push, v, lane);
     }
 
     // tier 1: rows of lo < len <= kGroupMax by 8-lane groups, four vertices per warp
@@ -692,6 +723,7 @@ __device__ __forceinline__ void sweep_tiers(const RankArgs<F32> &a, SweepIo<F32>
         if constexpr (DF) {
           if (expand) expand_if(push, item.x);
         }
+        if constexpr (CONT) record_expansion(a, push, item.x, lane);
       }
     }
 
@@ -767,6 +799,7 @@ __device__ __forceinline__ void sweep_tiers(const RankArgs<F32> &a, SweepIo<F32>
             my_xe += o.xe;
           }
         }
+        if constexpr (CONT) record_expansion(a, lane == 0 && exp_now, v, lane);
       }
     }
 
@@ -903,7 +936,33 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
   }
   const uint32_t zero_cnt[3] = {0, 0, 0};
   WarpBuf wb{s_mbuf[wib], {0u, 0u, 0u}, false};
-  if (df && !a.start_full) {
+  // a resumed call: list lengths and compaction as the handing-off launch left them
+  uint32_t saved_cnt[3] = {0, 0, 0};
+  if (df && a.resume) {
+#pragma unroll
+    for (int bb = 0; bb < 3; bb++) saved_cnt[bb] = ldcg(&ctl->save_cnt[bb]);
+  }
+  if (df && a.resume) {
+    // expansions the continuation recorded in iteration it0 - 1: their marks join at it0
+    const uint32_t slot0 = (uint32_t)a.it0;
+    wb.dense = true;
+    const uint32_t xend = ldcg(&ctl->xcnt);
+    for (uint32_t k0 = gwarp * 32; k0 < xend; k0 += nwarps * 32) {
+      const bool p = k0 + lane < xend;
+      const uint32_t x = p ? ldcg(a.xlist + k0 + lane) : 0u;
+      const ExpandOut o = expand_lanes(a, p ? 1 : 0, x, slot0, saved_cnt[0], saved_cnt[1], saved_cnt[2], &wb);
+      my_app += o.app;
+      my_xv += o.xv;
+      my_xe += o.xe;
+    }
+    flush_marks(a, slot0, saved_cnt, lane, wb);
+    if (!grid_sync(ctl, epoch, &s_err)) return;
+    if (__ldcg(&ctl->hubq[slot0]) != 0) {
+      my_app += hub_pass(a, slot0, saved_cnt, lane, gwarp, nwarps, wb);
+      flush_marks(a, slot0, saved_cnt, lane, wb);
+      if (!grid_sync(ctl, epoch, &s_err)) return;
+    }
+  } else if (df && !a.start_full) {
     // sources: mark G^t.out(u), one warp per source
     for (uint32_t k = gwarp; k < a.n_pend_src; k += nwarps) {
       uint32_t u = __ldg(a.pend_src + k);
@@ -916,19 +975,25 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
       my_app += warp_mark_range(a, a.pend_tgt + k0, cnt_left, 0, 32, 0, zero_cnt, lane, wb);
     }
   }
-  flush_marks(a, 0u, zero_cnt, lane, wb);
-  if (a.teleport) block_dead_partial(0);
-  if (!grid_sync(ctl, epoch, &s_err)) return;
-  if (df && __ldcg(&ctl->hubq[0]) != 0) {
-    my_app += hub_pass(a, 0, zero_cnt, lane, gwarp, nwarps, wb);
+  if (!(df && a.resume)) {
     flush_marks(a, 0u, zero_cnt, lane, wb);
+    if (a.teleport) block_dead_partial(0);
     if (!grid_sync(ctl, epoch, &s_err)) return;
+    if (df && __ldcg(&ctl->hubq[0]) != 0) {
+      my_app += hub_pass(a, 0, zero_cnt, lane, gwarp, nwarps, wb);
+      flush_marks(a, 0u, zero_cnt, lane, wb);
+      if (!grid_sync(ctl, epoch, &s_err)) return;
+    }
+    if (blockIdx.x == 0 && tid == 0) ctl->t_ns[1] = globaltimer_ns();
   }
-  if (blockIdx.x == 0 && tid == 0) ctl->t_ns[1] = globaltimer_ns();
 
   uint32_t cnt[3];
+  const int it_begin = df && a.resume ? a.it0 : 0;
 #pragma unroll
-  for (int bb = 0; bb < 3; bb++) cnt[bb] = df && !a.start_full ? ldcg(&ctl->tail[0][bb]) : 0u;
+  for (int bb = 0; bb < 3; bb++) {
+    if (df && a.resume) cnt[bb] = saved_cnt[bb] + ldcg(&ctl->tail[it_begin][bb]);
+    else cnt[bb] = df && !a.start_full ? ldcg(&ctl->tail[0][bb]) : 0u;
+  }
   long long Dn = 0;
   double Dd = 0.0;
   if (a.teleport) Dn = grid_dead_total(0, &Dd);
@@ -942,9 +1007,17 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
   uint32_t prev_total = 0xFFFFFFFFu; // affected count at the start of the previous iteration
   uint32_t cmp_n[3] = {0, 0, 0};
   uint32_t deact = 0, cmp_deact = 0;  // iterations in which some graph stopped (batched form)
+  if (df && a.resume) {
+#pragma unroll
+    for (int t = 0; t < 3; t++) cmp_n[t] = ldcg(&ctl->save_cmp[t]);
+    cmp_total = ldcg(&ctl->save_cmp_total);
+    prev_total = cmp_total;
+    iters = (uint32_t)it_begin;
+  }
+  bool handed_off = false;
 
   // ------------------------------------------------------------- iterations
-  for (int it = 0; it < a.max_iter; it++) {
+  for (int it = it_begin; it < a.max_iter; it++) {
     Iter<F32> I;
     I.tele = a.teleport ? tele_of(Dn, Dd) : (R)0;
     if (df && a.teleport && !ever_full && Num<F32>::delta(I.tele, tele_prev) > a.ftol) {
@@ -970,6 +1043,22 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
     const bool scan_all = dense && total_now != cmp_total && total_now > a.n / 4 &&
                           (prev_total == 0xFFFFFFFFu || total_now - prev_total > total_now / 16);
     prev_total = total_now;
+    // a settled affected set (compacted items current, nothing marked since) continues in
+    // the lean continuation kernel; this launch stops here
+    if (df && a.split && dense && !scan_all && total_now == cmp_total) {
+      if (blockIdx.x == 0 && tid == 0) {
+#pragma unroll
+        for (int bb = 0; bb < 3; bb++) {
+          ctl->save_cnt[bb] = cnt[bb];
+          ctl->save_cmp[bb] = cmp_n[bb];
+        }
+        ctl->save_cmp_total = cmp_total;
+        ctl->next_it = (uint32_t)it;
+        ctl->status = kStatusHandoff;
+      }
+      handed_off = true;
+      break;
+    }
     const bool expand = df && !I.full;
     const uint32_t slot = (uint32_t)it + 1;
     B my_max = 0;
@@ -1070,7 +1159,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
       io.wb = &wb;
       io.dacc = dacc;
       io.my_max = my_max;
-      sweep_tiers<F32, DF>(a, io);
+      sweep_tiers<F32, DF ? 1 : 0>(a, io);
       my_max = io.my_max;
       dacc = io.dacc;
       my_v += io.my_v;
@@ -1284,7 +1373,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
   __syncthreads();
   if (ever_full)
     for (uint32_t v = gtid; v < a.n; v += nthreads) copy_final(v);
-  if (df) {
+  if (df && !handed_off) {
     const uint32_t *lists[3] = {a.list0, a.list1, a.list2};
     for (int bb = 0; bb < 3; bb++) {
       for (uint32_t k = gtid; k < cnt[bb]; k += nthreads) {
@@ -1313,12 +1402,152 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
     }
   }
   if (blockIdx.x == 0 && tid == 0) {
+    for (int bb = 0; bb < 3; bb++) ctl->final_cnt[bb] = cnt[bb];
+    if (!handed_off) {
+      ctl->iterations = iters;
+      ctl->converged = converged ? 1u : 0u;
+      ctl->last_key = last_key;
+      ctl->D_final = Dd;
+      ctl->D_final_n = Dn;
+      ctl->status = kStatusDone;
+    }
+  }
+}
+
+// Continuation of a split Dynamic Frontier call: the affected set has settled, so every
+// iteration sweeps the compacted sweep items left by the handing-off launch, with none of
+// the marking code (the same sweep as Static and Naive-dynamic, plus the expand-once test).
+// A vertex whose change exceeds tau_f for the first time is recorded; the launch then stops
+// after its iteration and a Dynamic Frontier launch resumes the call, expanding those
+// vertices (their marks join in the next iteration, as in a single launch).  Ranks, stamps
+// and lists are left for k_df_finish.
+template <bool F32>
+__global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank_cont(const RankArgs<F32> a) {
+  using S = Store<F32>;
+  using R = typename S::R;
+  using C = typename S::C;
+  using B = typename Num<F32>::B;
+  __shared__ uint32_t s_err;
+  __shared__ unsigned long long s_key[kWarps];
+  __shared__ uint32_t s_mbuf[kWarps][3 * kMarkBuf];
+  const uint32_t tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
+  RankCtl *ctl = a.ctl;
+  uint32_t epoch = 0;
+  uint32_t cnt[3], cmp_n[3];
+#pragma unroll
+  for (int bb = 0; bb < 3; bb++) {
+    cnt[bb] = ldcg(&ctl->save_cnt[bb]);
+    cmp_n[bb] = ldcg(&ctl->save_cmp[bb]);
+  }
+  const uint32_t total = cnt[0] + cnt[1] + cnt[2];
+  WarpBuf wb{s_mbuf[wib], {0u, 0u, 0u}, true};
+  Mass<F32> dacc;
+  uint32_t my_v = 0, my_e = 0;
+  uint32_t iters = (uint32_t)a.it0, status = kStatusCont;
+  bool converged = false;
+  unsigned long long last_key = 0;
+  for (int it = a.it0; it < a.max_iter; it++) {
+    const int par = it & 1;
+    if (blockIdx.x == 0 && tid == 0) {
+      ctl->it_aff[it] = total;
+      ctl->it_kind[it] = 5;
+    }
+    SweepIo<F32> io;
+    io.Rin = par ? a.R1 : a.R0;
+    io.Cin = par ? a.C1 : a.C0;
+    io.Rout = par ? a.R0 : a.R1;
+    io.Cout = par ? a.C0 : a.C1;
+    io.T = a.items_cmp;
+    io.n0 = cmp_n[0];
+    io.n1 = cmp_n[1];
+    io.n2 = cmp_n[2];
+    io.off1 = a.it_c0;
+    io.off2 = a.it_c0 + a.it_c1;
+    io.it = (uint32_t)it;
+    io.slot = (uint32_t)it + 1;
+    io.cnt[0] = cnt[0];
+    io.cnt[1] = cnt[1];
+    io.cnt[2] = cnt[2];
+    io.scan_all = false;
+    io.expand = true;
+    io.I.full = false;
+    io.I.tele = (R)0;
+    io.s_base = nullptr;
+    io.s_kmax = nullptr;
+    io.s_active = nullptr;
+    io.wb = &wb;
+    io.dacc = dacc;
+    io.my_max = 0;
+    sweep_tiers<F32, 2>(a, io);
+    my_v += io.my_v;
+    my_e += io.my_e;
+    unsigned long long m = Num<F32>::key(io.my_max);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(kFull, m, o));
+    if (lane == 0) s_key[wib] = m;
+    __syncthreads();
+    if (tid == 0) {
+      unsigned long long bm = 0;
+      for (int w = 0; w < kWarps; w++) bm = max(bm, s_key[w]);
+      if (bm) atomicMax(&ctl->dR_bits[it], bm);
+    }
+    if (!grid_sync(ctl, epoch, &s_err)) return;
+    const unsigned long long dR = __ldcg(&ctl->dR_bits[it]);
+    iters = (uint32_t)it + 1;
+    last_key = dR;
+    if (blockIdx.x == 0 && tid == 0) ctl->t_ns[it + 2] = globaltimer_ns();
+    if (dR <= a.tol_key) {
+      converged = true;
+      break;
+    }
+    if (ldcg(&ctl->xcnt) != 0 && it + 1 < a.max_iter) {
+      status = kStatusExpand;
+      break;
+    }
+  }
+  {
+    unsigned long long vals[2] = {my_v, my_e};
+    unsigned long long *dst[2] = {&ctl->vproc, &ctl->eproc};
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+      unsigned long long x = warp_sum(vals[k]);
+      if (lane == 0 && x) atomicAdd(dst[k], x);
+    }
+  }
+  if (blockIdx.x == 0 && tid == 0) {
     ctl->iterations = iters;
     ctl->converged = converged ? 1u : 0u;
     ctl->last_key = last_key;
-    ctl->D_final = Dd;
-    ctl->D_final_n = Dn;
-    for (int bb = 0; bb < 3; bb++) ctl->final_cnt[bb] = cnt[bb];
+    ctl->next_it = iters;
+    ctl->status = status;
+  }
+}
+
+// End of a split Dynamic Frontier call: both parities of every affected vertex take its
+// final values (parity iterations & 1) and the per-call marks are cleared.
+template <bool F32>
+__global__ void k_df_finish(const RankArgs<F32> a) {
+  using S = Store<F32>;
+  using R = typename S::R;
+  using C = typename S::C;
+  const RankCtl *ctl = a.ctl;
+  const bool fp = ldcg(&ctl->iterations) & 1;
+  const R *Rf = fp ? a.R1 : a.R0;
+  const C *Cf = fp ? a.C1 : a.C0;
+  R *Ro = fp ? a.R0 : a.R1;
+  C *Co = fp ? a.C0 : a.C1;
+  const uint32_t *lists[3] = {a.list0, a.list1, a.list2};
+  const uint32_t nthreads = gridDim.x * blockDim.x, gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int bb = 0; bb < 3; bb++) {
+    const uint32_t c = ldcg(&ctl->final_cnt[bb]);
+    for (uint32_t k = gtid; k < c; k += nthreads) {
+      const uint32_t v = ldcg(lists[bb] + k);
+      Ro[v] = ldcg(Rf + v);
+      Co[v] = ldcg(Cf + v);
+      a.bitmap[v >> 5] = 0u;
+      a.xbits[v >> 5] = 0u;
+      a.stamp[v] = kNoStamp;
+    }
   }
 }
 
@@ -1347,6 +1576,10 @@ static cudaError_t grid_blocks(int sm_count, size_t smem, int *blocks) {
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_df, k_rank<F32, true>, kRankBlock, smem);
   if (e != cudaSuccess) return e;
   per_sm = std::min(per_sm, per_sm_df);
+  int per_sm_cont = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_cont, k_rank_cont<F32>, kRankBlock, 0);
+  if (e != cudaSuccess) return e;
+  per_sm = std::min(per_sm, per_sm_cont);
   per_sm = std::max(1, std::min(per_sm, 4));
   *blocks = per_sm * sm_count;
   return cudaSuccess;
@@ -1435,12 +1668,46 @@ static pr_status launch(Graph *g, RankMode mode, bool start_full) {
   a.comp_out = g->comp_out;
   a.comp_last = g->comp_last;
   a.dense_div = g->dense_div;
+  a.xlist = g->xlist;
+  a.split = mode == kModeDF && g->split_df && !g->use_graph && g->ncomp == 1 && !g->teleport && !start_full;
+  a.resume = 0;
+  a.it0 = 0;
   void *args[] = {(void *)&a};
   const void *fn = mode == kModeDF ? (const void *)k_rank<F32, true> : (const void *)k_rank<F32, false>;
   if (!g->use_graph) {
     CK(cudaLaunchCooperativeKernel(fn, dim3(g->rank_grid), dim3(kRankBlock), args,
                                    rank_smem(g->ncomp), g->st));
     count_launch();
+    // a split call: the host reads the status each launch leaves and starts the next one
+    // (continuation, resumed marking launch, or the final writeback); every launch restarts
+    // the grid-barrier count
+    for (int round = 0; a.split && round < 2 * kMaxIterLimit + 2; round++) {
+      CK(cudaMemcpyAsync(g->ctl_h, g->ctl, offsetof(RankCtl, final_cnt), cudaMemcpyDeviceToHost, g->st));
+      CK(cudaStreamSynchronize(g->st));
+      const RankCtl &h = *g->ctl_h;
+      if (h.err) break;
+      if (h.status == kStatusHandoff || h.status == kStatusExpand) {
+        CK(cudaMemsetAsync(&g->ctl->bar, 0, sizeof(uint32_t), g->st));
+        if (h.status == kStatusHandoff) {
+          CK(cudaMemsetAsync(&g->ctl->xcnt, 0, sizeof(uint32_t), g->st));
+          a.resume = 0;
+        } else {
+          a.resume = 1;
+        }
+        a.it0 = (int)h.next_it;
+        const void *next = h.status == kStatusHandoff ? (const void *)k_rank_cont<F32> : (const void *)k_rank<F32, true>;
+        CK(cudaLaunchCooperativeKernel(next, dim3(g->rank_grid), dim3(kRankBlock), args,
+                                       h.status == kStatusHandoff ? 0 : rank_smem(g->ncomp), g->st));
+        count_launch();
+      } else {
+        if (h.status == kStatusCont) {
+          k_df_finish<F32><<<g->sm_count * 8, 256, 0, g->st>>>(a);
+          count_launch();
+          CK(cudaGetLastError());
+        }
+        break;
+      }
+    }
     return PR_OK;
   }
   // CUDA-graph launch: the control-block reset, the event records and the cooperative

@@ -58,7 +58,8 @@ class pr_stats(ctypes.Structure):
 
 class pr_tuning(ctypes.Structure):
     _fields_ = [("bin_lo", ctypes.c_int32), ("bin_hi", ctypes.c_int32), ("dense_div", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32), ("ms", ctypes.c_double)]
+                ("blocks_per_sm", ctypes.c_int32), ("df_split", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -236,8 +237,8 @@ def pr_get_component_stats(h: int, ncomp: int):
     return [arr[i] for i in range(ncomp)]
 
 
-def pr_set_tuning(h: int, bin_lo: int, bin_hi: int, dense_div: int, blocks_per_sm: int) -> None:
-    t = pr_tuning(bin_lo, bin_hi, dense_div, blocks_per_sm, 0.0)
+def pr_set_tuning(h: int, bin_lo: int, bin_hi: int, dense_div: int, blocks_per_sm: int, df_split: int = 1) -> None:
+    t = pr_tuning(bin_lo, bin_hi, dense_div, blocks_per_sm, df_split, 0, 0.0)
     _check(load().pr_set_tuning(h, ctypes.byref(t)), h)
 
 
@@ -366,7 +367,8 @@ def pr_get_csr(h: int, direction: int):
 
 def pr_get_trace(h: int) -> dict:
     """Device-clock trace of the last rank call: phase-0 ms and per-iteration ms, affected
-    counts and kinds (0 lists, 1 dense reused, 2 dense compacted, 3 all vertices)."""
+    counts and kinds (0 lists, 1 dense reused, 2 dense compacted, 3 all vertices, 4 all items
+    with stamp checks, 5 continuation of a split call)."""
     cnt = ctypes.c_int32()
     _check(load().pr_get_trace(h, 0, None, None, None, None, ctypes.byref(cnt)), h)
     k = cnt.value
@@ -417,8 +419,8 @@ class Graph:
     def tuning(self) -> pr_tuning:
         return pr_get_tuning(self.h)
 
-    def set_tuning(self, bin_lo: int, bin_hi: int, dense_div: int, blocks_per_sm: int):
-        pr_set_tuning(self.h, bin_lo, bin_hi, dense_div, blocks_per_sm)
+    def set_tuning(self, bin_lo: int, bin_hi: int, dense_div: int, blocks_per_sm: int, df_split: int = 1):
+        pr_set_tuning(self.h, bin_lo, bin_hi, dense_div, blocks_per_sm, df_split)
 
     def set_graph_launch(self, enable: bool):
         pr_set_graph_launch(self.h, enable)

@@ -199,3 +199,30 @@ def test_results_do_not_depend_on_tuning(prdf, lo, bps):
             A.frontier()
             out.append(A.ranks().copy())
     assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_split_frontier_call_equals_single_launch(prdf, prec):
+    # a Dynamic Frontier call that continues in the lean kernel once its affected set has
+    # settled (and resumes the marking kernel when a vertex needs expanding) gives exactly
+    # the single-launch result: the same sums in the same order
+    g = synth.rmat(14, 16, seed=21)
+    bs = [b for b in (synth.BatchStream(g, seed=22).next(f) for f in (1e-5, 1e-4, 1e-3))]
+    p = _params(prdf, precision=prdf.PR_F32 if prec == "f32" else prdf.PR_F64)
+    out, kinds = [], []
+    for split in (0, 1):
+        with prdf.Graph(g.n, g.src, g.dst, p) as A:
+            t = A.tuning()
+            A.set_tuning(t.bin_lo, t.bin_hi, t.dense_div, t.blocks_per_sm, split)
+            A.static()
+            res = []
+            for b in bs:
+                A.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+                st = A.frontier()
+                res.append((A.ranks().copy(), st.iterations, st.affected_final, sorted(A.affected().tolist())))
+                kinds.append((split, list(A.trace()["kind"])))
+            out.append(res)
+    for (r0, i0, a0, s0), (r1, i1, a1, s1) in zip(out[0], out[1]):
+        assert np.array_equal(r0, r1) and i0 == i1 and a0 == a1 and s0 == s1
+    assert any(5 in k for sp, k in kinds if sp == 1)  # the continuation did run
+    assert not any(5 in k for sp, k in kinds if sp == 0)
