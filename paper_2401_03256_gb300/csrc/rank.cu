@@ -260,8 +260,8 @@ __device__ __forceinline__ int bin_of(uint32_t deg, uint32_t lo, uint32_t hi) {
 // needs every affected vertex in some list.
 constexpr uint32_t kMarkBuf = 64;
 struct WarpBuf {
-  uint32_t *buf;   // [3][kMarkBuf] entries of this warp's shared memory
-  uint32_t n[3];   // entries held per bin (the same in every lane)
+  uint32_t *buf;   // [4][kMarkBuf] entries of this warp's shared memory: bins 0-2, expansions
+  uint32_t n[4];   // entries held per run (the same in every lane)
   bool dense;
 };
 
@@ -281,11 +281,40 @@ __device__ __forceinline__ void flush_bin(const RankArgs<F32> &a, int bb, uint32
   wb.n[bb] = 0;
 }
 
+// Vertices a dense or full sweep found to expand, appended to the call's expansion list
+// (each vertex at most once per call: first_expansion) in runs; the grid scans their
+// out-rows after the iteration's barrier, so the sweep loops carry no marking code.
+template <bool F32>
+__device__ __forceinline__ void flush_expansions(const RankArgs<F32> &a, uint32_t lane, WarpBuf &wb) {
+  __syncwarp();
+  const uint32_t k = wb.n[3];
+  if (k) {
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(&a.ctl->xcnt, k);
+    base = __shfl_sync(kFull, base, 0);
+    for (uint32_t i = lane; i < k; i += 32) a.xlist[base + i] = wb.buf[3 * kMarkBuf + i];
+  }
+  __syncwarp();
+  wb.n[3] = 0;
+}
+
+template <bool F32>
+__device__ __forceinline__ void queue_expansion(const RankArgs<F32> &a, bool push, uint32_t v, uint32_t lane,
+                                                WarpBuf &wb) {
+  const uint32_t mask = __ballot_sync(kFull, push);
+  if (mask) {
+    if (wb.n[3] + __popc(mask) > kMarkBuf) flush_expansions(a, lane, wb);
+    if (push) wb.buf[3 * kMarkBuf + wb.n[3] + __popc(mask & lanemask_lt())] = v;
+    wb.n[3] += __popc(mask);
+  }
+}
+
 template <bool F32>
 __device__ __forceinline__ void flush_marks(const RankArgs<F32> &a, uint32_t slot, const uint32_t cnt[3],
                                             uint32_t lane, WarpBuf &wb) {
 #pragma unroll
   for (int bb = 0; bb < 3; bb++) flush_bin(a, bb, slot, cnt, lane, wb);
+  flush_expansions(a, lane, wb);
 }
 
 // Appends w where fresh to its bin's run in the warp's buffer.  Called by a whole warp.
@@ -648,14 +677,6 @@ __device__ __forceinline__ void sweep_tiers(const RankArgs<F32> &a, SweepIo<F32>
     else my_max = dr > my_max ? dr : my_max;
     return dr;
   };
-  auto expand_if = [&](int push, uint32_t v) {
-    if (__any_sync(kFull, push)) {
-      const ExpandOut o = expand_lanes(a, push, v, slot, cnt[0], cnt[1], cnt[2], &wb);
-      my_app += o.app;
-      my_xv += o.xv;
-      my_xe += o.xe;
-    }
-  };
 
     // tier 0: one thread per vertex, 32 consecutive items per warp
     for (uint32_t b0 = gwarp * 32; b0 < n0; b0 += nwarps * 32) {
@@ -675,7 +696,7 @@ __device__ __forceinline__ void sweep_tiers(const RankArgs<F32> &a, SweepIo<F32>
         push = expand && dr > a.ftol && first_expansion_pre(a.xbits, v, xw);
       }
       if constexpr (DF) {
-        if (expand) expand_if(push, v);
+        if (expand) queue_expansion(a, push, v, lane, wb);
       }
       if constexpr (CONT) record_expansion(a, push, v, lane);
     }
@@ -721,7 +742,7 @@ __device__ __forceinline__ void sweep_tiers(const RankArgs<F32> &a, SweepIo<F32>
           push = expand && dr > a.ftol && first_expansion_pre(a.xbits, item.x, xw);
         }
         if constexpr (DF) {
-          if (expand) expand_if(push, item.x);
+          if (expand) queue_expansion(a, push, item.x, lane, wb);
         }
         if constexpr (CONT) record_expansion(a, push, item.x, lane);
       }
@@ -791,13 +812,7 @@ __device__ __forceinline__ void sweep_tiers(const RankArgs<F32> &a, SweepIo<F32>
           exp_now = expand && dr > a.ftol && first_expansion_pre(a.xbits, v, xw);
         }
         if constexpr (DF) {
-          exp_now = __shfl_sync(kFull, exp_now, 0);
-          if (exp_now) {
-            const ExpandOut o = expand_one(a, v, slot, cnt[0], cnt[1], cnt[2], &wb);
-            my_app += o.app;
-            my_xv += o.xv;
-            my_xe += o.xe;
-          }
+          if (expand) queue_expansion(a, lane == 0 && exp_now, v, lane, wb);
         }
         if constexpr (CONT) record_expansion(a, lane == 0 && exp_now, v, lane);
       }
@@ -827,7 +842,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
   __shared__ unsigned long long s_key[kWarps];
   __shared__ double s_ds[kWarps], s_dc[kWarps];
   __shared__ int s_expand;
-  __shared__ uint32_t s_mbuf[kWarps][3 * kMarkBuf];
+  __shared__ uint32_t s_mbuf[kWarps][4 * kMarkBuf];
 
   const uint32_t tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
   const uint32_t nblk = gridDim.x;
@@ -935,7 +950,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
     for (uint32_t k = gtid; k < a.n_dead; k += nthreads) dacc.add(ldcg(a.R0 + __ldg(a.dead + k)));
   }
   const uint32_t zero_cnt[3] = {0, 0, 0};
-  WarpBuf wb{s_mbuf[wib], {0u, 0u, 0u}, false};
+  WarpBuf wb{s_mbuf[wib], {0u, 0u, 0u, 0u}, false};
   // a resumed call: list lengths and compaction as the handing-off launch left them
   uint32_t saved_cnt[3] = {0, 0, 0};
   if (df && a.resume) {
@@ -1015,6 +1030,8 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
     iters = (uint32_t)it_begin;
   }
   bool handed_off = false;
+  // expansion-list entries already scanned (a resumed launch has scanned the continuation's)
+  uint32_t xdone = df && a.resume ? ldcg(&ctl->xcnt) : 0u;
 
   // ------------------------------------------------------------- iterations
   for (int it = it_begin; it < a.max_iter; it++) {
@@ -1293,6 +1310,24 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
     }
     if (a.teleport) block_dead_partial((it + 1) & 1);
     if (!grid_sync(ctl, epoch, &s_err)) return;
+    if (expand) {
+      // out-rows of the vertices this iteration's sweep queued, 32 per warp round, one
+      // vertex per lane; rows longer than 128 go to the hub queue
+      const uint32_t xend = ldcg(&ctl->xcnt);
+      if (xend > xdone) {
+        for (uint32_t k0 = xdone + gwarp * 32; k0 < xend; k0 += nwarps * 32) {
+          const bool p = k0 + lane < xend;
+          const uint32_t x = p ? ldcg(a.xlist + k0 + lane) : 0u;
+          const ExpandOut o = expand_lanes(a, p ? 1 : 0, x, slot, cnt[0], cnt[1], cnt[2], &wb);
+          my_app += o.app;
+          my_xv += o.xv;
+          my_xe += o.xe;
+        }
+        xdone = xend;
+        flush_marks(a, slot, cnt, lane, wb);
+        if (!grid_sync(ctl, epoch, &s_err)) return;
+      }
+    }
     if (expand && __ldcg(&ctl->hubq[slot]) != 0) {
       my_app += hub_pass(a, slot, cnt, lane, gwarp, nwarps, wb);
       flush_marks(a, slot, cnt, lane, wb);
@@ -1429,7 +1464,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank_cont(
   using B = typename Num<F32>::B;
   __shared__ uint32_t s_err;
   __shared__ unsigned long long s_key[kWarps];
-  __shared__ uint32_t s_mbuf[kWarps][3 * kMarkBuf];
+  __shared__ uint32_t s_mbuf[kWarps][4 * kMarkBuf];
   const uint32_t tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
   RankCtl *ctl = a.ctl;
   uint32_t epoch = 0;
@@ -1440,7 +1475,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank_cont(
     cmp_n[bb] = ldcg(&ctl->save_cmp[bb]);
   }
   const uint32_t total = cnt[0] + cnt[1] + cnt[2];
-  WarpBuf wb{s_mbuf[wib], {0u, 0u, 0u}, true};
+  WarpBuf wb{s_mbuf[wib], {0u, 0u, 0u, 0u}, true};
   Mass<F32> dacc;
   uint32_t my_v = 0, my_e = 0;
   uint32_t iters = (uint32_t)a.it0, status = kStatusCont;
