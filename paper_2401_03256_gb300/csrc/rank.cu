@@ -544,8 +544,8 @@ __device__ __forceinline__ typename Num<F32>::B finish_vertex(const RankArgs<F32
 __device__ __forceinline__ uint4 ldcg(const uint4 *p) { return __ldcg(p); }
 
 // Frontier expansion of the lanes' vertices that changed by more than tau_f (push):
-// short out-rows by their own lanes together, longer ones by the whole warp (or the hub
-// queue) one at a time.  Out of line: it runs only when some lane of the warp expands, and
+// short out-rows by their own lanes, medium ones flattened across the warp, hub rows
+// queued for the grid.  Out of line: it runs only when some lane of the warp expands, and
 // keeping its registers out of the sweep loops keeps those loops free of spills.  Called
 // by a whole warp.
 struct ExpandOut {
@@ -560,13 +560,63 @@ __device__ __noinline__ ExpandOut expand_lanes(const RankArgs<F32> &a, int push,
   ExpandOut o{0u, 0u, 0u};
   uint2 od = make_uint2(0, 0);
   if (push) od = __ldg(&a.out_rd[v]);
+  // short rows: each lane its own
   const bool mine = push && od.y <= kThreadOut;
   if (__any_sync(kFull, mine)) o.app += lane_mark_rows(a, mine, od, slot, cnt, lane, wb);
-  if (mine) {
+  // medium rows: the rows of all such lanes flattened into one run of entries, marked 128
+  // at a time (four per lane; the column loads, bitmap reads and atomics of a round are in
+  // flight together), so the warp spends ceil(total / 128) rounds instead of one round per
+  // 32 entries of every row in turn
+  const bool med = push && od.y > kThreadOut && od.y <= kInlineOut;
+  const uint32_t mlen = med ? od.y : 0u;
+  uint32_t incl = mlen;
+#pragma unroll
+  for (int k = 1; k < 32; k <<= 1) {
+    const uint32_t y = __shfl_up_sync(kFull, incl, k);
+    if (lane >= (uint32_t)k) incl += y;
+  }
+  const uint32_t total = __shfl_sync(kFull, incl, 31);
+  const uint32_t excl = incl - mlen;
+  for (uint32_t e0 = 0; e0 < total; e0 += 128) {
+    uint32_t w[4], word[4];
+    bool valid[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const uint32_t e = e0 + 32u * k + lane;
+      // the lane whose run [excl, incl) holds entry e
+      uint32_t owner = 0;
+#pragma unroll
+      for (uint32_t step = 16; step > 0; step >>= 1) {
+        const uint32_t probe = __shfl_sync(kFull, incl, owner + step - 1);
+        if (probe <= e) owner += step;
+      }
+      const uint32_t base = __shfl_sync(kFull, od.x, owner & 31u);
+      const uint32_t first = __shfl_sync(kFull, excl, owner & 31u);
+      valid[k] = e < total;
+      w[k] = valid[k] ? __ldg(a.out_col + base + (e - first)) : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++) word[k] = valid[k] ? ldcg(a.bitmap + (w[k] >> 5)) : ~0u;
+    uint32_t fresh = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const uint32_t bit = 1u << (w[k] & 31);
+      if (!(word[k] & bit) && !(atomicOr(a.bitmap + (w[k] >> 5), bit) & bit)) fresh |= 1u << k;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const bool f = (fresh >> k) & 1u;
+      if (f) a.stamp[w[k]] = (uint16_t)slot;
+      append_mark(a, f, w[k], slot, cnt, lane, wb);
+      o.app += f ? 1u : 0u;
+    }
+  }
+  if (mine || med) {
     o.xv++;
     o.xe += od.y;
   }
-  uint32_t mask = __ballot_sync(kFull, push && !mine);
+  // hub rows: queued for the grid
+  uint32_t mask = __ballot_sync(kFull, push && od.y > kInlineOut);
   while (mask) {
     const uint32_t src = __ffs(mask) - 1;
     mask &= mask - 1;
