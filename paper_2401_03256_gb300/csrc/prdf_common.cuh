@@ -136,7 +136,9 @@ struct RankCtl {
   unsigned long long hubq[kMaxIterLimit + 2];     // per slot: queued long out-rows << 32 | their chunks
   unsigned long long vproc, eproc, expv, expe, appended;
   uint32_t save_cnt[3], save_cmp[3], save_cmp_total;  // split calls: lists and compaction at the handoff
-  uint32_t xcnt;                                      // split calls: vertices recorded for expansion
+  uint32_t xcnt;                                      // entries of the expansion list (cursor)
+  uint32_t xit[kMaxIterLimit + 2];                    // entries appended for each slot: read after the
+                                                      // barrier, when no block can append to that slot
   // trace (written by block 0): %globaltimer at kernel start, after phase 0 and after each
   // iteration's barrier; affected vertices at the start of each iteration; iteration kind
   unsigned long long t_ns[kMaxIterLimit + 2];

@@ -263,6 +263,7 @@ struct WarpBuf {
   uint32_t *buf;   // [4][kMarkBuf] entries of this warp's shared memory: bins 0-2, expansions
   uint32_t n[4];   // entries held per run (the same in every lane)
   bool dense;
+  uint32_t slot;   // iteration the queued expansions' marks join (their count per slot)
 };
 
 template <bool F32>
@@ -290,7 +291,10 @@ __device__ __forceinline__ void flush_expansions(const RankArgs<F32> &a, uint32_
   const uint32_t k = wb.n[3];
   if (k) {
     uint32_t base = 0;
-    if (lane == 0) base = atomicAdd(&a.ctl->xcnt, k);
+    if (lane == 0) {
+      base = atomicAdd(&a.ctl->xcnt, k);
+      atomicAdd(&a.ctl->xit[wb.slot], k);
+    }
     base = __shfl_sync(kFull, base, 0);
     for (uint32_t i = lane; i < k; i += 32) a.xlist[base + i] = wb.buf[3 * kMarkBuf + i];
   }
@@ -653,12 +657,16 @@ __device__ __noinline__ ExpandOut expand_one(const RankArgs<F32> &a, uint32_t v,
 // change above tau_f): they are listed for the Dynamic Frontier launch that resumes the
 // call.  Rare, so a plain warp-aggregated append.
 template <bool F32>
-__device__ __forceinline__ void record_expansion(const RankArgs<F32> &a, bool push, uint32_t v, uint32_t lane) {
+__device__ __forceinline__ void record_expansion(const RankArgs<F32> &a, bool push, uint32_t v, uint32_t lane,
+                                                 uint32_t slot) {
   const uint32_t mask = __ballot_sync(kFull, push);
   if (mask) {
     const uint32_t leader = __ffs(mask) - 1;
     uint32_t base = 0;
-    if (lane == leader) base = atomicAdd(&a.ctl->xcnt, (uint32_t)__popc(mask));
+    if (lane == leader) {
+      base = atomicAdd(&a.ctl->xcnt, (uint32_t)__popc(mask));
+      atomicAdd(&a.ctl->xit[slot], (uint32_t)__popc(mask));
+    }
     base = __shfl_sync(kFull, base, leader);
     if (push) a.xlist[base + __popc(mask & lanemask_lt())] = v;
   }
@@ -748,7 +756,7 @@ __device__ __forceinline__ void sweep_tiers(const RankArgs<F32> &a, SweepIo<F32>
       if constexpr (DF) {
         if (expand) queue_expansion(a, push, v, lane, wb);
       }
-      if constexpr (CONT) record_expansion(a, push, v, lane);
+      if constexpr (CONT) record_expansion(a, push, v, lane, slot);
     }
 
     // tier 1: rows of lo < len <= kGroupMax by 8-lane groups, four vertices per warp
@@ -794,7 +802,7 @@ __device__ __forceinline__ void sweep_tiers(const RankArgs<F32> &a, SweepIo<F32>
         if constexpr (DF) {
           if (expand) queue_expansion(a, push, item.x, lane, wb);
         }
-        if constexpr (CONT) record_expansion(a, push, item.x, lane);
+        if constexpr (CONT) record_expansion(a, push, item.x, lane, slot);
       }
     }
 
@@ -864,7 +872,7 @@ __device__ __forceinline__ void sweep_tiers(const RankArgs<F32> &a, SweepIo<F32>
         if constexpr (DF) {
           if (expand) queue_expansion(a, lane == 0 && exp_now, v, lane, wb);
         }
-        if constexpr (CONT) record_expansion(a, lane == 0 && exp_now, v, lane);
+        if constexpr (CONT) record_expansion(a, lane == 0 && exp_now, v, lane, slot);
       }
     }
 
@@ -1000,9 +1008,12 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
     for (uint32_t k = gtid; k < a.n_dead; k += nthreads) dacc.add(ldcg(a.R0 + __ldg(a.dead + k)));
   }
   const uint32_t zero_cnt[3] = {0, 0, 0};
-  WarpBuf wb{s_mbuf[wib], {0u, 0u, 0u, 0u}, false};
+  WarpBuf wb{s_mbuf[wib], {0u, 0u, 0u, 0u}, false, 0u};
   // a resumed call: list lengths and compaction as the handing-off launch left them
   uint32_t saved_cnt[3] = {0, 0, 0};
+  // expansion-list entries already scanned; read before any barrier of this launch, since
+  // the sweeps append to the list once the first barrier is passed
+  uint32_t xdone = 0;
   if (df && a.resume) {
 #pragma unroll
     for (int bb = 0; bb < 3; bb++) saved_cnt[bb] = ldcg(&ctl->save_cnt[bb]);
@@ -1012,6 +1023,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
     const uint32_t slot0 = (uint32_t)a.it0;
     wb.dense = true;
     const uint32_t xend = ldcg(&ctl->xcnt);
+    xdone = xend;
     for (uint32_t k0 = gwarp * 32; k0 < xend; k0 += nwarps * 32) {
       const bool p = k0 + lane < xend;
       const uint32_t x = p ? ldcg(a.xlist + k0 + lane) : 0u;
@@ -1080,8 +1092,6 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
     iters = (uint32_t)it_begin;
   }
   bool handed_off = false;
-  // expansion-list entries already scanned (a resumed launch has scanned the continuation's)
-  uint32_t xdone = df && a.resume ? ldcg(&ctl->xcnt) : 0u;
 
   // ------------------------------------------------------------- iterations
   for (int it = it_begin; it < a.max_iter; it++) {
@@ -1111,8 +1121,10 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
                           (prev_total == 0xFFFFFFFFu || total_now - prev_total > total_now / 16);
     prev_total = total_now;
     // a settled affected set (compacted items current, nothing marked since) continues in
-    // the lean continuation kernel; this launch stops here
-    if (df && a.split && dense && !scan_all && total_now == cmp_total) {
+    // the lean continuation kernel; this launch stops here (a resumed launch first runs
+    // four iterations itself, so that a chain of late expansions does not bounce between
+    // the kernels every iteration)
+    if (df && a.split && dense && !scan_all && total_now == cmp_total && it >= it_begin + (a.resume ? 4 : 0)) {
       if (blockIdx.x == 0 && tid == 0) {
 #pragma unroll
         for (int bb = 0; bb < 3; bb++) {
@@ -1136,6 +1148,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
     }
 
     wb.dense = dense;
+    wb.slot = slot;
 
     auto expand_if = [&](int push, uint32_t v) {
       if (__any_sync(kFull, push)) {
@@ -1363,7 +1376,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
     if (expand) {
       // out-rows of the vertices this iteration's sweep queued, 32 per warp round, one
       // vertex per lane; rows longer than 128 go to the hub queue
-      const uint32_t xend = ldcg(&ctl->xcnt);
+      const uint32_t xend = xdone + ldcg(&ctl->xit[slot]);
       if (xend > xdone) {
         for (uint32_t k0 = xdone + gwarp * 32; k0 < xend; k0 += nwarps * 32) {
           const bool p = k0 + lane < xend;
@@ -1525,7 +1538,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank_cont(
     cmp_n[bb] = ldcg(&ctl->save_cmp[bb]);
   }
   const uint32_t total = cnt[0] + cnt[1] + cnt[2];
-  WarpBuf wb{s_mbuf[wib], {0u, 0u, 0u, 0u}, true};
+  WarpBuf wb{s_mbuf[wib], {0u, 0u, 0u, 0u}, true, 0u};
   Mass<F32> dacc;
   uint32_t my_v = 0, my_e = 0;
   uint32_t iters = (uint32_t)a.it0, status = kStatusCont;
@@ -1585,7 +1598,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank_cont(
       converged = true;
       break;
     }
-    if (ldcg(&ctl->xcnt) != 0 && it + 1 < a.max_iter) {
+    if (ldcg(&ctl->xit[it + 1]) != 0 && it + 1 < a.max_iter) {
       status = kStatusExpand;
       break;
     }

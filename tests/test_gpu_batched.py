@@ -226,3 +226,34 @@ def test_split_frontier_call_equals_single_launch(prdf, prec):
         assert np.array_equal(r0, r1) and i0 == i1 and a0 == a1 and s0 == s1
     assert any(5 in k for sp, k in kinds if sp == 1)  # the continuation did run
     assert not any(5 in k for sp, k in kinds if sp == 0)
+
+
+@pytest.mark.parametrize("split", [0, 1])
+def test_late_expansions_resume_the_marking_kernel(prdf, split):
+    # every vertex of a 100-vertex chain is affected from the start (out-neighbours of a
+    # hub whose out-degree the batch keeps), but the change entering at the chain's end
+    # reaches vertex i only after 100 - i iterations: each vertex expands late, while the
+    # affected set has long settled, so a split call keeps handing the call back to the
+    # marking kernel.  Ranks, iterations and affected set must match the single launch and
+    # the oracle.
+    n = 128
+    pairs = [(0, v) for v in range(1, 101)] + [(v, v - 1) for v in range(2, 101)] + [(101, 0), (102, 101)]
+    g = synth.from_pairs(n, pairs, "hub-chain")
+    G = oracle.Graph.build(g.n, g.src, g.dst)
+    R0, _ = oracle.static_pr(G)
+    dele, ins = [(0, 100)], [(0, 102)]
+    H, ed, ei = G.apply([0], [100], [0], [102])
+    Rn, aff, so = oracle.df_sync(G, H, ed, ei, R0)
+    with prdf.Graph(g.n, g.src, g.dst) as A:
+        t = A.tuning()
+        A.set_tuning(t.bin_lo, t.bin_hi, t.dense_div, t.blocks_per_sm, split)
+        A.set_ranks(R0)
+        A.apply([0], [100], [0], [102])
+        st = A.frontier()
+        kinds = "".join(str(int(k)) for k in A.trace()["kind"])
+        assert np.max(np.abs(A.ranks() - Rn)) <= TOL64
+        assert abs(st.iterations - so.iterations) <= 1
+        assert st.affected_final == so.affected_final
+    if split:
+        # the continuation ran, and a marking launch resumed after it
+        assert "5" in kinds and any(k != "5" for k in kinds[kinds.index("5"):]), kinds
