@@ -139,6 +139,7 @@ struct RankCtl {
   uint32_t xcnt;                                      // entries of the expansion list (cursor)
   uint32_t xit[kMaxIterLimit + 2];                    // entries appended for each slot: read after the
                                                       // barrier, when no block can append to that slot
+  uint32_t xneed[kMaxIterLimit + 2];                  // continuation: a recorded expansion would mark
   // trace (written by block 0): %globaltimer at kernel start, after phase 0 and after each
   // iteration's barrier; affected vertices at the start of each iteration; iteration kind
   unsigned long long t_ns[kMaxIterLimit + 2];

@@ -1121,10 +1121,10 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
                           (prev_total == 0xFFFFFFFFu || total_now - prev_total > total_now / 16);
     prev_total = total_now;
     // a settled affected set (compacted items current, nothing marked since) continues in
-    // the lean continuation kernel; this launch stops here (a resumed launch first runs
-    // four iterations itself, so that a chain of late expansions does not bounce between
-    // the kernels every iteration)
-    if (df && a.split && dense && !scan_all && total_now == cmp_total && it >= it_begin + (a.resume ? 4 : 0)) {
+    // the lean continuation kernel; this launch stops here.  A resumed launch hands off
+    // again at once when its expansions marked nothing new: a relaunch costs far less than
+    // an iteration of this kernel
+    if (df && a.split && dense && !scan_all && total_now == cmp_total) {
       if (blockIdx.x == 0 && tid == 0) {
 #pragma unroll
         for (int bb = 0; bb < 3; bb++) {
@@ -1512,6 +1512,46 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
   }
 }
 
+// Would expanding the recorded vertices xlist[first, first + k) mark anything?  Scans their
+// out-rows against the affected bitmap (no marking): a vertex every out-neighbour of which
+// is affected already expands to nothing (Algorithm 1's marking of marked vertices is a
+// no-op), so the continuation goes on.  Sets xneed[slot] otherwise, and for any row longer
+// than kCheckMax (the marking kernel handles those through its hub queue).  Out of line: it
+// runs only in iterations that recorded expansions.
+constexpr uint32_t kCheckMax = 4096;  // longer out-rows are not scanned: the call resumes
+constexpr uint32_t kNoEntry = 0xFFFFFFFFu;  // no vertex id (ids are below n <= 2^32 - 1)
+template <bool F32>
+__device__ __noinline__ void check_recorded(const RankArgs<F32> &a, uint32_t first, uint32_t k, uint32_t slot) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t nwarps = (gridDim.x * kRankBlock) >> 5, gwarp = (blockIdx.x * kRankBlock + threadIdx.x) >> 5;
+  for (uint32_t i = gwarp; i < k; i += nwarps) {
+    if (ldcg(&a.ctl->xneed[slot])) return;  // decided already
+    const uint32_t v = ldcg(a.xlist + first + i);
+    const uint2 od = __ldg(&a.out_rd[v]);
+    if (od.y > kCheckMax) {
+      if (lane == 0) atomicOr(&a.ctl->xneed[slot], 1u);
+      return;
+    }
+    // 128 entries per round, four per lane, loads in flight together
+    for (uint32_t j0 = 0; j0 < od.y; j0 += 128) {
+      uint32_t w[4];
+#pragma unroll
+      for (int r = 0; r < 4; r++) {
+        const uint32_t j = j0 + 32u * r + lane;
+        w[r] = j < od.y ? __ldg(a.out_col + od.x + j) : kNoEntry;
+      }
+      bool unmarked = false;
+#pragma unroll
+      for (int r = 0; r < 4; r++)
+        if (w[r] != kNoEntry) unmarked = unmarked || !(ldcg(a.bitmap + (w[r] >> 5)) & (1u << (w[r] & 31)));
+      if (__any_sync(kFull, unmarked)) {
+        if (lane == 0) atomicOr(&a.ctl->xneed[slot], 1u);
+        return;
+      }
+    }
+  }
+}
+
 // Continuation of a split Dynamic Frontier call: the affected set has settled, so every
 // iteration sweeps the compacted sweep items left by the handing-off launch, with none of
 // the marking code (the same sweep as Static and Naive-dynamic, plus the expand-once test).
@@ -1542,6 +1582,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank_cont(
   Mass<F32> dacc;
   uint32_t my_v = 0, my_e = 0;
   uint32_t iters = (uint32_t)a.it0, status = kStatusCont;
+  uint32_t xfirst = 0;  // recorded expansions found to mark nothing (this launch)
   bool converged = false;
   unsigned long long last_key = 0;
   for (int it = a.it0; it < a.max_iter; it++) {
@@ -1598,9 +1639,16 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank_cont(
       converged = true;
       break;
     }
-    if (ldcg(&ctl->xit[it + 1]) != 0 && it + 1 < a.max_iter) {
-      status = kStatusExpand;
-      break;
+    const uint32_t nrec = ldcg(&ctl->xit[it + 1]);
+    if (nrec != 0 && it + 1 < a.max_iter) {
+      // resume the marking kernel only if some recorded expansion would mark a vertex
+      check_recorded(a, xfirst, nrec, (uint32_t)it + 1);
+      if (!grid_sync(ctl, epoch, &s_err)) return;
+      if (ldcg(&ctl->xneed[it + 1]) != 0) {
+        status = kStatusExpand;
+        break;
+      }
+      xfirst += nrec;
     }
   }
   {

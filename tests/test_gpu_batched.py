@@ -230,30 +230,38 @@ def test_split_frontier_call_equals_single_launch(prdf, prec):
 
 @pytest.mark.parametrize("split", [0, 1])
 def test_late_expansions_resume_the_marking_kernel(prdf, split):
-    # every vertex of a 100-vertex chain is affected from the start (out-neighbours of a
-    # hub whose out-degree the batch keeps), but the change entering at the chain's end
-    # reaches vertex i only after 100 - i iterations: each vertex expands late, while the
-    # affected set has long settled, so a split call keeps handing the call back to the
-    # marking kernel.  Ranks, iterations and affected set must match the single launch and
-    # the oracle.
-    n = 128
-    pairs = [(0, v) for v in range(1, 101)] + [(v, v - 1) for v in range(2, 101)] + [(101, 0), (102, 101)]
-    g = synth.from_pairs(n, pairs, "hub-chain")
+    # a hub makes a 12-vertex chain affected from the start, the batch changes the flow
+    # into the chain's far end, and the change reaches vertex 1 only after 11 iterations;
+    # its expansion then marks a new vertex (its leaf, 50).  Until then the affected set is
+    # settled: a split call continues in the continuation kernel, whose late expansions mark
+    # nothing (chain neighbours are affected) until vertex 1's, which resumes the marking
+    # kernel.  Starting from fully converged ranks, so that nothing else crosses tau_f.
+    # Ranks, iterations and affected set must match the single launch and the oracle.
+    n = 64
+    pairs = [(0, v) for v in range(1, 13)] + [(v, v - 1) for v in range(2, 13)] + [(1, 50), (41, 0), (42, 41)]
+    g = synth.from_pairs(n, pairs, "hub-chain-leaf")
     G = oracle.Graph.build(g.n, g.src, g.dst)
-    R0, _ = oracle.static_pr(G)
-    dele, ins = [(0, 100)], [(0, 102)]
-    H, ed, ei = G.apply([0], [100], [0], [102])
+    R0 = oracle.reference_static(G)
+    R0 = R0[0] if isinstance(R0, tuple) else R0
+    H, ed, ei = G.apply([0], [12], [0], [40])
     Rn, aff, so = oracle.df_sync(G, H, ed, ei, R0)
+    assert aff[50]  # the late expansion happened in the oracle too
     with prdf.Graph(g.n, g.src, g.dst) as A:
         t = A.tuning()
         A.set_tuning(t.bin_lo, t.bin_hi, t.dense_div, t.blocks_per_sm, split)
         A.set_ranks(R0)
-        A.apply([0], [100], [0], [102])
+        A.apply([0], [12], [0], [40])
+        l0 = prdf.pr_kernel_launches()
         st = A.frontier()
+        launches = prdf.pr_kernel_launches() - l0
         kinds = "".join(str(int(k)) for k in A.trace()["kind"])
         assert np.max(np.abs(A.ranks() - Rn)) <= TOL64
         assert abs(st.iterations - so.iterations) <= 1
         assert st.affected_final == so.affected_final
+        assert sorted(A.affected().tolist()) == np.nonzero(aff)[0].tolist()
     if split:
-        # the continuation ran, and a marking launch resumed after it
-        assert "5" in kinds and any(k != "5" for k in kinds[kinds.index("5"):]), kinds
+        # the continuation ran, and a marking launch resumed after it: more launches than
+        # one marking launch, one continuation and the writeback
+        assert "5" in kinds and launches > 3, (kinds, launches)
+    else:
+        assert launches == 1 and "5" not in kinds
