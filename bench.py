@@ -145,6 +145,25 @@ def _cpu_worker(scale, ef, seed, fracs, q):
         q.put({"error": repr(e)})
 
 
+# --------------------------------------------------------- multi-GPU runs ----
+# Replicas only: every rank updates its own copy of the workload (seed 1 + rank) with no
+# data-path exchange; the ranks meet only at the barriers around the timed region and in
+# this reduction of the timings.
+
+def replica_seed(rank: int) -> int:
+    return 1 + rank
+
+
+def max_over_ranks(values, device):
+    """The job's figure for each time-like value: the slowest rank's."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
 # ------------------------------------------------------------- GPU arm ----
 
 def run_ours(args, rank: int, world: int, local_rank: int):
@@ -174,7 +193,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 
         dist.init_process_group("nccl", device_id=dev)
 
-    seed = 1 + rank
+    seed = replica_seed(rank)
     g = synth.rmat(args.scale, args.ef, seed=seed)
     params = prdf.pr_params_default()
     params.precision = prdf.PR_F32 if args.precision == "fp32" else prdf.PR_F64
@@ -307,9 +326,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     ms_per_step = (t1 - t0) / K * 1e3
 
     if dist:
-        t = torch.tensor([value, e2e_value, ms_per_step], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        value, e2e_value, ms_per_step = t.tolist()
+        value, e2e_value, ms_per_step = max_over_ranks([value, e2e_value, ms_per_step], dev)
 
     cpu = None
     if proc is not None:
