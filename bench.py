@@ -259,6 +259,46 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         t1 = time.perf_counter()
         launches = prdf.pr_kernel_launches() - l0
         clk = clocks.stop()
+        R_final64 = R_cur.clone()
+
+        # the same chain of updates with FP32 ranks (untimed by the step clock; its own events)
+        fp32 = None
+        if args.precision == "fp64" and not args.no_fp32:
+            p32 = prdf.pr_params_default()
+            p32.precision = prdf.PR_F32
+            G32 = prdf.Graph(g.n, g.src, g.dst, p32, stream.cuda_stream)
+            G32.static()
+            rec32 = {f: {"df": [], "naive": [], "static": []} for f in FRACS}
+            P = torch.empty(n, dtype=torch.float64, device=dev)
+            Q = torch.empty(n, dtype=torch.float64, device=dev)
+            for i in range(W + K):
+                for fi, f in enumerate(FRACS):
+                    b = batches[i][fi]
+                    G32.ranks(P)
+                    G32.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+                    flush.zero_()
+                    sd = G32.frontier()
+                    G32.ranks(Q)
+                    G32.set_ranks(P)
+                    flush.zero_()
+                    sn = G32.naive()
+                    flush.zero_()
+                    ss = G32.static()
+                    G32.set_ranks(Q)
+                    if i >= W:
+                        rec32[f]["df"].append(sd.ms_rank)
+                        rec32[f]["naive"].append(sn.ms_rank)
+                        rec32[f]["static"].append(ss.ms_rank)
+            G32.ranks(Q)
+            err = float((Q - R_final64).abs().max())
+            G32.close()
+            avg = lambda xs: sum(xs) / len(xs)
+            fp32 = {"value": geomean([avg(rec32[f]["df"]) for f in FRACS]), "unit": "ms",
+                    "linf_vs_fp64_after_chain": err,
+                    "per_frac": {f"{f:g}": {"df_ms": avg(rec32[f]["df"]), "naive_ms": avg(rec32[f]["naive"]),
+                                           "static_ms": avg(rec32[f]["static"])} for f in FRACS},
+                    "note": "same batches, FP32 ranks and contributions; error = L-inf between the FP32 "
+                            "and FP64 chains' ranks after all updates"}
 
         # end to end through the C ABI with pinned host buffers
         out_h = torch.empty(n, dtype=torch.float64, pin_memory=True)
@@ -364,6 +404,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                      "kernel": "k_rank (Static full sweep launches)",
                      "all_rank_launches_gbs": all_bytes / (all_ms * 1e-3) / 1e9},
         "per_frac": per_f,
+        "fp32": fp32,
         "speedup_vs_static_geomean": geomean([per_f[k]["speedup_vs_static"] for k in per_f]),
         "speedup_vs_naive_geomean": geomean([per_f[k]["speedup_vs_naive"] for k in per_f]),
         "clocks": clk,
@@ -746,6 +787,7 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "fp32"], default=None,
                     help="default fp64 for the plain workload, fp32 for the batched form")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true", help="plain workload: skip the FP32 leg")
     ap.add_argument("--cpu-timeout", type=float, default=600.0)
     ap.add_argument("--config", choices=["plain", "precision", "batched", "serving"], default="plain",
                     help="plain: the headline workload (R-MAT s22 sweep); precision / batched / serving: "

@@ -88,7 +88,7 @@ def _load():
         f = getattr(lib, name)
         f.restype = ctypes.c_int
         f.argtypes = [vp, ctypes.POINTER(_Params), vp, ctypes.POINTER(_Stats)]
-    for name in ("or_df_sync", "or_df_async"):
+    for name in ("or_df_sync", "or_df_async", "or_dt_sync"):
         f = getattr(lib, name)
         f.restype = ctypes.c_int
         f.argtypes = [vp, vp, ctypes.POINTER(_Params), u64, vp, vp, u64, vp, vp, vp, vp,
@@ -230,6 +230,11 @@ def df_sync(g_old: Graph, g_new: Graph, eff_del, eff_ins, R_prev, params: Params
 def df_async(g_old: Graph, g_new: Graph, eff_del, eff_ins, R_prev, params: Params | None = None):
     """Dynamic Frontier, asynchronous (paper's CPU form): (ranks, affected flags, Stats)."""
     return _df(_load().or_df_async, g_old, g_new, eff_del, eff_ins, R_prev, params)
+
+
+def dt_sync(g_old: Graph, g_new: Graph, eff_del, eff_ins, R_prev, params: Params | None = None):
+    """Dynamic Traversal (Section 3.3.2): (ranks, affected flags, Stats)."""
+    return _df(_load().or_dt_sync, g_old, g_new, eff_del, eff_ins, R_prev, params)
 
 
 def reference_static(g: Graph, dead_end: int = SELF_LOOPS):

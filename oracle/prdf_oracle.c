@@ -17,6 +17,8 @@
  *   or_naive            Section 3.3.1: the same sweep started from previous ranks.
  *   or_df_sync          Algorithm 1 with the synchronous (two-vector, Jacobi) reading
  *                       of Section 4.2: marks made in iteration i take effect in i+1.
+ *   or_dt_sync          Dynamic Traversal (Section 3.3.2): vertices reachable from the
+ *                       changed edges' sources in G^{t-1} or G^t, iterated synchronously.
  *   or_df_async         Algorithm 1 with the asynchronous (one-vector) reading of
  *                       Section 4.2: vertices swept in ascending id, in place, marks
  *                       take effect at once.  The paper's CPU choice.
@@ -391,6 +393,76 @@ int or_df_sync(const or_graph *gold, const or_graph *gnew, const or_params *p,
     st->affected_final = count_marked(aff, n);
     if (aff_out) memcpy(aff_out, aff, n);
     free(aff); free(next); free(Rn);
+    return 0;
+}
+
+/*
+ * Dynamic Traversal (Section 3.3.2, the comparator of Section 5): for every (u, v) in
+ * Delta^- U Delta^+, every vertex reachable from u in G^{t-1} or in G^t is affected
+ * (breadth-first search in each graph separately; a vertex reaches itself).  The affected
+ * vertices are then iterated as in or_df_sync, but nothing further is ever marked.  In
+ * teleport mode a changed dead-end mass moves every rank, so every vertex is affected.
+ */
+static void reach(const or_graph *g, uint32_t u, uint8_t *seen, uint32_t *queue)
+{
+    if (seen[u]) return;
+    uint64_t head = 0, tail = 0;
+    seen[u] = 1;
+    queue[tail++] = u;
+    while (head < tail) {
+        uint32_t x = queue[head++];
+        for (uint64_t j = g->out_off[x]; j < g->out_off[x + 1]; j++) {
+            uint32_t w = g->out_col[j];
+            if (!seen[w]) {
+                seen[w] = 1;
+                queue[tail++] = w;
+            }
+        }
+    }
+}
+
+int or_dt_sync(const or_graph *gold, const or_graph *gnew, const or_params *p,
+               uint64_t nd, const uint32_t *ds, const uint32_t *dd,
+               uint64_t ni, const uint32_t *is, const uint32_t *id,
+               double *R, uint8_t *aff_out, or_stats *st)
+{
+    (void)dd; (void)id;
+    uint32_t n = gnew->n;
+    uint8_t *seen_old = (uint8_t *)calloc(n ? n : 1, 1);
+    uint8_t *seen_new = (uint8_t *)calloc(n ? n : 1, 1);
+    uint8_t *aff = (uint8_t *)calloc(n ? n : 1, 1);
+    uint32_t *queue = (uint32_t *)malloc(sizeof(uint32_t) * (n ? n : 1));
+    double *Rn = (double *)malloc(sizeof(double) * (n ? n : 1));
+    memset(st, 0, sizeof(*st));
+    for (uint64_t k = 0; k < nd + ni; k++) {
+        uint32_t u = k < nd ? ds[k] : is[k - nd];
+        reach(gold, u, seen_old, queue);
+        reach(gnew, u, seen_new, queue);
+    }
+    for (uint32_t v = 0; v < n; v++) aff[v] = (uint8_t)(seen_old[v] | seen_new[v]);
+    if (p->dead_end == 1 && nd + ni > 0)
+        for (uint32_t v = 0; v < n; v++) aff[v] = 1;
+    for (int32_t i = 0; i < p->max_iter; i++) {
+        double D = p->dead_end == 1 ? dead_end_mass(gnew, R) : 0.0;
+        memcpy(Rn, R, sizeof(double) * n);
+        double dR = 0.0;
+        for (uint32_t v = 0; v < n; v++) {
+            if (!aff[v]) continue;
+            double r = rank_of(gnew, p, R, v, D);
+            double d = fabs(r - R[v]);
+            Rn[v] = r;
+            if (d > dR) dR = d;
+            st->vertices_processed++;
+            st->edges_processed += (int64_t)(gnew->in_off[v + 1] - gnew->in_off[v]);
+        }
+        memcpy(R, Rn, sizeof(double) * n);
+        st->iterations = i + 1;
+        st->last_delta = dR;
+        if (dR <= p->tol) { st->converged = 1; break; }
+    }
+    st->affected_final = count_marked(aff, n);
+    if (aff_out) memcpy(aff_out, aff, n);
+    free(seen_old); free(seen_new); free(aff); free(queue); free(Rn);
     return 0;
 }
 

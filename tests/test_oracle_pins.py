@@ -341,3 +341,64 @@ def test_df_error_not_above_static_error():
         Rs, _ = oracle.static_pr(H)
         assert np.abs(R - ref).sum() <= np.abs(Rs - ref).sum()
         G = H
+
+
+def _union_reach(n, old_pairs, new_pairs, sources):
+    """Brute force: vertices reachable from the sources in the union of both edge sets
+    (self-loops added).  Every edge in only one graph starts at a source, so this is the
+    set reachable from some source in G^{t-1} or in G^t."""
+    adj = {v: {v} for v in range(n)}
+    for u, v in list(old_pairs) + list(new_pairs):
+        adj[u].add(v)
+    seen, stack = set(), list(sources)
+    while stack:
+        x = stack.pop()
+        if x in seen:
+            continue
+        seen.add(x)
+        stack.extend(adj[x] - seen)
+    return seen
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_dt_affected_set_is_reachability(seed):
+    """Section 3.3.2: Dynamic Traversal marks exactly the vertices reachable from the
+    sources of the effective changes in G^{t-1} or G^t (checked against a brute-force
+    search), and that set contains everything Dynamic Frontier marks."""
+    rng = random.Random(seed)
+    n = 40
+    pairs = {(rng.randrange(n), rng.randrange(n)) for _ in range(50)}
+    pairs = {(u, v) for u, v in pairs if u != v}
+    g = synth.from_pairs(n, sorted(pairs), "random")
+    G = oracle.Graph.build(n, g.src, g.dst)
+    R, _ = oracle.static_pr(G)
+    dels = rng.sample(sorted(pairs), 3)
+    ins = [(rng.randrange(n), rng.randrange(n)) for _ in range(3)]
+    H, ed, ei = G.apply([u for u, _ in dels], [v for _, v in dels], [u for u, _ in ins], [v for _, v in ins])
+    new_pairs = (pairs - set(dels)) | {(u, v) for u, v in ins if u != v}
+    sources = set(ed[0].tolist()) | set(ei[0].tolist())
+    Rt, aff_t, _ = oracle.dt_sync(G, H, ed, ei, R)
+    Rf, aff_f, _ = oracle.df_sync(G, H, ed, ei, R)
+    assert set(np.nonzero(aff_t)[0].tolist()) == _union_reach(n, pairs, new_pairs, sources)
+    assert not np.any(aff_f & ~aff_t)
+
+
+def test_dt_reaches_the_exact_solution():
+    """Vertices no source reaches keep their in-rows and their in-neighbours' out-degrees,
+    so their exact ranks do not change; Dynamic Traversal from the exact old ranks must
+    therefore land on the exact new ranks (dense solve), up to the iteration tolerance."""
+    g = synth.rmat(8, 4, seed=7)
+    n = g.n
+    G = oracle.Graph.build(n, g.src, g.dst)
+    R = oracle.dense_solve(n, g.src, g.dst)
+    s = synth.BatchStream(g, seed=7)
+    p = oracle.Params(tol=1e-14)
+    for t in range(3):
+        b = s.next(2e-2)
+        H, ed, ei = G.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+        R, aff, st = oracle.dt_sync(G, H, ed, ei, R, p)
+        assert st.converged and 0 < st.affected_final <= n
+        cur = s.current()
+        exact = oracle.dense_solve(n, cur.src, cur.dst)
+        assert np.max(np.abs(R - exact)) <= 1e-12
+        G = H
