@@ -174,6 +174,14 @@ pr_status pr_naive_dynamic(pr_graph *g, pr_stats *stats);
  * the next iteration.  Stops when the L-inf change is <= tol or after max_iter iterations. */
 pr_status pr_dynamic_frontier(pr_graph *g, pr_stats *stats);
 
+/* Dynamic Traversal (Section 3.3.2, the paper's third comparator): every vertex reachable
+ * from a source of the pending changes in G^{t-1} or G^t is affected (breadth-first
+ * search in G^t from the sources and the deleted targets, which reaches the same set;
+ * searches deeper than 1000 levels take every vertex), then the affected vertices iterate
+ * as in pr_dynamic_frontier with no further marking.  In teleport mode any change affects
+ * every vertex.  Consumes the pending marks like pr_dynamic_frontier. */
+pr_status pr_dynamic_traversal(pr_graph *g, pr_stats *stats);
+
 /* Copies the n ranks (widened to double in FP32 mode) into out (host or device). */
 pr_status pr_get_ranks(pr_graph *g, double *out, uint32_t n);
 

@@ -428,6 +428,7 @@ static pr_status run(pr_graph *h, prdf::RankMode mode, pr_stats *stats) {
 pr_status pr_static(pr_graph *h, pr_stats *stats) { return run(h, prdf::kModeStatic, stats); }
 pr_status pr_naive_dynamic(pr_graph *h, pr_stats *stats) { return run(h, prdf::kModeNaive, stats); }
 pr_status pr_dynamic_frontier(pr_graph *h, pr_stats *stats) { return run(h, prdf::kModeDF, stats); }
+pr_status pr_dynamic_traversal(pr_graph *h, pr_stats *stats) { return run(h, prdf::kModeDT, stats); }
 
 static pr_status ensure_stage(pr_graph *h) {
   if (h->stage) return PR_OK;

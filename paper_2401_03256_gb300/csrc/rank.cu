@@ -889,6 +889,74 @@ __device__ __forceinline__ void sweep_tiers(const RankArgs<F32> &a, SweepIo<F32>
 
 // DF: compiled for Dynamic Frontier calls (marking and frontier expansion); Static and
 // Naive-dynamic use the instance without them, which needs fewer registers.
+// Dynamic Traversal (Section 3.3.2): breadth-first search from the seeds phase 0 marked (the
+// sources, via their self-loops and new out-rows, and the deleted targets; together they reach
+// exactly what the sources reach in G^{t-1} or G^t). Round r expands the vertices that joined
+// in round r - 1; slot r's tails and hub queue keep rounds apart. When the search closes every
+// stamp is reset to iteration 0. A search deeper than the round limit reports `all`: every
+// vertex is then taken as affected.
+struct DtOut {
+  uint32_t cnt[3];
+  uint32_t app, xv, xe, epoch;
+  bool ok, all;
+};
+template <bool F32>
+__device__ __noinline__ DtOut dt_search(const RankArgs<F32> &a, uint32_t epoch, uint32_t c0, uint32_t c1,
+                                        uint32_t c2, WarpBuf *wbp) {
+  __shared__ uint32_t s_err;
+  const uint32_t tid = threadIdx.x, lane = tid & 31;
+  const uint32_t nthreads = gridDim.x * kRankBlock;
+  const uint32_t gtid = blockIdx.x * kRankBlock + tid;
+  const uint32_t nwarps = nthreads >> 5, gwarp = gtid >> 5;
+  RankCtl *ctl = a.ctl;
+  DtOut o{{c0, c1, c2}, 0u, 0u, 0u, epoch, false, false};
+  WarpBuf wb = *wbp;
+  wb.dense = false;
+  const uint32_t *lists[3] = {a.list0, a.list1, a.list2};
+  uint32_t done[3] = {0u, 0u, 0u};
+  uint32_t r = 1;
+  for (; r <= (uint32_t)kMaxIterLimit; r++) {
+#pragma unroll
+    for (int bb = 0; bb < 3; bb++) {
+      for (uint32_t k0 = done[bb] + gwarp * 32; k0 < o.cnt[bb]; k0 += nwarps * 32) {
+        const bool p = k0 + lane < o.cnt[bb];
+        const uint32_t x = p ? ldcg(lists[bb] + k0 + lane) : 0u;
+        const ExpandOut e = expand_lanes(a, p ? 1 : 0, x, r, o.cnt[0], o.cnt[1], o.cnt[2], &wb);
+        o.app += e.app;
+        o.xv += e.xv;
+        o.xe += e.xe;
+      }
+    }
+    flush_marks(a, r, o.cnt, lane, wb);
+    if (!grid_sync(ctl, o.epoch, &s_err)) return o;
+    if (__ldcg(&ctl->hubq[r]) != 0) {
+      o.app += hub_pass(a, r, o.cnt, lane, gwarp, nwarps, wb);
+      flush_marks(a, r, o.cnt, lane, wb);
+      if (!grid_sync(ctl, o.epoch, &s_err)) return o;
+    }
+    uint32_t added = 0;
+#pragma unroll
+    for (int bb = 0; bb < 3; bb++) {
+      const uint32_t t = ldcg(&ctl->tail[r][bb]);
+      done[bb] = o.cnt[bb];
+      o.cnt[bb] += t;
+      added += t;
+    }
+    if (added == 0) break;
+  }
+  if (r > (uint32_t)kMaxIterLimit) {
+    o.all = true;
+  } else {
+#pragma unroll
+    for (int bb = 0; bb < 3; bb++)
+      for (uint32_t k = gtid; k < o.cnt[bb]; k += nthreads) a.stamp[ldcg(lists[bb] + k)] = 0;
+    if (!grid_sync(ctl, o.epoch, &s_err)) return o;
+  }
+  *wbp = wb;
+  o.ok = true;
+  return o;
+}
+
 template <bool F32, bool DF>
 __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const RankArgs<F32> a) {
   using S = Store<F32>;
@@ -1071,11 +1139,28 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
     if (df && a.resume) cnt[bb] = saved_cnt[bb] + ldcg(&ctl->tail[it_begin][bb]);
     else cnt[bb] = df && !a.start_full ? ldcg(&ctl->tail[0][bb]) : 0u;
   }
+  // Dynamic Traversal: every vertex reachable from the seeds phase 0 marked joins iteration 0
+  // and nothing is marked afterwards
+  const bool dt = df && a.mode == kModeDT;
+  bool dt_all = false;
+  if (dt && !a.start_full) {
+    const DtOut o = dt_search(a, epoch, cnt[0], cnt[1], cnt[2], &wb);
+    if (!o.ok) return;
+    epoch = o.epoch;
+#pragma unroll
+    for (int bb = 0; bb < 3; bb++) cnt[bb] = o.cnt[bb];
+    my_app += o.app;
+    my_xv += o.xv;
+    my_xe += o.xe;
+    dt_all = o.all;
+    if (dt_all && blockIdx.x == 0 && tid == 0) ctl->full_from = 1u;
+    if (blockIdx.x == 0 && tid == 0) ctl->t_ns[1] = globaltimer_ns();
+  }
   long long Dn = 0;
   double Dd = 0.0;
   if (a.teleport) Dn = grid_dead_total(0, &Dd);
   R tele_prev = a.teleport ? tele_of(a.D_ref_n, a.D_ref_d) : (R)0;
-  bool ever_full = !df || a.start_full;
+  bool ever_full = !df || a.start_full || dt_all;
   uint32_t iters = 0;
   bool converged = false;
   unsigned long long last_key = 0;
@@ -1138,7 +1223,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
       handed_off = true;
       break;
     }
-    const bool expand = df && !I.full;
+    const bool expand = df && !dt && !I.full;
     const uint32_t slot = (uint32_t)it + 1;
     B my_max = 0;
     if (blockIdx.x == 0 && tid == 0) {
@@ -1431,7 +1516,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
       }
       dR = any_active ? a.tol_key + 1 : 0;  // stop when no component is still iterating
     }
-    if (df && !I.full) {
+    if (expand) {
 #pragma unroll
       for (int bb = 0; bb < 3; bb++) cnt[bb] += ldcg(&ctl->tail[slot][bb]);
     }
@@ -1819,7 +1904,8 @@ static pr_status launch(Graph *g, RankMode mode, bool start_full) {
   a.resume = 0;
   a.it0 = 0;
   void *args[] = {(void *)&a};
-  const void *fn = mode == kModeDF ? (const void *)k_rank<F32, true> : (const void *)k_rank<F32, false>;
+  const bool marking = mode == kModeDF || mode == kModeDT;
+  const void *fn = marking ? (const void *)k_rank<F32, true> : (const void *)k_rank<F32, false>;
   if (!g->use_graph) {
     CK(cudaLaunchCooperativeKernel(fn, dim3(g->rank_grid), dim3(kRankBlock), args,
                                    rank_smem(g->ncomp), g->st));
@@ -1864,7 +1950,7 @@ static pr_status launch(Graph *g, RankMode mode, bool start_full) {
   kp.blockDim = dim3(kRankBlock);
   kp.sharedMemBytes = (unsigned)rank_smem(g->ncomp);
   kp.kernelParams = args;
-  if (g->cg_exec && (g->cg_f32 != F32 || g->cg_df != (mode == kModeDF))) {
+  if (g->cg_exec && (g->cg_f32 != F32 || g->cg_df != marking)) {
     cudaGraphExecDestroy(g->cg_exec);
     cudaGraphDestroy(g->cg);
     g->cg_exec = nullptr;
@@ -1889,7 +1975,7 @@ static pr_status launch(Graph *g, RankMode mode, bool start_full) {
     g->cg = graph;
     g->cg_kernel = kern;
     g->cg_f32 = F32;
-    g->cg_df = mode == kModeDF;
+    g->cg_df = marking;
   } else {
     CK(cudaGraphExecKernelNodeSetParams(g->cg_exec, g->cg_kernel, &kp));
   }
@@ -1900,7 +1986,10 @@ static pr_status launch(Graph *g, RankMode mode, bool start_full) {
 
 pr_status rank_run(Graph *g, RankMode mode, pr_stats *stats) {
   pr_status rc;
-  const bool start_full = mode == kModeDF && g->pend_all;
+  const bool marking = mode == kModeDF || mode == kModeDT;
+  // Dynamic Traversal in teleport mode: a changed dead-end mass moves every rank
+  const bool start_full = marking && (g->pend_all || (mode == kModeDT && g->teleport &&
+                                                      (g->n_pend_src > 0 || g->n_pend_tgt > 0)));
   if (g->teleport && (rc = graph_refresh_dead(g)) != PR_OK) return rc;
   if ((rc = graph_refresh_ident(g)) != PR_OK) return rc;
   if (!g->use_graph) CK(cudaMemsetAsync(g->ctl, 0, sizeof(RankCtl), g->st));
@@ -1941,9 +2030,9 @@ pr_status rank_run(Graph *g, RankMode mode, pr_stats *stats) {
       g->trace_kind[i] = h.it_kind[i];
     }
   }
-  const bool full = mode != kModeDF || start_full || h.full_from != 0;
+  const bool full = !marking || start_full || h.full_from != 0;
   g->last_full = full;
-  for (int b = 0; b < 3; b++) g->last_list_cnt[b] = mode == kModeDF ? h.final_cnt[b] : 0;
+  for (int b = 0; b < 3; b++) g->last_list_cnt[b] = marking ? h.final_cnt[b] : 0;
   g->n_pend_src = 0;
   g->n_pend_tgt = 0;
   g->pend_all = false;

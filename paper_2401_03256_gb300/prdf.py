@@ -30,7 +30,7 @@ PR_DEADEND_TELEPORT = 1
 
 EXPORTED = (
     "pr_params_default", "pr_graph_create", "pr_graph_destroy", "pr_apply_batch", "pr_apply_batches", "pr_static",
-    "pr_naive_dynamic", "pr_dynamic_frontier", "pr_get_ranks", "pr_set_ranks", "pr_graph_info",
+    "pr_naive_dynamic", "pr_dynamic_frontier", "pr_dynamic_traversal", "pr_get_ranks", "pr_set_ranks", "pr_graph_info",
     "pr_get_csr", "pr_get_affected", "pr_get_trace", "pr_kernel_launches", "pr_last_error", "pr_status_string",
     "pr_graph_create_batched", "pr_get_component_stats", "pr_set_tuning", "pr_get_tuning", "pr_autotune",
     "pr_set_graph_launch", "pr_server_config_default", "pr_server_create", "pr_server_add_graph",
@@ -110,7 +110,7 @@ def load(path: str = LIB_PATH):
     lib.pr_static_noalloc.argtypes = [ctypes.c_uint32, i64, vp, vp, vp, vp, vp, vp]
     lib.pr_apply_batches.restype = ctypes.c_int
     lib.pr_apply_batches.argtypes = [vp, ctypes.c_int32, vp, vp, vp, vp, vp, vp]
-    for name in ("pr_static", "pr_naive_dynamic", "pr_dynamic_frontier"):
+    for name in ("pr_static", "pr_naive_dynamic", "pr_dynamic_frontier", "pr_dynamic_traversal"):
         f = getattr(lib, name)
         f.restype = ctypes.c_int
         f.argtypes = [vp, ctypes.POINTER(pr_stats)]
@@ -327,6 +327,10 @@ def pr_dynamic_frontier(h: int) -> pr_stats:
     return _rank(load().pr_dynamic_frontier, h)
 
 
+def pr_dynamic_traversal(h: int) -> pr_stats:
+    return _rank(load().pr_dynamic_traversal, h)
+
+
 def pr_graph_info(h: int):
     n = ctypes.c_uint32()
     m = ctypes.c_int64()
@@ -387,7 +391,7 @@ def pr_kernel_launches() -> int:
 
 
 def pr_get_affected(h: int) -> np.ndarray:
-    """Vertices marked affected by the last pr_dynamic_frontier call (unordered)."""
+    """Vertices marked affected by the last Dynamic Frontier or Traversal call (unordered)."""
     cnt = ctypes.c_int64()
     _check(load().pr_get_affected(h, None, 0, ctypes.byref(cnt)), h)
     out = np.empty(max(cnt.value, 1), np.uint32)
@@ -439,6 +443,9 @@ class Graph:
 
     def frontier(self) -> pr_stats:
         return pr_dynamic_frontier(self.h)
+
+    def traversal(self) -> pr_stats:
+        return pr_dynamic_traversal(self.h)
 
     def ranks(self, out=None):
         return pr_get_ranks(self.h, out)
