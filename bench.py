@@ -203,6 +203,10 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         G = prdf.Graph(g.n, g.src, g.dst, params, stream.cuda_stream)
         n, m = G.info()
         G.static()
+        # Dynamic Traversal and asynchronous DF consume pending marks too: each runs on a
+        # handle of its own that receives the same batches and starts from the same ranks
+        G_dt = prdf.Graph(g.n, g.src, g.dst, params, stream.cuda_stream)
+        G_as = prdf.Graph(g.n, g.src, g.dst, params, stream.cuda_stream)
         bs = synth.BatchStream(g, seed=seed)
         batches = [[bs.next(f) for f in FRACS] for _ in range(W + K)]
         e2e_batches = [[bs.next(f) for f in FRACS] for _ in range(K)]
@@ -211,7 +215,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         R_cur = torch.empty(n, dtype=torch.float64, device=dev)
         rec = {f: {"df": [], "naive": [], "static": [], "apply": [], "df_iters": [], "df_affected": [],
                    "df_bytes": [], "naive_iters": [], "static_iters": [], "static_bytes": [], "naive_bytes": [],
-                   "df_edges": []} for f in FRACS}
+                   "df_edges": [], "dt": [], "dt_iters": [], "dt_affected": [], "dfa": [], "dfa_iters": []} for f in FRACS}
 
         def step(i, record):
             for fi, f in enumerate(FRACS):
@@ -222,6 +226,14 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 sd = G.frontier()
                 G.ranks(R_cur)
                 G.set_ranks(R_prev)
+                G_dt.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+                G_dt.set_ranks(R_prev)
+                flush.zero_()
+                st = G_dt.traversal()
+                G_as.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+                G_as.set_ranks(R_prev)
+                flush.zero_()
+                sa = G_as.frontier_async()
                 flush.zero_()
                 sn = G.naive()
                 flush.zero_()
@@ -241,6 +253,11 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                     r["static_iters"].append(ss.iterations)
                     r["static_bytes"].append(ss.bytes_algorithmic)
                     r["naive_bytes"].append(sn.bytes_algorithmic)
+                    r["dt"].append(st.ms_rank)
+                    r["dt_iters"].append(st.iterations)
+                    r["dt_affected"].append(st.affected_final)
+                    r["dfa"].append(sa.ms_rank)
+                    r["dfa_iters"].append(sa.iterations)
 
         for i in range(W):
             step(i, False)
@@ -324,6 +341,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 G.ranks(out_h)
                 e2e[f].append((time.perf_counter() - t) * 1e3)
         G.close()
+        G_dt.close()
+        G_as.close()
 
     def mean(xs):
         return sum(xs) / len(xs) if xs else float("nan")
@@ -359,6 +378,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             "speedup_vs_naive": mean(r["naive"]) / df_ms[f], "df_iterations": mean(r["df_iters"]),
             "naive_iterations": mean(r["naive_iters"]), "static_iterations": mean(r["static_iters"]),
             "df_affected": mean(r["df_affected"]),
+            "dt_ms": mean(r["dt"]), "dt_iterations": mean(r["dt_iters"]), "dt_affected": mean(r["dt_affected"]),
+            "speedup_vs_dt": mean(r["dt"]) / df_ms[f],
+            "df_async_ms": mean(r["dfa"]), "df_async_iterations": mean(r["dfa_iters"]),
             "df_gbs": (sum(r["df_bytes"]) / (sum(r["df"]) * 1e-3) / 1e9) if sum(r["df"]) > 0 else None,
             "e2e_ms": mean(e2e[f]),
         }

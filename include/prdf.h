@@ -182,6 +182,14 @@ pr_status pr_dynamic_frontier(pr_graph *g, pr_stats *stats);
  * every vertex.  Consumes the pending marks like pr_dynamic_frontier. */
 pr_status pr_dynamic_traversal(pr_graph *g, pr_stats *stats);
 
+/* Asynchronous Dynamic Frontier (Section 4.2, the form the paper runs on the CPU): as
+ * pr_dynamic_frontier, but with one rank vector updated in place, so a vertex may read
+ * in-neighbour ranks already updated in the same iteration.  Results depend on the order
+ * in which the GPU's threads run (not bit-reproducible from run to run); every run stops
+ * under the same L-inf test.  Needs a single-graph handle in self-loop mode without graph
+ * launch (PR_ERR_INVALID_ARG otherwise). */
+pr_status pr_dynamic_frontier_async(pr_graph *g, pr_stats *stats);
+
 /* Copies the n ranks (widened to double in FP32 mode) into out (host or device). */
 pr_status pr_get_ranks(pr_graph *g, double *out, uint32_t n);
 

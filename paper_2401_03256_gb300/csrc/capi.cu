@@ -429,6 +429,7 @@ pr_status pr_static(pr_graph *h, pr_stats *stats) { return run(h, prdf::kModeSta
 pr_status pr_naive_dynamic(pr_graph *h, pr_stats *stats) { return run(h, prdf::kModeNaive, stats); }
 pr_status pr_dynamic_frontier(pr_graph *h, pr_stats *stats) { return run(h, prdf::kModeDF, stats); }
 pr_status pr_dynamic_traversal(pr_graph *h, pr_stats *stats) { return run(h, prdf::kModeDT, stats); }
+pr_status pr_dynamic_frontier_async(pr_graph *h, pr_stats *stats) { return run(h, prdf::kModeDFAsync, stats); }
 
 static pr_status ensure_stage(pr_graph *h) {
   if (h->stage) return PR_OK;

@@ -124,7 +124,7 @@ void graph_free(Graph *g);
 pr_status cuda_fail(Graph *g, cudaError_t e, const char *what);
 
 // rank.cu
-enum RankMode { kModeDF = 0, kModeNaive = 1, kModeStatic = 2, kModeDT = 3 };
+enum RankMode { kModeDF = 0, kModeNaive = 1, kModeStatic = 2, kModeDT = 3, kModeDFAsync = 4 };
 pr_status rank_setup(Graph *g);  // grid size, control block
 pr_status rank_run(Graph *g, RankMode mode, pr_stats *stats);
 pr_status rank_init_contrib(Graph *g);  // C = R * adeg for all v, both parities

@@ -1143,7 +1143,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
   // and nothing is marked afterwards
   const bool dt = df && a.mode == kModeDT;
   bool dt_all = false;
-  if (dt && !a.start_full) {
+  if (dt && !a.start_full && !a.resume) {
     const DtOut o = dt_search(a, epoch, cnt[0], cnt[1], cnt[2], &wb);
     if (!o.ok) return;
     epoch = o.epoch;
@@ -1693,7 +1693,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank_cont(
     io.cnt[1] = cnt[1];
     io.cnt[2] = cnt[2];
     io.scan_all = false;
-    io.expand = true;
+    io.expand = a.mode != kModeDT;  // Dynamic Traversal marks nothing after its search
     io.I.full = false;
     io.I.tele = (R)0;
     io.s_base = nullptr;
@@ -1886,7 +1886,15 @@ static pr_status launch(Graph *g, RankMode mode, bool start_full) {
   a.D_ref_d = g->D_ref;
   a.teleport = g->teleport ? 1 : 0;
   a.max_iter = g->p.max_iter;
-  a.mode = (int)mode;
+  // asynchronous Dynamic Frontier (Section 4.2): one rank and one contribution vector, read
+  // and written in place, so a vertex sees the ranks its in-neighbours already updated in the
+  // same iteration; the marking instance runs unchanged on the aliased buffers
+  const bool async = mode == kModeDFAsync;
+  if (async) {
+    a.R1 = a.R0;
+    a.C1 = a.C0;
+  }
+  a.mode = (int)(async ? kModeDF : mode);
   a.start_full = start_full ? 1 : 0;
   a.bin_lo = (uint32_t)g->p.bin_lo;
   a.bin_hi = (uint32_t)g->p.bin_hi;
@@ -1900,11 +1908,11 @@ static pr_status launch(Graph *g, RankMode mode, bool start_full) {
   a.comp_last = g->comp_last;
   a.dense_div = g->dense_div;
   a.xlist = g->xlist;
-  a.split = mode == kModeDF && g->split_df && !g->use_graph && g->ncomp == 1 && !g->teleport && !start_full;
+  a.split = (mode == kModeDF || async || mode == kModeDT) && g->split_df && !g->use_graph && g->ncomp == 1 && !g->teleport && !start_full;
   a.resume = 0;
   a.it0 = 0;
   void *args[] = {(void *)&a};
-  const bool marking = mode == kModeDF || mode == kModeDT;
+  const bool marking = mode == kModeDF || mode == kModeDT || async;
   const void *fn = marking ? (const void *)k_rank<F32, true> : (const void *)k_rank<F32, false>;
   if (!g->use_graph) {
     CK(cudaLaunchCooperativeKernel(fn, dim3(g->rank_grid), dim3(kRankBlock), args,
@@ -1939,6 +1947,10 @@ static pr_status launch(Graph *g, RankMode mode, bool start_full) {
         }
         break;
       }
+    }
+    if (async) {  // the second parity takes the in-place result
+      CK(cudaMemcpyAsync(g->R[1], g->R[0], sizeof(typename S::R) * (size_t)g->n, cudaMemcpyDeviceToDevice, g->st));
+      CK(cudaMemcpyAsync(g->C[1], g->C[0], sizeof(typename S::C) * (size_t)g->n, cudaMemcpyDeviceToDevice, g->st));
     }
     return PR_OK;
   }
@@ -1986,7 +1998,11 @@ static pr_status launch(Graph *g, RankMode mode, bool start_full) {
 
 pr_status rank_run(Graph *g, RankMode mode, pr_stats *stats) {
   pr_status rc;
-  const bool marking = mode == kModeDF || mode == kModeDT;
+  const bool marking = mode == kModeDF || mode == kModeDT || mode == kModeDFAsync;
+  if (mode == kModeDFAsync && (g->teleport || g->ncomp > 1 || g->use_graph)) {
+    g->err = "asynchronous Dynamic Frontier needs a single graph in self-loop mode";
+    return PR_ERR_INVALID_ARG;
+  }
   // Dynamic Traversal in teleport mode: a changed dead-end mass moves every rank
   const bool start_full = marking && (g->pend_all || (mode == kModeDT && g->teleport &&
                                                       (g->n_pend_src > 0 || g->n_pend_tgt > 0)));

@@ -30,7 +30,8 @@ PR_DEADEND_TELEPORT = 1
 
 EXPORTED = (
     "pr_params_default", "pr_graph_create", "pr_graph_destroy", "pr_apply_batch", "pr_apply_batches", "pr_static",
-    "pr_naive_dynamic", "pr_dynamic_frontier", "pr_dynamic_traversal", "pr_get_ranks", "pr_set_ranks", "pr_graph_info",
+    "pr_naive_dynamic", "pr_dynamic_frontier", "pr_dynamic_traversal", "pr_dynamic_frontier_async",
+    "pr_get_ranks", "pr_set_ranks", "pr_graph_info",
     "pr_get_csr", "pr_get_affected", "pr_get_trace", "pr_kernel_launches", "pr_last_error", "pr_status_string",
     "pr_graph_create_batched", "pr_get_component_stats", "pr_set_tuning", "pr_get_tuning", "pr_autotune",
     "pr_set_graph_launch", "pr_server_config_default", "pr_server_create", "pr_server_add_graph",
@@ -110,7 +111,8 @@ def load(path: str = LIB_PATH):
     lib.pr_static_noalloc.argtypes = [ctypes.c_uint32, i64, vp, vp, vp, vp, vp, vp]
     lib.pr_apply_batches.restype = ctypes.c_int
     lib.pr_apply_batches.argtypes = [vp, ctypes.c_int32, vp, vp, vp, vp, vp, vp]
-    for name in ("pr_static", "pr_naive_dynamic", "pr_dynamic_frontier", "pr_dynamic_traversal"):
+    for name in ("pr_static", "pr_naive_dynamic", "pr_dynamic_frontier", "pr_dynamic_traversal",
+                 "pr_dynamic_frontier_async"):
         f = getattr(lib, name)
         f.restype = ctypes.c_int
         f.argtypes = [vp, ctypes.POINTER(pr_stats)]
@@ -331,6 +333,10 @@ def pr_dynamic_traversal(h: int) -> pr_stats:
     return _rank(load().pr_dynamic_traversal, h)
 
 
+def pr_dynamic_frontier_async(h: int) -> pr_stats:
+    return _rank(load().pr_dynamic_frontier_async, h)
+
+
 def pr_graph_info(h: int):
     n = ctypes.c_uint32()
     m = ctypes.c_int64()
@@ -446,6 +452,9 @@ class Graph:
 
     def traversal(self) -> pr_stats:
         return pr_dynamic_traversal(self.h)
+
+    def frontier_async(self) -> pr_stats:
+        return pr_dynamic_frontier_async(self.h)
 
     def ranks(self, out=None):
         return pr_get_ranks(self.h, out)

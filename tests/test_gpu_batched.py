@@ -201,11 +201,13 @@ def test_results_do_not_depend_on_tuning(prdf, lo, bps):
     assert np.array_equal(out[0], out[1])
 
 
+@pytest.mark.parametrize("mode", ["frontier", "traversal"])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-def test_split_frontier_call_equals_single_launch(prdf, prec):
+def test_split_frontier_call_equals_single_launch(prdf, prec, mode):
     # a Dynamic Frontier call that continues in the lean kernel once its affected set has
     # settled (and resumes the marking kernel when a vertex needs expanding) gives exactly
-    # the single-launch result: the same sums in the same order
+    # the single-launch result: the same sums in the same order.  Dynamic Traversal, whose
+    # set is fixed after its search, continues there too
     g = synth.rmat(14, 16, seed=21)
     bs = [b for b in (synth.BatchStream(g, seed=22).next(f) for f in (1e-5, 1e-4, 1e-3))]
     p = _params(prdf, precision=prdf.PR_F32 if prec == "f32" else prdf.PR_F64)
@@ -218,7 +220,7 @@ def test_split_frontier_call_equals_single_launch(prdf, prec):
             res = []
             for b in bs:
                 A.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
-                st = A.frontier()
+                st = getattr(A, mode)()
                 res.append((A.ranks().copy(), st.iterations, st.affected_final, sorted(A.affected().tolist())))
                 kinds.append((split, list(A.trace()["kind"])))
             out.append(res)
