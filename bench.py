@@ -754,6 +754,151 @@ def run_precision(args, rank: int, world: int, local_rank: int):
         print(json.dumps(line))
 
 
+def run_mixes(args, rank: int, world: int, local_rank: int):
+    """Update mixes and frontier tolerance (Sections 5.1.3, 5.2): insertion-only,
+    deletion-only and 80/20 batches of 1e-7 ... 1e-3 |E| on R-MAT (scale --scale, edge
+    factor --ef) and on a 2048 x 2048 grid with 1% long-range arcs.  Static, Naive-dynamic,
+    Dynamic Traversal and Dynamic Frontier (synchronous and asynchronous) each run on a
+    handle of their own that receives the same batches and continues from its own ranks, as
+    in the paper's runs; after every update each result's L1 distance to a reference Static
+    PageRank (tau = 1e-100, 500 iterations) on the same graph is taken.  On insertion-only
+    batches Dynamic Frontier also runs with tau_f = tau / 10^k, k = 0 ... 4 (k = 5 is the
+    default).  value = geometric mean of the Dynamic Frontier times."""
+    import torch
+
+    import synth
+    from paper_2401_03256_gb300 import build as libbuild
+
+    libbuild.build()
+    from paper_2401_03256_gb300 import prdf
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    W, K = args.warmup, args.steps
+    shapes = [(f"R-MAT s{args.scale} ef{args.ef}", lambda: synth.rmat(args.scale, args.ef, seed=41 + rank)),
+              ("grid 2048x2048 + 1% long-range", lambda: synth.grid(2048, 2048, 0.01, seed=42 + rank))]
+    mixes = [("insert-only", 1.0), ("delete-only", 0.0), ("80/20", 0.8)]
+    methods = ["static", "naive", "dt", "df", "df_async"]
+    tauf_k = [0, 1, 2, 3, 4]
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    mean = lambda xs: sum(xs) / len(xs) if xs else float("nan")
+    out, dfs = {}, []
+    launches = 0
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    t_start = time.perf_counter()
+    for sname, make in shapes:
+        g = make()
+        out[sname] = {}
+        for mname, share in mixes:
+            with torch.cuda.stream(stream):
+                pref = prdf.pr_params_default()
+                pref.tol = 1e-100
+                pref.max_iter = 500
+                H = {m: prdf.Graph(g.n, g.src, g.dst, None, stream.cuda_stream) for m in methods}
+                ref = prdf.Graph(g.n, g.src, g.dst, pref, stream.cuda_stream)
+                sweep = {}
+                if share == 1.0:
+                    for k in tauf_k:
+                        pk = prdf.pr_params_default()
+                        pk.frontier_tol = pk.tol / 10 ** k
+                        sweep[k] = prdf.Graph(g.n, g.src, g.dst, pk, stream.cuda_stream)
+                n, m = ref.info()
+                H["static"].static()
+                R0 = torch.empty(n, dtype=torch.float64, device=dev)
+                H["static"].ranks(R0)
+                for h in list(H.values()) + list(sweep.values()):
+                    h.set_ranks(R0)
+                Rr = torch.empty(n, dtype=torch.float64, device=dev)
+                Rm = torch.empty(n, dtype=torch.float64, device=dev)
+                bs = synth.BatchStream(g, seed=43 + rank)
+                rec = {f: {"ms": {x: [] for x in methods}, "err": {x: [] for x in methods},
+                           "it": {x: [] for x in methods}, "aff_df": [], "aff_dt": [],
+                           "sweep_ms": {k: [] for k in tauf_k}, "sweep_err": {k: [] for k in tauf_k},
+                           "sweep_aff": {k: [] for k in tauf_k}} for f in FRACS}
+                l0 = prdf.pr_kernel_launches()
+                calls = {"static": lambda h: h.static(), "naive": lambda h: h.naive(),
+                         "dt": lambda h: h.traversal(), "df": lambda h: h.frontier(),
+                         "df_async": lambda h: h.frontier_async()}
+                for i in range(W + K):
+                    for f in FRACS:
+                        b = bs.next(f, ins_share=share)
+                        for h in [ref] + list(H.values()) + list(sweep.values()):
+                            h.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+                        res = {}
+                        for x in methods:
+                            flush.zero_()
+                            res[x] = calls[x](H[x])
+                        sres = {}
+                        for k, h in sweep.items():
+                            flush.zero_()
+                            sres[k] = h.frontier()
+                        if i < W:
+                            continue
+                        ref.static()
+                        ref.ranks(Rr)
+                        r = rec[f]
+                        for x in methods:
+                            H[x].ranks(Rm)
+                            r["ms"][x].append(res[x].ms_rank)
+                            r["err"][x].append(float((Rm - Rr).abs().sum()))
+                            r["it"][x].append(res[x].iterations)
+                        r["aff_df"].append(res["df"].affected_final)
+                        r["aff_dt"].append(res["dt"].affected_final)
+                        for k, h in sweep.items():
+                            h.ranks(Rm)
+                            r["sweep_ms"][k].append(sres[k].ms_rank)
+                            r["sweep_err"][k].append(float((Rm - Rr).abs().sum()))
+                            r["sweep_aff"][k].append(sres[k].affected_final)
+                torch.cuda.synchronize(dev)
+                launches += prdf.pr_kernel_launches() - l0
+                for h in [ref] + list(H.values()) + list(sweep.values()):
+                    h.close()
+            per = {}
+            for f in FRACS:
+                r = rec[f]
+                per[f"{f:g}"] = {
+                    **{f"{x}_ms": mean(r["ms"][x]) for x in methods},
+                    **{f"{x}_l1_err": mean(r["err"][x]) for x in methods},
+                    **{f"{x}_iterations": mean(r["it"][x]) for x in methods},
+                    "df_affected": mean(r["aff_df"]), "dt_affected": mean(r["aff_dt"]),
+                }
+                dfs.append(mean(r["ms"]["df"]))
+            gm = lambda x: geomean([mean(rec[f]["ms"][x]) for f in FRACS])
+            entry = {"n": n, "m_with_self_loops": m, "per_frac": per,
+                     "df_speedup_geomean": {x: gm(x) / gm("df") for x in methods if x != "df"}}
+            if sweep:
+                entry["tau_f_sweep"] = {
+                    f"tau/1e{k}": {"df_ms_geomean": geomean([mean(rec[f]["sweep_ms"][k]) for f in FRACS]),
+                                   "l1_err_mean": mean([mean(rec[f]["sweep_err"][k]) for f in FRACS]),
+                                   "affected_mean": mean([mean(rec[f]["sweep_aff"][k]) for f in FRACS])}
+                    for k in tauf_k}
+                entry["tau_f_sweep"]["tau/1e5"] = {
+                    "df_ms_geomean": gm("df"),
+                    "l1_err_mean": mean([mean(rec[f]["err"]["df"]) for f in FRACS]),
+                    "affected_mean": mean([mean(rec[f]["aff_df"]) for f in FRACS])}
+                entry["static_l1_err_mean"] = mean([mean(rec[f]["err"]["static"]) for f in FRACS])
+            out[sname][mname] = entry
+        del g
+    t_end = time.perf_counter()
+    clk = clocks.stop()
+    line = {
+        "metric": "update mixes: Dynamic Frontier update ms (geomean over graphs, mixes and batch sizes)",
+        "value": geomean(dfs), "unit": "ms", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": (t_end - t_start) * 1e3 / (K + W), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "i64", "data": "synthetic",
+        "config": {"workload": f"R-MAT s{args.scale} ef{args.ef} and 2048x2048 grid + 1% long-range; "
+                               "insertion-only, deletion-only and 80/20 batches 1e-7..1e-3 |E|; tau_f sweep "
+                               "tau..tau/1e5 on insertion-only batches",
+                   "l2": "flushed (256 MB write) before every timed call",
+                   "error_reference": "Static PageRank, tau = 1e-100, 500 iterations, same graph"},
+        "graphs": out, "gpu_launches": launches, "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+
+
 # -------------------------------------------------------- reference arm ----
 
 def run_reference(args, rank: int, world: int):
@@ -811,9 +956,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true", help="plain workload: skip the FP32 leg")
     ap.add_argument("--cpu-timeout", type=float, default=600.0)
-    ap.add_argument("--config", choices=["plain", "precision", "batched", "serving"], default="plain",
+    ap.add_argument("--config", choices=["plain", "precision", "batched", "serving", "mixes"], default="plain",
                     help="plain: the headline workload (R-MAT s22 sweep); precision / batched / serving: "
-                         "those forms")
+                         "those forms; mixes: insertion-only / deletion-only / 80/20 batches and the tau_f "
+                         "sweep, with L1 errors against a reference Static PageRank")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: Poisson arrivals per second")
     ap.add_argument("--duration", type=float, default=2.0, help="serving: seconds of arrivals")
     ap.add_argument("--slots", type=int, default=2, help="serving: concurrent updates")
@@ -836,6 +982,8 @@ def main():
         run_batched(args, rank, world, local_rank)
     elif args.config == "serving":
         run_serving(args, rank, world, local_rank)
+    elif args.config == "mixes":
+        run_mixes(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

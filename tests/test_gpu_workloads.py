@@ -1,0 +1,103 @@
+"""Update mixes and frontier tolerances of the paper's experiments (Sections 5.1.3, 5.2):
+insertion-only and deletion-only batches, and tau_f from tau down to tau / 10^5, each held
+to the oracle with the same parameters (ranks within 1e-9; affected sets within 1%).
+"""
+import numpy as np
+import pytest
+
+import __graft_entry__
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-9
+
+
+@pytest.fixture(scope="module")
+def prdf():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    __graft_entry__.build()
+    from paper_2401_03256_gb300 import prdf as mod
+
+    mod.load()
+    return mod
+
+
+def _chain(prdf, g, fracs, ins_share, seed, ftol=None):
+    """Each side runs Dynamic Frontier over the same batches, both from the oracle's
+    previous ranks; returns the last (GPU ranks, oracle ranks, oracle graph)."""
+    p = prdf.pr_params_default()
+    op = oracle.Params()
+    if ftol is not None:
+        p.frontier_tol = ftol
+        op = oracle.Params(frontier_tol=ftol)
+    G = oracle.Graph.build(g.n, g.src, g.dst)
+    R_or, _ = oracle.static_pr(G)
+    s = synth.BatchStream(g, seed=seed)
+    with prdf.Graph(g.n, g.src, g.dst, p) as dg:
+        for frac in fracs:
+            b = s.next(frac, ins_share=ins_share)
+            if ins_share == 1.0:
+                assert b.del_src.shape[0] == 0 and b.ins_src.shape[0] > 0
+            if ins_share == 0.0:
+                assert b.ins_src.shape[0] == 0 and b.del_src.shape[0] > 0
+            dg.set_ranks(R_or)
+            dg.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+            H, ed, ei = G.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+            st = dg.frontier()
+            R_df, aff, st_or = oracle.df_sync(G, H, ed, ei, R_or, op)
+            R = dg.ranks()
+            assert np.max(np.abs(R - R_df)) <= TOL64
+            assert abs(st.iterations - st_or.iterations) <= 1
+            got = set(dg.affected().tolist())
+            want = set(np.nonzero(aff)[0].tolist())
+            assert len(got ^ want) <= max(2, 0.01 * len(want))
+            G, R_or = H, R_df
+    return R, R_or, G
+
+
+@pytest.mark.parametrize("ins_share", [1.0, 0.0])
+def test_insert_only_and_delete_only(prdf, ins_share):
+    _chain(prdf, synth.rmat(14, 8, seed=31), (1e-5, 1e-4, 1e-3, 1e-2), ins_share, 31)
+
+
+@pytest.mark.parametrize("k", [0, 1, 3, 5])
+def test_frontier_tolerance_sweep(prdf, k):
+    """tau_f = tau / 10^k on insertion-only batches (the paper's tau_f experiment), on a
+    grid, where the frontier stays local and tau_f decides how far it spreads."""
+    _chain(prdf, synth.grid(100, 100, seed=6), (1e-4, 1e-3), 1.0, 6, ftol=1e-10 / 10 ** k)
+
+
+def test_frontier_tolerance_trades_error_for_work(prdf):
+    """A looser tau_f marks fewer vertices (grid); at tau / 10^5 the L1 error against the
+    reference Static PageRank is not above Static's own (R-MAT, Section 5.2)."""
+    g = synth.grid(100, 100, seed=6)
+    b = synth.BatchStream(g, seed=6).next(1e-4, ins_share=1.0)
+    R0, _ = oracle.static_pr(oracle.Graph.build(g.n, g.src, g.dst))
+    aff = []
+    for k in (0, 1, 2):
+        p = prdf.pr_params_default()
+        p.frontier_tol = 1e-10 / 10 ** k
+        with prdf.Graph(g.n, g.src, g.dst, p) as dg:
+            dg.set_ranks(R0)
+            dg.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+            aff.append(dg.frontier().affected_final)
+    assert aff[0] <= aff[1] <= aff[2] and aff[0] < aff[2]
+
+    g = synth.rmat(12, 8, seed=33)
+    G = oracle.Graph.build(g.n, g.src, g.dst)
+    R0, _ = oracle.static_pr(G)
+    b = synth.BatchStream(g, seed=33).next(1e-3, ins_share=1.0)
+    H, _, _ = G.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+    ref, _ = oracle.reference_static(H)
+    Rs, _ = oracle.static_pr(H)
+    p = prdf.pr_params_default()
+    p.frontier_tol = 1e-15
+    with prdf.Graph(g.n, g.src, g.dst, p) as dg:
+        dg.set_ranks(R0)
+        dg.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+        dg.frontier()
+        assert np.abs(dg.ranks() - ref).sum() <= np.abs(Rs - ref).sum()
