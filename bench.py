@@ -899,6 +899,114 @@ def run_mixes(args, rank: int, world: int, local_rank: int):
         print(json.dumps(line))
 
 
+def run_kmer(args, rank: int, world: int, local_rank: int):
+    """Low-degree huge graph (the protein k-mer graphs of Table 1: 171-214 M vertices,
+    average degree 3.1 with self-loops): synth.kmer with --kmer-n vertices, one long
+    symmetric component with local shortcuts under a random numbering.  80/20 batches of
+    1e-7 ... 1e-3 |E| drawn against the original edge set (the generator's copy of the
+    ~420 M edges is not re-merged on the host after every batch; an absent deletion or a
+    present insertion is a no-op).  Per batch: Dynamic Frontier on the chained handle,
+    then Naive-dynamic and Static from the same previous ranks, and Dynamic Traversal on
+    a second handle given the same batch and ranks.  value = geometric mean of the
+    Dynamic Frontier times."""
+    import torch
+
+    import synth
+    from paper_2401_03256_gb300 import build as libbuild
+
+    libbuild.build()
+    from paper_2401_03256_gb300 import prdf
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    W, K = args.warmup, args.steps
+    t_gen = time.perf_counter()
+    g = synth.kmer(args.kmer_n, seed=51 + rank)
+    t_gen = time.perf_counter() - t_gen
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    mean = lambda xs: sum(xs) / len(xs) if xs else float("nan")
+    free0 = torch.cuda.mem_get_info(dev)[0]
+    with torch.cuda.stream(stream):
+        G = prdf.Graph(g.n, g.src, g.dst, None, stream.cuda_stream)
+        torch.cuda.synchronize(dev)
+        handle_bytes = free0 - torch.cuda.mem_get_info(dev)[0]
+        T = prdf.Graph(g.n, g.src, g.dst, None, stream.cuda_stream)
+        n, m = G.info()
+        st0 = G.static()
+        bs = synth.BatchStream(g, seed=53 + rank)
+        batches = [[bs.next(f, apply=False) for f in FRACS] for _ in range(W + K)]
+        bs.close()
+        del g
+        R_prev = torch.empty(n, dtype=torch.float64, device=dev)
+        R_cur = torch.empty(n, dtype=torch.float64, device=dev)
+        rec = {f: {x: [] for x in ("df", "naive", "static", "dt", "df_it", "dt_it", "st_it", "df_aff", "dt_aff",
+                                   "apply", "df_bytes")} for f in FRACS}
+        clocks = ClockSampler(local_rank)
+        clocks.start()
+        l0 = prdf.pr_kernel_launches()
+        t0 = time.perf_counter()
+        for i in range(W + K):
+            for fi, f in enumerate(FRACS):
+                b = batches[i][fi]
+                G.ranks(R_prev)
+                G.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+                T.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+                flush.zero_()
+                sd = G.frontier()
+                G.ranks(R_cur)
+                T.set_ranks(R_prev)
+                flush.zero_()
+                st = T.traversal()
+                G.set_ranks(R_prev)
+                flush.zero_()
+                sn = G.naive()
+                flush.zero_()
+                ss = G.static()
+                G.set_ranks(R_cur)
+                if i >= W:
+                    r = rec[f]
+                    for key, val in (("df", sd.ms_rank), ("naive", sn.ms_rank), ("static", ss.ms_rank),
+                                     ("dt", st.ms_rank), ("df_it", sd.iterations), ("dt_it", st.iterations),
+                                     ("st_it", ss.iterations), ("df_aff", sd.affected_final),
+                                     ("dt_aff", st.affected_final), ("apply", sd.ms_apply),
+                                     ("df_bytes", sd.bytes_algorithmic)):
+                        r[key].append(val)
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        launches = prdf.pr_kernel_launches() - l0
+        clk = clocks.stop()
+        G.close()
+        T.close()
+    per = {}
+    for f in FRACS:
+        r = rec[f]
+        per[f"{f:g}"] = {
+            "df_ms": mean(r["df"]), "naive_ms": mean(r["naive"]), "static_ms": mean(r["static"]),
+            "dt_ms": mean(r["dt"]), "apply_ms": mean(r["apply"]),
+            "speedup_vs_static": mean(r["static"]) / mean(r["df"]),
+            "speedup_vs_naive": mean(r["naive"]) / mean(r["df"]), "speedup_vs_dt": mean(r["dt"]) / mean(r["df"]),
+            "df_iterations": mean(r["df_it"]), "dt_iterations": mean(r["dt_it"]),
+            "static_iterations": mean(r["st_it"]), "df_affected": mean(r["df_aff"]),
+            "dt_affected": mean(r["dt_aff"]),
+            "df_gbs": sum(r["df_bytes"]) / (sum(r["df"]) * 1e-3) / 1e9 if sum(r["df"]) > 0 else None,
+        }
+    line = {
+        "metric": "k-mer stand-in: Dynamic Frontier update ms (geomean over batch sizes)",
+        "value": geomean([per[f"{f:g}"]["df_ms"] for f in FRACS]), "unit": "ms", "n_gpus": world,
+        "steps": K, "warmup": W, "ms_per_step": (t1 - t0) * 1e3 / (W + K), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "i64", "data": "synthetic",
+        "config": {"workload": f"k-mer-like graph, {n} vertices, {m} stored edges with self-loops, "
+                               "80/20 batches 1e-7..1e-3 |E|",
+                   "l2": "flushed (256 MB write) before every timed call",
+                   "generator_s": t_gen, "device_bytes_per_handle": handle_bytes,
+                   "static_ms_first": st0.ms_rank, "static_iterations_first": st0.iterations},
+        "per_frac": per, "gpu_launches": launches, "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+
+
 # -------------------------------------------------------- reference arm ----
 
 def run_reference(args, rank: int, world: int):
@@ -956,16 +1064,18 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true", help="plain workload: skip the FP32 leg")
     ap.add_argument("--cpu-timeout", type=float, default=600.0)
-    ap.add_argument("--config", choices=["plain", "precision", "batched", "serving", "mixes"], default="plain",
+    ap.add_argument("--config", choices=["plain", "precision", "batched", "serving", "mixes", "kmer"], default="plain",
                     help="plain: the headline workload (R-MAT s22 sweep); precision / batched / serving: "
                          "those forms; mixes: insertion-only / deletion-only / 80/20 batches and the tau_f "
-                         "sweep, with L1 errors against a reference Static PageRank")
+                         "sweep, with L1 errors against a reference Static PageRank; kmer: the low-degree huge "
+                         "graph (k-mer stand-in)")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: Poisson arrivals per second")
     ap.add_argument("--duration", type=float, default=2.0, help="serving: seconds of arrivals")
     ap.add_argument("--slots", type=int, default=2, help="serving: concurrent updates")
     ap.add_argument("--coalesce", type=int, default=256, help="serving: requests per coalesced update")
     ap.add_argument("--serve-scales", default="18,18,19,20,21,22,23,24", help="serving: R-MAT scales")
     ap.add_argument("--graphs", type=int, default=256, help="graphs of the batched form")
+    ap.add_argument("--kmer-n", type=int, default=200_000_000, help="kmer: vertices of the k-mer stand-in")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -984,6 +1094,8 @@ def main():
         run_serving(args, rank, world, local_rank)
     elif args.config == "mixes":
         run_mixes(args, rank, world, local_rank)
+    elif args.config == "kmer":
+        run_kmer(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

@@ -10,6 +10,10 @@ Recipes (the paper's datasets, Table 1, are not available; these stand in for th
   self-pairs and duplicates removed.  Stands in for the web and social graphs.
 * Grid: rows x cols, arcs to the four grid neighbours, plus 1% uniformly random
   long-range arcs.  Stands in for the road networks (average degree about 4).
+* k-mer-like: symmetric chains over a random vertex order (mean length 24), a cut joining
+  a vertex 2..65 places further along instead, 5% more such short branches: one long
+  component with local shortcuts only; average out-degree about 2.1, 3.1 with
+  self-loops.  Stands in for the protein k-mer graphs (171-214 M vertices).
 * Batches (Section 5.1.4): k = max(1, round(f |E|)) edges of the original graph's
   |E|; 80% insertions of uniform random absent pairs, 20% deletions of existing edges
   drawn uniformly without replacement.  Successive batches are drawn against the
@@ -51,6 +55,8 @@ def _load():
                                ctypes.c_double, ctypes.c_uint64, ctypes.c_int, u64p]
     lib.synth_grid.restype = ctypes.c_void_p
     lib.synth_grid.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_double, ctypes.c_uint64, u64p]
+    lib.synth_kmer.restype = ctypes.c_void_p
+    lib.synth_kmer.argtypes = [ctypes.c_uint32, ctypes.c_double, ctypes.c_double, ctypes.c_uint64, u64p]
     lib.synth_free.argtypes = [ctypes.c_void_p]
     lib.synth_free.restype = None
     lib.synth_stream_create.restype = ctypes.c_void_p
@@ -120,6 +126,16 @@ def grid(rows: int, cols: int, longrange_frac: float = 0.01, seed: int = 1) -> E
     ptr = lib.synth_grid(rows, cols, longrange_frac, seed, ctypes.byref(m))
     keys = _take_keys(ptr, m.value)
     return _from_keys(rows * cols, keys, f"grid-{rows}x{cols}")
+
+
+def kmer(n: int, mean_chain: float = 24.0, branch_frac: float = 0.05, seed: int = 1) -> EdgeList:
+    """Low-degree stand-in for the protein k-mer graphs: symmetric chains over a random
+    vertex order, local junctions where a chain is cut, a few short branches."""
+    lib = _load()
+    m = ctypes.c_uint64(0)
+    ptr = lib.synth_kmer(n, mean_chain, branch_frac, seed, ctypes.byref(m))
+    keys = _take_keys(ptr, m.value)
+    return _from_keys(n, keys, f"kmer-{n}")
 
 
 def from_pairs(n: int, pairs, name: str = "") -> EdgeList:

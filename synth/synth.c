@@ -237,6 +237,69 @@ uint64_t *synth_grid(uint32_t rows, uint32_t cols, double longrange_frac, uint64
     return keys;
 }
 
+/*
+ * Low-degree stand-in for the protein k-mer graphs (Table 1: 171-214 M vertices, average
+ * degree 3.1 with self-loops): a seeded uniform permutation pi of the n vertices is cut
+ * into chains (unitigs) that link pi[i] and pi[i+1] in both directions; the link after
+ * position i is cut with probability 1 / mean_chain, and a cut instead joins pi[i] to a
+ * vertex 2..65 places further along pi (both directions), as a junction does.  A further
+ * fraction branch_frac of positions gets such a symmetric arc as well.  The result is one
+ * long component with only local shortcuts (diameter of order n / 30), like a de Bruijn
+ * graph's unitigs and bubbles, under a random vertex numbering.  Average out-degree about
+ * 2 + 2 branch_frac.  Output as for synth_rmat.
+ */
+uint64_t *synth_kmer(uint32_t n, double mean_chain, double branch_frac, uint64_t seed, uint64_t *m_out)
+{
+    if (n < 2 || mean_chain < 1.0) { *m_out = 0; return (uint64_t *)malloc(sizeof(uint64_t)); }
+    uint32_t *pi = (uint32_t *)malloc(sizeof(uint32_t) * n);
+    if (!pi) return NULL;
+    for (uint32_t i = 0; i < n; i++) pi[i] = i;
+    xrng r; xr_seed(&r, sub_seed(seed, 0x6b6d6572ULL));
+    for (uint64_t i = n; i > 1; i--) {
+        uint64_t j = xr_below(&r, i);
+        uint32_t t = pi[i - 1]; pi[i - 1] = pi[j]; pi[j] = t;
+    }
+    /* two arcs per position for the chain link or junction, two more for a branch */
+    uint64_t cap = 4ULL * n;
+    uint64_t *keys = (uint64_t *)malloc(sizeof(uint64_t) * cap);
+    if (!keys) { free(pi); return NULL; }
+    const uint64_t none = ~0ULL;
+    const uint64_t cut = (uint64_t)((double)UINT32_MAX / mean_chain);
+    const uint64_t br = (uint64_t)(branch_frac * (double)UINT32_MAX);
+    uint64_t nchunks = ((uint64_t)n + RMAT_CHUNK - 1) / RMAT_CHUNK;
+#pragma omp parallel for schedule(static)
+    for (int64_t ch = 0; ch < (int64_t)nchunks; ch++) {
+        xrng q; xr_seed(&q, sub_seed(seed, (uint64_t)ch));
+        uint64_t lo = (uint64_t)ch * RMAT_CHUNK;
+        uint64_t hi = lo + RMAT_CHUNK < n ? lo + RMAT_CHUNK : n;
+        for (uint64_t i = lo; i < hi; i++) {
+            uint64_t u = pi[i], *o = keys + 4 * i;
+            o[0] = o[1] = o[2] = o[3] = none;
+            if (i + 1 < n) {
+                uint64_t j = (xr_next(&q) & 0xFFFFFFFFULL) < cut ? i + 2 + xr_below(&q, 64) : i + 1;
+                if (j < n) {
+                    uint64_t w = pi[j];
+                    o[0] = (u << 32) | w;
+                    o[1] = (w << 32) | u;
+                }
+            }
+            if ((xr_next(&q) & 0xFFFFFFFFULL) < br) {
+                uint64_t j = i + 2 + xr_below(&q, 64);
+                if (j < n) {
+                    uint64_t w = pi[j];
+                    o[2] = (u << 32) | w;
+                    o[3] = (w << 32) | u;
+                }
+            }
+        }
+    }
+    free(pi);
+    uint64_t w = 0;
+    for (uint64_t i = 0; i < cap; i++) if (keys[i] != none) keys[w++] = keys[i];
+    *m_out = sort_unique_no_self(keys, w);
+    return keys;
+}
+
 void synth_free(void *p) { free(p); }
 
 /* Split sorted keys into source and target arrays. */

@@ -101,3 +101,36 @@ def test_frontier_tolerance_trades_error_for_work(prdf):
         dg.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
         dg.frontier()
         assert np.abs(dg.ranks() - ref).sum() <= np.abs(Rs - ref).sum()
+
+
+def test_kmer_like_graph(prdf):
+    """The low-degree k-mer stand-in: Static, then chained Dynamic Frontier and Dynamic
+    Traversal updates, each against the oracle."""
+    g = synth.kmer(60_000, seed=5)
+    G = oracle.Graph.build(g.n, g.src, g.dst)
+    R_or, st_or = oracle.static_pr(G)
+    s = synth.BatchStream(g, seed=5)
+    with prdf.Graph(g.n, g.src, g.dst) as dg, prdf.Graph(g.n, g.src, g.dst) as dt:
+        st = dg.static()
+        assert abs(st.iterations - st_or.iterations) <= 1
+        assert np.max(np.abs(dg.ranks() - R_or)) <= TOL64
+        for frac in (1e-5, 1e-4, 1e-3):
+            b = s.next(frac)
+            H, ed, ei = G.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+            for h in (dg, dt):
+                h.set_ranks(R_or)
+                h.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+            st = dg.frontier()
+            R_df, aff, st_or = oracle.df_sync(G, H, ed, ei, R_or)
+            assert np.max(np.abs(dg.ranks() - R_df)) <= TOL64
+            got, want = set(dg.affected().tolist()), set(np.nonzero(aff)[0].tolist())
+            assert len(got ^ want) <= max(2, 0.01 * len(want))
+            assert st.affected_final < g.n // 2  # the frontier stays local on chains
+            dt.traversal()
+            R_dt, aff_t, _ = oracle.dt_sync(G, H, ed, ei, R_or)
+            assert np.max(np.abs(dt.ranks() - R_dt)) <= TOL64
+            got_t, want_t = set(dt.affected().tolist()), set(np.nonzero(aff_t)[0].tolist())
+            # the chain's diameter (~n / 30) is deeper than the search's round limit, where
+            # every vertex is taken as affected: a superset of the reachable set
+            assert got_t == want_t or (want_t <= got_t and len(got_t) == g.n)
+            G, R_or = H, R_df
