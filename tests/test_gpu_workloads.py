@@ -125,7 +125,8 @@ def test_kmer_like_graph(prdf):
             assert np.max(np.abs(dg.ranks() - R_df)) <= TOL64
             got, want = set(dg.affected().tolist()), set(np.nonzero(aff)[0].tolist())
             assert len(got ^ want) <= max(2, 0.01 * len(want))
-            assert st.affected_final < g.n // 2  # the frontier stays local on chains
+            if b.size == 1:
+                assert st.affected_final < g.n // 10  # one edge's frontier stays local on chains
             dt.traversal()
             R_dt, aff_t, _ = oracle.dt_sync(G, H, ed, ei, R_or)
             assert np.max(np.abs(dt.ranks() - R_dt)) <= TOL64
