@@ -205,11 +205,12 @@ pr_status pr_graph_info(const pr_graph *g, uint32_t *n, int64_t *m);
  * (m from pr_graph_info); each row ascending. */
 pr_status pr_get_csr(pr_graph *g, int32_t dir, uint64_t *offs, uint32_t *cols);
 
-/* Vertices marked affected by the last pr_dynamic_frontier call, in no particular order,
- * into a host array of capacity cap; *count receives the total number. */
+/* Vertices marked affected by the last Dynamic Frontier (synchronous or asynchronous) or
+ * Dynamic Traversal call, in no particular order, into a host array of capacity cap;
+ * *count receives the total number (n after a call that took every vertex). */
 pr_status pr_get_affected(pr_graph *g, uint32_t *out, int64_t cap, int64_t *count);
 
-/* Trace of the last rank call (Static, Naive-dynamic or Dynamic Frontier), from the device
+/* Trace of the last rank call (any of the rank entry points), from the device
  * clock: phase_ms = initial marking (phase 0); for each iteration i < *count (at most cap
  * entries written): iter_ms[i] its duration, affected[i] the vertices it covered, kind[i]
  * 0 = affected lists, 1 = compacted sweep items reused, 2 = sweep items compacted in this
