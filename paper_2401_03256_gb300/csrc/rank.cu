@@ -52,6 +52,7 @@ constexpr uint32_t kStatusDone = 1;     // the call is complete (writeback done)
 constexpr uint32_t kStatusHandoff = 2;  // continue in k_rank_cont from next_it
 constexpr uint32_t kStatusCont = 3;     // the continuation finished the iterations: k_df_finish
 constexpr uint32_t kStatusExpand = 4;   // resume the marking kernel at next_it
+constexpr uint32_t kStatusFull = 5;     // every vertex is affected: the full-sweep instance iterates
 constexpr uint32_t kInlineOut = 128;  // longer out-rows are marked by the whole grid (hub queue)
 #ifndef PRDF_RANK_MIN_BLOCKS
 #define PRDF_RANK_MIN_BLOCKS 4  // resident blocks per SM the register budget must allow
@@ -1155,6 +1156,29 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
     dt_all = o.all;
     if (dt_all && blockIdx.x == 0 && tid == 0) ctl->full_from = 1u;
     if (blockIdx.x == 0 && tid == 0) ctl->t_ns[1] = globaltimer_ns();
+    if (dt_all && a.split) {
+      // every vertex is affected, so the iterations are those of Naive-dynamic: the search's
+      // marks are cleared and the host runs the iterations in the full-sweep instance, which
+      // carries none of the marking code
+      const uint32_t *lists[3] = {a.list0, a.list1, a.list2};
+#pragma unroll
+      for (int bb = 0; bb < 3; bb++)
+        for (uint32_t k = gtid; k < cnt[bb]; k += nthreads) {
+          const uint32_t v = ldcg(lists[bb] + k);
+          a.bitmap[v >> 5] = 0u;
+          a.xbits[v >> 5] = 0u;
+          a.stamp[v] = kNoStamp;
+        }
+      const unsigned long long xv = warp_sum((unsigned long long)my_xv), xe = warp_sum((unsigned long long)my_xe),
+                               ap = warp_sum((unsigned long long)my_app);
+      if (lane == 0) {
+        if (xv) atomicAdd(&ctl->expv, xv);
+        if (xe) atomicAdd(&ctl->expe, xe);
+        if (ap) atomicAdd(&ctl->appended, ap);
+      }
+      if (blockIdx.x == 0 && tid == 0) ctl->status = kStatusFull;
+      return;
+    }
   }
   long long Dn = 0;
   double Dd = 0.0;
@@ -1830,6 +1854,23 @@ pr_status rank_setup(Graph *g) {
   return PR_OK;
 }
 
+// The full-sweep instance in Naive-dynamic mode on the arguments of a marking call whose
+// affected set is all of V (nothing to mark, every vertex iterated from the current ranks).
+template <bool F32>
+static cudaError_t launch_full_sweep(Graph *g, const RankArgs<F32> &a) {
+  RankArgs<F32> b = a;
+  b.mode = (int)kModeNaive;
+  b.start_full = 0;
+  b.split = 0;
+  b.resume = 0;
+  b.it0 = 0;
+  void *args[] = {(void *)&b};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_rank<F32, false>, dim3(g->rank_grid), dim3(kRankBlock),
+                                              args, rank_smem(g->ncomp), g->st);
+  if (e == cudaSuccess) count_launch();
+  return e;
+}
+
 template <bool F32>
 static pr_status launch(Graph *g, RankMode mode, bool start_full) {
   using S = Store<F32>;
@@ -1913,6 +1954,15 @@ static pr_status launch(Graph *g, RankMode mode, bool start_full) {
   a.it0 = 0;
   void *args[] = {(void *)&a};
   const bool marking = mode == kModeDF || mode == kModeDT || async;
+  if (marking && start_full && !g->use_graph) {
+    // every vertex is affected from iteration 0 and nothing is ever marked: Naive-dynamic
+    CK(launch_full_sweep<F32>(g, a));
+    if (async) {
+      CK(cudaMemcpyAsync(g->R[1], g->R[0], sizeof(typename S::R) * (size_t)g->n, cudaMemcpyDeviceToDevice, g->st));
+      CK(cudaMemcpyAsync(g->C[1], g->C[0], sizeof(typename S::C) * (size_t)g->n, cudaMemcpyDeviceToDevice, g->st));
+    }
+    return PR_OK;
+  }
   const void *fn = marking ? (const void *)k_rank<F32, true> : (const void *)k_rank<F32, false>;
   if (!g->use_graph) {
     CK(cudaLaunchCooperativeKernel(fn, dim3(g->rank_grid), dim3(kRankBlock), args,
@@ -1926,6 +1976,11 @@ static pr_status launch(Graph *g, RankMode mode, bool start_full) {
       CK(cudaStreamSynchronize(g->st));
       const RankCtl &h = *g->ctl_h;
       if (h.err) break;
+      if (h.status == kStatusFull) {
+        CK(cudaMemsetAsync(&g->ctl->bar, 0, sizeof(uint32_t), g->st));
+        CK(launch_full_sweep<F32>(g, a));
+        break;
+      }
       if (h.status == kStatusHandoff || h.status == kStatusExpand) {
         CK(cudaMemsetAsync(&g->ctl->bar, 0, sizeof(uint32_t), g->st));
         if (h.status == kStatusHandoff) {

@@ -171,3 +171,30 @@ def test_dt_fp32(prdf):
             assert sorted(dg.affected().tolist()) == sorted(np.nonzero(aff)[0].tolist())
             assert np.max(np.abs(dg.ranks() - R_or)) <= TOL32
             G = H
+
+
+@pytest.mark.parametrize("split", [0, 1])
+def test_dt_beyond_the_round_limit_iterates_as_naive(prdf, split):
+    """A search deeper than the round limit takes all of V, so the iterations are exactly
+    Naive-dynamic's from the same ranks (bit for bit in 64-bit mode); with split calls they
+    run in the full-sweep instance."""
+    n = 1300
+    src = np.arange(n - 1, dtype=np.uint32)
+    dst = src + 1
+    G = oracle.Graph.build(n, src, dst)
+    R_or, _ = oracle.static_pr(G)
+    out = []
+    for call in ("traversal", "naive"):
+        with prdf.Graph(n, src, dst) as dg:
+            t = dg.tuning()
+            dg.set_tuning(t.bin_lo, t.bin_hi, t.dense_div, t.blocks_per_sm, split)
+            dg.set_ranks(R_or)
+            dg.apply([], [], [0], [2])
+            l0 = prdf.pr_kernel_launches()
+            st = getattr(dg, call)()
+            out.append((dg.ranks().copy(), st.iterations, prdf.pr_kernel_launches() - l0))
+            if call == "traversal":
+                assert dg.affected().shape[0] == n
+    (r_dt, it_dt, l_dt), (r_nv, it_nv, l_nv) = out
+    assert np.array_equal(r_dt, r_nv) and it_dt == it_nv
+    assert l_dt - l_nv == (1 if split else 0)  # the marking launch that ran the search
