@@ -343,6 +343,28 @@ def test_df_error_not_above_static_error():
         G = H
 
 
+def test_dt_teleport_reaches_the_exact_solution():
+    """Without self-loops a batch moves the dead-end mass D and with it the teleport share
+    alpha D / n of every vertex, reached or not: Dynamic Traversal from the exact old ranks
+    must still land on the exact new ranks (dense solve with teleport), which it can only
+    do by taking every vertex as affected."""
+    g = synth.rmat(8, 4, seed=9)
+    n = g.n
+    op = oracle.Params(tol=1e-14, dead_end=oracle.TELEPORT)
+    G = oracle.Graph.build(n, g.src, g.dst, self_loops=False)
+    R = oracle.dense_solve(n, g.src, g.dst, self_loops=False)
+    s = synth.BatchStream(g, seed=9)
+    for t in range(2):
+        b = s.next(2e-2)
+        H, ed, ei = G.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+        R, aff, st = oracle.dt_sync(G, H, ed, ei, R, op)
+        assert st.converged and st.affected_final == n
+        cur = s.current()
+        exact = oracle.dense_solve(n, cur.src, cur.dst, self_loops=False)
+        assert np.max(np.abs(R - exact)) <= 1e-12
+        G = H
+
+
 def _union_reach(n, old_pairs, new_pairs, sources):
     """Brute force: vertices reachable from the sources in the union of both edge sets
     (self-loops added).  Every edge in only one graph starts at a source, so this is the
