@@ -225,6 +225,8 @@ def test_empty_batch_leaves_ranks_bit_identical():
     assert st.iterations == 1 and st.converged and st.affected_final == 0 and not aff.any()
     Ra, _, sta = oracle.df_async(G, H, ed, ei, R0)
     assert np.array_equal(Ra, R0) and sta.iterations == 1
+    Rt, afft, stt = oracle.dt_sync(G, H, ed, ei, R0)
+    assert np.array_equal(Rt, R0) and stt.iterations == 1 and not afft.any()
 
 
 def test_df_with_everything_affected_and_zero_tau_f_is_naive():
