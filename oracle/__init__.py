@@ -18,6 +18,12 @@ Functions and the passages they follow:
 
 Every function is pinned by ``tests/test_oracle_pins.py``; only the later iterations of
 the paper's worked example (Figure 1, whose drawing is missing) are parity unpinned.
+
+``use_threads(k)`` switches a process to the -fopenmp build of the same C source (its
+vertex loops are annotated with schedule(dynamic, 2048), the paper's CPU schedule); its
+results equal the sequential build's bit for bit (``tests/test_oracle_threads.py``).  It
+times the oracle on all host cores and computes the expected values of the largest
+workloads; the default is the sequential build.
 """
 from __future__ import annotations
 
@@ -31,7 +37,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "prdf_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
 _lib = None
+_want_threads = 1
 
 # Section 5.1.2 and Section 4.3 constants.
 ALPHA = 0.85
@@ -42,14 +50,42 @@ SELF_LOOPS = 0
 TELEPORT = 1
 
 
-def build(force: bool = False) -> str:
-    """Compile liboracle.so with gcc (IEEE double, no contraction, no fast-math)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile liboracle.so with gcc (IEEE double, no contraction, no fast-math), or with
+    openmp=True the same source with -fopenmp as liboracle_omp.so."""
+    lib = _LIB_OMP if openmp else _LIB
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(_SRC):
         cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC",
-               "-std=c11", _SRC, "-o", _LIB + ".tmp", "-lm"]
+               "-std=c11", *(["-fopenmp"] if openmp else []), _SRC, "-o", lib + ".tmp", "-lm"]
         subprocess.check_call(cmd)
-        os.replace(_LIB + ".tmp", _LIB)
-    return _LIB
+        os.replace(lib + ".tmp", lib)
+    return lib
+
+
+def host_cores() -> int:
+    """Host cores this process may run on (sched_getaffinity)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def use_threads(k: int) -> int:
+    """Run this process's oracle on k threads (k > 1: the -fopenmp build of the same
+    source, whose results equal the sequential build's bit for bit).  The build is chosen
+    by the first oracle call of the process; returns the threads in effect."""
+    global _want_threads
+    k = max(1, int(k))
+    if _lib is None:
+        _want_threads = k
+    elif (k > 1) != (_want_threads > 1):
+        raise RuntimeError("oracle: the sequential or threaded build is fixed once loaded")
+    return int(_load().or_threads(k if k > 1 else 0))
+
+
+def threads() -> int:
+    """Threads the loaded oracle runs its vertex loops on."""
+    return int(_load().or_threads(0))
 
 
 class _Params(ctypes.Structure):
@@ -68,10 +104,14 @@ def _load():
     global _lib
     if _lib is not None:
         return _lib
-    build()
-    lib = ctypes.CDLL(_LIB)
+    par = _want_threads > 1
+    lib = ctypes.CDLL(build(openmp=par))
     vp = ctypes.c_void_p
     u64 = ctypes.c_uint64
+    lib.or_threads.restype = ctypes.c_int
+    lib.or_threads.argtypes = [ctypes.c_int]
+    if par:
+        lib.or_threads(_want_threads)
     lib.or_graph_build.restype = vp
     lib.or_graph_build.argtypes = [ctypes.c_uint32, u64, vp, vp, ctypes.c_int]
     lib.or_graph_free.restype = None

@@ -29,6 +29,14 @@
  * teleport mode (mode 1) no self-loops are added and a dead end u spreads its rank over
  * all n vertices: R[v] gets alpha * D / n with D = sum of R over dead ends.
  *
+ * Threads: the vertex loops of the synchronous sweeps carry OpenMP annotations
+ * (schedule(dynamic, 2048), the paper's CPU schedule, Section 5.1.2).  The parity oracle
+ * is built without -fopenmp, so they are ignored and every loop runs in order.  A second
+ * build with -fopenmp times the same code on all host cores; it gives the same results
+ * bit for bit, because each vertex's sum is still taken by one thread in in-edge order,
+ * the L-inf maximum is exact, and marking only sets flags to 1.  The asynchronous
+ * reading (or_df_async) is never parallel: its result depends on the sweep order.
+ *
  * Parity notes for dynamic frontier with teleport (the paper avoids this mode): D is
  * recomputed at the start of every iteration from that iteration's input ranks; if
  * alpha * |D - D_prev| / n exceeds the frontier tolerance, every vertex is marked
@@ -39,6 +47,9 @@
 #include <stdlib.h>
 #include <string.h>
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef struct {
     uint32_t n;
@@ -66,6 +77,19 @@ typedef struct {
     int64_t edges_processed;
     double last_delta;
 } or_stats;
+
+/* Threads of the vertex loops: 1 in the sequential build; in the -fopenmp build k > 0
+ * sets the count.  Returns the count in effect. */
+int or_threads(int k)
+{
+#ifdef _OPENMP
+    if (k > 0) omp_set_num_threads(k);
+    return omp_get_max_threads();
+#else
+    (void)k;
+    return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------ graph ---- */
 
@@ -285,13 +309,16 @@ static void sweep_until_converged(const or_graph *g, const or_params *p, double 
     for (int32_t i = 0; i < p->max_iter; i++) {
         double D = p->dead_end == 1 ? dead_end_mass(g, R) : 0.0;
         double dR = 0.0;
+        int64_t edges = 0;
+        #pragma omp parallel for schedule(dynamic, 2048) reduction(max : dR) reduction(+ : edges)
         for (uint32_t v = 0; v < n; v++) {
             double r = rank_of(g, p, R, v, D);
             double d = fabs(r - R[v]);
             if (d > dR) dR = d;
             Rn[v] = r;
-            st->edges_processed += (int64_t)(g->in_off[v + 1] - g->in_off[v]);
+            edges += (int64_t)(g->in_off[v + 1] - g->in_off[v]);
         }
+        st->edges_processed += edges;
         st->vertices_processed += n;
         memcpy(R, Rn, sizeof(double) * n);
         st->iterations = i + 1;
@@ -373,6 +400,8 @@ int or_df_sync(const or_graph *gold, const or_graph *gnew, const or_params *p,
         memcpy(next, aff, n);
         memcpy(Rn, R, sizeof(double) * n);
         double dR = 0.0;
+        int64_t verts = 0, edges = 0;
+        #pragma omp parallel for schedule(dynamic, 2048) reduction(max : dR) reduction(+ : verts, edges)
         for (uint32_t v = 0; v < n; v++) {
             if (!aff[v]) continue;
             double r = rank_of(gnew, p, R, v, D);
@@ -380,10 +409,13 @@ int or_df_sync(const or_graph *gold, const or_graph *gnew, const or_params *p,
             Rn[v] = r;
             if (d > dR) dR = d;
             if (d > p->frontier_tol)
-                for (uint64_t j = gnew->out_off[v]; j < gnew->out_off[v + 1]; j++) next[gnew->out_col[j]] = 1;
-            st->vertices_processed++;
-            st->edges_processed += (int64_t)(gnew->in_off[v + 1] - gnew->in_off[v]);
+                for (uint64_t j = gnew->out_off[v]; j < gnew->out_off[v + 1]; j++)
+                    __atomic_store_n(&next[gnew->out_col[j]], (uint8_t)1, __ATOMIC_RELAXED);
+            verts++;
+            edges += (int64_t)(gnew->in_off[v + 1] - gnew->in_off[v]);
         }
+        st->vertices_processed += verts;
+        st->edges_processed += edges;
         memcpy(R, Rn, sizeof(double) * n);
         memcpy(aff, next, n);
         st->iterations = i + 1;
@@ -446,15 +478,19 @@ int or_dt_sync(const or_graph *gold, const or_graph *gnew, const or_params *p,
         double D = p->dead_end == 1 ? dead_end_mass(gnew, R) : 0.0;
         memcpy(Rn, R, sizeof(double) * n);
         double dR = 0.0;
+        int64_t verts = 0, edges = 0;
+        #pragma omp parallel for schedule(dynamic, 2048) reduction(max : dR) reduction(+ : verts, edges)
         for (uint32_t v = 0; v < n; v++) {
             if (!aff[v]) continue;
             double r = rank_of(gnew, p, R, v, D);
             double d = fabs(r - R[v]);
             Rn[v] = r;
             if (d > dR) dR = d;
-            st->vertices_processed++;
-            st->edges_processed += (int64_t)(gnew->in_off[v + 1] - gnew->in_off[v]);
+            verts++;
+            edges += (int64_t)(gnew->in_off[v + 1] - gnew->in_off[v]);
         }
+        st->vertices_processed += verts;
+        st->edges_processed += edges;
         memcpy(R, Rn, sizeof(double) * n);
         st->iterations = i + 1;
         st->last_delta = dR;
