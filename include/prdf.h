@@ -43,6 +43,23 @@ typedef enum {
     PR_ERR_CAPACITY = 6        /* the graph would exceed 2^32 - 1 stored edges */
 } pr_status;
 
+/* Rank arithmetic.  The paper computes in FP64 (Section 5.1.2); its tests are absolute
+ * (L-inf change <= tau = 1e-10 stops, a change > tau_f = 1e-15 marks).
+ *  PR_F64: 64-bit fixed point.  Ranks and contributions are int64 counts of 2^-62 (about
+ *    2.2e-19); ranks enter as doubles rounded to the nearest unit and leave as the nearest
+ *    double.  In-edge sums, the L-inf maximum and the dead-end mass are exact integer
+ *    operations (so results do not depend on the order of the sums); each contribution
+ *    alpha R[u] / |out(u)| is rounded once.  One sweep of Eq. 1 is therefore off the exact
+ *    sweep of the same input by at most 2^-62 per in-edge of a vertex, and a whole call
+ *    accumulates at most m * 2^-62 / (1 - alpha) in the L1 norm (m = stored edges), which
+ *    bounds the L-inf error as well (7e-11 for m = 5e7; observed differences to FP64 are
+ *    near 1e-17).  The resolution is absolute: a rank near 1/n keeps about 62 - log2(n)
+ *    significant bits (40 at n = 2^22, 34 at n = 2^28), against 53 for an IEEE double.
+ *    Values must stay below 2; pr_set_ranks enforces a distribution (sum <= 1), under
+ *    which no rank or in-edge sum can reach that.
+ *  PR_F32: IEEE single precision for ranks and contributions (half the bytes per gathered
+ *    contribution); the L-inf test compares the float changes widened to double; in
+ *    teleport mode the dead-end mass is summed in FP64 with Neumaier compensation. */
 typedef enum { PR_F64 = 0, PR_F32 = 1 } pr_precision;
 
 /* Dead ends (Section 3.1): the paper adds a self-loop to every vertex so no vertex has
@@ -55,7 +72,7 @@ typedef struct {
     double tol;           /* iteration tolerance tau on the L-inf norm; 1e-10 (Section 5.1.2) */
     double frontier_tol;  /* frontier tolerance tau_f; tau / 1e5 (Section 4.3) */
     int32_t max_iter;     /* MAX_ITERATIONS; 500 (Section 5.1.2); at most 1000 */
-    int32_t precision;    /* pr_precision: rank and contribution storage (FP64 or FP32) */
+    int32_t precision;    /* pr_precision: rank arithmetic (64-bit fixed point or FP32) */
     int32_t dead_end;     /* pr_deadend */
     int32_t bin_lo;       /* in-degree <= bin_lo: one thread per vertex (0 = default 8) */
     int32_t bin_hi;       /* in-degree >  bin_hi: one block per vertex (0 = default 4096) */
@@ -107,10 +124,12 @@ pr_status pr_get_component_stats(const pr_graph *g, pr_stats *stats, int32_t nco
 /* Work distribution of the rank kernel (results do not depend on it): in-degree thresholds
  * of the thread and block bins, the dense-iteration divisor (an iteration sweeps the
  * compacted affected set once it exceeds n / dense_div vertices), the resident blocks per
- * SM of the persistent launch, and df_split (1, the default: a Dynamic Frontier call on a
- * single-graph handle in self-loop mode continues in a lean kernel without marking code
- * once its affected set has settled, going back to the marking kernel if a vertex needs
- * expanding; 0: one launch).  ms is the time the autotuner measured (0 otherwise). */
+ * SM of the persistent launch, and df_split (1, the default: a Dynamic Frontier, Dynamic
+ * Traversal or asynchronous call on a single-graph handle in self-loop mode continues in
+ * per-iteration launches once its affected set is dense (after its search for Dynamic
+ * Traversal), growing the set by pulling marks from per-vertex change flags or pushing the
+ * out-rows of first expansions; 0: everything in the one persistent launch).  ms is the
+ * time the autotuner measured (0 otherwise). */
 typedef struct {
     int32_t bin_lo, bin_hi, dense_div, blocks_per_sm;
     int32_t df_split, reserved;
@@ -194,7 +213,10 @@ pr_status pr_dynamic_frontier_async(pr_graph *g, pr_stats *stats);
 pr_status pr_get_ranks(pr_graph *g, double *out, uint32_t n);
 
 /* Replaces the ranks with in[0..n) (host or device), e.g. to resume or to start every
- * implementation from the same previous ranks.  Pending marks are kept. */
+ * implementation from the same previous ranks.  Pending marks are kept.  The ranks must be
+ * a distribution: every value finite and in [0, 2], and their sum at most 1 + 1e-6 (for a
+ * batched handle, the sum over each graph's vertices); otherwise PR_ERR_INVALID_ARG and
+ * the ranks are unchanged. */
 pr_status pr_set_ranks(pr_graph *g, const double *in, uint32_t n);
 
 /* Number of vertices and of stored edges (self-loops included). */
@@ -212,11 +234,13 @@ pr_status pr_get_affected(pr_graph *g, uint32_t *out, int64_t cap, int64_t *coun
 
 /* Trace of the last rank call (any of the rank entry points), from the device
  * clock: phase_ms = initial marking (phase 0); for each iteration i < *count (at most cap
- * entries written): iter_ms[i] its duration, affected[i] the vertices it covered, kind[i]
- * 0 = affected lists, 1 = compacted sweep items reused, 2 = sweep items compacted in this
- * iteration, 3 = all vertices, 4 = all sweep items scanned, those of vertices stamped later
- * skipped, 5 = compacted items swept by the continuation kernel of a split call.  Any of
- * the output arrays may be NULL (host memory). */
+ * entries written): iter_ms[i] its duration, affected[i] the vertices affected after it,
+ * kind[i]: in the persistent marking launch 0 = affected lists, 1 = compacted sweep items
+ * reused, 2 = sweep items compacted in this iteration, 4 = all sweep items scanned, those
+ * of vertices stamped later skipped; 3 = all vertices; in the per-iteration launches of a
+ * split call 5 = compacted items, 6 = all items with the stamp check, 7 = all items, vertices
+ * not yet affected joining by pull from the previous iteration's change flags, 8 = compacted
+ * items rebuilt before the sweep.  Any of the output arrays may be NULL (host memory). */
 pr_status pr_get_trace(const pr_graph *g, int32_t cap, double *phase_ms, double *iter_ms, int64_t *affected,
                        int32_t *kind, int32_t *count);
 

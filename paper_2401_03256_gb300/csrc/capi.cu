@@ -65,6 +65,7 @@ using prdf::Graph;
 namespace prdf {
 static std::atomic<unsigned long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(unsigned long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 }  // namespace prdf
 
 extern "C" {
@@ -463,11 +464,15 @@ pr_status pr_set_ranks(pr_graph *h, const double *in, uint32_t n) {
   Graph &g = h->g;
   if (!in || n != g.n) return invalid(&g, "in must hold exactly n doubles");
   DeviceGuard dg(g.device);
-  if (is_device_ptr(in)) return prdf::rank_set(&g, in);
-  pr_status rc = ensure_stage(h);
-  if (rc != PR_OK) return rc;
+  pr_status rc;
+  if (is_device_ptr(in)) {
+    if ((rc = prdf::rank_check(&g, in)) != PR_OK) return rc;
+    return prdf::rank_set(&g, in);
+  }
+  if ((rc = ensure_stage(h)) != PR_OK) return rc;
   cudaError_t e = cudaMemcpyAsync(h->stage, in, sizeof(double) * n, cudaMemcpyHostToDevice, g.st);
   if (e != cudaSuccess) return prdf::cuda_fail(&g, e, "set ranks");
+  if ((rc = prdf::rank_check(&g, h->stage)) != PR_OK) return rc;
   return prdf::rank_set(&g, h->stage);
 }
 

@@ -54,6 +54,7 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 
 // Kernel-launch accounting (pr_kernel_launches); bumped after every launch.
 void count_launch();
+void count_launches(unsigned long long k);
 
 // ------------------------------------------------------------- rank storage ---
 // Ranks R, cached contributions C[u] = alpha R[u] / |out(u)| and the per-vertex factor A
@@ -140,6 +141,33 @@ struct RankCtl {
   uint32_t xit[kMaxIterLimit + 2];                    // entries appended for each slot: read after the
                                                       // barrier, when no block can append to that slot
   uint32_t xneed[kMaxIterLimit + 2];                  // continuation: a recorded expansion would mark
+  // per-iteration sweep launches (sweep.cu): what one launch leaves for the next
+  uint32_t ticket;        // blocks of the current sweep launch that have finished
+  uint32_t it_cur;        // iteration the next sweep launch computes
+  uint32_t sw_all[3];     // sweep items per tier (all vertices)
+  uint32_t sw_off[2];     // first item of tiers 1 and 2 (in the item and compacted arrays)
+  uint32_t m_cur;         // stored edges (in-edges of all vertices)
+  uint32_t dmode;         // dense Dynamic Frontier: 1 = every item swept with the stamp check, 0 = compacted items
+  uint32_t pull_check;    // this iteration pulls marks from the previous iteration's changes
+  uint32_t erec;          // this iteration records per-vertex change flags (the next may pull)
+  uint32_t push_items;    // pushed marks append their sweep items to the compacted items
+  uint32_t push_lo, push_n;   // the prologue pushes the out-rows of these expansion-list entries
+  uint32_t compact_now;   // the prologue recompacts the affected items
+  uint32_t dexpand;       // record first expansions (0 for Dynamic Traversal after its search)
+  uint32_t xdone;         // expansion-list entries pushed or skipped
+  uint32_t dcnt[3];       // affected-list lengths committed before the current iteration
+  uint32_t cmp_cur[3];    // compacted items per tier, items of later marks appended
+  uint32_t cmp_total;     // affected vertices when the compacted items were last rebuilt
+  uint32_t app_since;     // vertices whose items were appended since then
+  uint32_t kind_cur;      // trace kind of the current iteration
+  uint32_t launches;      // sweep and prologue launches the device-side loop made
+  uint32_t xcap;          // expansion-list entries this iteration writes at most (more: it only counts)
+  uint32_t jtotal;        // vertices that joined by pulls (not in the lists)
+  uint32_t dense_ran;     // the per-iteration loop ran: its writeback listed the affected set
+  uint32_t aff_total;     // affected vertices listed by that writeback (list 0)
+  uint32_t pull_all;      // the pull kernel also pulls tier-0/1 rows (the marks after the last iteration)
+  uint32_t fin_only;      // a marking launch handed off only for the marks of its last iteration
+  unsigned long long eprev;  // edges processed before the current iteration
   // trace (written by block 0): %globaltimer at kernel start, after phase 0 and after each
   // iteration's barrier; affected vertices at the start of each iteration; iteration kind
   unsigned long long t_ns[kMaxIterLimit + 2];

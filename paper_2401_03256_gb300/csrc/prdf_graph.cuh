@@ -107,6 +107,13 @@ struct Graph {
   std::vector<int64_t> trace_aff;    // affected vertices at the start of each iteration
   std::vector<int32_t> trace_kind;   // 0 sparse, 1 dense, 2 dense after compaction, 3 all vertices
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // per-iteration sweep launches (sweep.cu): change flags of the dense Dynamic Frontier
+  // iterations and the CUDA graphs that loop over the iterations on the device
+  uint8_t *emap = nullptr;           // [2][n] rank change above tau_f, by iteration parity; 0 between calls
+  void *loops = nullptr;             // sweep.cu's cached graphs
+  int sweep_grid = 0;                // blocks of a sweep launch
+  int pro_grid = 0;                  // blocks of the cooperative prologue launch
+  bool loop_sweeps = true;           // single-graph self-loop handles iterate in per-iteration launches
   std::string err;
 };
 
@@ -128,10 +135,20 @@ enum RankMode { kModeDF = 0, kModeNaive = 1, kModeStatic = 2, kModeDT = 3, kMode
 pr_status rank_setup(Graph *g);  // grid size, control block
 pr_status rank_run(Graph *g, RankMode mode, pr_stats *stats);
 pr_status rank_init_contrib(Graph *g);  // C = R * adeg for all v, both parities
+pr_status rank_check(Graph *g, const double *in_d);  // PR_ERR_INVALID_ARG unless finite, >= 0, sum <= 1 + 1e-6
 pr_status rank_set(Graph *g, const double *in_d);
 pr_status rank_get(Graph *g, double *out_d);
 pr_status rank_dead_mass(Graph *g, double *D);
 pr_status components_setup(Graph *g, const std::vector<uint32_t> &comp_n);  // after graph_build
+
+// sweep.cu: Static / Naive-dynamic iterations, and the dense iterations of a Dynamic
+// Frontier, Dynamic Traversal or asynchronous call, one launch per iteration inside a
+// CUDA-graph loop whose condition the last block of each sweep sets on the device.
+pr_status sweep_setup(Graph *g);
+bool sweep_eligible(const Graph *g);  // single graph, self-loop mode, no graph-launch mode
+pr_status sweep_full(Graph *g, bool from_init);                  // all vertices, every iteration
+pr_status sweep_dense(Graph *g, RankMode mode, const void *rank_args);  // after the marking launch's handoff
+void sweep_free(Graph *g);
 
 }  // namespace prdf
 

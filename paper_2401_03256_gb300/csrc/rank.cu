@@ -38,640 +38,13 @@
 #include <cmath>
 #include <cstring>
 #include <type_traits>
+#include <vector>
 
 #include "prdf_graph.cuh"
 
+#include "rank_dev.cuh"
+
 namespace prdf {
-
-constexpr uint64_t kBarrierTimeoutNs = 4000000000ull;  // 4 s
-constexpr int kWarps = kRankBlock / 32;
-constexpr uint32_t kFull = 0xffffffffu;
-constexpr uint16_t kNoStamp = 0xFFFF;
-// RankCtl::status after a launch of a split call
-constexpr uint32_t kStatusDone = 1;     // the call is complete (writeback done)
-constexpr uint32_t kStatusHandoff = 2;  // continue in k_rank_cont from next_it
-constexpr uint32_t kStatusCont = 3;     // the continuation finished the iterations: k_df_finish
-constexpr uint32_t kStatusExpand = 4;   // resume the marking kernel at next_it
-constexpr uint32_t kStatusFull = 5;     // every vertex is affected: the full-sweep instance iterates
-constexpr uint32_t kInlineOut = 128;  // longer out-rows are marked by the whole grid (hub queue)
-#ifndef PRDF_RANK_MIN_BLOCKS
-#define PRDF_RANK_MIN_BLOCKS 4  // resident blocks per SM the register budget must allow
-#endif
-
-// Per-mode arithmetic of the kernel.  Rank changes are compared as "delta bits"
-// (non-negative values that order like unsigned integers) and reduced to an L-inf key
-// (uint64, same order) for the grid-wide max and the convergence test.
-template <bool F32>
-struct Num;
-
-template <>
-struct Num<false> {  // 64-bit fixed point, 2^-62 units
-  using R = long long;
-  using B = unsigned long long;
-  __device__ static B delta(R r, R rold) {
-    long long d = r - rold;
-    return (B)(d < 0 ? -d : d);
-  }
-  __device__ static unsigned long long key(B d) { return d; }
-};
-
-template <>
-struct Num<true> {  // float ranks; the key is the bits of the change widened to double
-  using R = float;
-  using B = unsigned int;
-  __device__ static B delta(R r, R rold) { return __float_as_uint(fabsf(r - rold)); }
-  __device__ static unsigned long long key(B d) {
-    return (unsigned long long)__double_as_longlong((double)__uint_as_float(d));
-  }
-};
-
-template <bool F32>
-struct RankArgs {
-  using S = Store<F32>;
-  using R = typename S::R;
-  using B = typename Num<F32>::B;
-  uint32_t n;
-  const uint2 *in_rd;
-  const uint32_t *in_col;
-  const uint2 *out_rd;
-  const uint32_t *out_col;
-  R *R0, *R1;
-  typename S::C *C0, *C1;
-  const typename S::A *adeg;
-  uint32_t *bitmap;  // affected (ever marked in this call)
-  uint32_t *xbits;   // out-row already scanned in this call
-  uint16_t *stamp;   // iteration a vertex joins (kNoStamp = not affected)
-  uint32_t *list0, *list1, *list2;
-  const uint4 *items;    // sweep items in tier order (see the graph handle)
-  uint4 *items_cmp;      // affected items, compacted in dense iterations
-  uint32_t it_c0, it_c1, it_c2;
-  typename S::C *partials;
-  uint32_t *chunk_done;
-  uint32_t *hub_v, *hub_base;  // hub queue of the current slot
-  // batched form (ncomp > 1): component of each vertex and per-component constants
-  uint32_t ncomp;
-  const uint16_t *comp;
-  const R *comp_base, *comp_init;
-  unsigned long long *dRc;        // [3][ncomp] per-component L-inf keys, rotating by iteration
-  uint32_t *comp_out;             // [ncomp][4] iterations, converged, affected
-  unsigned long long *comp_last;  // [ncomp] last L-inf key
-  uint32_t dense_div;
-  const uint32_t *pend_src;
-  uint32_t n_pend_src;
-  const uint32_t *pend_tgt;
-  uint32_t n_pend_tgt;
-  const uint32_t *dead;
-  uint32_t n_dead;
-  DeadPart *dpart;        // [2][gridDim.x]
-  R base;                 // (1 - alpha) / n in the rank representation
-  R init;                 // 1 / n (Static start)
-  B ftol;                 // tau_f as delta bits
-  unsigned long long tol_key;  // tau as an L-inf key
-  unsigned long long tele_frac;  // alpha / n * 2^64 (64-bit mode, teleport)
-  double tele_d;          // alpha / n (FP32 mode, teleport)
-  long long D_ref_n;      // dead-end mass of the previous ranks on the previous graph
-  double D_ref_d;
-  int max_iter;
-  int mode;  // RankMode
-  int teleport;
-  int start_full;  // Dynamic Frontier with every vertex affected from iteration 0
-  uint32_t bin_lo, bin_hi;
-  RankCtl *ctl;
-  // split Dynamic Frontier calls (single graph, self-loop mode): once the affected set has
-  // settled the call continues in k_rank_cont; a Dynamic Frontier launch resumes it when
-  // the continuation finds vertices to expand
-  int split;              // this call may hand off to the continuation
-  int resume;             // this launch resumes a call at iteration it0
-  int it0;
-  uint32_t *xlist;        // vertices to expand, recorded by the continuation (n)
-};
-
-// Neumaier's compensated summation (Neumaier 1974), for the FP32 mode's dead-end mass.
-struct Neu {
-  double s = 0.0, c = 0.0;
-  __device__ __forceinline__ void add(double x) {
-    double t = s + x;
-    if (fabs(s) >= fabs(x)) c += (s - t) + x; else c += (x - t) + s;
-    s = t;
-  }
-  __device__ __forceinline__ void merge(double os, double oc) {
-    add(os);
-    c += oc;
-  }
-};
-
-// ------------------------------------------------------------ memory access ----
-
-__device__ __forceinline__ unsigned long long l2_evict_first() {
-  unsigned long long p;
-  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ unsigned long long l2_evict_last() {
-  unsigned long long p;
-  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-// Four column ids of a 16-byte aligned run (read-only during the kernel).
-__device__ __forceinline__ uint4 ld_cols(const uint32_t *p, unsigned long long pol) {
-  uint4 r;
-  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
-               : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-               : "l"(p), "l"(pol));
-  return r;
-}
-// Contribution gathers.  C of the iteration's input parity is not written during the
-// iteration, and the grid barrier's acquire orders every block after all writes of the
-// previous iteration, so the gathers may be served by L1 (PRDF_GATHER_L2_ONLY=0); measured
-// slower on GB300 than keeping them at L2 (the default).
-#ifndef PRDF_GATHER_L2_ONLY
-#define PRDF_GATHER_L2_ONLY 1
-#endif
-#if PRDF_GATHER_L2_ONLY
-#define PRDF_GATHER_COP "cg"
-#else
-#define PRDF_GATHER_COP "ca"
-#endif
-__device__ __forceinline__ long long ld_keep(const long long *p, unsigned long long pol) {
-  long long r;
-  asm("ld.global." PRDF_GATHER_COP ".L2::cache_hint.b64 %0, [%1], %2;" : "=l"(r) : "l"(p), "l"(pol));
-  return r;
-}
-__device__ __forceinline__ float ld_keep(const float *p, unsigned long long pol) {
-  float r;
-  asm("ld.global." PRDF_GATHER_COP ".L2::cache_hint.f32 %0, [%1], %2;" : "=f"(r) : "l"(p), "l"(pol));
-  return r;
-}
-__device__ __forceinline__ void st_keep(long long *p, long long v, unsigned long long pol) {
-  asm volatile("st.global.L2::cache_hint.b64 [%0], %1, %2;" ::"l"(p), "l"(v), "l"(pol) : "memory");
-}
-__device__ __forceinline__ void st_keep(float *p, float v, unsigned long long pol) {
-  asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
-}
-
-__device__ __forceinline__ long long ldcg(const long long *p) { return __ldcg(p); }
-__device__ __forceinline__ float ldcg(const float *p) { return __ldcg(p); }
-__device__ __forceinline__ uint32_t ldcg(const uint32_t *p) { return __ldcg(p); }
-__device__ __forceinline__ uint16_t ldcg(const uint16_t *p) {
-  return __ldcg(reinterpret_cast<const unsigned short *>(p));
-}
-
-// Grid-wide barrier with a bounded wait.  Returns false (in every thread of the block)
-// if the device control block holds an error.
-__device__ __forceinline__ bool grid_sync(RankCtl *ctl, uint32_t &epoch, uint32_t *s_err) {
-  __syncthreads();
-  epoch++;
-  if (threadIdx.x == 0) {
-    __threadfence();
-    red_release_add_u32(&ctl->bar, 1u);
-    const uint32_t target = epoch * gridDim.x;
-    uint64_t t0 = 0;
-    uint32_t spins = 0;
-    while (ld_acquire_u32(&ctl->bar) < target) {
-      if (*(volatile uint32_t *)&ctl->err) break;
-      __nanosleep(32);
-      if ((++spins & 127) == 0) {
-        uint64_t t = globaltimer_ns();
-        if (t0 == 0) {
-          t0 = t;
-        } else if (t - t0 > kBarrierTimeoutNs) {
-          atomicExch(&ctl->err_where, epoch);
-          atomicOr(&ctl->err, 1u);
-          break;
-        }
-      }
-    }
-    __threadfence();
-    *s_err = *(volatile uint32_t *)&ctl->err;
-  }
-  __syncthreads();
-  return *s_err == 0;
-}
-
-__device__ __forceinline__ int bin_of(uint32_t deg, uint32_t lo, uint32_t hi) {
-  return deg <= lo ? 0 : (deg <= hi ? 1 : 2);
-}
-
-// Newly marked vertices are buffered per warp in shared memory, one run per bin, and
-// appended to the bin's list with one global atomic per run rather than one per marking
-// round (the list tails are contended by every warp of the grid).  Every buffer is flushed
-// before the grid barrier after which the tails are read.  In dense iterations all marks
-// go to list 0 and the in-degree lookup for the bin is skipped: later iterations are dense
-// too (the affected set only grows) and sweep the sweep items, and the writeback only
-// needs every affected vertex in some list.
-constexpr uint32_t kMarkBuf = 64;
-struct WarpBuf {
-  uint32_t *buf;   // [4][kMarkBuf] entries of this warp's shared memory: bins 0-2, expansions
-  uint32_t n[4];   // entries held per run (the same in every lane)
-  bool dense;
-  uint32_t slot;   // iteration the queued expansions' marks join (their count per slot)
-};
-
-template <bool F32>
-__device__ __forceinline__ void flush_bin(const RankArgs<F32> &a, int bb, uint32_t slot, const uint32_t cnt[3],
-                                          uint32_t lane, WarpBuf &wb) {
-  __syncwarp();
-  const uint32_t k = wb.n[bb];
-  if (k) {
-    uint32_t *lists[3] = {a.list0, a.list1, a.list2};
-    uint32_t base = 0;
-    if (lane == 0) base = atomicAdd(&a.ctl->tail[slot][bb], k);
-    base = __shfl_sync(kFull, base, 0);
-    for (uint32_t i = lane; i < k; i += 32) lists[bb][cnt[bb] + base + i] = wb.buf[bb * kMarkBuf + i];
-  }
-  __syncwarp();
-  wb.n[bb] = 0;
-}
-
-// Vertices a dense or full sweep found to expand, appended to the call's expansion list
-// (each vertex at most once per call: first_expansion) in runs; the grid scans their
-// out-rows after the iteration's barrier, so the sweep loops carry no marking code.
-template <bool F32>
-__device__ __forceinline__ void flush_expansions(const RankArgs<F32> &a, uint32_t lane, WarpBuf &wb) {
-  __syncwarp();
-  const uint32_t k = wb.n[3];
-  if (k) {
-    uint32_t base = 0;
-    if (lane == 0) {
-      base = atomicAdd(&a.ctl->xcnt, k);
-      atomicAdd(&a.ctl->xit[wb.slot], k);
-    }
-    base = __shfl_sync(kFull, base, 0);
-    for (uint32_t i = lane; i < k; i += 32) a.xlist[base + i] = wb.buf[3 * kMarkBuf + i];
-  }
-  __syncwarp();
-  wb.n[3] = 0;
-}
-
-template <bool F32>
-__device__ __forceinline__ void queue_expansion(const RankArgs<F32> &a, bool push, uint32_t v, uint32_t lane,
-                                                WarpBuf &wb) {
-  const uint32_t mask = __ballot_sync(kFull, push);
-  if (mask) {
-    if (wb.n[3] + __popc(mask) > kMarkBuf) flush_expansions(a, lane, wb);
-    if (push) wb.buf[3 * kMarkBuf + wb.n[3] + __popc(mask & lanemask_lt())] = v;
-    wb.n[3] += __popc(mask);
-  }
-}
-
-template <bool F32>
-__device__ __forceinline__ void flush_marks(const RankArgs<F32> &a, uint32_t slot, const uint32_t cnt[3],
-                                            uint32_t lane, WarpBuf &wb) {
-#pragma unroll
-  for (int bb = 0; bb < 3; bb++) flush_bin(a, bb, slot, cnt, lane, wb);
-  flush_expansions(a, lane, wb);
-}
-
-// Appends w where fresh to its bin's run in the warp's buffer.  Called by a whole warp.
-template <bool F32>
-__device__ __forceinline__ void append_mark(const RankArgs<F32> &a, bool fresh, uint32_t w, uint32_t slot,
-                                            const uint32_t cnt[3], uint32_t lane, WarpBuf &wb) {
-  int bin = -1;
-  if (fresh) bin = wb.dense ? 0 : bin_of(__ldg(&a.in_rd[w]).y, a.bin_lo, a.bin_hi);
-  const int nb = wb.dense ? 1 : 3;
-  for (int bb = 0; bb < nb; bb++) {
-    const uint32_t mask = __ballot_sync(kFull, bin == bb);
-    if (mask) {
-      if (wb.n[bb] + __popc(mask) > kMarkBuf) flush_bin(a, bb, slot, cnt, lane, wb);
-      if (bin == bb) wb.buf[bb * kMarkBuf + wb.n[bb] + __popc(mask & lanemask_lt())] = w;
-      wb.n[bb] += __popc(mask);
-    }
-  }
-}
-
-// Marks w (where valid) for iteration `slot`: a plain read of the bitmap first, then the
-// atomic; a newly marked vertex is stamped and appended through the warp's buffer.  Called
-// by a whole warp; returns 1 where this lane marked a new vertex.
-template <bool F32>
-__device__ __forceinline__ uint32_t mark_one(const RankArgs<F32> &a, bool valid, uint32_t w, uint32_t slot,
-                                             const uint32_t cnt[3], uint32_t lane, WarpBuf &wb) {
-  bool fresh = false;
-  if (valid) {
-    uint32_t bit = 1u << (w & 31);
-    uint32_t *word = a.bitmap + (w >> 5);
-    if (!(ldcg(word) & bit)) {
-      uint32_t old = atomicOr(word, bit);
-      if (!(old & bit)) {
-        fresh = true;
-        a.stamp[w] = (uint16_t)slot;
-      }
-    }
-  }
-  append_mark(a, fresh, w, slot, cnt, lane, wb);
-  return fresh ? 1u : 0u;
-}
-
-// Marks cols[first + 32 k + lane] (k = 0, 1, ...; stride `stride`), stamping newly marked
-// vertices with `slot` (the iteration they join).  Called by a whole warp.
-template <bool F32>
-__device__ __forceinline__ uint32_t warp_mark_range(const RankArgs<F32> &a, const uint32_t *cols, uint32_t len,
-                                                    uint32_t first, uint32_t stride, uint32_t slot,
-                                                    const uint32_t cnt[3], uint32_t lane, WarpBuf &wb) {
-  uint32_t newly_total = 0;
-  for (uint32_t j0 = first; j0 < len; j0 += stride) {
-    const uint32_t j = j0 + lane;
-    const bool valid = j < len;
-    newly_total += mark_one(a, valid, valid ? __ldg(cols + j) : 0u, slot, cnt, lane, wb);
-  }
-  return newly_total;
-}
-
-// Short out-rows (at most kThreadOut entries; a row starts 16-byte aligned and its slots
-// come in whole groups of four): every lane in `mine` marks its own row.  The bitmap words
-// of all its entries are read together and the atomics for the clear bits are issued
-// together, so a row costs two dependent round trips rather than a pair per entry; the
-// stamps and warp-aggregated appends follow entry by entry.  Called by a whole warp.
-constexpr uint32_t kThreadOut = 8;
-template <bool F32>
-__device__ __forceinline__ uint32_t lane_mark_rows(const RankArgs<F32> &a, bool mine, uint2 od, uint32_t slot,
-                                                   const uint32_t cnt[3], uint32_t lane, WarpBuf &wb) {
-  const uint32_t len = mine ? od.y : 0u;
-  const uint32_t rounds = __reduce_max_sync(kFull, len);
-  uint4 q0 = make_uint4(0, 0, 0, 0), q1 = q0;
-  if (len > 0) q0 = __ldg(reinterpret_cast<const uint4 *>(a.out_col + od.x));
-  if (len > 4) q1 = __ldg(reinterpret_cast<const uint4 *>(a.out_col + od.x + 4));
-  const uint32_t w[kThreadOut] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
-  uint32_t word[kThreadOut];
-#pragma unroll
-  for (uint32_t k = 0; k < kThreadOut; k++) word[k] = k < len ? ldcg(a.bitmap + (w[k] >> 5)) : ~0u;
-  uint32_t fresh = 0;  // bit k: entry k newly marked by this lane
-#pragma unroll
-  for (uint32_t k = 0; k < kThreadOut; k++) {
-    const uint32_t bit = 1u << (w[k] & 31);
-    if (!(word[k] & bit) && !(atomicOr(a.bitmap + (w[k] >> 5), bit) & bit)) fresh |= 1u << k;
-  }
-  uint32_t newly = 0;
-#pragma unroll
-  for (uint32_t k = 0; k < kThreadOut; k++) {
-    if (k < rounds) {
-      const bool f = (fresh >> k) & 1u;
-      if (f) a.stamp[w[k]] = (uint16_t)slot;
-      append_mark(a, f, w[k], slot, cnt, lane, wb);
-      newly += f ? 1u : 0u;
-    }
-  }
-  return newly;
-}
-
-// True the first time v asks (per call): its out-row is then scanned by the caller.  A
-// plain read first, so a vertex that keeps changing costs one load per iteration, not an
-// atomic.
-__device__ __forceinline__ bool first_expansion(uint32_t *xbits, uint32_t v) {
-  uint32_t bit = 1u << (v & 31);
-  if (__ldcg(xbits + (v >> 5)) & bit) return false;
-  return !(atomicOr(xbits + (v >> 5), bit) & bit);
-}
-// The same with the word read beforehand (issued with the row's loads, so the test adds no
-// round trip); the atomic still decides, so a stale word only costs an atomic.
-__device__ __forceinline__ bool first_expansion_pre(uint32_t *xbits, uint32_t v, uint32_t word) {
-  uint32_t bit = 1u << (v & 31);
-  if (word & bit) return false;
-  return !(atomicOr(xbits + (v >> 5), bit) & bit);
-}
-
-// Marks the out-neighbours of v for iteration `slot`: short out-rows by the calling warp,
-// long ones queued for the cooperative pass that follows the iteration's barrier (entry
-// index and chunk base are reserved by one 64-bit atomic, so bases ascend with the index).
-// Called by a whole warp; returns the vertices this warp newly marked.
-template <bool F32>
-__device__ __forceinline__ uint32_t expand_vertex(const RankArgs<F32> &a, uint32_t v, uint2 od, uint32_t slot,
-                                                  const uint32_t cnt[3], uint32_t lane, WarpBuf &wb) {
-  if (od.y <= kInlineOut) return warp_mark_range(a, a.out_col + od.x, od.y, 0, 32, slot, cnt, lane, wb);
-  if (lane == 0) {
-    const uint32_t nch = (od.y + kChunk - 1) / kChunk;
-    const unsigned long long old = atomicAdd(&a.ctl->hubq[slot], (1ull << 32) | nch);
-    const uint32_t e = (uint32_t)(old >> 32);
-    a.hub_v[e] = v;
-    a.hub_base[e] = (uint32_t)old;
-  }
-  return 0;
-}
-
-// The cooperative pass over the queued long out-rows of `slot`: kChunk-entry chunks
-// dealt round-robin to all warps of the grid.
-template <bool F32>
-__device__ uint32_t hub_pass(const RankArgs<F32> &a, uint32_t slot, const uint32_t cnt[3], uint32_t lane,
-                             uint32_t gwarp, uint32_t nwarps, WarpBuf &wb) {
-  const unsigned long long hq = __ldcg(&a.ctl->hubq[slot]);
-  const uint32_t ne = (uint32_t)(hq >> 32), K = (uint32_t)hq;
-  uint32_t newly = 0;
-  for (uint32_t k = gwarp; k < K; k += nwarps) {
-    uint32_t lo = 0, hi = ne;
-    while (hi - lo > 1) {
-      const uint32_t mid = (lo + hi) >> 1;
-      if (__ldcg(a.hub_base + mid) <= k) lo = mid; else hi = mid;
-    }
-    const uint32_t v = __ldcg(a.hub_v + lo), c = k - __ldcg(a.hub_base + lo);
-    const uint2 od = __ldg(&a.out_rd[v]);
-    const uint32_t start = c * kChunk;
-    newly += warp_mark_range(a, a.out_col + od.x + start, min(kChunk, od.y - start), 0, 32, slot, cnt, lane, wb);
-  }
-  return newly;
-}
-
-template <class C>
-__device__ __forceinline__ C gather4(const C *Cv, uint4 q, uint32_t valid, unsigned long long pol) {
-  C s = (C)0;
-  if (valid > 0) s += ld_keep(Cv + q.x, pol);
-  if (valid > 1) s += ld_keep(Cv + q.y, pol);
-  if (valid > 2) s += ld_keep(Cv + q.z, pol);
-  if (valid > 3) s += ld_keep(Cv + q.w, pol);
-  return s;
-}
-
-// Sum of C over one whole row by one thread: runs of 8 columns, all loads of a run in
-// flight together.
-template <class C>
-__device__ __forceinline__ C row_sum_thread(const C *Cv, const uint32_t *cols, uint32_t len,
-                                            unsigned long long pol_cols, unsigned long long pol_c) {
-  C sum = (C)0;
-  for (uint32_t j0 = 0; j0 < len; j0 += 8) {
-    uint4 q[2];
-#pragma unroll
-    for (int k = 0; k < 2; k++)
-      if (j0 + 4 * k < len) q[k] = ld_cols(cols + j0 + 4 * k, pol_cols);
-#pragma unroll
-    for (int k = 0; k < 2; k++)
-      if (j0 + 4 * k < len) sum += gather4(Cv, q[k], min(4u, len - j0 - 4 * k), pol_c);
-  }
-  return sum;
-}
-
-template <class X>
-__device__ __forceinline__ X warp_sum(X x) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
-  return x;
-}
-
-// Dead-end mass accumulator: exact integer in 64-bit mode, Neumaier pair in FP32 mode.
-template <bool F32>
-struct Mass;
-template <>
-struct Mass<false> {
-  long long s = 0;
-  __device__ void add(long long x) { s += x; }
-};
-template <>
-struct Mass<true> {
-  Neu n;
-  __device__ void add(double x) { n.add(x); }
-};
-
-template <bool F32>
-struct Iter {
-  bool full;
-  typename Store<F32>::R tele;  // alpha D / n in the rank representation
-};
-
-// Rank of v from its in-edge sum, given R[v] and A[v] loaded beforehand; writes the new
-// rank and contribution; returns the delta bits of |r - R[v]|.
-template <bool F32>
-__device__ __forceinline__ typename Num<F32>::B finish_vertex(const RankArgs<F32> &a, typename Store<F32>::R *Rout,
-                                                              typename Store<F32>::C *Cout, uint32_t v,
-                                                              typename Store<F32>::C sum, typename Store<F32>::R rold,
-                                                              typename Store<F32>::A ad, const Iter<F32> &I,
-                                                              Mass<F32> &dacc, unsigned long long pol_c,
-                                                              typename Store<F32>::R base) {
-  using S = Store<F32>;
-  using R = typename S::R;
-  R r = base + sum;
-  if (a.teleport) r += I.tele;
-  Rout[v] = r;
-  st_keep(Cout + v, S::contrib(r, ad), pol_c);
-  if (a.teleport && ad == (typename S::A)0) {
-    if constexpr (F32) dacc.add(I.full ? (double)r : (double)r - (double)rold);
-    else dacc.add(I.full ? r : r - rold);
-  }
-  return Num<F32>::delta(r, rold);
-}
-
-__device__ __forceinline__ uint4 ldcg(const uint4 *p) { return __ldcg(p); }
-
-// Frontier expansion of the lanes' vertices that changed by more than tau_f (push):
-// short out-rows by their own lanes, medium ones flattened across the warp, hub rows
-// queued for the grid.  Out of line: it runs only when some lane of the warp expands, and
-// keeping its registers out of the sweep loops keeps those loops free of spills.  Called
-// by a whole warp.
-struct ExpandOut {
-  uint32_t app, xv, xe;  // vertices appended; vertices and out-edges expanded (this lane)
-};
-template <bool F32>
-__device__ __noinline__ ExpandOut expand_lanes(const RankArgs<F32> &a, int push, uint32_t v, uint32_t slot,
-                                               uint32_t c0, uint32_t c1, uint32_t c2, WarpBuf *wbp) {
-  const uint32_t lane = threadIdx.x & 31;
-  const uint32_t cnt[3] = {c0, c1, c2};
-  WarpBuf wb = *wbp;
-  ExpandOut o{0u, 0u, 0u};
-  uint2 od = make_uint2(0, 0);
-  if (push) od = __ldg(&a.out_rd[v]);
-  // short rows: each lane its own
-  const bool mine = push && od.y <= kThreadOut;
-  if (__any_sync(kFull, mine)) o.app += lane_mark_rows(a, mine, od, slot, cnt, lane, wb);
-  // medium rows: the rows of all such lanes flattened into one run of entries, marked 128
-  // at a time (four per lane; the column loads, bitmap reads and atomics of a round are in
-  // flight together), so the warp spends ceil(total / 128) rounds instead of one round per
-  // 32 entries of every row in turn
-  const bool med = push && od.y > kThreadOut && od.y <= kInlineOut;
-  const uint32_t mlen = med ? od.y : 0u;
-  uint32_t incl = mlen;
-#pragma unroll
-  for (int k = 1; k < 32; k <<= 1) {
-    const uint32_t y = __shfl_up_sync(kFull, incl, k);
-    if (lane >= (uint32_t)k) incl += y;
-  }
-  const uint32_t total = __shfl_sync(kFull, incl, 31);
-  const uint32_t excl = incl - mlen;
-  for (uint32_t e0 = 0; e0 < total; e0 += 128) {
-    uint32_t w[4], word[4];
-    bool valid[4];
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-      const uint32_t e = e0 + 32u * k + lane;
-      // the lane whose run [excl, incl) holds entry e
-      uint32_t owner = 0;
-#pragma unroll
-      for (uint32_t step = 16; step > 0; step >>= 1) {
-        const uint32_t probe = __shfl_sync(kFull, incl, owner + step - 1);
-        if (probe <= e) owner += step;
-      }
-      const uint32_t base = __shfl_sync(kFull, od.x, owner & 31u);
-      const uint32_t first = __shfl_sync(kFull, excl, owner & 31u);
-      valid[k] = e < total;
-      w[k] = valid[k] ? __ldg(a.out_col + base + (e - first)) : 0u;
-    }
-#pragma unroll
-    for (int k = 0; k < 4; k++) word[k] = valid[k] ? ldcg(a.bitmap + (w[k] >> 5)) : ~0u;
-    uint32_t fresh = 0;
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-      const uint32_t bit = 1u << (w[k] & 31);
-      if (!(word[k] & bit) && !(atomicOr(a.bitmap + (w[k] >> 5), bit) & bit)) fresh |= 1u << k;
-    }
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-      const bool f = (fresh >> k) & 1u;
-      if (f) a.stamp[w[k]] = (uint16_t)slot;
-      append_mark(a, f, w[k], slot, cnt, lane, wb);
-      o.app += f ? 1u : 0u;
-    }
-  }
-  if (mine || med) {
-    o.xv++;
-    o.xe += od.y;
-  }
-  // hub rows: queued for the grid
-  uint32_t mask = __ballot_sync(kFull, push && od.y > kInlineOut);
-  while (mask) {
-    const uint32_t src = __ffs(mask) - 1;
-    mask &= mask - 1;
-    const uint32_t x = __shfl_sync(kFull, v, src);
-    const uint2 ox = make_uint2(__shfl_sync(kFull, od.x, src), __shfl_sync(kFull, od.y, src));
-    o.app += expand_vertex(a, x, ox, slot, cnt, lane, wb);
-    if (lane == 0) {
-      o.xv++;
-      o.xe += ox.y;
-    }
-  }
-  *wbp = wb;
-  return o;
-}
-
-// One vertex's out-row (hub rows queued), by the whole warp; out of line like expand_lanes.
-template <bool F32>
-__device__ __noinline__ ExpandOut expand_one(const RankArgs<F32> &a, uint32_t v, uint32_t slot, uint32_t c0,
-                                             uint32_t c1, uint32_t c2, WarpBuf *wbp) {
-  const uint32_t lane = threadIdx.x & 31;
-  const uint32_t cnt[3] = {c0, c1, c2};
-  WarpBuf wb = *wbp;
-  const uint2 od = __ldg(&a.out_rd[v]);
-  ExpandOut o{expand_vertex(a, v, od, slot, cnt, lane, wb), 0u, 0u};
-  if (lane == 0) {
-    o.xv = 1;
-    o.xe = od.y;
-  }
-  *wbp = wb;
-  return o;
-}
-
-// A continuation launch found vertices whose out-rows must now be scanned (their first
-// change above tau_f): they are listed for the Dynamic Frontier launch that resumes the
-// call.  Rare, so a plain warp-aggregated append.
-template <bool F32>
-__device__ __forceinline__ void record_expansion(const RankArgs<F32> &a, bool push, uint32_t v, uint32_t lane,
-                                                 uint32_t slot) {
-  const uint32_t mask = __ballot_sync(kFull, push);
-  if (mask) {
-    const uint32_t leader = __ffs(mask) - 1;
-    uint32_t base = 0;
-    if (lane == leader) {
-      base = atomicAdd(&a.ctl->xcnt, (uint32_t)__popc(mask));
-      atomicAdd(&a.ctl->xit[slot], (uint32_t)__popc(mask));
-    }
-    base = __shfl_sync(kFull, base, leader);
-    if (push) a.xlist[base + __popc(mask & lanemask_lt())] = v;
-  }
-}
 
 // In/out state of an out-of-line sweep of the sweep items (full and dense iterations).
 template <bool F32>
@@ -1078,42 +451,19 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
   }
   const uint32_t zero_cnt[3] = {0, 0, 0};
   WarpBuf wb{s_mbuf[wib], {0u, 0u, 0u, 0u}, false, 0u};
-  // a resumed call: list lengths and compaction as the handing-off launch left them
-  uint32_t saved_cnt[3] = {0, 0, 0};
   // expansion-list entries already scanned; read before any barrier of this launch, since
   // the sweeps append to the list once the first barrier is passed
   uint32_t xdone = 0;
-  if (df && a.resume) {
-#pragma unroll
-    for (int bb = 0; bb < 3; bb++) saved_cnt[bb] = ldcg(&ctl->save_cnt[bb]);
-  }
-  if (df && a.resume) {
-    // expansions the continuation recorded in iteration it0 - 1: their marks join at it0
-    const uint32_t slot0 = (uint32_t)a.it0;
-    wb.dense = true;
-    const uint32_t xend = ldcg(&ctl->xcnt);
-    xdone = xend;
-    for (uint32_t k0 = gwarp * 32; k0 < xend; k0 += nwarps * 32) {
-      const bool p = k0 + lane < xend;
-      const uint32_t x = p ? ldcg(a.xlist + k0 + lane) : 0u;
-      const ExpandOut o = expand_lanes(a, p ? 1 : 0, x, slot0, saved_cnt[0], saved_cnt[1], saved_cnt[2], &wb);
+  if (df && !a.start_full) {
+    // sources: mark G^t.out(u), 32 sources per warp round (short rows by their own lanes,
+    // medium rows flattened over the warp, long rows by the whole grid)
+    for (uint32_t k0 = gwarp * 32; k0 < a.n_pend_src; k0 += nwarps * 32) {
+      const bool p = k0 + lane < a.n_pend_src;
+      const uint32_t u = p ? __ldg(a.pend_src + k0 + lane) : 0u;
+      const ExpandOut o = expand_lanes(a, p ? 1 : 0, u, 0u, 0u, 0u, 0u, &wb);
       my_app += o.app;
       my_xv += o.xv;
       my_xe += o.xe;
-    }
-    flush_marks(a, slot0, saved_cnt, lane, wb);
-    if (!grid_sync(ctl, epoch, &s_err)) return;
-    if (__ldcg(&ctl->hubq[slot0]) != 0) {
-      my_app += hub_pass(a, slot0, saved_cnt, lane, gwarp, nwarps, wb);
-      flush_marks(a, slot0, saved_cnt, lane, wb);
-      if (!grid_sync(ctl, epoch, &s_err)) return;
-    }
-  } else if (df && !a.start_full) {
-    // sources: mark G^t.out(u), one warp per source
-    for (uint32_t k = gwarp; k < a.n_pend_src; k += nwarps) {
-      uint32_t u = __ldg(a.pend_src + k);
-      uint2 od = __ldg(&a.out_rd[u]);
-      my_app += expand_vertex(a, u, od, 0, zero_cnt, lane, wb);
     }
     // deleted targets, 32 per warp round
     for (uint32_t k0 = gwarp * 32; k0 < a.n_pend_tgt; k0 += nwarps * 32) {
@@ -1121,30 +471,34 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
       my_app += warp_mark_range(a, a.pend_tgt + k0, cnt_left, 0, 32, 0, zero_cnt, lane, wb);
     }
   }
-  if (!(df && a.resume)) {
+  flush_marks(a, 0u, zero_cnt, lane, wb);
+  if (a.teleport) block_dead_partial(0);
+  if (!grid_sync(ctl, epoch, &s_err)) return;
+  if (df && __ldcg(&ctl->hubq[0]) != 0) {
+    my_app += hub_pass(a, 0, zero_cnt, lane, gwarp, nwarps, wb);
     flush_marks(a, 0u, zero_cnt, lane, wb);
-    if (a.teleport) block_dead_partial(0);
     if (!grid_sync(ctl, epoch, &s_err)) return;
-    if (df && __ldcg(&ctl->hubq[0]) != 0) {
-      my_app += hub_pass(a, 0, zero_cnt, lane, gwarp, nwarps, wb);
-      flush_marks(a, 0u, zero_cnt, lane, wb);
-      if (!grid_sync(ctl, epoch, &s_err)) return;
-    }
-    if (blockIdx.x == 0 && tid == 0) ctl->t_ns[1] = globaltimer_ns();
   }
+  if (blockIdx.x == 0 && tid == 0) ctl->t_ns[1] = globaltimer_ns();
 
   uint32_t cnt[3];
-  const int it_begin = df && a.resume ? a.it0 : 0;
 #pragma unroll
-  for (int bb = 0; bb < 3; bb++) {
-    if (df && a.resume) cnt[bb] = saved_cnt[bb] + ldcg(&ctl->tail[it_begin][bb]);
-    else cnt[bb] = df && !a.start_full ? ldcg(&ctl->tail[0][bb]) : 0u;
-  }
+  for (int bb = 0; bb < 3; bb++) cnt[bb] = df && !a.start_full ? ldcg(&ctl->tail[0][bb]) : 0u;
+  // counters of a launch that stops early and leaves the iterations to other launches
+  auto fold_counters = [&]() {
+    const unsigned long long xv = warp_sum((unsigned long long)my_xv), xe = warp_sum((unsigned long long)my_xe),
+                             ap = warp_sum((unsigned long long)my_app);
+    if (lane == 0) {
+      if (xv) atomicAdd(&ctl->expv, xv);
+      if (xe) atomicAdd(&ctl->expe, xe);
+      if (ap) atomicAdd(&ctl->appended, ap);
+    }
+  };
   // Dynamic Traversal: every vertex reachable from the seeds phase 0 marked joins iteration 0
   // and nothing is marked afterwards
   const bool dt = df && a.mode == kModeDT;
   bool dt_all = false;
-  if (dt && !a.start_full && !a.resume) {
+  if (dt && !a.start_full) {
     const DtOut o = dt_search(a, epoch, cnt[0], cnt[1], cnt[2], &wb);
     if (!o.ok) return;
     epoch = o.epoch;
@@ -1169,14 +523,19 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
           a.xbits[v >> 5] = 0u;
           a.stamp[v] = kNoStamp;
         }
-      const unsigned long long xv = warp_sum((unsigned long long)my_xv), xe = warp_sum((unsigned long long)my_xe),
-                               ap = warp_sum((unsigned long long)my_app);
-      if (lane == 0) {
-        if (xv) atomicAdd(&ctl->expv, xv);
-        if (xe) atomicAdd(&ctl->expe, xe);
-        if (ap) atomicAdd(&ctl->appended, ap);
-      }
+      fold_counters();
       if (blockIdx.x == 0 && tid == 0) ctl->status = kStatusFull;
+      return;
+    }
+    if (a.split) {
+      // the set is fixed: every iteration runs in the per-iteration launches
+      fold_counters();
+      if (blockIdx.x == 0 && tid == 0) {
+#pragma unroll
+        for (int bb = 0; bb < 3; bb++) ctl->save_cnt[bb] = cnt[bb];
+        ctl->next_it = 0;
+        ctl->status = kStatusDense;
+      }
       return;
     }
   }
@@ -1193,17 +552,10 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
   uint32_t prev_total = 0xFFFFFFFFu; // affected count at the start of the previous iteration
   uint32_t cmp_n[3] = {0, 0, 0};
   uint32_t deact = 0, cmp_deact = 0;  // iterations in which some graph stopped (batched form)
-  if (df && a.resume) {
-#pragma unroll
-    for (int t = 0; t < 3; t++) cmp_n[t] = ldcg(&ctl->save_cmp[t]);
-    cmp_total = ldcg(&ctl->save_cmp_total);
-    prev_total = cmp_total;
-    iters = (uint32_t)it_begin;
-  }
   bool handed_off = false;
 
   // ------------------------------------------------------------- iterations
-  for (int it = it_begin; it < a.max_iter; it++) {
+  for (int it = 0; it < a.max_iter; it++) {
     Iter<F32> I;
     I.tele = a.teleport ? tele_of(Dn, Dd) : (R)0;
     if (df && a.teleport && !ever_full && Num<F32>::delta(I.tele, tele_prev) > a.ftol) {
@@ -1229,25 +581,26 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
     const bool scan_all = dense && total_now != cmp_total && total_now > a.n / 4 &&
                           (prev_total == 0xFFFFFFFFu || total_now - prev_total > total_now / 16);
     prev_total = total_now;
-    // a settled affected set (compacted items current, nothing marked since) continues in
-    // the lean continuation kernel; this launch stops here.  A resumed launch hands off
-    // again at once when its expansions marked nothing new: a relaunch costs far less than
-    // an iteration of this kernel
-    if (df && a.split && dense && !scan_all && total_now == cmp_total) {
+    // split calls: once the affected set is dense, the iterations continue in the
+    // per-iteration launches (which grow the set by pulling or pushing); this launch stops
+    // before the iteration, whose marks are in place
+    if (df && a.split && dense) {
       if (blockIdx.x == 0 && tid == 0) {
 #pragma unroll
-        for (int bb = 0; bb < 3; bb++) {
-          ctl->save_cnt[bb] = cnt[bb];
-          ctl->save_cmp[bb] = cmp_n[bb];
-        }
-        ctl->save_cmp_total = cmp_total;
+        for (int bb = 0; bb < 3; bb++) ctl->save_cnt[bb] = cnt[bb];
         ctl->next_it = (uint32_t)it;
-        ctl->status = kStatusHandoff;
+        ctl->status = kStatusDense;
       }
       handed_off = true;
       break;
     }
     const bool expand = df && !dt && !I.full;
+    // split calls: a sparse iteration over a set whose out-rows would likely make the next
+    // set dense (defer_at, from the average degree) pushes nothing; it records each
+    // vertex's change flag (and marks the first expansions as done), and the next
+    // iteration, the first of the per-iteration launches, pulls its marks from them
+    // (pushing that many out-rows costs more than one pull over every item)
+    const bool defer = expand && a.split && !dense && total_now > a.defer_at;
     const uint32_t slot = (uint32_t)it + 1;
     B my_max = 0;
     if (blockIdx.x == 0 && tid == 0) {
@@ -1275,6 +628,18 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
       if (multi) atomicMax(&s_kmax[c], Num<F32>::key(dr));
       else my_max = dr > my_max ? dr : my_max;
       return dr;
+    };
+    // sparse iterations: whether v's out-row is marked now; a deferred iteration records
+    // the change flag instead (the out-row is then marked by the next iteration's pull)
+    auto sparse_push = [&](uint32_t v, B dr) -> int {
+      if (!expand) return 0;
+      const bool big = dr > a.ftol;
+      if (defer) {
+        a.emap[(size_t)(it & 1) * a.n + v] = big ? 1 : 0;
+        if (big) first_expansion(a.xbits, v);
+        return 0;
+      }
+      return big && first_expansion(a.xbits, v);
     };
 
     if (I.full || dense) {
@@ -1371,7 +736,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
           B dr = finish_at(v, sum, rold, ad);
           my_v++;
           my_e += d.y;
-          push = expand && dr > a.ftol && first_expansion(a.xbits, v);
+          push = sparse_push(v, dr);
         }
         if (expand) expand_if(push, v);
       }
@@ -1393,7 +758,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
           B dr = finish_at(v, sum, ldcg(Rin + v), __ldg(a.adeg + v));
           my_v++;
           my_e += d.y;
-          exp_now = expand && dr > a.ftol && first_expansion(a.xbits, v);
+          exp_now = sparse_push(v, dr);
         }
         exp_now = __shfl_sync(kFull, exp_now, 0);
         if (exp_now) {
@@ -1438,7 +803,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
           B dr = finish_at(v, tot, ldcg(Rin + v), __ldg(a.adeg + v));
           my_v++;
           my_e += d.y;
-          s_expand = expand && dr > a.ftol && first_expansion(a.xbits, v);
+          s_expand = sparse_push(v, dr);
         }
         __syncthreads();
         if (s_expand) {
@@ -1558,6 +923,28 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
     iters = (uint32_t)it + 1;
     last_key = dR;
     if (blockIdx.x == 0 && tid == 0) ctl->t_ns[it + 2] = globaltimer_ns();
+    if (defer) {
+      // tier-2 rows pull before the handoff (the first per-iteration sweep pulls tier-0/1
+      // rows itself).  If this was the last iteration (converged or max_iter), the launches
+      // that follow only make its marks, which belong to the affected set (Algorithm 1
+      // marks in every iteration, the last included)
+      const bool last = dR <= a.tol_key || it + 1 >= a.max_iter;
+      my_app += pull_tier2(a, slot, cnt[0], a.it_c2, a.it_c0 + a.it_c1);
+      if (!grid_sync(ctl, epoch, &s_err)) return;
+      if (blockIdx.x == 0 && tid == 0) {
+#pragma unroll
+        for (int bb = 0; bb < 3; bb++) ctl->save_cnt[bb] = cnt[bb] + (bb == 0 ? ldcg(&ctl->tail[slot][0]) : 0u);
+        ctl->next_it = slot;
+        ctl->pull_check = 1;
+        ctl->fin_only = last ? 1u : 0u;
+        ctl->iterations = slot;
+        ctl->converged = dR <= a.tol_key ? 1u : 0u;
+        ctl->last_key = dR;
+        ctl->status = kStatusDense;
+      }
+      handed_off = true;
+      break;
+    }
     if (dR <= a.tol_key) {
       converged = true;
       break;
@@ -1590,6 +977,10 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
         a.bitmap[v >> 5] = 0u;
         a.xbits[v >> 5] = 0u;
         a.stamp[v] = kNoStamp;
+        if (a.emap) {
+          a.emap[v] = 0;
+          a.emap[a.n + v] = 0;
+        }
       }
     }
     if (multi) {
@@ -1621,191 +1012,6 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
   }
 }
 
-// Would expanding the recorded vertices xlist[first, first + k) mark anything?  Scans their
-// out-rows against the affected bitmap (no marking): a vertex every out-neighbour of which
-// is affected already expands to nothing (Algorithm 1's marking of marked vertices is a
-// no-op), so the continuation goes on.  Sets xneed[slot] otherwise, and for any row longer
-// than kCheckMax (the marking kernel handles those through its hub queue).  Out of line: it
-// runs only in iterations that recorded expansions.
-constexpr uint32_t kCheckMax = 4096;  // longer out-rows are not scanned: the call resumes
-constexpr uint32_t kNoEntry = 0xFFFFFFFFu;  // no vertex id (ids are below n <= 2^32 - 1)
-template <bool F32>
-__device__ __noinline__ void check_recorded(const RankArgs<F32> &a, uint32_t first, uint32_t k, uint32_t slot) {
-  const uint32_t lane = threadIdx.x & 31;
-  const uint32_t nwarps = (gridDim.x * kRankBlock) >> 5, gwarp = (blockIdx.x * kRankBlock + threadIdx.x) >> 5;
-  for (uint32_t i = gwarp; i < k; i += nwarps) {
-    if (ldcg(&a.ctl->xneed[slot])) return;  // decided already
-    const uint32_t v = ldcg(a.xlist + first + i);
-    const uint2 od = __ldg(&a.out_rd[v]);
-    if (od.y > kCheckMax) {
-      if (lane == 0) atomicOr(&a.ctl->xneed[slot], 1u);
-      return;
-    }
-    // 128 entries per round, four per lane, loads in flight together
-    for (uint32_t j0 = 0; j0 < od.y; j0 += 128) {
-      uint32_t w[4];
-#pragma unroll
-      for (int r = 0; r < 4; r++) {
-        const uint32_t j = j0 + 32u * r + lane;
-        w[r] = j < od.y ? __ldg(a.out_col + od.x + j) : kNoEntry;
-      }
-      bool unmarked = false;
-#pragma unroll
-      for (int r = 0; r < 4; r++)
-        if (w[r] != kNoEntry) unmarked = unmarked || !(ldcg(a.bitmap + (w[r] >> 5)) & (1u << (w[r] & 31)));
-      if (__any_sync(kFull, unmarked)) {
-        if (lane == 0) atomicOr(&a.ctl->xneed[slot], 1u);
-        return;
-      }
-    }
-  }
-}
-
-// Continuation of a split Dynamic Frontier call: the affected set has settled, so every
-// iteration sweeps the compacted sweep items left by the handing-off launch, with none of
-// the marking code (the same sweep as Static and Naive-dynamic, plus the expand-once test).
-// A vertex whose change exceeds tau_f for the first time is recorded; the launch then stops
-// after its iteration and a Dynamic Frontier launch resumes the call, expanding those
-// vertices (their marks join in the next iteration, as in a single launch).  Ranks, stamps
-// and lists are left for k_df_finish.
-template <bool F32>
-__global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank_cont(const RankArgs<F32> a) {
-  using S = Store<F32>;
-  using R = typename S::R;
-  using C = typename S::C;
-  using B = typename Num<F32>::B;
-  __shared__ uint32_t s_err;
-  __shared__ unsigned long long s_key[kWarps];
-  __shared__ uint32_t s_mbuf[kWarps][4 * kMarkBuf];
-  const uint32_t tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
-  RankCtl *ctl = a.ctl;
-  uint32_t epoch = 0;
-  uint32_t cnt[3], cmp_n[3];
-#pragma unroll
-  for (int bb = 0; bb < 3; bb++) {
-    cnt[bb] = ldcg(&ctl->save_cnt[bb]);
-    cmp_n[bb] = ldcg(&ctl->save_cmp[bb]);
-  }
-  const uint32_t total = cnt[0] + cnt[1] + cnt[2];
-  WarpBuf wb{s_mbuf[wib], {0u, 0u, 0u, 0u}, true, 0u};
-  Mass<F32> dacc;
-  uint32_t my_v = 0, my_e = 0;
-  uint32_t iters = (uint32_t)a.it0, status = kStatusCont;
-  uint32_t xfirst = 0;  // recorded expansions found to mark nothing (this launch)
-  bool converged = false;
-  unsigned long long last_key = 0;
-  for (int it = a.it0; it < a.max_iter; it++) {
-    const int par = it & 1;
-    if (blockIdx.x == 0 && tid == 0) {
-      ctl->it_aff[it] = total;
-      ctl->it_kind[it] = 5;
-    }
-    SweepIo<F32> io;
-    io.Rin = par ? a.R1 : a.R0;
-    io.Cin = par ? a.C1 : a.C0;
-    io.Rout = par ? a.R0 : a.R1;
-    io.Cout = par ? a.C0 : a.C1;
-    io.T = a.items_cmp;
-    io.n0 = cmp_n[0];
-    io.n1 = cmp_n[1];
-    io.n2 = cmp_n[2];
-    io.off1 = a.it_c0;
-    io.off2 = a.it_c0 + a.it_c1;
-    io.it = (uint32_t)it;
-    io.slot = (uint32_t)it + 1;
-    io.cnt[0] = cnt[0];
-    io.cnt[1] = cnt[1];
-    io.cnt[2] = cnt[2];
-    io.scan_all = false;
-    io.expand = a.mode != kModeDT;  // Dynamic Traversal marks nothing after its search
-    io.I.full = false;
-    io.I.tele = (R)0;
-    io.s_base = nullptr;
-    io.s_kmax = nullptr;
-    io.s_active = nullptr;
-    io.wb = &wb;
-    io.dacc = dacc;
-    io.my_max = 0;
-    sweep_tiers<F32, 2>(a, io);
-    my_v += io.my_v;
-    my_e += io.my_e;
-    unsigned long long m = Num<F32>::key(io.my_max);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(kFull, m, o));
-    if (lane == 0) s_key[wib] = m;
-    __syncthreads();
-    if (tid == 0) {
-      unsigned long long bm = 0;
-      for (int w = 0; w < kWarps; w++) bm = max(bm, s_key[w]);
-      if (bm) atomicMax(&ctl->dR_bits[it], bm);
-    }
-    if (!grid_sync(ctl, epoch, &s_err)) return;
-    const unsigned long long dR = __ldcg(&ctl->dR_bits[it]);
-    iters = (uint32_t)it + 1;
-    last_key = dR;
-    if (blockIdx.x == 0 && tid == 0) ctl->t_ns[it + 2] = globaltimer_ns();
-    if (dR <= a.tol_key) {
-      converged = true;
-      break;
-    }
-    const uint32_t nrec = ldcg(&ctl->xit[it + 1]);
-    if (nrec != 0 && it + 1 < a.max_iter) {
-      // resume the marking kernel only if some recorded expansion would mark a vertex
-      check_recorded(a, xfirst, nrec, (uint32_t)it + 1);
-      if (!grid_sync(ctl, epoch, &s_err)) return;
-      if (ldcg(&ctl->xneed[it + 1]) != 0) {
-        status = kStatusExpand;
-        break;
-      }
-      xfirst += nrec;
-    }
-  }
-  {
-    unsigned long long vals[2] = {my_v, my_e};
-    unsigned long long *dst[2] = {&ctl->vproc, &ctl->eproc};
-#pragma unroll
-    for (int k = 0; k < 2; k++) {
-      unsigned long long x = warp_sum(vals[k]);
-      if (lane == 0 && x) atomicAdd(dst[k], x);
-    }
-  }
-  if (blockIdx.x == 0 && tid == 0) {
-    ctl->iterations = iters;
-    ctl->converged = converged ? 1u : 0u;
-    ctl->last_key = last_key;
-    ctl->next_it = iters;
-    ctl->status = status;
-  }
-}
-
-// End of a split Dynamic Frontier call: both parities of every affected vertex take its
-// final values (parity iterations & 1) and the per-call marks are cleared.
-template <bool F32>
-__global__ void k_df_finish(const RankArgs<F32> a) {
-  using S = Store<F32>;
-  using R = typename S::R;
-  using C = typename S::C;
-  const RankCtl *ctl = a.ctl;
-  const bool fp = ldcg(&ctl->iterations) & 1;
-  const R *Rf = fp ? a.R1 : a.R0;
-  const C *Cf = fp ? a.C1 : a.C0;
-  R *Ro = fp ? a.R0 : a.R1;
-  C *Co = fp ? a.C0 : a.C1;
-  const uint32_t *lists[3] = {a.list0, a.list1, a.list2};
-  const uint32_t nthreads = gridDim.x * blockDim.x, gtid = blockIdx.x * blockDim.x + threadIdx.x;
-  for (int bb = 0; bb < 3; bb++) {
-    const uint32_t c = ldcg(&ctl->final_cnt[bb]);
-    for (uint32_t k = gtid; k < c; k += nthreads) {
-      const uint32_t v = ldcg(lists[bb] + k);
-      Ro[v] = ldcg(Rf + v);
-      Co[v] = ldcg(Cf + v);
-      a.bitmap[v >> 5] = 0u;
-      a.xbits[v >> 5] = 0u;
-      a.stamp[v] = kNoStamp;
-    }
-  }
-}
-
 #undef pol_cols
 #undef pol_c
 
@@ -1831,10 +1037,6 @@ static cudaError_t grid_blocks(int sm_count, size_t smem, int *blocks) {
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_df, k_rank<F32, true>, kRankBlock, smem);
   if (e != cudaSuccess) return e;
   per_sm = std::min(per_sm, per_sm_df);
-  int per_sm_cont = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_cont, k_rank_cont<F32>, kRankBlock, 0);
-  if (e != cudaSuccess) return e;
-  per_sm = std::min(per_sm, per_sm_cont);
   per_sm = std::max(1, std::min(per_sm, 4));
   *blocks = per_sm * sm_count;
   return cudaSuccess;
@@ -1851,7 +1053,7 @@ pr_status rank_setup(Graph *g) {
   CK(cudaMalloc((void **)&g->dpart, sizeof(DeadPart) * 2 * (size_t)blocks));
   CK(cudaEventCreate(&g->ev0));
   CK(cudaEventCreate(&g->ev1));
-  return PR_OK;
+  return sweep_setup(g);
 }
 
 // The full-sweep instance in Naive-dynamic mode on the arguments of a marking call whose
@@ -1862,8 +1064,6 @@ static cudaError_t launch_full_sweep(Graph *g, const RankArgs<F32> &a) {
   b.mode = (int)kModeNaive;
   b.start_full = 0;
   b.split = 0;
-  b.resume = 0;
-  b.it0 = 0;
   void *args[] = {(void *)&b};
   cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_rank<F32, false>, dim3(g->rank_grid), dim3(kRankBlock),
                                               args, rank_smem(g->ncomp), g->st);
@@ -1949,65 +1149,53 @@ static pr_status launch(Graph *g, RankMode mode, bool start_full) {
   a.comp_last = g->comp_last;
   a.dense_div = g->dense_div;
   a.xlist = g->xlist;
-  a.split = (mode == kModeDF || async || mode == kModeDT) && g->split_df && !g->use_graph && g->ncomp == 1 && !g->teleport && !start_full;
-  a.resume = 0;
-  a.it0 = 0;
-  void *args[] = {(void *)&a};
+  a.emap = g->emap;
+  a.item_pos = g->item_pos;
   const bool marking = mode == kModeDF || mode == kModeDT || async;
-  if (marking && start_full && !g->use_graph) {
-    // every vertex is affected from iteration 0 and nothing is ever marked: Naive-dynamic
-    CK(launch_full_sweep<F32>(g, a));
-    if (async) {
+  const bool loops = sweep_eligible(g);
+  a.split = marking && loops && g->split_df && !start_full;
+  // expected marks of a set of k vertices: k * m / n; deferring pays once they would make
+  // the next set dense (more than n / dense_div)
+  a.defer_at = (uint32_t)std::min<double>((double)g->n, (double)g->n * (double)g->n /
+                                                            ((double)g->dense_div * std::max<double>(1.0, (double)g->m)));
+  void *args[] = {(void *)&a};
+  auto copy_async_parity = [&]() -> pr_status {
+    if (async) {  // the second parity takes the in-place result
       CK(cudaMemcpyAsync(g->R[1], g->R[0], sizeof(typename S::R) * (size_t)g->n, cudaMemcpyDeviceToDevice, g->st));
       CK(cudaMemcpyAsync(g->C[1], g->C[0], sizeof(typename S::C) * (size_t)g->n, cudaMemcpyDeviceToDevice, g->st));
     }
     return PR_OK;
+  };
+  if (loops && (!marking || start_full)) {
+    // every vertex every iteration (Static; Naive-dynamic, also for a marking call whose
+    // affected set is all of V): per-iteration launches in a device-side loop
+    pr_status rc = sweep_full(g, mode == kModeStatic);
+    if (rc != PR_OK) return rc;
+    return copy_async_parity();
+  }
+  if (marking && start_full && !g->use_graph) {
+    // every vertex is affected from iteration 0 and nothing is ever marked: Naive-dynamic
+    CK(launch_full_sweep<F32>(g, a));
+    return copy_async_parity();
   }
   const void *fn = marking ? (const void *)k_rank<F32, true> : (const void *)k_rank<F32, false>;
   if (!g->use_graph) {
     CK(cudaLaunchCooperativeKernel(fn, dim3(g->rank_grid), dim3(kRankBlock), args,
                                    rank_smem(g->ncomp), g->st));
     count_launch();
-    // a split call: the host reads the status each launch leaves and starts the next one
-    // (continuation, resumed marking launch, or the final writeback); every launch restarts
-    // the grid-barrier count
-    for (int round = 0; a.split && round < 2 * kMaxIterLimit + 2; round++) {
+    if (a.split) {
+      // the marking launch stops once the affected set is dense (or, for Dynamic
+      // Traversal, after its search); the host reads the status it left and starts the
+      // per-iteration loop, or the full sweeps if every vertex turned out affected
       CK(cudaMemcpyAsync(g->ctl_h, g->ctl, offsetof(RankCtl, final_cnt), cudaMemcpyDeviceToHost, g->st));
       CK(cudaStreamSynchronize(g->st));
       const RankCtl &h = *g->ctl_h;
-      if (h.err) break;
-      if (h.status == kStatusFull) {
-        CK(cudaMemsetAsync(&g->ctl->bar, 0, sizeof(uint32_t), g->st));
-        CK(launch_full_sweep<F32>(g, a));
-        break;
-      }
-      if (h.status == kStatusHandoff || h.status == kStatusExpand) {
-        CK(cudaMemsetAsync(&g->ctl->bar, 0, sizeof(uint32_t), g->st));
-        if (h.status == kStatusHandoff) {
-          CK(cudaMemsetAsync(&g->ctl->xcnt, 0, sizeof(uint32_t), g->st));
-          a.resume = 0;
-        } else {
-          a.resume = 1;
-        }
-        a.it0 = (int)h.next_it;
-        const void *next = h.status == kStatusHandoff ? (const void *)k_rank_cont<F32> : (const void *)k_rank<F32, true>;
-        CK(cudaLaunchCooperativeKernel(next, dim3(g->rank_grid), dim3(kRankBlock), args,
-                                       h.status == kStatusHandoff ? 0 : rank_smem(g->ncomp), g->st));
-        count_launch();
-      } else {
-        if (h.status == kStatusCont) {
-          k_df_finish<F32><<<g->sm_count * 8, 256, 0, g->st>>>(a);
-          count_launch();
-          CK(cudaGetLastError());
-        }
-        break;
-      }
+      pr_status rc = PR_OK;
+      if (!h.err && h.status == kStatusFull) rc = sweep_full(g, false);
+      else if (!h.err && h.status == kStatusDense) rc = sweep_dense(g, mode, &a);
+      if (rc != PR_OK) return rc;
     }
-    if (async) {  // the second parity takes the in-place result
-      CK(cudaMemcpyAsync(g->R[1], g->R[0], sizeof(typename S::R) * (size_t)g->n, cudaMemcpyDeviceToDevice, g->st));
-      CK(cudaMemcpyAsync(g->C[1], g->C[0], sizeof(typename S::C) * (size_t)g->n, cudaMemcpyDeviceToDevice, g->st));
-    }
-    return PR_OK;
+    return copy_async_parity();
   }
   // CUDA-graph launch: the control-block reset, the event records and the cooperative
   // kernel are captured once; later calls only replace the kernel's arguments and replay
@@ -2076,7 +1264,11 @@ pr_status rank_run(Graph *g, RankMode mode, pr_stats *stats) {
   CK(cudaMemcpyAsync(g->ctl_h, g->ctl, offsetof(RankCtl, dR_bits), cudaMemcpyDeviceToHost, g->st));
   CK(cudaMemcpyAsync(&g->ctl_h->vproc, &g->ctl->vproc, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                      g->st));
+  // the per-iteration loop's state (launch count, whether it ran, its affected count)
+  CK(cudaMemcpyAsync(&g->ctl_h->ticket, &g->ctl->ticket, offsetof(RankCtl, eprev) - offsetof(RankCtl, ticket),
+                     cudaMemcpyDeviceToHost, g->st));
   CK(cudaStreamSynchronize(g->st));
+  count_launches(g->ctl_h->launches);
   const RankCtl &h = *g->ctl_h;
   if (h.err) {
     g->err = "rank kernel: a grid barrier wait timed out";
@@ -2103,7 +1295,13 @@ pr_status rank_run(Graph *g, RankMode mode, pr_stats *stats) {
   }
   const bool full = !marking || start_full || h.full_from != 0;
   g->last_full = full;
-  for (int b = 0; b < 3; b++) g->last_list_cnt[b] = marking ? h.final_cnt[b] : 0;
+  uint32_t fcnt[3] = {h.final_cnt[0], h.final_cnt[1], h.final_cnt[2]};
+  if (h.dense_ran) {
+    // the per-iteration loop's writeback listed the whole affected set in list 0
+    fcnt[0] = h.aff_total;
+    fcnt[1] = fcnt[2] = 0;
+  }
+  for (int b = 0; b < 3; b++) g->last_list_cnt[b] = marking ? fcnt[b] : 0;
   g->n_pend_src = 0;
   g->n_pend_tgt = 0;
   g->pend_all = false;
@@ -2139,8 +1337,7 @@ pr_status rank_run(Graph *g, RankMode mode, pr_stats *stats) {
     else last = (double)h.last_key / kOne62;
     stats->iterations = (int32_t)h.iterations;
     stats->converged = all_conv ? 1 : 0;
-    stats->affected_final =
-        full ? (int64_t)g->n : (int64_t)h.final_cnt[0] + h.final_cnt[1] + h.final_cnt[2];
+    stats->affected_final = full ? (int64_t)g->n : (int64_t)fcnt[0] + fcnt[1] + fcnt[2];
     stats->vertices_processed = (int64_t)h.vproc;
     stats->edges_processed = (int64_t)h.eproc;
     stats->bytes_algorithmic = vb * (double)h.vproc + eb * (double)h.eproc + 8.0 * (double)h.expv +
@@ -2200,6 +1397,91 @@ __global__ void k_dead_mass(const uint32_t *dead, uint32_t n_dead, const typenam
     *out_d = td;
     *out_n = tn;
   }
+}
+
+// Validation of ranks a caller sets: every value finite and >= 0, and their sum at most
+// 1 + 1e-6 (ranks are a probability distribution; the 64-bit fixed point holds values below
+// 2, and with sum <= 1 no in-edge sum can reach that).  out[0] = bad values, out[1] = sum
+// (as bits of a double; the sum is exact enough for the bound).
+__global__ void k_check_ranks(const double *in, uint32_t n, unsigned long long *out) {
+  __shared__ double s_sum[8];
+  __shared__ uint32_t s_bad[8];
+  double sum = 0.0;
+  uint32_t bad = 0;
+  const uint32_t nthreads = gridDim.x * blockDim.x;
+  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += nthreads) {
+    const double x = in[v];
+    if (!(x >= 0.0) || !(x <= 2.0)) bad++;  // NaN, negative, or beyond the representable range
+    else sum += x;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    bad += __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    s_sum[threadIdx.x >> 5] = sum;
+    s_bad[threadIdx.x >> 5] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    uint32_t b = 0;
+    for (int w = 0; w < 8; w++) {
+      t += s_sum[w];
+      b += s_bad[w];
+    }
+    if (b) atomicAdd(out, (unsigned long long)b);
+    atomicAdd(reinterpret_cast<double *>(out + 1), t);
+  }
+}
+
+pr_status rank_check(Graph *g, const double *in_d) {
+  if (g->ncomp > 1) {
+    // batched handle: each graph's ranks are a distribution of their own
+    std::vector<double> h(g->n);
+    CK(cudaMemcpyAsync(h.data(), in_d, sizeof(double) * g->n, cudaMemcpyDeviceToHost, g->st));
+    CK(cudaStreamSynchronize(g->st));
+    for (uint32_t c = 0; c < g->ncomp; c++) {
+      double sum = 0.0;
+      for (uint32_t v = g->comp_first[c]; v < g->comp_first[c + 1]; v++) {
+        const double x = h[v];
+        if (!(x >= 0.0) || !(x <= 2.0)) {
+          g->err = "ranks must be finite and in [0, 2]";
+          return PR_ERR_INVALID_ARG;
+        }
+        sum += x;
+      }
+      if (!(sum <= 1.0 + 1e-6)) {
+        g->err = "the ranks of each graph must sum to at most 1 (a probability distribution)";
+        return PR_ERR_INVALID_ARG;
+      }
+    }
+    return PR_OK;
+  }
+  unsigned long long *dv = nullptr, hv[2] = {0, 0};
+  CK(cudaMalloc((void **)&dv, sizeof(hv)));
+  cudaError_t e = cudaMemsetAsync(dv, 0, sizeof(hv), g->st);
+  if (e == cudaSuccess) {
+    const unsigned grid = (unsigned)std::max(1, std::min((int)((g->n + 255) / 256), g->sm_count * 8));
+    k_check_ranks<<<grid, 256, 0, g->st>>>(in_d, g->n, dv);
+    count_launch();
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hv, dv, sizeof(hv), cudaMemcpyDeviceToHost, g->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+  cudaFree(dv);
+  if (e != cudaSuccess) return cuda_fail(g, e, "check ranks");
+  double sum = 0.0;
+  std::memcpy(&sum, &hv[1], sizeof(double));
+  if (hv[0] != 0) {
+    g->err = "ranks must be finite and in [0, 2]";
+    return PR_ERR_INVALID_ARG;
+  }
+  if (!(sum <= 1.0 + 1e-6)) {
+    g->err = "ranks must sum to at most 1 (a probability distribution)";
+    return PR_ERR_INVALID_ARG;
+  }
+  return PR_OK;
 }
 
 pr_status rank_set(Graph *g, const double *in_d) {

@@ -177,7 +177,7 @@ def test_dt_fp32(prdf):
 def test_dt_beyond_the_round_limit_iterates_as_naive(prdf, split):
     """A search deeper than the round limit takes all of V, so the iterations are exactly
     Naive-dynamic's from the same ranks (bit for bit in 64-bit mode); with split calls they
-    run in the full-sweep instance."""
+    run in the same per-iteration full sweeps as Naive-dynamic."""
     n = 1300
     src = np.arange(n - 1, dtype=np.uint32)
     dst = src + 1
@@ -197,4 +197,8 @@ def test_dt_beyond_the_round_limit_iterates_as_naive(prdf, split):
                 assert dg.affected().shape[0] == n
     (r_dt, it_dt, l_dt), (r_nv, it_nv, l_nv) = out
     assert np.array_equal(r_dt, r_nv) and it_dt == it_nv
-    assert l_dt - l_nv == (1 if split else 0)  # the marking launch that ran the search
+    # Naive-dynamic: the per-iteration loop (one launch per iteration, its init and
+    # writeback) after the same refresh launches; split: the marking launch that ran the
+    # search, then the same loop; otherwise the search and the iterations in that one launch
+    refresh = l_nv - it_nv - 2
+    assert l_dt - refresh == (1 + it_nv + 2 if split else 1), (l_dt, l_nv, it_nv)

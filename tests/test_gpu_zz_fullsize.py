@@ -2,8 +2,13 @@
 benchmark's graph), batches of the benchmark's stream, in the launch configuration the
 benchmark times (default grid, bins and split calls).
 
-The oracle cannot run Algorithm 1 on 69 M edges within a test, so these tests check, on
-every vertex, what holds at any size:
+Element by element against the oracle: Static PageRank from 1/n, then Dynamic Frontier
+updates at f = 1e-7 and 1e-3 |E| chained from the oracle's own ranks, in 64-bit mode
+(L-inf <= 1e-9) and FP32 (<= 1e-6), affected sets within 1% of the oracle's.  The oracle
+runs in a spawned process on all host cores (its -fopenmp build, which equals the
+sequential build bit for bit), about a minute in all.
+
+Besides, on every vertex, what holds at any size:
 
 * the CSR after an update equals the set semantics of Section 3.2 (bit for bit, built on
   the host with numpy);
@@ -15,10 +20,13 @@ every vertex, what holds at any size:
 * Dynamic Traversal marks exactly the vertices reachable from a changed edge's source in
   G^{t-1} or G^t (breadth-first search on the host with scipy).
 """
+import multiprocessing as mp
+
 import numpy as np
 import pytest
 
 import __graft_entry__
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -211,3 +219,66 @@ def test_fullsize_fp32_and_async_against_64bit(prdf, big):
         R = A.ranks()
         assert np.max(np.abs(F.ranks() - R)) <= 1e-6
         assert np.max(np.abs(S.ranks() - R)) <= 2e-9
+
+
+FULL_FRACS = (1e-7, 1e-3)
+
+
+def _oracle_chain(q):
+    """Oracle results for the full-size parity test (in a spawned process): Static ranks,
+    then each batch of FULL_FRACS from the benchmark's stream, chained."""
+    oracle.use_threads(oracle.host_cores())
+    g = synth.rmat(22, 16, seed=1)
+    G = oracle.Graph.build(g.n, g.src, g.dst)
+    R, st = oracle.static_pr(G)
+    out = {"static": (R.copy(), st.iterations), "threads": oracle.threads()}
+    s = synth.BatchStream(g, seed=1)
+    for f in FULL_FRACS:
+        b = s.next(f)
+        H, ed, ei = G.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+        Rn, aff, st = oracle.df_sync(G, H, ed, ei, R)
+        out[f] = (R.copy(), Rn.copy(), np.flatnonzero(aff).astype(np.uint32), st.iterations)
+        G.close()
+        G, R = H, Rn
+    q.put(out)
+
+
+@pytest.fixture(scope="module")
+def oracle_full():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    p = ctx.Process(target=_oracle_chain, args=(q,))
+    p.start()
+    try:
+        res = q.get(timeout=1800)
+    finally:
+        p.join(timeout=60)
+    return res
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_fullsize_against_oracle(prdf, big, oracle_full, prec):
+    g, _ = big
+    tol = 1e-6 if prec == "f32" else 1e-9
+    p = prdf.pr_params_default()
+    if prec == "f32":
+        p.precision = prdf.PR_F32
+    s = synth.BatchStream(g, seed=1)
+    with prdf.Graph(g.n, g.src, g.dst, p) as dg:
+        st = dg.static()
+        R_or, it_or = oracle_full["static"]
+        assert st.converged
+        assert np.max(np.abs(dg.ranks() - R_or)) <= tol
+        for f in FULL_FRACS:
+            b = s.next(f)
+            R_prev, R_df, aff_or, it_df = oracle_full[f]
+            dg.set_ranks(R_prev)
+            dg.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+            st = dg.frontier()
+            R = dg.ranks()
+            err = float(np.max(np.abs(R - R_df)))
+            assert st.converged and err <= tol, (f, err)
+            assert abs(st.iterations - it_df) <= 1, (f, st.iterations, it_df)
+            got = np.sort(dg.affected().astype(np.int64))
+            diff = np.setxor1d(got, aff_or.astype(np.int64)).shape[0]
+            assert diff <= max(2, 0.01 * aff_or.shape[0]), (f, diff, aff_or.shape[0])
