@@ -2,7 +2,7 @@
 """Dynamic Frontier PageRank benchmark on one GB300 (or N replicas, one per GPU).
 
 Workload: directed R-MAT scale 22, edge factor 16 (a, b, c, d = 0.57, 0.19, 0.19,
-0.05, duplicates removed, self-loops added), FP64 ranks, and a batch-size sweep of
+0.05, duplicates removed, self-loops added), 64-bit ranks, and a batch-size sweep of
 uniformly random 80/20 insertion/deletion batches of 1e-7 ... 1e-3 |E| (Section 5.1.4).
 
 One step = for every batch size f: apply one batch to the device-resident graph, bring
@@ -11,14 +11,20 @@ same snapshot with Naive-dynamic (from the previous ranks) and Static (from 1/n)
 paper's comparators (Section 5.2), then continue the chain from the DF ranks.
 
 value = geometric mean over f of the mean DF update time (CUDA events on the library's
-stream around the rank kernel: marking, iterations and convergence detection, as timed
-in Section 5.1.5; graph update excluded and reported as apply_ms).  e2e = the same per
-update measured on the host around the public C-ABI calls with pinned host buffers:
+stream around the rank computation: marking, iterations and convergence detection, as
+timed in Section 5.1.5; graph update excluded and reported as apply_ms).  e2e = the same
+per update measured on the host around the public C-ABI calls with pinned host buffers:
 pr_apply_batch (host batch -> device), pr_dynamic_frontier, pr_get_ranks (all n ranks
 device -> host).  L2 is flushed (256 MB write) before every timed call.
 
---impl reference times the FP64 sequential oracle (Algorithm 1, synchronous) on the
-host cores on the same workload, one update per step.
+The default run adds, after the timed region: the FP32 chain; the oracle (FP64, Algorithm
+1) timed on all host cores and on one core (cpu_baseline), with the GPU replaying its
+updates from its own previous ranks (parity: L-inf per f, 64-bit and FP32); the serving
+form at the configured and at a lower offered rate; the batched form; the precision form
+(config 3) against the oracle.  --no-legs keeps the headline, FP32 chain and parity only.
+
+--impl reference times the oracle (FP64, Algorithm 1, synchronous) on the host cores on
+the same workload, one update per step.
 """
 from __future__ import annotations
 
@@ -110,39 +116,150 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ CPU baseline ----
+# The oracle (plain FP64 C of Algorithm 1) runs in spawned processes while the GPU works:
+# first its -fopenmp build on every host core (the timed CPU baseline, and the expected
+# values of the parity leg), then, side by side, its sequential build on one core (a
+# one-update sample) and the expected values of the precision form on the other cores.
 
-def oracle_sample(scale: int, ef: int, seed: int, fracs, q=None):
-    """Times the FP64 sequential oracle's Dynamic Frontier update (Algorithm 1, sync) on
-    one batch per fraction, chained from the oracle's own Static ranks.  1 core."""
+PREC_FRACS = [1e-5, 1e-3]
+
+
+def precision_shapes(rank: int):
+    """Config 3's graphs: (name, generator) pairs."""
+    import synth
+
+    return [("kronecker s24 ef16", lambda: synth.rmat(24, 16, seed=11 + rank)),
+            ("grid 4900x4900 + 1% long-range", lambda: synth.grid(4900, 4900, 0.01, seed=12 + rank))]
+
+
+def _oracle_part(kind, scale, ef, seed, fracs, rank, cores, tmpdir, q):
+    """One oracle job in its own process (the build, sequential or threaded, is per process)."""
+    import numpy as np
+
     import oracle
     import synth
 
-    oracle.build()
-    t_setup = time.perf_counter()
-    g = synth.rmat(scale, ef, seed=seed)
-    G = oracle.Graph.build(g.n, g.src, g.dst)
-    R, _ = oracle.static_pr(G)
-    s = synth.BatchStream(g, seed=seed)
-    setup_s = time.perf_counter() - t_setup
-    per = {}
-    for f in fracs:
-        b = s.next(f)
-        H, ed, ei = G.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
-        t = time.perf_counter()
-        R, _, st = oracle.df_sync(G, H, ed, ei, R)
-        per[f] = (time.perf_counter() - t) * 1e3
-        G = H
-    res = {"per_frac_ms": per, "setup_s": setup_s}
-    if q is not None:
-        q.put(res)
-    return res
-
-
-def _cpu_worker(scale, ef, seed, fracs, q):
     try:
-        oracle_sample(scale, ef, seed, fracs, q)
+        threads = oracle.use_threads(cores)
+        if kind == "headline":
+            t0 = time.perf_counter()
+            g = synth.rmat(scale, ef, seed=seed)
+            G = oracle.Graph.build(g.n, g.src, g.dst)
+            t1 = time.perf_counter()
+            R, st = oracle.static_pr(G)
+            static_ms = (time.perf_counter() - t1) * 1e3
+            np.save(os.path.join(tmpdir, "R_static.npy"), R)
+            s = synth.BatchStream(g, seed=seed)
+            per, its, aff = {}, {}, {}
+            for k, f in enumerate(fracs):
+                b = s.next(f)
+                H, ed, ei = G.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+                t = time.perf_counter()
+                Rn, a, st = oracle.df_sync(G, H, ed, ei, R)
+                per[f] = (time.perf_counter() - t) * 1e3
+                its[f] = st.iterations
+                np.save(os.path.join(tmpdir, f"R_df_{k}.npy"), Rn)
+                np.save(os.path.join(tmpdir, f"aff_{k}.npy"), np.flatnonzero(a).astype(np.uint32))
+                aff[f] = int(a.sum())
+                G.close()
+                G, R = H, Rn
+            q.put(("headline", {"per_frac_ms": per, "iterations": its, "affected": aff, "static_ms": static_ms,
+                                "setup_s": t1 - t0, "threads": threads}))
+        elif kind == "sequential":
+            g = synth.rmat(scale, ef, seed=seed)
+            G = oracle.Graph.build(g.n, g.src, g.dst)
+            R = np.load(os.path.join(tmpdir, "R_static.npy"))
+            b = synth.BatchStream(g, seed=seed).next(fracs[0])
+            H, ed, ei = G.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+            t = time.perf_counter()
+            oracle.df_sync(G, H, ed, ei, R)
+            q.put(("sequential", {"f": fracs[0], "ms": (time.perf_counter() - t) * 1e3, "threads": threads}))
+        elif kind == "precision":
+            out = {}
+            for si, (name, make) in enumerate(precision_shapes(rank)):
+                g = make()
+                G = oracle.Graph.build(g.n, g.src, g.dst)
+                del g
+                R, _ = oracle.static_pr(G)
+                np.save(os.path.join(tmpdir, f"p{si}_static.npy"), R)
+                g = make()
+                s = synth.BatchStream(g, seed=13 + rank)
+                del g
+                its = {}
+                for k, f in enumerate(PREC_FRACS):
+                    b = s.next(f)
+                    H, ed, ei = G.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+                    Rn, _, st = oracle.df_sync(G, H, ed, ei, R)
+                    its[f] = st.iterations
+                    np.save(os.path.join(tmpdir, f"p{si}_df_{k}.npy"), Rn)
+                    G.close()
+                    G, R = H, Rn
+                G.close()
+                out[name] = {"iterations": its}
+            q.put(("precision", {"shapes": out, "threads": threads}))
     except Exception as e:  # reported, not fatal
-        q.put({"error": repr(e)})
+        q.put((kind, {"error": repr(e)}))
+
+
+def _oracle_chain(scale, ef, seed, fracs, rank, jobs, tmpdir, q):
+    """The threaded headline job on every core, then the sequential sample on one core
+    beside the precision job on the rest (jobs: which of the three to run)."""
+    ctx = mp.get_context("spawn")
+    import oracle
+
+    cores = oracle.host_cores()
+    if "headline" in jobs:
+        pa = ctx.Process(target=_oracle_part, args=("headline", scale, ef, seed, fracs, rank, cores, tmpdir, q))
+        pa.start()
+        pa.join()
+    both = "sequential" in jobs and "precision" in jobs
+    procs = []
+    if "sequential" in jobs:
+        procs.append(ctx.Process(target=_oracle_part, args=("sequential", scale, ef, seed, fracs, rank, 1, tmpdir, q)))
+    if "precision" in jobs:
+        procs.append(ctx.Process(target=_oracle_part, args=("precision", scale, ef, seed, fracs, rank,
+                                                             max(1, cores - 1) if both else cores, tmpdir, q)))
+    for j in procs:
+        j.start()
+    for j in procs:
+        j.join()
+    q.put(("done", None))
+
+
+def start_oracle(args, rank, jobs):
+    """Spawns the oracle chain (before the first GPU call); returns its results handle."""
+    ctx = mp.get_context("spawn")
+    tmpdir = tempfile.mkdtemp(prefix="prdf_oracle_")
+    q = ctx.Queue()
+    proc = ctx.Process(target=_oracle_chain, args=(args.scale, args.ef, 1, FRACS, rank, jobs, tmpdir, q))
+    proc.start()
+    return OracleResults(q, proc, tmpdir)
+
+
+class OracleResults:
+    """Messages of the oracle chain, collected as they arrive."""
+
+    def __init__(self, q, proc, tmpdir):
+        self.q, self.proc, self.dir, self.res = q, proc, tmpdir, {}
+
+    def wait(self, kind, timeout):
+        t_end = time.time() + timeout
+        while kind not in self.res and "done" not in self.res:
+            try:
+                k, v = self.q.get(timeout=max(0.1, t_end - time.time()))
+            except Exception:
+                break
+            self.res[k] = v
+        return self.res.get(kind)
+
+    def close(self):
+        import shutil
+
+        if self.proc is not None:
+            self.proc.join(timeout=5)
+            if self.proc.is_alive():
+                self.proc.terminate()
+        shutil.rmtree(self.dir, ignore_errors=True)
 
 
 # --------------------------------------------------------- multi-GPU runs ----
@@ -164,17 +281,316 @@ def max_over_ranks(values, device):
     return t.tolist()
 
 
+# ------------------------------------------------------------- legs ----
+# Each leg returns a dict for the default line (and serves its --config run).
+
+def _leg(fn, *a, **kw):
+    """A leg of the default run; a failure is reported in its key, not fatal to the line."""
+    try:
+        return fn(*a, **kw)
+    except Exception as e:
+        import traceback
+
+        traceback.print_exc()
+        return {"error": repr(e)}
+
+
+def parity_leg(args, g, dev, stream, res, tmpdir):
+    """The oracle's chain of updates replayed on the GPU from the oracle's own previous
+    ranks (64-bit and FP32 handles): L-inf of the ranks and the affected-set difference per
+    f, after Static from 1/n."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2401_03256_gb300 import prdf
+
+    out = {"linf_vs_oracle": {}, "fp32_linf_vs_oracle": {}, "affected_symdiff": {}, "affected_oracle": {},
+           "iterations": {}, "iterations_oracle": {}}
+    R0 = np.load(os.path.join(tmpdir, "R_static.npy"))
+    p32 = prdf.pr_params_default()
+    p32.precision = prdf.PR_F32
+    with torch.cuda.stream(stream):
+        A = prdf.Graph(g.n, g.src, g.dst, None, stream.cuda_stream)
+        F = prdf.Graph(g.n, g.src, g.dst, p32, stream.cuda_stream)
+        A.static()
+        F.static()
+        out["static_linf_vs_oracle"] = float(np.max(np.abs(A.ranks() - R0)))
+        out["fp32_static_linf_vs_oracle"] = float(np.max(np.abs(F.ranks() - R0)))
+        s = synth.BatchStream(g, seed=1)
+        R_prev = R0
+        for k, f in enumerate(FRACS):
+            b = s.next(f)
+            R_df = np.load(os.path.join(tmpdir, f"R_df_{k}.npy"))
+            aff = np.load(os.path.join(tmpdir, f"aff_{k}.npy")).astype(np.int64)
+            for h in (A, F):
+                h.set_ranks(R_prev)
+                h.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+            st = A.frontier()
+            F.frontier()
+            key = f"{f:g}"
+            out["linf_vs_oracle"][key] = float(np.max(np.abs(A.ranks() - R_df)))
+            out["fp32_linf_vs_oracle"][key] = float(np.max(np.abs(F.ranks() - R_df)))
+            out["affected_symdiff"][key] = int(np.setxor1d(A.affected().astype(np.int64), aff).shape[0])
+            out["affected_oracle"][key] = int(aff.shape[0])
+            out["iterations"][key] = st.iterations
+            out["iterations_oracle"][key] = res["iterations"][f]
+            R_prev = R_df
+        A.close()
+        F.close()
+    out["bound"] = {"fp64_mode": 1e-9, "fp32": 1e-6}
+    return out
+
+
+def serving_leg(args, dev, g22, rank, rates, duration=None, gcache=None):
+    """Serving form (config 5): 8 resident R-MAT graphs (scales 18, 18, 19, 20, 21, 22, 23,
+    24, edge factor 16, FP32 ranks), Poisson arrivals, target graph uniform, batch f ~
+    log-uniform [1e-7, 1e-3] of that graph's edges (80/20), admission by slots and free
+    HBM, continuous batching of each graph's queue.  One run per offered rate: the
+    configured rate (queueing once the largest graphs saturate) and a rate below it, where
+    latency is service time."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2401_03256_gb300 import prdf
+
+    duration = duration or args.serve_duration
+    scales = [int(x) for x in args.serve_scales.split(",")]
+    gcache = {} if gcache is None else gcache
+
+    def make(i, s):
+        if s == 22 and g22 is not None and g22.n == 1 << 22:
+            return g22  # the headline graph
+        if s == 24:  # the precision form's Kronecker graph, generated once for both
+            if "kron24" not in gcache:
+                gcache["kron24"] = precision_shapes(rank)[0][1]()
+            return gcache["kron24"]
+        return synth.rmat(s, 16, seed=500 + 10 * rank + i)
+
+    gs = [make(i, s) for i, s in enumerate(scales)]
+    params = prdf.pr_params_default()
+    params.precision = prdf.PR_F32
+    streams = [torch.cuda.Stream(device=dev) for _ in gs]
+    hs = [prdf.Graph(g.n, g.src, g.dst, params, st.cuda_stream) for g, st in zip(gs, streams)]
+    for h in hs:
+        h.static()
+    out = {"config": {"graphs": [f"R-MAT s{s} ef16" for s in scales], "slots": args.slots,
+                      "max_coalesce": args.coalesce, "precision": "fp32", "duration_s": duration,
+                      "batch": "f ~ logU[1e-7, 1e-3] of the target graph's edges, 80/20"}}
+    for ri, rate in enumerate(rates):
+        rng = np.random.default_rng(1 + rank + 7 * ri)
+        bstreams = [synth.BatchStream(g, seed=900 + 31 * ri + i) for i, g in enumerate(gs)]
+        nreq = max(1, int(rate * duration))
+        warm = 2 * len(gs)
+        targets = rng.integers(0, len(gs), nreq + warm)
+        fr = np.exp(rng.uniform(np.log(1e-7), np.log(1e-3), nreq + warm))
+        batches = [bstreams[t].next(float(f), apply=False) for t, f in zip(targets, fr)]
+        gaps = rng.exponential(1.0 / rate, nreq)
+        srv = prdf.Server(slots=args.slots, max_coalesce=args.coalesce, hbm_reserve_bytes=1 << 30)
+        idx = [srv.add(h) for h in hs]
+        for k in range(warm):
+            b = batches[k]
+            srv.submit(idx[targets[k]], b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+        srv.drain()
+        tickets = []
+        t0 = time.perf_counter()
+        due = t0
+        for k in range(nreq):
+            due += gaps[k]
+            while True:
+                now = time.perf_counter()
+                if now >= due:
+                    break
+                if due - now > 2e-4:
+                    time.sleep((due - now) * 0.5)
+            b = batches[warm + k]
+            tickets.append(srv.submit(idx[targets[warm + k]], b.del_src, b.del_dst, b.ins_src, b.ins_dst))
+        info = srv.drain()
+        res = [srv.wait(t) for t in tickets]
+        srv.close()
+        lat = np.array([r.t_done_ms - r.t_submit_ms for r in res])
+        svc = np.array([r.t_done_ms - r.t_start_ms for r in res])
+        span_ms = max(r.t_done_ms for r in res) - min(r.t_submit_ms for r in res)
+        out[f"rate_{rate:g}"] = {
+            "offered_per_s": rate, "requests": nreq, "ok": sum(1 for r in res if r.status == prdf.PR_OK),
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "service_p50_ms": float(np.percentile(svc, 50)), "service_p99_ms": float(np.percentile(svc, 99)),
+            "updates_per_s": nreq / (span_ms * 1e-3), "coalesced_mean": float(np.mean([r.coalesced for r in res])),
+            "waited_for_memory": info.waited_for_memory}
+    for h in hs:
+        h.close()
+    first = out[f"rate_{rates[0]:g}"]
+    out["p50_ms"], out["p99_ms"], out["updates_per_s"] = first["p50_ms"], first["p99_ms"], first["updates_per_s"]
+    return out
+
+
+def batched_leg(args, dev, rank, W=1, K=2, graphs=None):
+    """Batched form (config 4): 256 independent R-MAT graphs (scales uniform in 10..18, edge
+    factor 8), each with its own 80/20 batch of f ~ log-uniform [1e-4, 1e-2] of its edges;
+    one pr_apply_batch for all graphs and one Dynamic Frontier launch (CUDA-graph replay,
+    autotuned bins), FP32 ranks; against the same updates through standalone handles called
+    one after another."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2401_03256_gb300 import prdf
+
+    rng = np.random.default_rng(1 + rank)
+    Gn = graphs or args.graphs
+    scales = rng.integers(10, 19, Gn)
+    gs = [synth.rmat(int(s), 8, seed=1000 * (1 + rank) + i) for i, s in enumerate(scales)]
+    fr = np.exp(rng.uniform(np.log(1e-4), np.log(1e-2), Gn))
+    firsts = np.cumsum([0] + [g.n for g in gs])
+    src = np.concatenate([g.src.astype(np.uint64) + firsts[i] for i, g in enumerate(gs)]).astype(np.uint32)
+    dst = np.concatenate([g.dst.astype(np.uint64) + firsts[i] for i, g in enumerate(gs)]).astype(np.uint32)
+    params = prdf.pr_params_default()
+    params.precision = prdf.PR_F32 if args.precision != "fp64" or args.config == "plain" else prdf.PR_F64
+    streams = [synth.BatchStream(g, seed=77 + i) for i, g in enumerate(gs)]
+    steps = []
+    for _ in range(W + K):
+        bs = [s.next(float(fr[i])) for i, s in enumerate(streams)]
+        off = lambda a, i: (a.astype(np.uint64) + firsts[i]).astype(np.uint32)
+        comb = [np.concatenate([off(getattr(b, k), i) for i, b in enumerate(bs)])
+                for k in ("del_src", "del_dst", "ins_src", "ins_dst")]
+        steps.append((bs, comb))
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        B = prdf.Graph.batched([g.n for g in gs], src, dst, params, stream.cuda_stream)
+        tune = B.autotune(6)
+        B.set_graph_launch(True)
+        B.static()
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+        times, dfms, apms, iters = [], [], [], []
+        l0 = None
+        for i in range(W + K):
+            if i == W:
+                torch.cuda.synchronize(dev)
+                l0 = prdf.pr_kernel_launches()
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            t = time.perf_counter()
+            B.apply(*steps[i][1])
+            st = B.frontier()
+            torch.cuda.synchronize(dev)
+            if i >= W:
+                times.append((time.perf_counter() - t) * 1e3)
+                dfms.append(st.ms_rank)
+                apms.append(st.ms_apply)
+                iters.append(max(c.iterations for c in B.component_stats()))
+        launches = prdf.pr_kernel_launches() - l0
+        B.close()
+        As = [prdf.Graph(g.n, g.src, g.dst, params, stream.cuda_stream) for g in gs]
+        for A in As:
+            A.static()
+        seq = []
+        for i in range(W + K):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            t = time.perf_counter()
+            for j, A in enumerate(As):
+                b = steps[i][0][j]
+                A.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+                A.frontier()
+            torch.cuda.synchronize(dev)
+            if i >= W:
+                seq.append((time.perf_counter() - t) * 1e3)
+        for A in As:
+            A.close()
+    value = statistics.median(times)
+    return {"ms": value, "df_ms": statistics.median(dfms), "apply_ms": statistics.median(apms),
+            "sequential_ms": statistics.median(seq), "speedup_vs_sequential": statistics.median(seq) / value,
+            "max_graph_iterations": max(iters), "gpu_launches": launches, "steps": K, "warmup": W,
+            "config": {"workload": f"{Gn} R-MAT graphs, scales U{{10..18}}, edge factor 8, own 80/20 batch of "
+                                   f"f ~ logU[1e-4, 1e-2] each", "vertices": int(firsts[-1]), "edges": int(src.size),
+                       "precision": "fp32" if params.precision == prdf.PR_F32 else "fp64",
+                       "launch": "CUDA graph replay", "tuning": tune.as_dict()}}
+
+
+def precision_leg(args, dev, rank, orc=None, gcache=None):
+    """Precision form (config 3): FP32 ranks and contributions (FP64 compensated dead-end
+    mass) on a Kronecker scale-24 graph (edge factor 16) and on a 4900 x 4900 directed grid
+    with 1% random long-range arcs; one 80/20 batch of 1e-5 |E|, then one of 1e-3 |E|,
+    chained.  Every update starts from the oracle's previous ranks (when the oracle ran) in
+    an FP32 and a 64-bit handle; errors are L-inf against the oracle's result."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2401_03256_gb300 import prdf
+
+    ores = orc.wait("precision", args.cpu_timeout) if orc is not None else None
+    have = bool(ores) and "shapes" in ores
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    out = {"error_reference": "FP64 oracle (Algorithm 1), same previous ranks" if have else "64-bit path",
+           "oracle_note": None if have else (ores or {}).get("error", "oracle not run")}
+    gcache = {} if gcache is None else gcache
+    for si, (name, make) in enumerate(precision_shapes(rank)):
+        g = gcache.pop("kron24", None) if si == 0 else None
+        g = g if g is not None else make()
+        p32 = prdf.pr_params_default()
+        p32.precision = prdf.PR_F32
+        with torch.cuda.stream(stream):
+            A = prdf.Graph(g.n, g.src, g.dst, p32, stream.cuda_stream)
+            B = prdf.Graph(g.n, g.src, g.dst, None, stream.cuda_stream)
+            n, m = A.info()
+            st32 = A.static()
+            st64 = B.static()
+            R32, R64 = A.ranks(), B.ranks()
+            entry = {"n": n, "m_with_self_loops": m, "static_fp32_ms": st32.ms_rank, "static_fp64_ms": st64.ms_rank,
+                     "per_frac": {}}
+            if have:
+                R0 = np.load(os.path.join(orc.dir, f"p{si}_static.npy"))
+                entry["static_fp32_linf_vs_oracle"] = float(np.max(np.abs(R32 - R0)))
+                entry["static_fp64_linf_vs_oracle"] = float(np.max(np.abs(R64 - R0)))
+                R_prev = R0
+            else:
+                entry["static_fp32_linf_vs_fp64"] = float(np.max(np.abs(R32 - R64)))
+                R_prev = R64
+            s = synth.BatchStream(g, seed=13 + rank)
+            for k, f in enumerate(PREC_FRACS):
+                b = s.next(f)
+                for h in (A, B):
+                    h.set_ranks(R_prev)
+                    h.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+                flush.zero_()
+                s32 = A.frontier()
+                flush.zero_()
+                s64 = B.frontier()
+                r32, r64 = A.ranks(), B.ranks()
+                ref = np.load(os.path.join(orc.dir, f"p{si}_df_{k}.npy")) if have else r64
+                A.set_ranks(R_prev)
+                flush.zero_()
+                sn = A.naive()
+                flush.zero_()
+                ss = A.static()
+                e = {"df_fp32_ms": s32.ms_rank, "df_fp64_ms": s64.ms_rank, "naive_fp32_ms": sn.ms_rank,
+                     "static_fp32_ms": ss.ms_rank, "speedup_vs_naive": sn.ms_rank / s32.ms_rank,
+                     "speedup_vs_static": ss.ms_rank / s32.ms_rank, "df_fp32_iterations": s32.iterations,
+                     "df_fp64_iterations": s64.iterations, "df_affected": s32.affected_final,
+                     "fp32_linf": float(np.max(np.abs(r32 - ref)))}
+                if have:
+                    e["fp64_linf_vs_oracle"] = float(np.max(np.abs(r64 - ref)))
+                    e["oracle_iterations"] = ores["shapes"][name]["iterations"][f]
+                entry["per_frac"][f"{f:g}"] = e
+                R_prev = ref
+            A.close()
+            B.close()
+        out[name] = entry
+        del g
+    return out
+
+
 # ------------------------------------------------------------- GPU arm ----
 
 def run_ours(args, rank: int, world: int, local_rank: int):
-    ctx = mp.get_context("spawn")
-    q = None
-    proc = None
+    orc = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        # started before the first GPU call; runs on its own core while the GPU works
-        q = ctx.Queue()
-        proc = ctx.Process(target=_cpu_worker, args=(args.scale, args.ef, 1, FRACS, q), daemon=True)
-        proc.start()
+        # started before the first GPU call; the oracle runs on the host cores while the
+        # GPU works (its expected values feed the parity and precision legs)
+        orc = start_oracle(args, rank, ["headline", "sequential"] + ([] if args.no_legs else ["precision"]))
 
     import numpy as np
     import torch
@@ -391,23 +807,35 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         value, e2e_value, ms_per_step = max_over_ranks([value, e2e_value, ms_per_step], dev)
 
     cpu = None
-    if proc is not None:
-        try:
-            res = q.get(timeout=args.cpu_timeout)
-        except Exception:
-            res = {"error": "timed out"}
-        proc.join(timeout=5)
-        if proc.is_alive():
-            proc.terminate()
-        if "per_frac_ms" in res:
+    legs = {}
+    if orc is not None:
+        res = orc.wait("headline", args.cpu_timeout)
+        if res and "per_frac_ms" in res:
             cpu_val = geomean(res["per_frac_ms"].values())
-            cpu = {"value": cpu_val, "unit": "ms", "cores": 1, "kind": "oracle",
-                   "sample": (f"sequential FP64 oracle, Algorithm 1 synchronous, one 80/20 batch per f in "
-                              f"{[f'{x:g}' for x in FRACS]} on the same R-MAT s{args.scale} ef{args.ef} graph, "
-                              f"chained from its own Static ranks (setup {res['setup_s']:.0f} s untimed)"),
-                   "per_frac_ms": {f"{k:g}": v for k, v in res["per_frac_ms"].items()}}
+            seq = orc.wait("sequential", args.cpu_timeout)
+            cpu = {"value": cpu_val, "unit": "ms", "cores": res["threads"], "kind": "oracle",
+                   "sample": (f"FP64 oracle (Algorithm 1, synchronous), its -fopenmp build with schedule(dynamic, "
+                              f"2048) on {res['threads']} host cores (sched_getaffinity), one 80/20 batch per f in "
+                              f"{[f'{x:g}' for x in FRACS]} on the same R-MAT s{args.scale} ef{args.ef} graph, chained "
+                              f"from its own Static ranks (graph build {res['setup_s']:.0f} s and Static "
+                              f"{res['static_ms'] / 1e3:.1f} s untimed)"),
+                   "per_frac_ms": {f"{k:g}": v for k, v in res["per_frac_ms"].items()},
+                   "iterations": {f"{k:g}": v for k, v in res["iterations"].items()}}
+            if seq and "ms" in seq:
+                cpu["sequential_1core"] = {"value": seq["ms"], "unit": "ms", "cores": 1, "f": seq["f"],
+                                           "sample": "the sequential build of the same source, one update at this f"}
+            legs["parity"] = _leg(parity_leg, args, g, dev, stream, res, orc.dir)
         else:
-            cpu = {"value": None, "unit": "ms", "cores": 1, "kind": "oracle", "sample": res.get("error")}
+            cpu = {"value": None, "unit": "ms", "cores": None, "kind": "oracle",
+                   "sample": (res or {}).get("error", "timed out")}
+    if not args.no_legs and rank == 0:
+        gcache = {}
+        legs["serving"] = _leg(serving_leg, args, dev, g, rank, rates=(args.rate, args.sub_rate), gcache=gcache)
+        legs["batched"] = _leg(batched_leg, args, dev, rank)
+        legs["precision"] = _leg(precision_leg, args, dev, rank, orc, gcache=gcache)
+        gcache.clear()
+    if orc is not None:
+        orc.close()
 
     line = {
         "metric": METRIC, "value": value, "unit": "ms", "n_gpus": world, "steps": K, "warmup": W,
@@ -433,323 +861,79 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    line.update(legs)
     if rank == 0:
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
 
 
-# ------------------------------------------------------------- batched form ----
+# ------------------------------------------------------- single-form configs ----
+
+def _setup_device(local_rank):
+    import torch
+
+    from paper_2401_03256_gb300 import build as libbuild
+
+    libbuild.build()
+    torch.cuda.set_device(local_rank)
+    return torch.device("cuda", local_rank)
+
+
+def _form_line(metric, value, world, steps, warmup, dtype, config, extra, clk=None):
+    line = {"metric": metric, "value": value, "unit": "ms", "n_gpus": world, "steps": steps, "warmup": warmup,
+            "ms_per_step": value, "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+            "data": "synthetic", "config": config}
+    line.update(extra)
+    if clk is not None:
+        line["clocks"] = clk
+    return line
+
 
 def run_batched(args, rank: int, world: int, local_rank: int):
-    """Batched form (config 4): 256 independent R-MAT graphs (scales uniform in 10..18, edge
-    factor 8), each with its own 80/20 batch of f ~ log-uniform [1e-4, 1e-2] of its edges;
-    one pr_apply_batch for all graphs and one Dynamic Frontier launch (CUDA-graph replay,
-    autotuned bins), FP32 ranks.  Compared with the same updates as 256 standalone handles
-    called one after another.  value = ms per batched update (apply + DF)."""
-    import numpy as np
-    import torch
-
-    import synth
-    from paper_2401_03256_gb300 import build as libbuild
-
-    libbuild.build()
-    from paper_2401_03256_gb300 import prdf
-
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    rng = np.random.default_rng(1 + rank)
-    G = args.graphs
-    scales = rng.integers(10, 19, G)
-    gs = [synth.rmat(int(s), 8, seed=1000 * (1 + rank) + i) for i, s in enumerate(scales)]
-    fr = np.exp(rng.uniform(np.log(1e-4), np.log(1e-2), G))
-    firsts = np.cumsum([0] + [g.n for g in gs])
-    src = np.concatenate([g.src.astype(np.uint64) + firsts[i] for i, g in enumerate(gs)]).astype(np.uint32)
-    dst = np.concatenate([g.dst.astype(np.uint64) + firsts[i] for i, g in enumerate(gs)]).astype(np.uint32)
-    params = prdf.pr_params_default()
-    params.precision = prdf.PR_F32 if args.precision != "fp64" else prdf.PR_F64
-    W, K = args.warmup, args.steps
-    streams = [synth.BatchStream(g, seed=77 + i) for i, g in enumerate(gs)]
-    steps = []
-    for _ in range(W + K):
-        bs = [s.next(float(fr[i])) for i, s in enumerate(streams)]
-        off = lambda a, i: (a.astype(np.uint64) + firsts[i]).astype(np.uint32)
-        comb = [np.concatenate([off(getattr(b, k), i) for i, b in enumerate(bs)])
-                for k in ("del_src", "del_dst", "ins_src", "ins_dst")]
-        steps.append((bs, comb))
-    stream = torch.cuda.Stream(device=dev)
-    res = {}
-    with torch.cuda.stream(stream):
-        B = prdf.Graph.batched([g.n for g in gs], src, dst, params, stream.cuda_stream)
-        tune = B.autotune(6)
-        B.set_graph_launch(True)
-        B.static()
-        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
-        times, dfms, apms, iters = [], [], [], []
-        l0 = None
-        for i in range(W + K):
-            if i == W:
-                torch.cuda.synchronize(dev)
-                l0 = prdf.pr_kernel_launches()
-            flush.zero_()
-            torch.cuda.synchronize(dev)
-            t = time.perf_counter()
-            B.apply(*steps[i][1])
-            st = B.frontier()
-            torch.cuda.synchronize(dev)
-            if i >= W:
-                times.append((time.perf_counter() - t) * 1e3)
-                dfms.append(st.ms_rank)
-                apms.append(st.ms_apply)
-                iters.append(max(c.iterations for c in B.component_stats()))
-        launches = prdf.pr_kernel_launches() - l0
-        B.close()
-        # the same updates, one standalone handle per graph, called one after another
-        As = [prdf.Graph(g.n, g.src, g.dst, params, stream.cuda_stream) for g in gs]
-        for A in As:
-            A.static()
-        seq = []
-        for i in range(W + K):
-            flush.zero_()
-            torch.cuda.synchronize(dev)
-            t = time.perf_counter()
-            for j, A in enumerate(As):
-                b = steps[i][0][j]
-                A.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
-                A.frontier()
-            torch.cuda.synchronize(dev)
-            if i >= W:
-                seq.append((time.perf_counter() - t) * 1e3)
-        for A in As:
-            A.close()
-    value = statistics.median(times)
-    line = {
-        "metric": "batched form: ms per update of all graphs (apply + Dynamic Frontier, one launch)",
-        "value": value, "unit": "ms", "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": value,
-        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if args.precision != "fp64" else "i64", "data": "synthetic",
-        "config": {"workload": f"{G} R-MAT graphs, scales U{{10..18}}, edge factor 8, own 80/20 batch of "
-                               f"f ~ logU[1e-4, 1e-2] each", "vertices": int(firsts[-1]), "edges": int(src.size),
-                   "precision": args.precision, "launch": "CUDA graph replay", "tuning": tune.as_dict()},
-        "df_ms_median": statistics.median(dfms), "apply_ms_median": statistics.median(apms),
-        "max_graph_iterations": max(iters), "sequential_ms_median": statistics.median(seq),
-        "speedup_vs_sequential": statistics.median(seq) / value, "gpu_launches": launches,
-    }
+    """--config batched: the batched form alone (batched_leg), K timed updates."""
+    dev = _setup_device(local_rank)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    r = batched_leg(args, dev, rank, W=args.warmup, K=args.steps)
+    clk = clocks.stop()
+    line = _form_line("batched form: ms per update of all graphs (apply + Dynamic Frontier, one launch)", r["ms"],
+                      world, args.steps, args.warmup, r["config"]["precision"], r.pop("config"), r, clk)
     if rank == 0:
         print(json.dumps(line))
 
-
-# ------------------------------------------------------------- serving form ----
 
 def run_serving(args, rank: int, world: int, local_rank: int):
-    """Serving form (config 5): 8 resident R-MAT graphs (scales 18, 18, 19, 20, 21, 22, 23,
-    24, edge factor 16, FP32 ranks), Poisson arrivals at --rate requests/s for --duration s,
-    target graph uniform, batch f ~ log-uniform [1e-7, 1e-3] of that graph's edges (80/20,
-    drawn against the resident graph), admission by slots and free HBM, continuous batching
-    of each graph's queue.  value = p99 latency (submit -> ranks updated) in ms."""
-    import numpy as np
-    import torch
-
-    import synth
-    from paper_2401_03256_gb300 import build as libbuild
-
-    libbuild.build()
-    from paper_2401_03256_gb300 import prdf
-
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    scales = [int(x) for x in args.serve_scales.split(",")]
-    rng = np.random.default_rng(1 + rank)
-    gs = [synth.rmat(s, 16, seed=500 + 10 * rank + i) for i, s in enumerate(scales)]
-    params = prdf.pr_params_default()
-    params.precision = prdf.PR_F32 if args.precision != "fp64" else prdf.PR_F64
-    streams = [torch.cuda.Stream(device=dev) for _ in gs]
-    hs = [prdf.Graph(g.n, g.src, g.dst, params, s.cuda_stream) for g, s in zip(gs, streams)]
-    for h in hs:
-        h.static()
-    bstreams = [synth.BatchStream(g, seed=900 + i) for i, g in enumerate(gs)]
-    nreq = int(args.rate * args.duration)
-    warm = 4 * len(gs)
-    targets = rng.integers(0, len(gs), nreq + warm)
-    fr = np.exp(rng.uniform(np.log(1e-7), np.log(1e-3), nreq + warm))
-    batches = [bstreams[t].next(float(f), apply=False) for t, f in zip(targets, fr)]
-    gaps = rng.exponential(1.0 / args.rate, nreq)
-    srv = prdf.Server(slots=args.slots, max_coalesce=args.coalesce, hbm_reserve_bytes=1 << 30)
-    idx = [srv.add(h) for h in hs]
-    for k in range(warm):  # warm-up, untimed
-        b = batches[k]
-        srv.submit(idx[targets[k]], b.del_src, b.del_dst, b.ins_src, b.ins_dst)
-    srv.drain()
+    """--config serving: the serving form alone (serving_leg) at --rate for --duration s."""
+    dev = _setup_device(local_rank)
     clocks = ClockSampler(local_rank)
     clocks.start()
-    l0 = prdf.pr_kernel_launches()
-    tickets = []
-    t0 = time.perf_counter()
-    due = t0
-    for k in range(nreq):
-        due += gaps[k]
-        while True:
-            now = time.perf_counter()
-            if now >= due:
-                break
-            if due - now > 2e-4:
-                time.sleep((due - now) * 0.5)
-        b = batches[warm + k]
-        tickets.append(srv.submit(idx[targets[warm + k]], b.del_src, b.del_dst, b.ins_src, b.ins_dst))
-    t_submitted = time.perf_counter()
-    info = srv.drain()
-    t_end = time.perf_counter()
+    r = serving_leg(args, dev, None, rank, rates=(args.rate,), duration=args.duration)
     clk = clocks.stop()
-    launches = prdf.pr_kernel_launches() - l0
-    res = [srv.wait(t) for t in tickets]
-    srv.close()
-    lat = np.array([r.t_done_ms - r.t_submit_ms for r in res])
-    ok = sum(1 for r in res if r.status == prdf.PR_OK)
-    span_ms = max(r.t_done_ms for r in res) - min(r.t_submit_ms for r in res)
-    pairs = [int(batches[warm + k].size) for k in range(nreq)]
-    line = {
-        "metric": "serving p50/p99 ms", "value": float(np.percentile(lat, 99)), "unit": "ms",
-        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-        "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
-        "updates_per_s": nreq / (span_ms * 1e-3), "offered_rate_per_s": args.rate,
-        "achieved_submit_rate_per_s": nreq / (t_submitted - t0), "requests": nreq, "ok": ok,
-        "coalesced_mean": float(np.mean([r.coalesced for r in res])),
-        "waited_for_memory": info.waited_for_memory, "wall_s": t_end - t0,
-        "n_gpus": world, "steps": nreq, "warmup": warm, "ms_per_step": span_ms / nreq,
-        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if args.precision != "fp64" else "i64", "data": "synthetic",
-        "config": {"workload": f"{len(gs)} resident R-MAT graphs scales {scales}, edge factor 16, Poisson "
-                               f"{args.rate:g}/s, f ~ logU[1e-7, 1e-3], 80/20", "slots": args.slots,
-                   "max_coalesce": args.coalesce, "batch_pairs_mean": float(np.mean(pairs)),
-                   "vertices": int(sum(g.n for g in gs))},
-        "gpu_launches": launches, "clocks": clk,
-    }
-    for h in hs:
-        h.close()
+    line = _form_line("serving p50/p99 ms", r["p99_ms"], world, r[f"rate_{args.rate:g}"]["requests"], 0, "f32",
+                      r.pop("config"), r, clk)
     if rank == 0:
         print(json.dumps(line))
 
 
-# ----------------------------------------------------------- precision form ----
-
 def run_precision(args, rank: int, world: int, local_rank: int):
-    """Precision form (config 3): FP32 ranks and contributions with FP64 compensated
-    reductions, on a Kronecker (R-MAT initiator 0.57/0.19/0.19/0.05) scale-24 graph with
-    edge factor 16 and on a 4900 x 4900 directed grid with 1% random long-range arcs;
-    80/20 batches of 1e-5 and 1e-3 |E|.  Every update is run twice, by an FP32 handle and by
-    an FP64 handle of the same graph from the same previous ranks, and the L-inf distance of
-    the two results is the FP32 error (the FP64 path is the one held to the oracle at
-    1e-9).  value = geometric mean of the FP32 Dynamic Frontier times."""
-    import numpy as np
-    import torch
-
-    import synth
-    from paper_2401_03256_gb300 import build as libbuild
-
-    libbuild.build()
-    from paper_2401_03256_gb300 import prdf
-
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    fracs = [1e-5, 1e-3]
-    shapes = [("kronecker s24 ef16", lambda: synth.rmat(24, 16, seed=11 + rank)),
-              ("grid 4900x4900 + 1% long-range", lambda: synth.grid(4900, 4900, 0.01, seed=12 + rank))]
-    W, K = args.warmup, args.steps
-    stream = torch.cuda.Stream(device=dev)
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
-    out = {}
-    dfs = []
-    launches = 0
+    """--config precision: the precision form alone (precision_leg), errors against the
+    FP64 oracle run on the host cores meanwhile."""
+    orc = start_oracle(args, rank, ["precision"]) if rank == 0 and world == 1 and not args.no_cpu_baseline else None
+    dev = _setup_device(local_rank)
     clocks = ClockSampler(local_rank)
     clocks.start()
-    t_start = time.perf_counter()
-    for name, make in shapes:
-        g = make()
-        p32 = prdf.pr_params_default()
-        p32.precision = prdf.PR_F32
-        p64 = prdf.pr_params_default()
-        with torch.cuda.stream(stream):
-            A = prdf.Graph(g.n, g.src, g.dst, p32, stream.cuda_stream)
-            B = prdf.Graph(g.n, g.src, g.dst, p64, stream.cuda_stream)
-            n, m = A.info()
-            st32 = A.static()
-            st64 = B.static()
-            R32 = torch.empty(n, dtype=torch.float64, device=dev)
-            R64 = torch.empty(n, dtype=torch.float64, device=dev)
-            Rp = torch.empty(n, dtype=torch.float64, device=dev)
-            A.ranks(R32)
-            B.ranks(R64)
-            static_err = float((R32 - R64).abs().max())
-            A.set_ranks(R64)  # both chains start from the same FP64 ranks
-            bs = synth.BatchStream(g, seed=13 + rank)
-            rec = {f: {"df": [], "naive": [], "static": [], "apply": [], "err": [], "it": [], "it64": [],
-                       "aff": [], "bytes": [], "df64": []} for f in fracs}
-            l0 = prdf.pr_kernel_launches()
-            for i in range(W + K):
-                for f in fracs:
-                    b = bs.next(f)
-                    B.ranks(Rp)
-                    A.set_ranks(Rp)
-                    A.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
-                    B.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
-                    flush.zero_()
-                    s32 = A.frontier()
-                    flush.zero_()
-                    s64 = B.frontier()
-                    A.ranks(R32)
-                    B.ranks(R64)
-                    err = float((R32 - R64).abs().max())
-                    A.set_ranks(Rp)
-                    flush.zero_()
-                    sn = A.naive()
-                    flush.zero_()
-                    ss = A.static()
-                    if i >= W:
-                        r = rec[f]
-                        r["df"].append(s32.ms_rank)
-                        r["df64"].append(s64.ms_rank)
-                        r["apply"].append(s32.ms_apply)
-                        r["naive"].append(sn.ms_rank)
-                        r["static"].append(ss.ms_rank)
-                        r["err"].append(err)
-                        r["it"].append(s32.iterations)
-                        r["it64"].append(s64.iterations)
-                        r["aff"].append(s32.affected_final)
-                        r["bytes"].append(s32.bytes_algorithmic)
-            torch.cuda.synchronize(dev)
-            launches += prdf.pr_kernel_launches() - l0
-            A.close()
-            B.close()
-        mean = lambda xs: sum(xs) / len(xs)
-        per = {}
-        for f in fracs:
-            r = rec[f]
-            dfs.append(mean(r["df"]))
-            per[f"{f:g}"] = {
-                "df_ms": mean(r["df"]), "df_fp64_ms": mean(r["df64"]), "naive_ms": mean(r["naive"]),
-                "static_ms": mean(r["static"]), "apply_ms": mean(r["apply"]),
-                "speedup_vs_static": mean(r["static"]) / mean(r["df"]),
-                "speedup_vs_naive": mean(r["naive"]) / mean(r["df"]),
-                "df_gbs": sum(r["bytes"]) / (sum(r["df"]) * 1e-3) / 1e9,
-                "linf_err_vs_fp64_max": max(r["err"]), "df_iterations": mean(r["it"]),
-                "df_fp64_iterations": mean(r["it64"]), "df_affected": mean(r["aff"]),
-            }
-        out[name] = {"n": n, "m_with_self_loops": m, "static_linf_err_vs_fp64": static_err,
-                     "static_fp32_ms": st32.ms_rank, "static_fp64_ms": st64.ms_rank, "per_frac": per}
-        del g
-    t_end = time.perf_counter()
+    r = precision_leg(args, dev, rank, orc)
     clk = clocks.stop()
-    value = geomean(dfs)
-    line = {
-        "metric": "precision form: FP32 Dynamic Frontier update ms (geomean over shapes and batch sizes)",
-        "value": value, "unit": "ms", "n_gpus": world, "steps": K, "warmup": W,
-        "ms_per_step": (t_end - t_start) * 1e3 / (K + W), "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "Kronecker s24 ef16 and 4900x4900 grid + 1% long-range, 80/20 batches 1e-5 and "
-                               "1e-3 |E|, FP32 ranks/contributions, FP64 compensated reductions",
-                   "l2": "flushed (256 MB write) before every timed call", "error_reference": "FP64 path, same inputs"},
-        "shapes": out, "gpu_launches": launches, "clocks": clk,
-    }
+    if orc is not None:
+        orc.close()
+    dfs = [e["df_fp32_ms"] for k, v in r.items() if isinstance(v, dict) and "per_frac" in v
+           for e in v["per_frac"].values()]
+    line = _form_line("precision form: FP32 Dynamic Frontier update ms (geomean over shapes and batch sizes)",
+                      geomean(dfs), world, len(dfs), 0, "f32",
+                      {"workload": "Kronecker s24 ef16 and 4900x4900 grid + 1% long-range, 80/20 batches 1e-5 then "
+                                   "1e-3 |E|, FP32 ranks/contributions, FP64 compensated dead-end mass",
+                       "l2": "flushed (256 MB write) before every timed call"}, {"shapes": r}, clk)
     if rank == 0:
         print(json.dumps(line))
 
@@ -1015,7 +1199,7 @@ def run_reference(args, rank: int, world: int):
     import oracle
     import synth
 
-    oracle.build()
+    cores = oracle.use_threads(oracle.host_cores())
     g = synth.rmat(args.scale, args.ef, seed=1)
     G = oracle.Graph.build(g.n, g.src, g.dst)
     R, _ = oracle.static_pr(G)
@@ -1035,8 +1219,9 @@ def run_reference(args, rank: int, world: int):
     means = [sum(v) / len(v) for v in times.values() if v]
     value = geomean(means)
     all_t = [x for v in times.values() for x in v]
-    sample = (f"sequential FP64 oracle (Algorithm 1, synchronous) on R-MAT s{args.scale} ef{args.ef}; step i "
-              f"updates one 80/20 batch of f = FRACS[i mod 5]; {K} timed steps after {W} warm-up steps")
+    sample = (f"FP64 oracle (Algorithm 1, synchronous), its -fopenmp build on {cores} host cores, on R-MAT "
+              f"s{args.scale} ef{args.ef}; step i updates one 80/20 batch of f = FRACS[i mod 5]; {K} timed steps "
+              f"after {W} warm-up steps")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": world, "steps": K,
         "warmup": W, "ms_per_step": sum(all_t) / len(all_t) if all_t else None, "higher_is_better": False,
@@ -1044,7 +1229,7 @@ def run_reference(args, rank: int, world: int):
         "config": {"workload": f"R-MAT scale {args.scale} edge factor {args.ef}, 80/20 batches f=1e-7..1e-3 |E|, "
                                f"Dynamic Frontier vs Static vs Naive-dynamic", "batch_fracs": FRACS,
                    "precision": "fp64"},
-        "cpu_baseline": {"value": value, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "per_frac_ms": {f"{f:g}": (sum(v) / len(v) if v else None) for f, v in times.items()},
     }
@@ -1070,7 +1255,13 @@ def main():
                          "sweep, with L1 errors against a reference Static PageRank; kmer: the low-degree huge "
                          "graph (k-mer stand-in)")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: Poisson arrivals per second")
+    ap.add_argument("--sub-rate", type=float, default=50.0,
+                    help="serving leg of the default run: a second, lower offered rate")
     ap.add_argument("--duration", type=float, default=2.0, help="serving: seconds of arrivals")
+    ap.add_argument("--serve-duration", type=float, default=1.0,
+                    help="serving leg of the default run: seconds of arrivals per rate")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="default run: skip the serving, batched and precision legs (and the precision oracle)")
     ap.add_argument("--slots", type=int, default=2, help="serving: concurrent updates")
     ap.add_argument("--coalesce", type=int, default=256, help="serving: requests per coalesced update")
     ap.add_argument("--serve-scales", default="18,18,19,20,21,22,23,24", help="serving: R-MAT scales")
