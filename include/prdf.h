@@ -121,18 +121,30 @@ pr_status pr_graph_create_batched(int32_t ncomp, const uint32_t *comp_n, int64_t
  * iterations, converged, affected_final, last_delta; ms_rank is the whole launch. */
 pr_status pr_get_component_stats(const pr_graph *g, pr_stats *stats, int32_t ncomp);
 
-/* Work distribution of the rank kernel (results do not depend on it): in-degree thresholds
- * of the thread and block bins, the dense-iteration divisor (an iteration sweeps the
+/* Work distribution of the rank kernels: in-degree thresholds of the thread and block bins
+ * (bin_lo also bounds the rows a sweep gives one thread each), the dense-iteration divisor (an iteration sweeps the
  * compacted affected set once it exceeds n / dense_div vertices), the resident blocks per
  * SM of the persistent launch, and df_split (1, the default: a Dynamic Frontier, Dynamic
  * Traversal or asynchronous call on a single-graph handle in self-loop mode continues in
  * per-iteration launches once its affected set is dense (after its search for Dynamic
  * Traversal), growing the set by pulling marks from per-vertex change flags or pushing the
- * out-rows of first expansions; 0: everything in the one persistent launch).  ms is the
- * time the autotuner measured (0 otherwise). */
+ * out-rows of first expansions; 0: everything in the one persistent launch), and the sweep
+ * tiles: rows of bin_lo < in-degree <= max(bin_lo, group_max) take an 8-lane group each,
+ * longer rows are cut into chunks of chunk_len in-edges taken by whole warps.  ms is the
+ * time the autotuner measured (0 otherwise).  With PR_F64 results do not depend on any of
+ * these (fixed-point sums are exact in any order); with PR_F32 a different tiling adds a
+ * vertex's contributions in another order, which changes ranks by FP32 rounding only.
+ * Defaults: bin_lo 8, bin_hi 4096, dense_div 16, chunk_len 512, group_max 64. */
 typedef struct {
     int32_t bin_lo, bin_hi, dense_div, blocks_per_sm;
-    int32_t df_split, reserved;
+    int32_t df_split;
+    int32_t barrier_us;  /* bounded wait of a grid barrier in the persistent launches, in
+                            microseconds (0 = the default 4 s); a wait that runs out ends the
+                            launch and the call returns PR_ERR_DEVICE_TIMEOUT.  A short value
+                            exercises that path in tests. */
+    int32_t chunk_len;   /* a multiple of 32 in [32, 512]; a vertex may have at most
+                            2^21 chunks (else PR_ERR_CAPACITY) */
+    int32_t group_max;   /* [0, 64] */
     double ms;
 } pr_tuning;
 
@@ -149,6 +161,13 @@ pr_status pr_autotune(pr_graph *g, int32_t sweep_iters, pr_tuning *chosen);
  * persistent kernel), captured on first use; only the kernel's arguments change between
  * replays. */
 pr_status pr_set_graph_launch(pr_graph *g, int32_t enable);
+
+/* Fault injection on the host, for tests of the out-of-memory path: after this call the
+ * next `after` allocations of graph storage and batch scratch (all handles, this process)
+ * succeed and the following ones fail with PR_ERR_OUT_OF_MEMORY, as cudaMalloc failing
+ * would; a negative `after` switches the injection off.  A failing call leaves the graph
+ * as it was.  Never fails. */
+void pr_inject_alloc_failure(int32_t after);
 
 /* Frees all device memory of the handle.  NULL is accepted. */
 pr_status pr_graph_destroy(pr_graph *g);
@@ -214,9 +233,11 @@ pr_status pr_get_ranks(pr_graph *g, double *out, uint32_t n);
 
 /* Replaces the ranks with in[0..n) (host or device), e.g. to resume or to start every
  * implementation from the same previous ranks.  Pending marks are kept.  The ranks must be
- * a distribution: every value finite and in [0, 2], and their sum at most 1 + 1e-6 (for a
- * batched handle, the sum over each graph's vertices); otherwise PR_ERR_INVALID_ARG and
- * the ranks are unchanged. */
+ * a distribution up to drift: every value finite and in [0, 2], and their sum at most 2
+ * (for a batched handle, the sum over each graph's vertices).  Exact methods keep the sum
+ * at 1; Dynamic Frontier leaves vertices outside its affected set as they were, so chained
+ * updates drift from 1 slightly.  Otherwise PR_ERR_INVALID_ARG and the ranks are
+ * unchanged. */
 pr_status pr_set_ranks(pr_graph *g, const double *in, uint32_t n);
 
 /* Number of vertices and of stored edges (self-loops included). */
@@ -255,12 +276,13 @@ uint64_t pr_kernel_launches(void);
  * device-wide synchronisation of cudaMalloc / cudaFree, and plugins that are handed device
  * buffers but not the right to allocate.  Everything else in this library allocates.
  *
- * Static PageRank (Eq. 1, iterated from 1/n until the L-inf change is <= params->tol or
- * params->max_iter iterations ran) of a graph given as an in-edge CSR in device memory:
- * in_off[0..n] (non-decreasing from 0 to m) and in_col[0..m) = the sources u of the edges
- * (u, v) of row v, in the layout pr_get_csr(g, 1, ...) exports.  Every vertex needs an
- * out-edge (the self-loops of Section 3.1 give one).  The n ranks are written to `ranks`
- * (device memory); the work runs on cuda_stream and the call returns when it is done.
+ * Static PageRank (the same computation as pr_static: ranks iterated from 1/n until the
+ * L-inf change is <= params->tol or params->max_iter iterations ran) of a graph given as
+ * an in-edge CSR in device memory: in_off[0..n] (non-decreasing from 0 to m) and
+ * in_col[0..m) = the sources u of the edges (u, v) of row v, in the layout
+ * pr_get_csr(g, 1, ...) exports.  Every vertex needs an out-edge (a self-loop on every
+ * vertex gives one).  The n ranks are written to `ranks` (device memory); the work runs on
+ * cuda_stream and the call is synchronous: it returns when that work has finished.
  * params may be NULL (defaults); it must ask for PR_F64 and PR_DEADEND_SELFLOOP.  stats
  * may be NULL; its timing fields stay 0.  Arithmetic is plain FP64, so the ranks agree
  * with pr_static's within the usual L-inf tolerance, not bit for bit.

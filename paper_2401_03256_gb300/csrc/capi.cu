@@ -66,6 +66,13 @@ namespace prdf {
 static std::atomic<unsigned long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void count_launches(unsigned long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+static std::atomic<long long> g_alloc_left{-1};  // allocations that still succeed (-1: no injection)
+bool alloc_fault() {
+  long long left = g_alloc_left.load(std::memory_order_relaxed);
+  while (left > 0 && !g_alloc_left.compare_exchange_weak(left, left - 1, std::memory_order_relaxed)) {
+  }
+  return left == 0;
+}
 }  // namespace prdf
 
 extern "C" {
@@ -117,6 +124,10 @@ pr_status pr_get_trace(const pr_graph *h, int32_t cap, double *phase_ms, double 
 
 uint64_t pr_kernel_launches(void) { return prdf::g_launches.load(std::memory_order_relaxed); }
 
+void pr_inject_alloc_failure(int32_t after) {
+  prdf::g_alloc_left.store(after < 0 ? -1 : (long long)after, std::memory_order_relaxed);
+}
+
 const char *pr_last_error(const pr_graph *h) { return h ? h->g.err.c_str() : g_create_err.c_str(); }
 
 static pr_status create_impl(uint32_t n, int64_t m, const uint32_t *src, const uint32_t *dst, const pr_params *params,
@@ -159,16 +170,36 @@ pr_status pr_set_tuning(pr_graph *h, const pr_tuning *t) {
   if (!h) return invalid(nullptr, "graph is NULL");
   Graph &g = h->g;
   if (!t || t->bin_lo < 1 || t->bin_hi < t->bin_lo || t->dense_div < 1 || t->blocks_per_sm < 1 ||
-      t->blocks_per_sm * g.sm_count > g.rank_grid_max || (t->df_split != 0 && t->df_split != 1))
-    return invalid(&g, "need 1 <= bin_lo <= bin_hi, dense_div >= 1, blocks_per_sm within the resident limit");
+      t->blocks_per_sm * g.sm_count > g.rank_grid_max || (t->df_split != 0 && t->df_split != 1) || t->barrier_us < 0 ||
+      t->chunk_len < 32 || t->chunk_len > (int32_t)prdf::kChunk || t->chunk_len % 32 != 0 || t->group_max < 0 ||
+      t->group_max > (int32_t)prdf::kGroupMax)
+    return invalid(&g, "need 1 <= bin_lo <= bin_hi, dense_div >= 1, blocks_per_sm within the resident limit, "
+                       "barrier_us >= 0, chunk_len a multiple of 32 in [32, 512], group_max in [0, 64]");
   DeviceGuard dg(g.device);
-  if (t->bin_lo != g.p.bin_lo) g.ident_dirty = true;
-  g.p.bin_lo = t->bin_lo;
-  g.p.bin_hi = t->bin_hi;
-  g.dense_div = (uint32_t)t->dense_div;
-  g.rank_grid = t->blocks_per_sm * g.sm_count;
-  g.split_df = t->df_split != 0;
-  return prdf::graph_refresh_ident(&g);
+  pr_tuning old;
+  pr_get_tuning(h, &old);
+  auto store = [&g](const pr_tuning &u) {
+    if (u.bin_lo != g.p.bin_lo || (uint32_t)u.chunk_len != g.chunk_len || (uint32_t)u.group_max != g.group_max)
+      g.ident_dirty = true;
+    g.chunk_len = (uint32_t)u.chunk_len;
+    g.group_max = (uint32_t)u.group_max;
+    g.p.bin_lo = u.bin_lo;
+    g.p.bin_hi = u.bin_hi;
+    g.dense_div = (uint32_t)u.dense_div;
+    g.rank_grid = u.blocks_per_sm * g.sm_count;
+    g.split_df = u.df_split != 0;
+    g.barrier_us = u.barrier_us;
+  };
+  store(*t);
+  pr_status rc = prdf::graph_refresh_ident(&g);
+  if (rc == PR_ERR_CAPACITY) {  // a tile this graph does not fit: keep the previous tuning
+    const std::string why = g.err;
+    store(old);
+    pr_status r2 = prdf::graph_refresh_ident(&g);
+    g.err = why;
+    if (r2 != PR_OK) return r2;
+  }
+  return rc;
 }
 
 pr_status pr_get_tuning(const pr_graph *h, pr_tuning *t) {
@@ -179,7 +210,9 @@ pr_status pr_get_tuning(const pr_graph *h, pr_tuning *t) {
   t->dense_div = (int32_t)g.dense_div;
   t->blocks_per_sm = g.rank_grid / g.sm_count;
   t->df_split = g.split_df ? 1 : 0;
-  t->reserved = 0;
+  t->barrier_us = g.barrier_us;
+  t->chunk_len = (int32_t)g.chunk_len;
+  t->group_max = (int32_t)g.group_max;
   t->ms = 0.0;
   return PR_OK;
 }
@@ -191,8 +224,9 @@ pr_status pr_set_graph_launch(pr_graph *h, int32_t enable) {
 }
 
 // Autotuner: times Naive-dynamic sweeps of sweep_iters iterations (the full-sweep cost the
-// thresholds steer) for every candidate bin_lo x blocks-per-SM, keeps the fastest, and
-// restores the ranks.  Results do not depend on the choice.
+// thresholds steer) for every candidate bin_lo x blocks-per-SM, then, at the fastest of
+// those, every sweep tile (chunk_len x group_max); keeps the fastest and restores the ranks.
+// FP64 results do not depend on the choice; FP32 ones only through the order of additions.
 pr_status pr_autotune(pr_graph *h, int32_t sweep_iters, pr_tuning *chosen) {
   if (!h) return invalid(nullptr, "graph is NULL");
   Graph &g = h->g;
@@ -212,28 +246,45 @@ pr_status pr_autotune(pr_graph *h, int32_t sweep_iters, pr_tuning *chosen) {
   const int32_t los[] = {4, 8, 16, 32};
   const int per_sm_max = std::max(1, g.rank_grid_max / g.sm_count);
   g.p.max_iter = sweep_iters;
+  // time candidate t (best of two); a capacity refusal of a tile only skips that tile
+  auto trial = [&](const pr_tuning &t) -> pr_status {
+    pr_status r = pr_set_tuning(h, &t);
+    if (r == PR_ERR_CAPACITY) return PR_OK;
+    if (r != PR_OK) return r;
+    pr_stats st;
+    double ms = 1e30;
+    for (int rep = 0; rep < 2 && r == PR_OK; rep++) {
+      g.n_pend_src = 0;
+      g.n_pend_tgt = 0;
+      if ((r = prdf::rank_run(&g, prdf::kModeNaive, &st)) == PR_OK) ms = std::min(ms, st.ms_rank);
+      if (r == PR_OK) r = prdf::rank_set(&g, h->stage);
+    }
+    if (r == PR_OK && ms < best.ms) {
+      best = t;
+      best.ms = ms;
+    }
+    return r;
+  };
   for (int32_t lo : los) {
-    for (int bps = std::max(1, per_sm_max - 2); bps <= per_sm_max; bps++) {
+    for (int bps = std::max(1, per_sm_max - 2); bps <= per_sm_max && rc == PR_OK; bps++) {
       pr_tuning t = cur;
       t.bin_lo = lo;
       t.bin_hi = std::max(cur.bin_hi, lo);
       t.blocks_per_sm = bps;
-      if ((rc = pr_set_tuning(h, &t)) != PR_OK) break;
-      pr_stats st;
-      double ms = 1e30;
-      for (int rep = 0; rep < 2 && rc == PR_OK; rep++) {  // best of two
-        g.n_pend_src = 0;
-        g.n_pend_tgt = 0;
-        if ((rc = prdf::rank_run(&g, prdf::kModeNaive, &st)) == PR_OK) ms = std::min(ms, st.ms_rank);
-        if (rc == PR_OK) rc = prdf::rank_set(&g, h->stage);
-      }
-      if (rc != PR_OK) break;
-      if (ms < best.ms) {
-        best = t;
-        best.ms = ms;
-      }
+      rc = trial(t);
     }
     if (rc != PR_OK) break;
+  }
+  const int32_t chunks[] = {128, 256, 512}, groups[] = {16, 32, 64};
+  const pr_tuning base = best;
+  for (int32_t c : chunks) {
+    for (int32_t gm : groups) {
+      if (rc != PR_OK || (c == base.chunk_len && gm == base.group_max)) continue;
+      pr_tuning t = base;
+      t.chunk_len = c;
+      t.group_max = gm;
+      rc = trial(t);
+    }
   }
   g.p.max_iter = keep_iter;
   g.n_pend_src = keep_pend_src;

@@ -36,6 +36,7 @@ pr_status cuda_fail(Graph *g, cudaError_t e, const char *what) {
 template <class T>
 static cudaError_t dalloc(T **p, uint64_t count) {
   *p = nullptr;
+  if (alloc_fault()) return cudaErrorMemoryAllocation;
   return cudaMalloc((void **)p, sizeof(T) * (count ? count : 1));
 }
 
@@ -141,10 +142,11 @@ __global__ void k_init_rank(const uint2 *out_rd, uint32_t n, double alpha, typen
 
 // ---- batch update ----
 
-// Chunk items of the tier-2 rows; chunk c of a row covers edges [c kChunk, (c+1) kChunk).
-__device__ __forceinline__ uint4 chunk_item(uint32_t v, uint2 d, uint32_t c, uint32_t nch, uint32_t number) {
-  uint32_t len = min(kChunk, d.y - c * kChunk);
-  return make_uint4(v, d.x + c * kChunk, len | (c << 10) | (nch > 1 ? 0x80000000u : 0u), number);
+// Chunk items of the tier-2 rows; chunk c of a row covers edges [c chunk, (c+1) chunk).
+__device__ __forceinline__ uint4 chunk_item(uint32_t v, uint2 d, uint32_t c, uint32_t nch, uint32_t number,
+                                            uint32_t chunk) {
+  uint32_t len = min(chunk, d.y - c * chunk);
+  return make_uint4(v, d.x + c * chunk, len | (c << 10) | (nch > 1 ? 0x80000000u : 0u), number);
 }
 
 
@@ -302,6 +304,7 @@ struct RowHook {
   uint32_t *pend_src, *pend_tgt;
   uint32_t pend_cap;
   uint32_t bin_lo, bin_hi;
+  uint32_t gmax, chunk;       // sweep tiers of the handle (sweep_tier)
   uint4 *items;               // in-rows: sweep items to patch (tier and chunk count unchanged)
   const uint32_t *item_pos;
 };
@@ -386,9 +389,9 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(uint2 *rd, uint32_t *ca
       cap[r] = move_cap(new_len);
       atomicAdd(garbage, (unsigned long long)cap_r);
     }
-    if (!hook.is_out && (sweep_tier(len, hook.bin_lo) != sweep_tier(new_len, hook.bin_lo) ||
-                         (sweep_tier(new_len, hook.bin_lo) == 2 &&
-                          (len + kChunk - 1) / kChunk != (new_len + kChunk - 1) / kChunk))) {
+    if (!hook.is_out && (sweep_tier(len, hook.bin_lo, hook.gmax) != sweep_tier(new_len, hook.bin_lo, hook.gmax) ||
+                         (sweep_tier(new_len, hook.bin_lo, hook.gmax) == 2 &&
+                          (len + hook.chunk - 1) / hook.chunk != (new_len + hook.chunk - 1) / hook.chunk))) {
       actl->bins_changed = 1;
       s_ok = 0;  // the sweep items are rebuilt after this update; nothing to patch
     }
@@ -410,12 +413,13 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(uint2 *rd, uint32_t *ca
     if (s_ok) {
       const uint2 nd = make_uint2(s_dest, new_len);
       const uint32_t pos = hook.item_pos[r];
-      if (sweep_tier(new_len, hook.bin_lo) < 2) {
+      if (sweep_tier(new_len, hook.bin_lo, hook.gmax) < 2) {
         if (tid == 0) hook.items[pos] = make_uint4(r, nd.x, nd.y, 0u);
       } else {
-        const uint32_t nch = (new_len + kChunk - 1) / kChunk;
+        const uint32_t nch = (new_len + hook.chunk - 1) / hook.chunk;
         const uint32_t number0 = hook.items[pos].w;
-        for (uint32_t c = tid; c < nch; c += kMergeThreads) hook.items[pos + c] = chunk_item(r, nd, c, nch, number0 + c);
+        for (uint32_t c = tid; c < nch; c += kMergeThreads)
+          hook.items[pos + c] = chunk_item(r, nd, c, nch, number0 + c, hook.chunk);
       }
     }
   }
@@ -456,17 +460,25 @@ __global__ void k_pack_rows(const uint2 *rd, uint32_t n, const uint32_t *col, co
   for (uint32_t j = lane; j < d.y; j += 32) packed[o + j] = col[d.x + j];
 }
 
-__global__ void k_bin_flags(const uint2 *rd, uint32_t n, uint32_t lo, int bin, uint32_t *flags) {
+__global__ void k_bin_flags(const uint2 *rd, uint32_t n, uint32_t lo, uint32_t gmax, int bin, uint32_t *flags) {
   uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= n) return;
-  flags[v] = sweep_tier(rd[v].y, lo) == bin;
+  flags[v] = sweep_tier(rd[v].y, lo, gmax) == bin;
 }
 
 // Chunks per long-row vertex (tier 2 of the sweep order).
-__global__ void k_chunk_counts(const uint32_t *big, uint32_t nb, const uint2 *rd, uint32_t *cnt) {
+// A chunk's index within its row has 21 bits in the item (chunk_item): `over` is set when a
+// row needs more than 2^21 chunks.
+__global__ void k_chunk_counts(const uint32_t *big, uint32_t nb, const uint2 *rd, uint32_t chunk, uint32_t *cnt,
+                               uint32_t *over) {
   uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < nb) cnt[i] = (rd[big[i]].y + kChunk - 1) / kChunk;
-  else if (i == nb) cnt[i] = 0;
+  if (i < nb) {
+    const uint32_t c = (rd[big[i]].y + chunk - 1) / chunk;
+    cnt[i] = c;
+    if (c > (1u << 21)) *over = 1u;
+  } else if (i == nb) {
+    cnt[i] = 0;
+  }
 }
 
 __global__ void k_items_simple(const uint32_t *ident, uint32_t cnt, const uint2 *rd, uint4 *items,
@@ -480,13 +492,13 @@ __global__ void k_items_simple(const uint32_t *ident, uint32_t cnt, const uint2 
 }
 
 __global__ void k_items_chunks(const uint32_t *big, uint32_t nb, const uint2 *rd, const uint32_t *start,
-                               uint32_t base, uint4 *items, uint32_t *item_pos) {
+                               uint32_t base, uint32_t chunk, uint4 *items, uint32_t *item_pos) {
   uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nb) return;
   uint32_t v = big[i];
   uint2 d = rd[v];
-  uint32_t nch = (d.y + kChunk - 1) / kChunk, s = start[i];
-  for (uint32_t c = 0; c < nch; c++) items[base + s + c] = chunk_item(v, d, c, nch, s + c);
+  uint32_t nch = (d.y + chunk - 1) / chunk, s = start[i];
+  for (uint32_t c = 0; c < nch; c++) items[base + s + c] = chunk_item(v, d, c, nch, s + c, chunk);
   item_pos[v] = base + s;
 }
 
@@ -834,8 +846,9 @@ pr_status graph_apply(Graph *g, uint64_t nd, const uint32_t *ds, const uint32_t 
   if (g->f32) {
     using S = Store<true>;
     RowHook<true> ho{true, g->p.alpha, (S::A *)g->adeg, (S::R *)g->R[0], (S::C *)g->C[0], (S::C *)g->C[1],
-                     g->pend_src, g->pend_tgt, g->pend_cap, lo, hi_b, nullptr, nullptr};
-    RowHook<true> hin{false, g->p.alpha, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, lo, hi_b,
+                     g->pend_src, g->pend_tgt, g->pend_cap, lo, hi_b, g->group_max, g->chunk_len, nullptr, nullptr};
+    RowHook<true> hin{false,   g->p.alpha,   nullptr,      nullptr,       nullptr, nullptr, nullptr,
+                      nullptr, 0,            lo,           hi_b,          g->group_max, g->chunk_len,
                       g->items, g->item_pos};
     k_merge<true><<<K, kMergeThreads, 0, st>>>(g->out.rd, g->out.cap, g->out.col, co, b, seg_o, &dctl->n_seg_out,
                                                tp_o, &dctl->tail_out, &dctl->garbage_out, g->big, &dctl->big_cursor,
@@ -848,8 +861,9 @@ pr_status graph_apply(Graph *g, uint64_t nd, const uint32_t *ds, const uint32_t 
   } else {
     using S = Store<false>;
     RowHook<false> ho{true, g->p.alpha, (S::A *)g->adeg, (S::R *)g->R[0], (S::C *)g->C[0], (S::C *)g->C[1],
-                      g->pend_src, g->pend_tgt, g->pend_cap, lo, hi_b, nullptr, nullptr};
-    RowHook<false> hin{false, g->p.alpha, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, lo, hi_b,
+                      g->pend_src, g->pend_tgt, g->pend_cap, lo, hi_b, g->group_max, g->chunk_len, nullptr, nullptr};
+    RowHook<false> hin{false,   g->p.alpha,   nullptr,      nullptr,       nullptr, nullptr, nullptr,
+                       nullptr, 0,            lo,           hi_b,          g->group_max, g->chunk_len,
                        g->items, g->item_pos};
     k_merge<false><<<K, kMergeThreads, 0, st>>>(g->out.rd, g->out.cap, g->out.col, co, b, seg_o, &dctl->n_seg_out,
                                                 tp_o, &dctl->tail_out, &dctl->garbage_out, g->big, &dctl->big_cursor,
@@ -917,7 +931,7 @@ pr_status graph_refresh_ident(Graph *g) {
   uint32_t *cnt = (uint32_t *)&g->actl->n_seg_out;  // reuse a device word
   uint32_t base = 0;
   for (int bin = 0; bin < 3; bin++) {
-    k_bin_flags<<<grid_for(n), 256, 0, st>>>(g->in.rd, n, (uint32_t)g->p.bin_lo, bin, g->gen_tmp);
+    k_bin_flags<<<grid_for(n), 256, 0, st>>>(g->in.rd, n, (uint32_t)g->p.bin_lo, g->group_max, bin, g->gen_tmp);
     count_launch();
     exclusive_scan_u32(g->gen_tmp, g->gen_tmp2, n, g->scan_tmp, st);
     k_compact_ids<<<grid_for(n), 256, 0, st>>>(g->gen_tmp, g->gen_tmp2, n, g->ident + base, cnt); count_launch();
@@ -927,17 +941,23 @@ pr_status graph_refresh_ident(Graph *g) {
     g->ident_cnt[bin] = c;
     base += c;
   }
-  // sweep items: tier 0 and 1 one per vertex, tier-2 rows as kChunk-edge chunks
+  // sweep items: tier 0 and 1 one per vertex, tier-2 rows as chunks of chunk_len edges
   const uint32_t c01 = g->ident_cnt[0] + g->ident_cnt[1];
   const uint32_t nb = g->ident_cnt[2];
   const uint32_t *big = g->ident + c01;
-  k_chunk_counts<<<grid_for((uint64_t)nb + 1), 256, 0, st>>>(big, nb, g->in.rd, g->gen_tmp);
+  CK(cudaMemsetAsync(cnt, 0, 4, st));
+  k_chunk_counts<<<grid_for((uint64_t)nb + 1), 256, 0, st>>>(big, nb, g->in.rd, g->chunk_len, g->gen_tmp, cnt);
   count_launch();
   exclusive_scan_u32(g->gen_tmp, g->gen_tmp2, (uint64_t)nb + 1, g->scan_tmp, st);
-  uint32_t total = 0;
+  uint32_t total = 0, over = 0;
   CK(cudaMemcpyAsync(&total, g->gen_tmp2 + nb, 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&over, cnt, 4, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  if ((uint64_t)c01 + total > g->items_cap) {
+  if (over) {
+    g->err = "a vertex has more in-edges than 2^21 sweep chunks hold (raise chunk_len)";
+    return PR_ERR_CAPACITY;
+  }
+  if ((uint64_t)c01 + total > g->items_cap || total > g->chunk_cap) {  // items, and partials by chunk number
     cudaFree(g->items);
     cudaFree(g->items_cmp);
     cudaFree(g->partials);
@@ -957,7 +977,8 @@ pr_status graph_refresh_ident(Graph *g) {
     count_launch();
   }
   if (nb) {
-    k_items_chunks<<<grid_for(nb), 256, 0, st>>>(big, nb, g->in.rd, g->gen_tmp2, c01, g->items, g->item_pos);
+    k_items_chunks<<<grid_for(nb), 256, 0, st>>>(big, nb, g->in.rd, g->gen_tmp2, c01, g->chunk_len, g->items,
+                                                  g->item_pos);
     count_launch();
   }
   CK(cudaGetLastError());

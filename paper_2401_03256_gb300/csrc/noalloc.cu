@@ -50,6 +50,7 @@ __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 std::mutex g_addr_mu;
 unsigned char *g_addr[kMaxDevices] = {};
+int g_sms[kMaxDevices] = {};  // multiprocessors of each device, read with the address
 
 // off must be non-decreasing from 0 to m.
 __global__ void k_na_offsets(const uint64_t *off, uint32_t n, uint64_t m, NaCtl *ctl) {
@@ -153,6 +154,7 @@ extern "C" pr_status pr_static_noalloc(uint32_t n, int64_t m, const uint64_t *in
   if (!on_device(in_off, dev) || !on_device(ranks, dev) || (m > 0 && !on_device(in_col, dev)))
     return PR_ERR_INVALID_ARG;
   unsigned char *base_ptr = nullptr;
+  int sm_count = 0;
   {
     std::lock_guard<std::mutex> lk(g_addr_mu);
     if (!g_addr[dev]) {
@@ -162,9 +164,16 @@ extern "C" pr_status pr_static_noalloc(uint32_t n, int64_t m, const uint64_t *in
         cudaGetLastError();
         return PR_ERR_CUDA;
       }
+      int sms = 0;
+      if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+        cudaGetLastError();
+        return PR_ERR_CUDA;
+      }
+      g_sms[dev] = sms;
       g_addr[dev] = (unsigned char *)a;
     }
     base_ptr = g_addr[dev];
+    sm_count = g_sms[dev];
   }
   NaCtl *ctl = (NaCtl *)base_ptr;
   uint32_t *deg = (uint32_t *)(base_ptr + kCtlBytes);
@@ -198,7 +207,7 @@ extern "C" pr_status pr_static_noalloc(uint32_t n, int64_t m, const uint64_t *in
   k_na_init<<<blocks_for(n), kThreads, 0, st>>>(n, deg, ranks, c[0]);
   prdf::count_launch();
   const double base = (1.0 - p.alpha) / (double)n;
-  const unsigned grid = std::min<unsigned>(blocks_for(n), 152u * 8u);
+  const unsigned grid = std::min<unsigned>(blocks_for(n), (unsigned)sm_count * 8u);  // grid-stride rows
   int32_t it = 0;
   while (it < p.max_iter) {
     const int32_t k = std::min<int32_t>(kChunkIters, p.max_iter - it);

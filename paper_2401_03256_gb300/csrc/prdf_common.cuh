@@ -18,14 +18,15 @@ constexpr int kMaxIterLimit = 1000;       // hard cap on max_iter (control array
 constexpr uint64_t kSentinel = ~0ull;     // key of a dropped pair
 constexpr int kRankBlock = 256;           // threads per block of the rank kernel
 constexpr uint32_t kSmallSort = 4096;     // largest key count sorted by one block
-constexpr uint32_t kChunk = 512;          // edges per chunk of a long row in full and dense sweeps
-constexpr uint32_t kGroupMax = 64;        // full/dense sweeps: rows up to this length use 8-lane groups
+constexpr uint32_t kChunk = 512;          // entries per chunk of a long row (hub out-rows; the most a sweep chunk holds)
+constexpr uint32_t kGroupMax = 64;        // the longest row an 8-lane group of a sweep takes (two runs of 32)
 constexpr uint32_t kMaxComponents = 1024; // graphs in one batched handle
 
 // Tier of an in-degree in the full/dense sweep order: 0 = one thread (<= lo), 1 = an
-// 8-lane group (<= max(lo, kGroupMax)), 2 = kChunk-edge chunks taken by whole warps.
-__host__ __device__ inline int sweep_tier(uint32_t d, uint32_t lo) {
-  return d <= lo ? 0 : (d <= (lo > kGroupMax ? lo : kGroupMax) ? 1 : 2);
+// 8-lane group (<= max(lo, gmax), gmax <= kGroupMax), 2 = chunks of `chunk` edges taken by
+// whole warps (chunk <= kChunk).  gmax and chunk are tuning parameters of a handle.
+__host__ __device__ inline int sweep_tier(uint32_t d, uint32_t lo, uint32_t gmax) {
+  return d <= lo ? 0 : (d <= (lo > gmax ? lo : gmax) ? 1 : 2);
 }
 
 // ----------------------------------------------------------------- device helpers ---
@@ -55,6 +56,8 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 // Kernel-launch accounting (pr_kernel_launches); bumped after every launch.
 void count_launch();
 void count_launches(unsigned long long k);
+// Host-side fault injection (pr_inject_alloc_failure): true if this allocation must fail.
+bool alloc_fault();
 
 // ------------------------------------------------------------- rank storage ---
 // Ranks R, cached contributions C[u] = alpha R[u] / |out(u)| and the per-vertex factor A
@@ -166,6 +169,7 @@ struct RankCtl {
   uint32_t dense_ran;     // the per-iteration loop ran: its writeback listed the affected set
   uint32_t aff_total;     // affected vertices listed by that writeback (list 0)
   uint32_t pull_all;      // the pull kernel also pulls tier-0/1 rows (the marks after the last iteration)
+  unsigned long long bar_limit_ns;  // grid-barrier wait limit (0 = the default)
   uint32_t fin_only;      // a marking launch handed off only for the marks of its last iteration
   unsigned long long eprev;  // edges processed before the current iteration
   // trace (written by block 0): %globaltimer at kernel start, after phase 0 and after each

@@ -44,7 +44,7 @@ struct Graph {
   uint32_t ident_cnt[3] = {0, 0, 0};
   bool ident_dirty = true;
   // Sweep items (16 B each) in tier order: tier 0 and 1 items {v, start, len, 0}, then the
-  // kChunk-edge chunks of tier-2 rows {v, start of chunk, len | index in row << 10 |
+  // chunk_len-edge chunks of tier-2 rows {v, start of chunk, len | index in row << 10 |
   // several-chunks flag << 31, chunk number}.  items_cmp holds the affected subset during
   // dense Dynamic Frontier iterations.
   uint4 *items = nullptr, *items_cmp = nullptr;
@@ -102,7 +102,10 @@ struct Graph {
   unsigned long long *comp_last = nullptr;
   std::vector<pr_stats> comp_stats;  // per graph, from the last rank call
   uint32_t dense_div = 16;           // dense iterations once affected > n / dense_div
-  bool split_df = true;              // Dynamic Frontier calls may continue in k_rank_cont
+  bool split_df = true;              // dense iterations of marking calls continue in per-iteration launches
+  int32_t barrier_us = 0;            // grid-barrier wait limit of the persistent launches (0 = 4 s)
+  uint32_t chunk_len = kChunk;       // sweep order: edges per chunk of a tier-2 row (128, 256 or 512)
+  uint32_t group_max = kGroupMax;    // sweep order: longest row of an 8-lane group (16, 32 or 64)
   std::vector<double> trace_ms;      // last rank call: phase 0, then each iteration (device clock)
   std::vector<int64_t> trace_aff;    // affected vertices at the start of each iteration
   std::vector<int32_t> trace_kind;   // 0 sparse, 1 dense, 2 dense after compaction, 3 all vertices
@@ -111,7 +114,8 @@ struct Graph {
   // iterations and the CUDA graphs that loop over the iterations on the device
   uint8_t *emap = nullptr;           // [2][n] rank change above tau_f, by iteration parity; 0 between calls
   void *loops = nullptr;             // sweep.cu's cached graphs
-  int sweep_grid = 0;                // blocks of a sweep launch
+  int sweep_grid = 0;                // blocks of a full-sweep launch
+  int dfsweep_grid = 0;              // blocks of a dense Dynamic Frontier sweep launch
   int pro_grid = 0;                  // blocks of the cooperative prologue launch
   bool loop_sweeps = true;           // single-graph self-loop handles iterate in per-iteration launches
   std::string err;
@@ -135,7 +139,7 @@ enum RankMode { kModeDF = 0, kModeNaive = 1, kModeStatic = 2, kModeDT = 3, kMode
 pr_status rank_setup(Graph *g);  // grid size, control block
 pr_status rank_run(Graph *g, RankMode mode, pr_stats *stats);
 pr_status rank_init_contrib(Graph *g);  // C = R * adeg for all v, both parities
-pr_status rank_check(Graph *g, const double *in_d);  // PR_ERR_INVALID_ARG unless finite, >= 0, sum <= 1 + 1e-6
+pr_status rank_check(Graph *g, const double *in_d);  // PR_ERR_INVALID_ARG unless finite, in [0, 2], sum <= 2
 pr_status rank_set(Graph *g, const double *in_d);
 pr_status rank_get(Graph *g, double *out_d);
 pr_status rank_dead_mass(Graph *g, double *D);

@@ -133,7 +133,7 @@ __device__ __forceinline__ void sweep_tiers(const RankArgs<F32> &a, SweepIo<F32>
       if constexpr (CONT) record_expansion(a, push, v, lane, slot);
     }
 
-    // tier 1: rows of lo < len <= kGroupMax by 8-lane groups, four vertices per warp
+    // tier 1: rows of lo < len <= group_max by 8-lane groups, four vertices per warp
     {
       const uint32_t grp = lane >> 3, gl = lane & 7;
       for (uint32_t b0 = gwarp * 4; b0 < n1; b0 += nwarps * 4) {
@@ -180,7 +180,7 @@ __device__ __forceinline__ void sweep_tiers(const RankArgs<F32> &a, SweepIo<F32>
       }
     }
 
-    // tier 2: kChunk-edge chunks dealt round-robin to warps (a hub's consecutive chunks
+    // tier 2: chunks of chunk_len edges dealt round-robin to warps (a hub's consecutive chunks
     // land on different warps); a row split into several chunks is finished by the warp
     // that completes its last chunk, which adds the partial sums in chunk order
     C *part = a.partials;
@@ -216,7 +216,7 @@ __device__ __forceinline__ void sweep_tiers(const RankArgs<F32> &a, SweepIo<F32>
       int finish = 1;
       if (multi) {
         // publish this chunk's partial; the last of the row's chunks adds them up
-        const uint32_t nch = (__shfl_sync(kFull, deg, 0) + kChunk - 1) / kChunk;
+        const uint32_t nch = (__shfl_sync(kFull, deg, 0) + a.chunk - 1) / a.chunk;
         uint32_t old = 0;
         if (lane == 0) {
           part[ch.w] = sum;
@@ -1139,6 +1139,8 @@ static pr_status launch(Graph *g, RankMode mode, bool start_full) {
   a.start_full = start_full ? 1 : 0;
   a.bin_lo = (uint32_t)g->p.bin_lo;
   a.bin_hi = (uint32_t)g->p.bin_hi;
+  a.gmax = g->group_max;
+  a.chunk = g->chunk_len;
   a.ctl = g->ctl;
   a.ncomp = g->ncomp;
   a.comp = g->comp;
@@ -1252,6 +1254,12 @@ pr_status rank_run(Graph *g, RankMode mode, pr_stats *stats) {
   if (g->teleport && (rc = graph_refresh_dead(g)) != PR_OK) return rc;
   if ((rc = graph_refresh_ident(g)) != PR_OK) return rc;
   if (!g->use_graph) CK(cudaMemsetAsync(g->ctl, 0, sizeof(RankCtl), g->st));
+  if (g->barrier_us > 0 && !g->use_graph) {
+    // a short bounded wait for the grid barriers (tests of the time-out path)
+    g->ctl_h->bar_limit_ns = 1000ull * (unsigned long long)g->barrier_us;
+    CK(cudaMemcpyAsync(&g->ctl->bar_limit_ns, &g->ctl_h->bar_limit_ns, sizeof(unsigned long long),
+                       cudaMemcpyHostToDevice, g->st));
+  }
   if (g->ncomp > 1) {
     CK(cudaMemsetAsync(g->dRc, 0, 3ull * g->ncomp * sizeof(unsigned long long), g->st));
     CK(cudaMemsetAsync(g->comp_out, 0, 16ull * g->ncomp, g->st));
@@ -1399,10 +1407,11 @@ __global__ void k_dead_mass(const uint32_t *dead, uint32_t n_dead, const typenam
   }
 }
 
-// Validation of ranks a caller sets: every value finite and >= 0, and their sum at most
-// 1 + 1e-6 (ranks are a probability distribution; the 64-bit fixed point holds values below
-// 2, and with sum <= 1 no in-edge sum can reach that).  out[0] = bad values, out[1] = sum
-// (as bits of a double; the sum is exact enough for the bound).
+// Validation of ranks a caller sets: every value finite and in [0, 2], their sum at most 2.
+// Ranks are a distribution (sum 1), up to the drift of methods that leave some vertices as
+// they were (Dynamic Frontier); the 64-bit fixed point holds values below 2, and a mass of
+// at most 2 keeps every in-edge sum (at most alpha times the mass) below that too.
+// out[0] = bad values, out[1] = sum (as the bits of a double).
 __global__ void k_check_ranks(const double *in, uint32_t n, unsigned long long *out) {
   __shared__ double s_sum[8];
   __shared__ uint32_t s_bad[8];
@@ -1451,8 +1460,8 @@ pr_status rank_check(Graph *g, const double *in_d) {
         }
         sum += x;
       }
-      if (!(sum <= 1.0 + 1e-6)) {
-        g->err = "the ranks of each graph must sum to at most 1 (a probability distribution)";
+      if (!(sum <= 2.0)) {
+        g->err = "the ranks of each graph must sum to at most 2 (a distribution, up to drift)";
         return PR_ERR_INVALID_ARG;
       }
     }
@@ -1477,8 +1486,8 @@ pr_status rank_check(Graph *g, const double *in_d) {
     g->err = "ranks must be finite and in [0, 2]";
     return PR_ERR_INVALID_ARG;
   }
-  if (!(sum <= 1.0 + 1e-6)) {
-    g->err = "ranks must sum to at most 1 (a probability distribution)";
+  if (!(sum <= 2.0)) {
+    g->err = "ranks must sum to at most 2 (a distribution, up to drift)";
     return PR_ERR_INVALID_ARG;
   }
   return PR_OK;

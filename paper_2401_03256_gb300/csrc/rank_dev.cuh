@@ -107,6 +107,7 @@ struct RankArgs {
   int teleport;
   int start_full;  // Dynamic Frontier with every vertex affected from iteration 0
   uint32_t bin_lo, bin_hi;
+  uint32_t gmax, chunk;    // sweep tiers (sweep_tier) and edges per tier-2 chunk
   RankCtl *ctl;
   // split calls (single graph, self-loop mode): once the affected set is dense the marking
   // launch stops and the iterations continue in per-iteration launches (sweep.cu)
@@ -199,14 +200,17 @@ __device__ __forceinline__ bool grid_sync(RankCtl *ctl, uint32_t &epoch, uint32_
     const uint32_t target = epoch * gridDim.x;
     uint64_t t0 = 0;
     uint32_t spins = 0;
+    // the default limit is checked every 128 spins; a short limit set for tests, every spin
+    const unsigned long long lim = *(volatile unsigned long long *)&ctl->bar_limit_ns;
+    const uint32_t every = lim ? 0u : 127u;
     while (ld_acquire_u32(&ctl->bar) < target) {
       if (*(volatile uint32_t *)&ctl->err) break;
       __nanosleep(32);
-      if ((++spins & 127) == 0) {
+      if ((++spins & every) == 0) {
         uint64_t t = globaltimer_ns();
         if (t0 == 0) {
           t0 = t;
-        } else if (t - t0 > kBarrierTimeoutNs) {
+        } else if (t - t0 > (lim ? lim : kBarrierTimeoutNs)) {
           atomicExch(&ctl->err_where, epoch);
           atomicOr(&ctl->err, 1u);
           break;
@@ -254,8 +258,8 @@ __device__ __noinline__ void append_items(const RankArgs<F32> &a, const uint32_t
     if (i < k) {
       const uint32_t w = run[i];
       const uint32_t d = __ldg(&a.in_rd[w]).y;
-      t = (uint32_t)sweep_tier(d, a.bin_lo);
-      cw = t == 2 ? (d + kChunk - 1) / kChunk : 1u;
+      t = (uint32_t)sweep_tier(d, a.bin_lo, a.gmax);
+      cw = t == 2 ? (d + a.chunk - 1) / a.chunk : 1u;
       pos = __ldg(&a.item_pos[w]);
     }
 #pragma unroll
@@ -686,7 +690,7 @@ __device__ __forceinline__ uint32_t pull_join(const RankArgs<F32> &a, bool join,
   return (uint32_t)__popc(mask);
 }
 
-// The pull of iteration it for tier-2 rows (longer than kGroupMax; all2 chunk items from
+// The pull of iteration it for tier-2 rows (longer than the group limit; all2 chunk items from
 // items[off2]): a row not yet affected joins if an in-neighbour's change exceeded tau_f in
 // iteration it - 1.  Its chunks go to several warps, so the warp of the first chunk
 // decides for the row before the sweep.  Tier-0/1 rows are pulled inline by the sweep.

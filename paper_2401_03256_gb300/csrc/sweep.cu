@@ -35,9 +35,13 @@
 namespace prdf {
 
 #ifndef PRDF_SWEEP_MIN_BLOCKS
-#define PRDF_SWEEP_MIN_BLOCKS 5  // resident blocks per SM the sweep's register budget allows
+#define PRDF_SWEEP_MIN_BLOCKS 5  // resident blocks per SM the full sweep's register budget allows
+#endif
+#ifndef PRDF_DF_MIN_BLOCKS
+#define PRDF_DF_MIN_BLOCKS 5  // the same for the dense Dynamic Frontier sweeps
 #endif
 constexpr int kSweepMinBlocks = PRDF_SWEEP_MIN_BLOCKS;
+constexpr int kDfMinBlocks = PRDF_DF_MIN_BLOCKS;
 constexpr uint32_t kPullDiv = 256;  // more than n / kPullDiv first expansions: the next iteration pulls
 constexpr uint32_t kPullMin = 64;   // and at least this many
 
@@ -67,6 +71,7 @@ struct SweepArgs {
   typename Num<F32>::B ftol;
   unsigned long long tol_key;
   uint32_t n;
+  uint32_t chunk;          // edges per chunk of a tier-2 row
   int max_iter;
   cudaGraphConditionalHandle h_loop, h_pro, h_mode, h_fin;
 };
@@ -194,6 +199,19 @@ __device__ void sweep_decide(const SweepArgs<F32> &a, uint32_t it, bool all_item
   cudaGraphSetConditional(a.h_loop, cont ? 1u : 0u);
 }
 
+// Compacted iterations: the first-expansion test of a vertex whose item has no cache bit
+// yet (the stamp's expanded bit or the marking launch's bitmap decides; the item's bit is
+// set either way).  Out of line: after the first iteration over a compaction it is rare,
+// and keeping it out of the sweep loop keeps their registers.
+__device__ __noinline__ bool first_expansion_cmp(uint16_t *stamp, const uint32_t *xbits, uint4 *items_cmp, uint32_t v,
+                                                 uint32_t ci) {
+  const uint16_t s2 = __ldcg(reinterpret_cast<const unsigned short *>(stamp + v));
+  const bool was = (s2 & kStampExp) || ((__ldcg(xbits + (v >> 5)) >> (v & 31)) & 1u);
+  if (!was) stamp[v] = (uint16_t)(s2 | kStampExp);
+  items_cmp[ci].w = 1u;
+  return !was;
+}
+
 // One iteration of Eq. 1 over sweep items.  MODE 0: every vertex (Static, Naive-dynamic).
 // MODE 1: a dense Dynamic Frontier iteration over every item, vertices not affected
 // skipped; when pulling, a tier-0/1 vertex not yet affected first checks its in-row
@@ -202,10 +220,10 @@ __device__ void sweep_decide(const SweepArgs<F32> &a, uint32_t it, bool all_item
 // affected vertices.  Dynamic Frontier modes record change flags when asked, and first
 // expansions (changes above tau_f of vertices whose out-row was never marked from; the
 // stamp's top bit then caches that it was).  Per-vertex sums are taken exactly as in the
-// persistent kernel's sweeps: thread rows in runs of eight, 8-lane groups, kChunk-edge
+// persistent kernel's sweeps: thread rows in runs of eight, 8-lane groups, chunk-edge
 // chunks added in chunk order.
 template <bool F32, int MODE>
-__global__ void __launch_bounds__(kRankBlock, kSweepMinBlocks) k_sweep(const SweepArgs<F32> a) {
+__global__ void __launch_bounds__(kRankBlock, MODE == 0 ? kSweepMinBlocks : kDfMinBlocks) k_sweep(const SweepArgs<F32> a) {
   constexpr bool DF = MODE != 0, ALL = MODE == 1, CMP = MODE == 2;
   using S = Store<F32>;
   using R = typename S::R;
@@ -277,17 +295,14 @@ __global__ void __launch_bounds__(kRankBlock, kSweepMinBlocks) k_sweep(const Swe
       return !was;
     }
     if (cache) return false;
-    const uint16_t s2 = ldcg(a.stamp + v);
-    const bool was = (s2 & kStampExp) || ((__ldcg(a.xbits + (v >> 5)) >> (v & 31)) & 1u);
-    if (!was) a.stamp[v] = (uint16_t)(s2 | kStampExp);
-    a.items_cmp[ci].w = 1u;
-    return !was;
+    return first_expansion_cmp(a.stamp, a.xbits, a.items_cmp, v, ci);
   };
 
   // tier 0: one thread per vertex, 32 consecutive items per warp.  In all-item iterations
   // the stamp, the expanded word, the rank, the factor and the first eight columns are
   // loaded together (the row's loads do not wait for the stamp; a vertex not affected
-  // wastes them)
+  // wastes them).  These launches serve self-loop mode only, where a one-entry row is the
+  // vertex's own self-loop.
   for (uint32_t b0 = gwarp * 32; b0 < n0; b0 += nwarps * 32) {
     const uint32_t i = b0 + lane;
     bool act = false, join = false, push = false;
@@ -306,8 +321,8 @@ __global__ void __launch_bounds__(kRankBlock, kSweepMinBlocks) k_sweep(const Swe
       }
       rold = ldcg(Rin + v);
       ad = __ldg(a.adeg + v);
-      if (item.z <= 8) {
-        if (item.z > 0) q0 = ld_cols(a.in_col + item.y, pol_cols);
+      if (item.z > 1 && item.z <= 8) {  // a one-entry row is v's self-loop: no column needed
+        q0 = ld_cols(a.in_col + item.y, pol_cols);
         if (item.z > 4) q1 = ld_cols(a.in_col + item.y + 4, pol_cols);
       }
       act = !ALL || (st & kStampIt) <= itk;
@@ -325,9 +340,13 @@ __global__ void __launch_bounds__(kRankBlock, kSweepMinBlocks) k_sweep(const Swe
     if (act || join) {
       const uint32_t v = item.x;
       C sum;
-      if (item.z <= 8) {  // the first round of row_sum_thread, from the columns in hand
+      if (item.z == 1) {
+        // self-loop mode: the row is v's self-loop, and C[v] is contrib(R[v], A[v]) (stored
+        // that way by the previous iteration), so it is recomputed from the values in hand
+        sum = (C)0 + S::contrib(rold, ad);
+      } else if (item.z <= 8) {  // the first round of row_sum_thread, from the columns in hand
         sum = (C)0;
-        if (item.z > 0) sum += gather4(Cin, q0, min(4u, item.z), pol_c);
+        sum += gather4(Cin, q0, min(4u, item.z), pol_c);
         if (item.z > 4) sum += gather4(Cin, q1, min(4u, item.z - 4), pol_c);
       } else {
         sum = row_sum_thread(Cin, a.in_col + item.y, item.z, pol_cols, pol_c);
@@ -340,7 +359,7 @@ __global__ void __launch_bounds__(kRankBlock, kSweepMinBlocks) k_sweep(const Swe
     if constexpr (DF) note_expansion(ctl, a.xlist, push, item.x, lane, cap_end, xfull, xloc);
   }
 
-  // tier 1: rows of lo < len <= kGroupMax by 8-lane groups, four vertices per warp
+  // tier 1: rows of lo < len <= group_max (<= kGroupMax) by 8-lane groups, four vertices per warp
   {
     const uint32_t grp = lane >> 3, gl = lane & 7;
     for (uint32_t b0 = gwarp * 4; b0 < n1; b0 += nwarps * 4) {
@@ -402,7 +421,7 @@ __global__ void __launch_bounds__(kRankBlock, kSweepMinBlocks) k_sweep(const Swe
     }
   }
 
-  // tier 2: kChunk-edge chunks dealt round-robin to warps; a row split into several chunks
+  // tier 2: chunks of at most kChunk edges dealt round-robin to warps; a row split into several chunks
   // is finished by the warp that completes its last chunk, which adds the partial sums in
   // chunk order
   C *part = a.partials;
@@ -442,7 +461,7 @@ __global__ void __launch_bounds__(kRankBlock, kSweepMinBlocks) k_sweep(const Swe
     sum = warp_sum(sum);
     bool fin = true;
     if (several) {
-      const uint32_t nch = (__shfl_sync(kFull, deg, 0) + kChunk - 1) / kChunk;
+      const uint32_t nch = (__shfl_sync(kFull, deg, 0) + a.chunk - 1) / a.chunk;
       uint32_t old = 0;
       if (lane == 0) {
         part[ch.w] = sum;
@@ -958,6 +977,7 @@ SweepArgs<F32> sweep_args(const Graph *g, bool async) {
     a.tol_key = (unsigned long long)std::floor(std::min(g->p.tol * one, 9.0e18));
   }
   a.n = g->n;
+  a.chunk = g->chunk_len;
   a.max_iter = g->p.max_iter;
   return a;
 }
@@ -1046,7 +1066,7 @@ pr_status dense_impl(Graph *g, RankMode mode, const RankArgs<F32> &ra_in) {
   std::vector<unsigned char> key;
   append_key(key, a);
   append_key(key, ra);
-  append_key(key, g->sweep_grid);
+  append_key(key, g->dfsweep_grid);
   append_key(key, g->pro_grid);
   if (lg.exec && key != lg.key) lg.release();
   DenseInit ip{};
@@ -1092,10 +1112,10 @@ pr_status dense_impl(Graph *g, RankMode mode, const RankArgs<F32> &ra_in) {
     cudaGraphNode_t swnode = nullptr, s0 = nullptr, s1 = nullptr;
     CKG(add_conditional(&swnode, body, &inode, 1, lg.h_mode, cudaGraphCondTypeSwitch, sw, 2));
     void *sargs[] = {(void *)&a};
-    CKG(add_kernel(&s0, sw[0], nullptr, 0, (const void *)k_sweep<F32, 2>, dim3(g->sweep_grid), dim3(kRankBlock), sargs,
-                   false));
-    CKG(add_kernel(&s1, sw[1], nullptr, 0, (const void *)k_sweep<F32, 1>, dim3(g->sweep_grid), dim3(kRankBlock), sargs,
-                   false));
+    CKG(add_kernel(&s0, sw[0], nullptr, 0, (const void *)k_sweep<F32, 2>, dim3(g->dfsweep_grid), dim3(kRankBlock),
+                   sargs, false));
+    CKG(add_kernel(&s1, sw[1], nullptr, 0, (const void *)k_sweep<F32, 1>, dim3(g->dfsweep_grid), dim3(kRankBlock),
+                   sargs, false));
     void *iargs[] = {(void *)&ip};
     CKG(add_kernel(&lg.init, lg.graph, nullptr, 0, (const void *)k_dense_init, dim3(1), dim3(32), iargs, false));
     cudaGraphEdgeData ed{};
@@ -1139,16 +1159,16 @@ pr_status sweep_setup(Graph *g) {
     CKG(cudaMalloc((void **)&g->emap, 2ull * g->n));
     CKG(cudaMemsetAsync(g->emap, 0, 2ull * g->n, g->st));
   }
-  int per_sm = 8;
   const void *fns[2][3] = {{(const void *)k_sweep<false, 0>, (const void *)k_sweep<false, 1>, (const void *)k_sweep<false, 2>},
                            {(const void *)k_sweep<true, 0>, (const void *)k_sweep<true, 1>, (const void *)k_sweep<true, 2>}};
+  int per_mode[3] = {0, 0, 0};
   for (int k = 0; k < 3; k++) {
-    int b = 0;
-    CKG(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fns[g->f32 ? 1 : 0][k], kRankBlock, 0));
-    per_sm = std::min(per_sm, b);
+    CKG(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_mode[k], fns[g->f32 ? 1 : 0][k], kRankBlock, 0));
+    per_mode[k] = std::max(1, std::min(per_mode[k], 8));
   }
-  per_sm = std::max(1, per_sm);
-  g->sweep_grid = per_sm * g->sm_count;
+  // the two dense modes share a grid (a compacted sweep reads what an all-item sweep wrote)
+  g->sweep_grid = per_mode[0] * g->sm_count;
+  g->dfsweep_grid = std::min(per_mode[1], per_mode[2]) * g->sm_count;
   int per_sm_pro = 0;
   CKG(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
       &per_sm_pro, g->f32 ? (const void *)k_df_push<true> : (const void *)k_df_push<false>, kRankBlock, 0));

@@ -36,6 +36,7 @@ EXPORTED = (
     "pr_graph_create_batched", "pr_get_component_stats", "pr_set_tuning", "pr_get_tuning", "pr_autotune",
     "pr_set_graph_launch", "pr_server_config_default", "pr_server_create", "pr_server_add_graph",
     "pr_server_submit", "pr_server_wait", "pr_server_drain", "pr_server_destroy", "pr_static_noalloc",
+    "pr_inject_alloc_failure",
 )
 
 PR_NOALLOC_MAX_VERTICES = 1 << 18
@@ -59,7 +60,8 @@ class pr_stats(ctypes.Structure):
 
 class pr_tuning(ctypes.Structure):
     _fields_ = [("bin_lo", ctypes.c_int32), ("bin_hi", ctypes.c_int32), ("dense_div", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32), ("df_split", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("df_split", ctypes.c_int32), ("barrier_us", ctypes.c_int32),
+                ("chunk_len", ctypes.c_int32), ("group_max", ctypes.c_int32),
                 ("ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
@@ -156,6 +158,8 @@ def load(path: str = LIB_PATH):
     lib.pr_get_trace.argtypes = [vp, i32, vp, vp, vp, vp, ctypes.POINTER(i32)]
     lib.pr_kernel_launches.restype = ctypes.c_uint64
     lib.pr_kernel_launches.argtypes = []
+    lib.pr_inject_alloc_failure.restype = None
+    lib.pr_inject_alloc_failure.argtypes = [i32]
     lib.pr_last_error.restype = ctypes.c_char_p
     lib.pr_last_error.argtypes = [vp]
     lib.pr_status_string.restype = ctypes.c_char_p
@@ -239,8 +243,9 @@ def pr_get_component_stats(h: int, ncomp: int):
     return [arr[i] for i in range(ncomp)]
 
 
-def pr_set_tuning(h: int, bin_lo: int, bin_hi: int, dense_div: int, blocks_per_sm: int, df_split: int = 1) -> None:
-    t = pr_tuning(bin_lo, bin_hi, dense_div, blocks_per_sm, df_split, 0, 0.0)
+def pr_set_tuning(h: int, bin_lo: int, bin_hi: int, dense_div: int, blocks_per_sm: int, df_split: int = 1,
+                  barrier_us: int = 0, chunk_len: int = 512, group_max: int = 64) -> None:
+    t = pr_tuning(bin_lo, bin_hi, dense_div, blocks_per_sm, df_split, barrier_us, chunk_len, group_max, 0.0)
     _check(load().pr_set_tuning(h, ctypes.byref(t)), h)
 
 
@@ -396,6 +401,12 @@ def pr_kernel_launches() -> int:
     return int(load().pr_kernel_launches())
 
 
+def pr_inject_alloc_failure(after: int) -> None:
+    """Host-side fault injection: the next `after` allocations succeed, later ones fail
+    (negative: off)."""
+    load().pr_inject_alloc_failure(int(after))
+
+
 def pr_get_affected(h: int) -> np.ndarray:
     """Vertices marked affected by the last Dynamic Frontier or Traversal call (unordered)."""
     cnt = ctypes.c_int64()
@@ -429,8 +440,9 @@ class Graph:
     def tuning(self) -> pr_tuning:
         return pr_get_tuning(self.h)
 
-    def set_tuning(self, bin_lo: int, bin_hi: int, dense_div: int, blocks_per_sm: int, df_split: int = 1):
-        pr_set_tuning(self.h, bin_lo, bin_hi, dense_div, blocks_per_sm, df_split)
+    def set_tuning(self, bin_lo: int, bin_hi: int, dense_div: int, blocks_per_sm: int, df_split: int = 1,
+                   barrier_us: int = 0, chunk_len: int = 512, group_max: int = 64):
+        pr_set_tuning(self.h, bin_lo, bin_hi, dense_div, blocks_per_sm, df_split, barrier_us, chunk_len, group_max)
 
     def set_graph_launch(self, enable: bool):
         pr_set_graph_launch(self.h, enable)

@@ -178,27 +178,75 @@ def test_autotune_keeps_ranks_and_pending_marks(prdf):
         before = A.ranks().copy()
         t = A.autotune(4)
         assert t.bin_lo in (4, 8, 16, 32) and t.blocks_per_sm >= 1 and t.ms > 0
+        assert t.chunk_len in (128, 256, 512) and t.group_max in (16, 32, 64)
         assert np.array_equal(A.ranks(), before)
         cur = A.tuning()
-        assert (cur.bin_lo, cur.blocks_per_sm) == (t.bin_lo, t.blocks_per_sm)
+        assert (cur.bin_lo, cur.blocks_per_sm, cur.chunk_len, cur.group_max) == \
+            (t.bin_lo, t.blocks_per_sm, t.chunk_len, t.group_max)
         A.frontier()  # pending marks of the batch survive the autotuner
         assert np.max(np.abs(A.ranks() - Rdf)) <= TOL64
 
 
-@pytest.mark.parametrize("lo,bps", [(1, 1), (4, 2), (32, 3)])
-def test_results_do_not_depend_on_tuning(prdf, lo, bps):
-    g = synth.rmat(13, 8, seed=9)
-    b = synth.BatchStream(g, seed=9).next(1e-3)
+_TILINGS = [(1, 1, 512, 64), (4, 2, 128, 16), (32, 3, 256, 32), (8, 1, 32, 0), (16, 2, 64, 8)]
+
+
+@pytest.mark.parametrize("lo,bps,chunk,gmax", _TILINGS)
+@pytest.mark.parametrize("dead_end", ["selfloop", "teleport"])
+def test_results_do_not_depend_on_tuning(prdf, lo, bps, chunk, gmax, dead_end):
+    # fixed-point sums are exact in any order: any work distribution and sweep tiling gives
+    # bit-identical ranks, in per-iteration launches (self-loop) and in the persistent launch
+    # (teleport).  rmat(14, 16) has rows of several chunks at every chunk length
+    p = _params(prdf, dead_end=prdf.PR_DEADEND_TELEPORT if dead_end == "teleport" else prdf.PR_DEADEND_SELFLOOP)
+    g = synth.rmat(14, 16, seed=9)
+    assert np.bincount(g.dst, minlength=g.n).max() > 4 * 512
+    bs = [synth.BatchStream(g, seed=9).next(f) for f in (1e-4, 1e-3)]
     out = []
     for tune in (None, (lo, max(lo, 64), 4, bps)):
-        with prdf.Graph(g.n, g.src, g.dst) as A:
+        with prdf.Graph(g.n, g.src, g.dst, p) as A:
             if tune:
-                A.set_tuning(*tune)
+                A.set_tuning(*tune, chunk_len=chunk, group_max=gmax)
+                t = A.tuning()
+                assert (t.bin_lo, t.chunk_len, t.group_max) == (lo, chunk, gmax)
+            res = [A.static().iterations, A.ranks().copy()]
+            for b in bs:
+                A.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+                res += [A.frontier().affected_final, A.ranks().copy(), A.naive().iterations, A.ranks().copy()]
+            out.append(res)
+    for x, y in zip(out[0], out[1]):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("chunk,gmax", [(128, 16), (32, 0)])
+def test_fp32_tiling_changes_only_rounding(prdf, chunk, gmax):
+    # FP32 sums follow the tiling's order: a different tiling moves ranks by rounding only
+    g = synth.rmat(14, 16, seed=10)
+    b = synth.BatchStream(g, seed=10).next(1e-3)
+    out = []
+    for tune in (False, True):
+        with prdf.Graph(g.n, g.src, g.dst, _params(prdf, precision=prdf.PR_F32)) as A:
+            if tune:
+                t = A.tuning()
+                A.set_tuning(t.bin_lo, t.bin_hi, t.dense_div, t.blocks_per_sm, chunk_len=chunk, group_max=gmax)
             A.static()
             A.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
-            A.frontier()
-            out.append(A.ranks().copy())
-    assert np.array_equal(out[0], out[1])
+            st = A.frontier()
+            out.append((A.ranks().copy(), st.iterations))
+    assert np.max(np.abs(out[0][0] - out[1][0])) <= 1e-6
+    assert abs(out[0][1] - out[1][1]) <= 2
+
+
+def test_tiling_is_validated_and_a_refused_tile_keeps_the_old_one(prdf):
+    g = synth.rmat(10, 8, seed=11)
+    with prdf.Graph(g.n, g.src, g.dst) as A:
+        t = A.tuning()
+        assert (t.chunk_len, t.group_max) == (512, 64)
+        for chunk, gmax in [(0, 64), (48, 64), (1024, 64), (512, -1), (512, 65)]:
+            with pytest.raises(prdf.PrdfError) as e:
+                A.set_tuning(t.bin_lo, t.bin_hi, t.dense_div, t.blocks_per_sm, chunk_len=chunk, group_max=gmax)
+            assert e.value.status == prdf.PR_ERR_INVALID_ARG
+        t2 = A.tuning()
+        assert (t2.chunk_len, t2.group_max) == (512, 64)
+        A.static()
 
 
 @pytest.mark.parametrize("mode", ["frontier", "traversal"])

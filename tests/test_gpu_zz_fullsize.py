@@ -282,3 +282,62 @@ def test_fullsize_against_oracle(prdf, big, oracle_full, prec):
             got = np.sort(dg.affected().astype(np.int64))
             diff = np.setxor1d(got, aff_or.astype(np.int64)).shape[0]
             assert diff <= max(2, 0.01 * aff_or.shape[0]), (f, diff, aff_or.shape[0])
+
+
+KMER_N = 20_000_000
+KMER_FRACS = (1e-6, 1e-4)
+
+
+def _oracle_kmer(q):
+    """Oracle chain on the k-mer stand-in with 2e7 vertices (ranks near 5e-8, where the
+    64-bit fixed point keeps about 37 significant bits)."""
+    oracle.use_threads(oracle.host_cores())
+    g = synth.kmer(KMER_N, seed=7)
+    G = oracle.Graph.build(g.n, g.src, g.dst)
+    R, st = oracle.static_pr(G)
+    out = {"static": (R.copy(), st.iterations)}
+    s = synth.BatchStream(g, seed=7)
+    for f in KMER_FRACS:
+        b = s.next(f)
+        H, ed, ei = G.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+        Rn, aff, st = oracle.df_sync(G, H, ed, ei, R)
+        out[f] = (R.copy(), Rn.copy(), np.flatnonzero(aff).astype(np.uint32), st.iterations)
+        G.close()
+        G, R = H, Rn
+    q.put(out)
+
+
+def test_small_rank_magnitude_against_oracle(prdf):
+    """64-bit mode where ranks are near 5e-8: absolute L-inf <= 1e-9 and a relative error
+    per vertex <= 1e-6 against the oracle, for Static and two chained Dynamic Frontier
+    updates; affected sets within 1%."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    p = ctx.Process(target=_oracle_kmer, args=(q,))
+    p.start()
+    try:
+        res = q.get(timeout=1800)
+    finally:
+        p.join(timeout=60)
+    g = synth.kmer(KMER_N, seed=7)
+    s = synth.BatchStream(g, seed=7)
+    with prdf.Graph(g.n, g.src, g.dst) as dg:
+        st = dg.static()
+        R_or, _ = res["static"]
+        R = dg.ranks()
+        assert st.converged and R_or.max() < 1e-6  # the small-rank regime
+        assert np.max(np.abs(R - R_or)) <= 1e-9
+        assert np.max(np.abs(R - R_or) / R_or) <= 1e-6
+        for f in KMER_FRACS:
+            b = s.next(f)
+            R_prev, R_df, aff_or, it_df = res[f]
+            dg.set_ranks(R_prev)
+            dg.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+            st = dg.frontier()
+            R = dg.ranks()
+            assert st.converged and abs(st.iterations - it_df) <= 1
+            assert np.max(np.abs(R - R_df)) <= 1e-9, f
+            assert np.max(np.abs(R - R_df) / R_df) <= 1e-6, f
+            got = np.sort(dg.affected().astype(np.int64))
+            diff = np.setxor1d(got, aff_or.astype(np.int64)).shape[0]
+            assert diff <= max(2, 0.01 * aff_or.shape[0]), (f, diff, aff_or.shape[0])

@@ -4,8 +4,9 @@ Such callers (code that takes all of its device memory from a host application's
 latency-critical code that cannot take the device-wide synchronisation of cudaMalloc, or
 plugins handed buffers without the right to allocate) pass the graph and the output in
 device memory, and the library works in a fixed array of its own.  The ranks must match
-the allocating entry point's (pr_static on a graph handle) within the FP64 tolerance of the
-other tests, on consecutive calls that share that array.
+the allocating entry point's (pr_static on a graph handle) and the FP64 oracle's within the
+tolerance of the other tests, on consecutive calls that share that array, up to the
+largest accepted size.
 
 This file is named so that pytest collects it last.
 """
@@ -15,6 +16,7 @@ import numpy as np
 import pytest
 
 import __graft_entry__
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -59,13 +61,18 @@ def _device_csr(torch, off, col):
 
 def test_matches_allocating_static_on_consecutive_calls(env):
     prdf, torch = env
-    graphs = [synth.rmat(14, 8, seed=61), synth.rmat(11, 16, seed=62)]
-    for g in graphs:
-        assert g.n <= prdf.PR_NOALLOC_MAX_VERTICES
+    # the largest accepted size (the last bytes of the array in use), a smaller graph, and
+    # the largest again: each call must start clean although the shared array keeps the
+    # previous call's contents
+    graphs = [synth.rmat(18, 8, seed=60), synth.rmat(14, 8, seed=61), synth.rmat(11, 16, seed=62)]
+    assert graphs[0].n == prdf.PR_NOALLOC_MAX_VERTICES
     refs = [_reference(prdf, g) for g in graphs]
-    # the larger graph, then the smaller one, then the larger one again: each call must
-    # start clean although the shared array keeps the previous call's contents
-    for k, gi in enumerate([0, 1, 0]):
+    ors = []
+    for g in graphs:
+        G = oracle.Graph.build(g.n, g.src, g.dst)
+        ors.append(oracle.static_pr(G)[0])
+        G.close()
+    for k, gi in enumerate([0, 1, 2, 0]):
         g = graphs[gi]
         R_ref, it_ref, off, col = refs[gi]
         off_d, col_d = _device_csr(torch, off, col)
@@ -76,7 +83,8 @@ def test_matches_allocating_static_on_consecutive_calls(env):
         torch.cuda.synchronize()
         assert st == prdf.PR_OK, k
         R = out.cpu().numpy()
-        assert np.max(np.abs(R - R_ref)) <= TOL64, k
+        assert np.max(np.abs(R - R_ref)) <= TOL64, k  # the allocating entry point
+        assert np.max(np.abs(R - ors[gi])) <= TOL64, k  # the oracle
         assert s.converged == 1 and abs(s.iterations - it_ref) <= 1, (k, s.iterations, it_ref)
         assert abs(R.sum() - 1.0) <= 1e-9
         if k >= 1:
