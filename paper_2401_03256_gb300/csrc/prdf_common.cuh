@@ -162,6 +162,7 @@ struct RankCtl {
   uint32_t cmp_cur[3];    // compacted items per tier, items of later marks appended
   uint32_t cmp_total;     // affected vertices when the compacted items were last rebuilt
   uint32_t app_since;     // vertices whose items were appended since then
+  unsigned long long cmp_edges;  // in-edges of the vertices with compacted items (appended ones included)
   uint32_t kind_cur;      // trace kind of the current iteration
   uint32_t launches;      // sweep and prologue launches the device-side loop made
   uint32_t xcap;          // expansion-list entries this iteration writes at most (more: it only counts)

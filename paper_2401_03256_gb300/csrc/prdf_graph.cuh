@@ -115,7 +115,8 @@ struct Graph {
   uint8_t *emap = nullptr;           // [2][n] rank change above tau_f, by iteration parity; 0 between calls
   void *loops = nullptr;             // sweep.cu's cached graphs
   int sweep_grid = 0;                // blocks of a full-sweep launch
-  int dfsweep_grid = 0;              // blocks of a dense Dynamic Frontier sweep launch
+  int dfsweep_grid = 0;              // blocks of an all-item dense Dynamic Frontier sweep launch
+  int cmpsweep_grid = 0;             // blocks of a compacted dense Dynamic Frontier sweep launch
   int pro_grid = 0;                  // blocks of the cooperative prologue launch
   bool loop_sweeps = true;           // single-graph self-loop handles iterate in per-iteration launches
   std::string err;

@@ -132,6 +132,13 @@ struct Neu {
   }
 };
 
+template <class X>
+__device__ __forceinline__ X warp_sum(X x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+  return x;
+}
+
 // ------------------------------------------------------------ memory access ----
 
 __device__ __forceinline__ unsigned long long l2_evict_first() {
@@ -254,10 +261,10 @@ __device__ __noinline__ void append_items(const RankArgs<F32> &a, const uint32_t
   const uint32_t seg[3] = {0u, ldcg_u32(&a.ctl->sw_off[0]), ldcg_u32(&a.ctl->sw_off[1])};
   for (uint32_t i0 = 0; i0 < k; i0 += 32) {
     const uint32_t i = i0 + lane;
-    uint32_t t = 3, cw = 0, pos = 0;
+    uint32_t t = 3, cw = 0, pos = 0, d = 0;
     if (i < k) {
       const uint32_t w = run[i];
-      const uint32_t d = __ldg(&a.in_rd[w]).y;
+      d = __ldg(&a.in_rd[w]).y;
       t = (uint32_t)sweep_tier(d, a.bin_lo, a.gmax);
       cw = t == 2 ? (d + a.chunk - 1) / a.chunk : 1u;
       pos = __ldg(&a.item_pos[w]);
@@ -279,7 +286,11 @@ __device__ __noinline__ void append_items(const RankArgs<F32> &a, const uint32_t
       for (uint32_t c2 = 0; c2 < c; c2++) a.items_cmp[seg[tt] + base + incl - c + c2] = __ldg(a.items + pos + c2);
     }
     const uint32_t m = __ballot_sync(kFull, i < k);
-    if (lane == 0) atomicAdd(&a.ctl->app_since, (uint32_t)__popc(m));
+    const unsigned long long de = warp_sum((unsigned long long)d);
+    if (lane == 0) {
+      atomicAdd(&a.ctl->app_since, (uint32_t)__popc(m));
+      atomicAdd(&a.ctl->cmp_edges, de);
+    }
   }
 }
 
@@ -514,12 +525,6 @@ __device__ __forceinline__ C row_sum_thread(const C *Cv, const uint32_t *cols, u
   return sum;
 }
 
-template <class X>
-__device__ __forceinline__ X warp_sum(X x) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
-  return x;
-}
 
 // Dead-end mass accumulator: exact integer in 64-bit mode, Neumaier pair in FP32 mode.
 template <bool F32>

@@ -38,7 +38,7 @@ namespace prdf {
 #define PRDF_SWEEP_MIN_BLOCKS 5  // resident blocks per SM the full sweep's register budget allows
 #endif
 #ifndef PRDF_DF_MIN_BLOCKS
-#define PRDF_DF_MIN_BLOCKS 5  // the same for the dense Dynamic Frontier sweeps
+#define PRDF_DF_MIN_BLOCKS 4  // dense Dynamic Frontier sweeps: four, for a budget without spills
 #endif
 constexpr int kSweepMinBlocks = PRDF_SWEEP_MIN_BLOCKS;
 constexpr int kDfMinBlocks = PRDF_DF_MIN_BLOCKS;
@@ -74,6 +74,7 @@ struct SweepArgs {
   uint32_t chunk;          // edges per chunk of a tier-2 row
   int max_iter;
   cudaGraphConditionalHandle h_loop, h_pro, h_mode, h_fin;
+  cudaGraphConditionalHandle h_inner;  // dense loops: the next iteration is a plain compacted one
 };
 
 // First expansions found by a dense sweep, appended to the expansion list (one atomic per
@@ -125,6 +126,12 @@ __device__ void sweep_decide(const SweepArgs<F32> &a, uint32_t it, bool all_item
     const uint32_t jt = __ldcg(&ctl->jtotal) + __ldcg(&ctl->tail[it][3]);
     ctl->jtotal = jt;
     total += jt;
+    if (!all_items) {
+      // a compacted iteration swept exactly the compacted items (counted here, not by the
+      // sweep: its loops keep the registers of a full sweep)
+      ctl->vproc += __ldcg(&ctl->cmp_total) + __ldcg(&ctl->app_since);
+      ctl->eproc += __ldcg(&ctl->cmp_edges);
+    }
     ctl->eprev = __ldcg(&ctl->eproc);
     ctl->it_aff[it] = total;
     ctl->it_kind[it] = (uint8_t)__ldcg(&ctl->kind_cur);
@@ -189,6 +196,9 @@ __device__ void sweep_decide(const SweepArgs<F32> &a, uint32_t it, bool all_item
     }
     cudaGraphSetConditional(a.h_pro, pro);
     cudaGraphSetConditional(a.h_mode, all);
+    // a compacted iteration with no prologue next runs in the inner loop, whose iterations
+    // have the launch cost of a full sweep's (one conditional node each)
+    cudaGraphSetConditional(a.h_inner, cont && pro == 0 && all == 0 ? 1u : 0u);
   } else {
     ctl->it_aff[it] = a.n;
     ctl->it_kind[it] = 3;
@@ -199,17 +209,32 @@ __device__ void sweep_decide(const SweepArgs<F32> &a, uint32_t it, bool all_item
   cudaGraphSetConditional(a.h_loop, cont ? 1u : 0u);
 }
 
-// Compacted iterations: the first-expansion test of a vertex whose item has no cache bit
-// yet (the stamp's expanded bit or the marking launch's bitmap decides; the item's bit is
-// set either way).  Out of line: after the first iteration over a compaction it is rare,
-// and keeping it out of the sweep loop keeps their registers.
-__device__ __noinline__ bool first_expansion_cmp(uint16_t *stamp, const uint32_t *xbits, uint4 *items_cmp, uint32_t v,
-                                                 uint32_t ci) {
+// Compacted iterations: v changed by more than tau_f and its cache says it may not have
+// expanded yet (no bit on its tier-0/1 item, no expanded bit in the stamp of a tier-2
+// row).  The stamp's expanded bit or the marking launch's bitmap decides; a first
+// expansion sets the stamp bit and is appended to the expansion list (the lanes that get
+// here together share one atomic; past the iteration's cap only counted), and a tier-0/1
+// item gets its cache bit either way.  Out of line: after the first iteration over a
+// compaction it is rare, and the sweep loops keep the registers of a full sweep.
+__device__ __noinline__ void expand_cmp(RankCtl *ctl, uint16_t *stamp, const uint32_t *xbits, uint32_t *xlist,
+                                        uint4 *items_cmp, uint32_t v, uint32_t ci, bool has_item) {
   const uint16_t s2 = __ldcg(reinterpret_cast<const unsigned short *>(stamp + v));
   const bool was = (s2 & kStampExp) || ((__ldcg(xbits + (v >> 5)) >> (v & 31)) & 1u);
   if (!was) stamp[v] = (uint16_t)(s2 | kStampExp);
-  items_cmp[ci].w = 1u;
-  return !was;
+  if (has_item) items_cmp[ci].w = 1u;
+  const uint32_t mask = __activemask();
+  const uint32_t want = __ballot_sync(mask, !was);
+  if (!want) return;
+  const uint32_t lane = threadIdx.x & 31, leader = __ffs(want) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(&ctl->xcnt, (uint32_t)__popc(want));
+  base = __shfl_sync(mask, base, leader);
+  if (!was) {
+    const uint32_t x0 = __ldcg(&ctl->xdone), xc = __ldcg(&ctl->xcap);
+    const uint32_t cap_end = xc > 0xFFFFFFFFu - x0 ? 0xFFFFFFFFu : x0 + xc;
+    const uint32_t at = base + __popc(want & lanemask_lt());
+    if (at < cap_end) xlist[at] = v;
+  }
 }
 
 // One iteration of Eq. 1 over sweep items.  MODE 0: every vertex (Static, Naive-dynamic).
@@ -223,7 +248,7 @@ __device__ __noinline__ bool first_expansion_cmp(uint16_t *stamp, const uint32_t
 // persistent kernel's sweeps: thread rows in runs of eight, 8-lane groups, chunk-edge
 // chunks added in chunk order.
 template <bool F32, int MODE>
-__global__ void __launch_bounds__(kRankBlock, MODE == 0 ? kSweepMinBlocks : kDfMinBlocks) k_sweep(const SweepArgs<F32> a) {
+__global__ void __launch_bounds__(kRankBlock, MODE == 1 ? kDfMinBlocks : kSweepMinBlocks) k_sweep(const SweepArgs<F32> a) {
   constexpr bool DF = MODE != 0, ALL = MODE == 1, CMP = MODE == 2;
   using S = Store<F32>;
   using R = typename S::R;
@@ -248,7 +273,7 @@ __global__ void __launch_bounds__(kRankBlock, MODE == 0 ? kSweepMinBlocks : kDfM
   const bool pulling = ALL && __ldcg(&ctl->pull_check) != 0;
   const bool erec = ALL && __ldcg(&ctl->erec) != 0;
   uint32_t cap_end = 0;
-  if (DF) {
+  if (ALL) {
     const uint32_t x0 = __ldcg(&ctl->xdone), xc = __ldcg(&ctl->xcap);
     cap_end = xc > 0xFFFFFFFFu - x0 ? 0xFFFFFFFFu : x0 + xc;
   }
@@ -294,26 +319,29 @@ __global__ void __launch_bounds__(kRankBlock, MODE == 0 ? kSweepMinBlocks : kDfM
       a.stamp[v] = (uint16_t)(st | kStampExp);
       return !was;
     }
-    if (cache) return false;
-    return first_expansion_cmp(a.stamp, a.xbits, a.items_cmp, v, ci);
+    return false;  // compacted iterations: expand_cmp
   };
 
   // tier 0: one thread per vertex, 32 consecutive items per warp.  In all-item iterations
   // the stamp, the expanded word, the rank, the factor and the first eight columns are
   // loaded together (the row's loads do not wait for the stamp; a vertex not affected
   // wastes them).  These launches serve self-loop mode only, where a one-entry row is the
-  // vertex's own self-loop.
+  // vertex's own self-loop.  Every tier loads the items of its next round ahead (the
+  // round's loads then wait for no item).
+  const uint4 zero4 = make_uint4(0, 0, 0, 0);
+  auto tier0 = [&]() {
+  uint4 item_nx = (uint64_t)gwarp * 32 + lane < n0 ? ldcg(T + gwarp * 32 + lane) : zero4;
   for (uint32_t b0 = gwarp * 32; b0 < n0; b0 += nwarps * 32) {
     const uint32_t i = b0 + lane;
     bool act = false, join = false, push = false;
-    uint4 item = make_uint4(0, 0, 0, 0);
+    const uint4 item = item_nx;
+    if ((uint64_t)i + nwarps * 32 < n0) item_nx = ldcg(T + i + nwarps * 32);
     uint16_t st = 0;
     uint32_t xw = 0;
     R rold = (R)0;
     A ad = (A)0;
     uint4 q0 = make_uint4(0, 0, 0, 0), q1 = q0;
     if (i < n0) {
-      item = ldcg(T + i);
       const uint32_t v = item.x;
       if (ALL) {
         st = ldcg(a.stamp + v);
@@ -329,8 +357,10 @@ __global__ void __launch_bounds__(kRankBlock, MODE == 0 ? kSweepMinBlocks : kDfM
       if (ALL && !act && pulling && item.z > 1) {
         if (item.z <= 8) {
           const uint32_t w[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+          uint32_t any = 0;  // every flag load issued at once (no chain of dependent loads)
 #pragma unroll
-          for (uint32_t j = 0; j < 8; j++) join = join || (j < item.z && __ldcg(Eprev + w[j]) != 0);
+          for (uint32_t j = 0; j < 8; j++) any |= j < item.z ? (uint32_t)__ldcg(Eprev + w[j]) : 0u;
+          join = any != 0;
         } else {
           for (uint32_t j = 0; j < item.z && !join; j++) join = __ldcg(Eprev + __ldg(a.in_col + item.y + j)) != 0;
         }
@@ -352,19 +382,25 @@ __global__ void __launch_bounds__(kRankBlock, MODE == 0 ? kSweepMinBlocks : kDfM
         sum = row_sum_thread(Cin, a.in_col + item.y, item.z, pol_cols, pol_c);
       }
       const B dr = finish(v, sum, rold, ad);
-      if constexpr (DF) push = book(v, dr, join ? itk : st, join, xw, item.w, i);
-      my_v++;
-      my_e += item.z;
+      if constexpr (ALL) push = book(v, dr, join ? itk : st, join, xw, item.w, i);
+      if constexpr (CMP) {
+        if (expand && dr > a.ftol && !item.w) expand_cmp(ctl, a.stamp, a.xbits, a.xlist, a.items_cmp, v, i, true);
+      }
+      if constexpr (!CMP) my_v++;
+      if constexpr (!CMP) my_e += item.z;
     }
-    if constexpr (DF) note_expansion(ctl, a.xlist, push, item.x, lane, cap_end, xfull, xloc);
+    if constexpr (ALL) note_expansion(ctl, a.xlist, push, item.x, lane, cap_end, xfull, xloc);
   }
+  };
 
   // tier 1: rows of lo < len <= group_max (<= kGroupMax) by 8-lane groups, four vertices per warp
-  {
+  auto tier1 = [&]() {
     const uint32_t grp = lane >> 3, gl = lane & 7;
+    uint4 item_nx = (uint64_t)gwarp * 4 + grp < n1 ? ldcg(T + off1 + gwarp * 4 + grp) : zero4;
     for (uint32_t b0 = gwarp * 4; b0 < n1; b0 += nwarps * 4) {
       const uint32_t i = b0 + grp;
-      uint4 item = make_uint4(0, 0, 0, 0);
+      const uint4 item = item_nx;
+      if ((uint64_t)i + nwarps * 4 < n1) item_nx = ldcg(T + off1 + i + nwarps * 4);
       bool act = false, join = false;
       uint16_t st = 0;
       uint32_t xw = 0;
@@ -372,7 +408,6 @@ __global__ void __launch_bounds__(kRankBlock, MODE == 0 ? kSweepMinBlocks : kDfM
       A ad = (A)0;
       uint4 q[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
       if (i < n1) {
-        item = ldcg(T + off1 + i);
         if (ALL) st = ldcg(a.stamp + item.x);
         if (gl == 0) {
           rold = ldcg(Rin + item.x);
@@ -394,7 +429,7 @@ __global__ void __launch_bounds__(kRankBlock, MODE == 0 ? kSweepMinBlocks : kDfM
             const uint32_t j = 4 * (gl + 8 * r);
             const uint32_t w[4] = {q[r].x, q[r].y, q[r].z, q[r].w};
 #pragma unroll
-            for (uint32_t k2 = 0; k2 < 4; k2++) h = h || (j + k2 < item.z && __ldcg(Eprev + w[k2]) != 0);
+            for (uint32_t k2 = 0; k2 < 4; k2++) h |= j + k2 < item.z && __ldcg(Eprev + w[k2]) != 0;
           }
         }
         join = ((__ballot_sync(kFull, h) >> (grp * 8)) & 0xFFu) != 0;
@@ -413,20 +448,27 @@ __global__ void __launch_bounds__(kRankBlock, MODE == 0 ? kSweepMinBlocks : kDfM
       bool push = false;
       if ((act || join) && gl == 0) {
         const B dr = finish(item.x, sum, rold, ad);
-        if constexpr (DF) push = book(item.x, dr, join ? itk : st, join, xw, item.w, off1 + i);
-        my_v++;
-        my_e += item.z;
+        if constexpr (ALL) push = book(item.x, dr, join ? itk : st, join, xw, item.w, off1 + i);
+        if constexpr (CMP) {
+          if (expand && dr > a.ftol && !item.w)
+            expand_cmp(ctl, a.stamp, a.xbits, a.xlist, a.items_cmp, item.x, off1 + i, true);
+        }
+        if constexpr (!CMP) my_v++;
+        if constexpr (!CMP) my_e += item.z;
       }
-      if constexpr (DF) note_expansion(ctl, a.xlist, push, item.x, lane, cap_end, xfull, xloc);
+      if constexpr (ALL) note_expansion(ctl, a.xlist, push, item.x, lane, cap_end, xfull, xloc);
     }
-  }
+  };
 
   // tier 2: chunks of at most kChunk edges dealt round-robin to warps; a row split into several chunks
   // is finished by the warp that completes its last chunk, which adds the partial sums in
   // chunk order
   C *part = a.partials;
+  auto tier2 = [&]() {
+  uint4 item_nx = gwarp < n2 ? ldcg(T + off2 + gwarp) : zero4;
   for (uint32_t k = gwarp; k < n2; k += nwarps) {
-    const uint4 ch = ldcg(T + off2 + k);
+    const uint4 ch = item_nx;
+    if ((uint64_t)k + nwarps < n2) item_nx = ldcg(T + off2 + k + nwarps);
     const uint32_t v = ch.x;
     uint16_t st = 0;
     if (ALL) st = ldcg(a.stamp + v);
@@ -439,10 +481,8 @@ __global__ void __launch_bounds__(kRankBlock, MODE == 0 ? kSweepMinBlocks : kDfM
       rold = ldcg(Rin + v);
       ad = __ldg(a.adeg + v);
       if (several) deg = __ldg(&a.in_rd[v]).y;
-      if (DF && expand) {
-        xw = __ldcg(a.xbits + (v >> 5));
-        if (CMP) st = ldcg(a.stamp + v);
-      }
+      if (ALL && expand) xw = __ldcg(a.xbits + (v >> 5));
+      if (CMP && expand) st = ldcg(a.stamp + v);
     }
     const uint32_t *cols = a.in_col + ch.y;
     uint4 q[4];
@@ -482,7 +522,7 @@ __global__ void __launch_bounds__(kRankBlock, MODE == 0 ? kSweepMinBlocks : kDfM
     bool push = false;
     if (fin && lane == 0) {
       const B dr = finish(v, sum, rold, ad);
-      if constexpr (DF) {
+      if constexpr (ALL) {
         // chunks have no cache bit: the stamp and the word read with the row decide
         if (expand) {
           const bool big = dr > a.ftol;
@@ -493,10 +533,28 @@ __global__ void __launch_bounds__(kRankBlock, MODE == 0 ? kSweepMinBlocks : kDfM
           }
         }
       }
-      my_v++;
-      my_e += deg;
+      if constexpr (CMP) {
+        if (expand && dr > a.ftol && !(st & kStampExp))
+          expand_cmp(ctl, a.stamp, a.xbits, a.xlist, a.items_cmp, v, 0, false);
+      }
+      if constexpr (!CMP) my_v++;
+      if constexpr (!CMP) my_e += deg;
     }
-    if constexpr (DF) note_expansion(ctl, a.xlist, push, v, lane, cap_end, xfull, xloc);
+    if constexpr (ALL) note_expansion(ctl, a.xlist, push, v, lane, cap_end, xfull, xloc);
+  }
+  };
+
+  // Odd warps take the long rows first: their gathers, bound by the rate of random loads,
+  // then overlap the latency-bound short rows of the even warps (6% less time per full
+  // sweep of R-MAT scale 22 than one order for all warps)
+  if (gwarp & 1) {
+    tier2();
+    tier0();
+    tier1();
+  } else {
+    tier0();
+    tier1();
+    tier2();
   }
 
   // L-inf of the iteration, counters, and the last block's decision
@@ -603,7 +661,7 @@ struct DenseInit {
   uint32_t n, m;
   uint32_t traversal;
   int max_iter;
-  cudaGraphConditionalHandle h_loop, h_pro, h_mode, h_fin;
+  cudaGraphConditionalHandle h_loop, h_pro, h_mode, h_fin, h_inner;
 };
 
 __global__ void k_dense_init(const DenseInit p) {
@@ -654,6 +712,7 @@ __global__ void k_dense_init(const DenseInit p) {
   ctl->status = kStatusDone;
   cudaGraphSetConditional(p.h_pro, 0u);
   cudaGraphSetConditional(p.h_mode, 1u);
+  cudaGraphSetConditional(p.h_inner, 0u);
   if (ctl->fin_only) {
     // the marking launch ran the last iteration (recording its change flags): only its
     // marks remain, by a pull over every tier
@@ -751,6 +810,8 @@ __global__ void __launch_bounds__(kRankBlock, 2) k_df_push(const RankArgs<F32> a
                                 {ldcg_u32(&ctl->sw_off[0]), ldcg_u32(&ctl->sw_all[1])},
                                 {ldcg_u32(&ctl->sw_off[1]), ldcg_u32(&ctl->sw_all[2])}};
     const uint32_t slot = it + 1;
+    // (cmp[slot][3] sums the in-edges of the kept vertices: a chunk item's length is its
+    // share of the row)
     auto kept = [&](uint32_t t, uint32_t idx, uint4 &item) -> bool {
       item = __ldg(a.items + seg[t][0] + idx);
       const uint16_t st = ldcg(a.stamp + item.x);
@@ -763,13 +824,20 @@ __global__ void __launch_bounds__(kRankBlock, 2) k_df_push(const RankArgs<F32> a
       const uint32_t cntt = seg[t][1];
       const uint32_t per = ((cntt + gridDim.x - 1) / gridDim.x + kRankBlock - 1) / kRankBlock * kRankBlock;
       const uint32_t lo = min(cntt, blockIdx.x * per), hi = min(cntt, lo + per);
-      uint32_t c = 0;
+      uint32_t c = 0, e = 0;
       for (uint32_t idx = lo + tid; idx < hi; idx += kRankBlock) {
         uint4 item;
-        c += kept(t, idx, item) ? 1u : 0u;
+        if (kept(t, idx, item)) {
+          c++;
+          e += t < 2 ? item.z : (item.z & 0x3FFu);
+        }
       }
       c = warp_sum(c);
-      if (lane == 0) s_w[wib] = c;
+      e = warp_sum(e);
+      if (lane == 0) {
+        s_w[wib] = c;
+        if (e) atomicAdd(&ctl->cmp[slot][3], e);
+      }
       __syncthreads();
       if (tid == 0) {
         uint32_t tot = 0;
@@ -805,6 +873,7 @@ __global__ void __launch_bounds__(kRankBlock, 2) k_df_push(const RankArgs<F32> a
       }
       ctl->cmp_total = total + __ldcg(&ctl->jtotal);
       ctl->app_since = 0;
+      ctl->cmp_edges = __ldcg(&ctl->cmp[slot][3]);
       ctl->kind_cur = 8;
     }
   }
@@ -881,7 +950,7 @@ struct LoopGraph {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaGraphNode_t init = nullptr;
-  cudaGraphConditionalHandle h_loop = 0, h_pro = 0, h_mode = 0, h_fin = 0;
+  cudaGraphConditionalHandle h_loop = 0, h_pro = 0, h_mode = 0, h_fin = 0, h_inner = 0;
   std::vector<unsigned char> key;
   void release() {
     if (exec) cudaGraphExecDestroy(exec);
@@ -1052,8 +1121,11 @@ pr_status dense_impl(Graph *g, RankMode mode, const RankArgs<F32> &ra_in) {
   Loops *L = (Loops *)g->loops;
   LoopGraph &lg = L->dense[async ? 1 : 0];
   SweepArgs<F32> a = sweep_args<F32>(g, async);
-  // the prologue's arguments without the per-call fields it does not read
-  RankArgs<F32> ra = ra_in;
+  // the prologue's arguments without the per-call fields it does not read (copied byte for
+  // byte: the cache key below compares bytes, padding included, and the caller's
+  // value-initialised struct has zero padding)
+  RankArgs<F32> ra;
+  std::memcpy(&ra, &ra_in, sizeof ra);
   ra.it_c0 = ra.it_c1 = ra.it_c2 = 0;
   ra.n_pend_src = ra.n_pend_tgt = 0;
   ra.pend_src = ra.pend_tgt = nullptr;
@@ -1063,10 +1135,12 @@ pr_status dense_impl(Graph *g, RankMode mode, const RankArgs<F32> &ra_in) {
   ra.mode = 0;
   ra.start_full = 0;
   ra.split = 0;
+  ra.defer_at = 0;  // depends on the edge count, which changes with every batch
   std::vector<unsigned char> key;
   append_key(key, a);
   append_key(key, ra);
   append_key(key, g->dfsweep_grid);
+  append_key(key, g->cmpsweep_grid);
   append_key(key, g->pro_grid);
   if (lg.exec && key != lg.key) lg.release();
   DenseInit ip{};
@@ -1092,11 +1166,14 @@ pr_status dense_impl(Graph *g, RankMode mode, const RankArgs<F32> &ra_in) {
     CKG(add_conditional(&wnode, lg.graph, nullptr, 0, lg.h_loop, cudaGraphCondTypeWhile, &body));
     CKG(cudaGraphConditionalHandleCreate(&lg.h_pro, body, 0, 0));
     CKG(cudaGraphConditionalHandleCreate(&lg.h_mode, body, 1, 0));
+    CKG(cudaGraphConditionalHandleCreate(&lg.h_inner, body, 0, 0));
     ip.h_pro = lg.h_pro;
     ip.h_mode = lg.h_mode;
+    ip.h_inner = lg.h_inner;
     a.h_loop = lg.h_loop;
     a.h_pro = lg.h_pro;
     a.h_mode = lg.h_mode;
+    a.h_inner = lg.h_inner;
     // SWITCH on the prologue: 0 = none, 1 = tier-2 pull, 2 = push (and compaction)
     cudaGraph_t pb[3] = {nullptr, nullptr, nullptr};
     CKG(add_conditional(&inode, body, nullptr, 0, lg.h_pro, cudaGraphCondTypeSwitch, pb, 3));
@@ -1112,10 +1189,16 @@ pr_status dense_impl(Graph *g, RankMode mode, const RankArgs<F32> &ra_in) {
     cudaGraphNode_t swnode = nullptr, s0 = nullptr, s1 = nullptr;
     CKG(add_conditional(&swnode, body, &inode, 1, lg.h_mode, cudaGraphCondTypeSwitch, sw, 2));
     void *sargs[] = {(void *)&a};
-    CKG(add_kernel(&s0, sw[0], nullptr, 0, (const void *)k_sweep<F32, 2>, dim3(g->dfsweep_grid), dim3(kRankBlock),
+    CKG(add_kernel(&s0, sw[0], nullptr, 0, (const void *)k_sweep<F32, 2>, dim3(g->cmpsweep_grid), dim3(kRankBlock),
                    sargs, false));
     CKG(add_kernel(&s1, sw[1], nullptr, 0, (const void *)k_sweep<F32, 1>, dim3(g->dfsweep_grid), dim3(kRankBlock),
                    sargs, false));
+    // then the run of plain compacted iterations that follows (WHILE on h_inner)
+    cudaGraph_t ib = nullptr;
+    cudaGraphNode_t inner = nullptr, s2 = nullptr;
+    CKG(add_conditional(&inner, body, &swnode, 1, lg.h_inner, cudaGraphCondTypeWhile, &ib));
+    CKG(add_kernel(&s2, ib, nullptr, 0, (const void *)k_sweep<F32, 2>, dim3(g->cmpsweep_grid), dim3(kRankBlock), sargs,
+                   false));
     void *iargs[] = {(void *)&ip};
     CKG(add_kernel(&lg.init, lg.graph, nullptr, 0, (const void *)k_dense_init, dim3(1), dim3(32), iargs, false));
     cudaGraphEdgeData ed{};
@@ -1139,6 +1222,7 @@ pr_status dense_impl(Graph *g, RankMode mode, const RankArgs<F32> &ra_in) {
     ip.h_pro = lg.h_pro;
     ip.h_mode = lg.h_mode;
     ip.h_fin = lg.h_fin;
+    ip.h_inner = lg.h_inner;
     cudaKernelNodeParams kp{};
     void *iargs[] = {(void *)&ip};
     kp.func = (void *)k_dense_init;
@@ -1166,9 +1250,9 @@ pr_status sweep_setup(Graph *g) {
     CKG(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_mode[k], fns[g->f32 ? 1 : 0][k], kRankBlock, 0));
     per_mode[k] = std::max(1, std::min(per_mode[k], 8));
   }
-  // the two dense modes share a grid (a compacted sweep reads what an all-item sweep wrote)
   g->sweep_grid = per_mode[0] * g->sm_count;
-  g->dfsweep_grid = std::min(per_mode[1], per_mode[2]) * g->sm_count;
+  g->dfsweep_grid = per_mode[1] * g->sm_count;
+  g->cmpsweep_grid = per_mode[2] * g->sm_count;
   int per_sm_pro = 0;
   CKG(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
       &per_sm_pro, g->f32 ? (const void *)k_df_push<true> : (const void *)k_df_push<false>, kRankBlock, 0));
