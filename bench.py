@@ -633,27 +633,36 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                    "df_bytes": [], "naive_iters": [], "static_iters": [], "static_bytes": [], "naive_bytes": [],
                    "df_edges": [], "dt": [], "dt_iters": [], "dt_affected": [], "dfa": [], "dfa_iters": []} for f in FRACS}
 
+        def call(name, fn):
+            if not args.nvtx:
+                return fn()
+            torch.cuda.nvtx.range_push(name)
+            try:
+                return fn()
+            finally:
+                torch.cuda.nvtx.range_pop()
+
         def step(i, record):
             for fi, f in enumerate(FRACS):
                 b = batches[i][fi]
                 G.ranks(R_prev)
                 G.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
                 flush.zero_()
-                sd = G.frontier()
+                sd = call("df", G.frontier)
                 G.ranks(R_cur)
                 G.set_ranks(R_prev)
                 G_dt.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
                 G_dt.set_ranks(R_prev)
                 flush.zero_()
-                st = G_dt.traversal()
+                st = call("dt", G_dt.traversal)
                 G_as.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
                 G_as.set_ranks(R_prev)
                 flush.zero_()
-                sa = G_as.frontier_async()
+                sa = call("df_async", G_as.frontier_async)
                 flush.zero_()
-                sn = G.naive()
+                sn = call("naive", G.naive)
                 flush.zero_()
-                ss = G.static()
+                ss = call("static", G.static)
                 G.set_ranks(R_cur)
                 if record:
                     r = rec[f]
@@ -1270,6 +1279,9 @@ def main():
     ap.add_argument("--duration", type=float, default=2.0, help="serving: seconds of arrivals")
     ap.add_argument("--serve-duration", type=float, default=1.0,
                     help="serving leg of the default run: seconds of arrivals per rate")
+    ap.add_argument("--nvtx", action="store_true",
+                    help="mark each timed rank call with an NVTX range named after it (static, naive, df, dt, "
+                         "df_async), so that a profiler can select one call")
     ap.add_argument("--no-legs", action="store_true",
                     help="default run: skip the serving, batched and precision legs (and the precision oracle)")
     ap.add_argument("--slots", type=int, default=2, help="serving: concurrent updates")

@@ -166,6 +166,7 @@ struct RankCtl {
   uint32_t kind_cur;      // trace kind of the current iteration
   uint32_t launches;      // sweep and prologue launches the device-side loop made
   uint32_t xcap;          // expansion-list entries this iteration writes at most (more: it only counts)
+  uint32_t x_long;        // a compacted iteration listed a vertex with an out-row longer than kInlineOut
   uint32_t jtotal;        // vertices that joined by pulls (not in the lists)
   uint32_t dense_ran;     // the per-iteration loop ran: its writeback listed the affected set
   uint32_t aff_total;     // affected vertices listed by that writeback (list 0)

@@ -1279,7 +1279,8 @@ pr_status rank_run(Graph *g, RankMode mode, pr_stats *stats) {
   count_launches(g->ctl_h->launches);
   const RankCtl &h = *g->ctl_h;
   if (h.err) {
-    g->err = "rank kernel: a grid barrier wait timed out";
+    g->err = (h.err & 1u) ? "rank kernel: a grid barrier wait timed out"
+                          : "sweep kernel: a staged copy into shared memory did not complete";
     return PR_ERR_DEVICE_TIMEOUT;
   }
   float ms = 0.f;

@@ -12,6 +12,7 @@ namespace prdf {
 
 
 constexpr uint64_t kBarrierTimeoutNs = 4000000000ull;  // 4 s
+constexpr uint64_t kStageTimeoutNs = 1000000000ull;    // 1 s: a staged copy that has not landed by then failed
 constexpr int kWarps = kRankBlock / 32;
 constexpr uint32_t kFull = 0xffffffffu;
 constexpr uint16_t kNoStamp = 0xFFFF;
@@ -137,6 +138,49 @@ __device__ __forceinline__ X warp_sum(X x) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
   return x;
+}
+
+// ------------------------------------------------- bulk copies into shared memory ----
+// A warp stages a contiguous run of sweep items (16-byte aligned, a multiple of 16 bytes)
+// into its own shared-memory buffer with one cp.async.bulk issued by lane 0; completion is
+// tracked by an mbarrier (arrival count 1: lane 0's arrive with the expected bytes).
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init1(uint32_t bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// lane 0: expect `bytes` on `bar` and copy them from global `src` to shared `dst`.  The
+// buffer's previous contents were read by the warp before (a __syncwarp orders those
+// reads; the proxy fence orders them before the copy's writes).
+__device__ __forceinline__ void bulk_stage(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// Bounded wait for the phase of `bar` with the given parity to complete; false after
+// limit_ns (the caller records the error and stops using the buffer).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+  uint64_t t0 = 0;
+  for (uint32_t k = 0;; k++) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((k & 255) == 0) {
+      const uint64_t t = globaltimer_ns();
+      if (k == 0) t0 = t;
+      else if (t - t0 > limit_ns) return false;
+    }
+  }
 }
 
 // ------------------------------------------------------------ memory access ----

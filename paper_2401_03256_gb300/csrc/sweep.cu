@@ -44,6 +44,7 @@ constexpr int kSweepMinBlocks = PRDF_SWEEP_MIN_BLOCKS;
 constexpr int kDfMinBlocks = PRDF_DF_MIN_BLOCKS;
 constexpr uint32_t kPullDiv = 256;  // more than n / kPullDiv first expansions: the next iteration pulls
 constexpr uint32_t kPullMin = 64;   // and at least this many
+constexpr uint32_t kLightPush = 16384;  // at most this many first expansions: the light push may mark them
 
 // Kernel parameters of k_sweep (fixed for a handle until a buffer moves; the per-call
 // sizes travel in the control block).
@@ -66,6 +67,7 @@ struct SweepArgs {
   uint32_t *xbits;
   uint32_t *xlist;
   uint8_t *emap;
+  const uint2 *out_rd;     // out-row descriptors (the compacted iterations' expansion path reads lengths)
   RankCtl *ctl;
   typename S::R base;      // (1 - alpha) / n
   typename Num<F32>::B ftol;
@@ -173,6 +175,8 @@ __device__ void sweep_decide(const SweepArgs<F32> &a, uint32_t it, bool all_item
       ctl->compact_now = 0;
       ctl->push_items = 0;
       ctl->xcap = 0xFFFFFFFFu;
+      const bool x_long = __ldcg(&ctl->x_long) != 0;
+      ctl->x_long = 0;
       if (all_items && recorded && x > pull_at) {
         // many first expansions after an iteration that recorded its change flags: the next
         // iteration pulls (tiers 0 and 1 inline, tier-2 rows in a prologue); its own first
@@ -191,6 +195,9 @@ __device__ void sweep_decide(const SweepArgs<F32> &a, uint32_t it, bool all_item
         ctl->push_items = all_items ? 0u : 1u;
         ctl->kind_cur = all_items ? 8u : 5u;
         pro = (x || all_items) ? 2u : 0u;
+        // a few first expansions after a compacted iteration, none with a long out-row:
+        // the light push (no grid barrier) marks them
+        if (!all_items && x && x <= kLightPush && !x_long) pro = 3u;
         all = 0;
       }
     }
@@ -217,10 +224,14 @@ __device__ void sweep_decide(const SweepArgs<F32> &a, uint32_t it, bool all_item
 // item gets its cache bit either way.  Out of line: after the first iteration over a
 // compaction it is rare, and the sweep loops keep the registers of a full sweep.
 __device__ __noinline__ void expand_cmp(RankCtl *ctl, uint16_t *stamp, const uint32_t *xbits, uint32_t *xlist,
-                                        uint4 *items_cmp, uint32_t v, uint32_t ci, bool has_item) {
+                                        uint4 *items_cmp, const uint2 *out_rd, uint32_t v, uint32_t ci,
+                                        bool has_item) {
   const uint16_t s2 = __ldcg(reinterpret_cast<const unsigned short *>(stamp + v));
   const bool was = (s2 & kStampExp) || ((__ldcg(xbits + (v >> 5)) >> (v & 31)) & 1u);
-  if (!was) stamp[v] = (uint16_t)(s2 | kStampExp);
+  if (!was) {
+    stamp[v] = (uint16_t)(s2 | kStampExp);
+    if (__ldg(&out_rd[v]).y > kInlineOut) atomicOr(&ctl->x_long, 1u);  // the next push needs the grid
+  }
   if (has_item) items_cmp[ci].w = 1u;
   const uint32_t mask = __activemask();
   const uint32_t want = __ballot_sync(mask, !was);
@@ -256,8 +267,17 @@ __global__ void __launch_bounds__(kRankBlock, MODE == 1 ? kDfMinBlocks : kSweepM
   using A = typename S::A;
   using B = typename Num<F32>::B;
   __shared__ unsigned long long s_key[kWarps];
+  // compacted sweeps: tier-0 tiles of the compacted affected items (32 items of a round),
+  // double-buffered per warp, and their barriers
+  __shared__ __align__(128) uint4 s_items[CMP ? kWarps : 1][2][32];
+  __shared__ __align__(8) unsigned long long s_ibar[CMP ? kWarps : 1][2];
   RankCtl *ctl = a.ctl;
   const uint32_t tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
+  if (CMP && lane == 0) {
+    mbar_init1(smem_addr(&s_ibar[wib][0]));
+    mbar_init1(smem_addr(&s_ibar[wib][1]));
+  }
+  __syncwarp();
   const uint32_t nwarps = (gridDim.x * kRankBlock) >> 5, gwarp = (blockIdx.x * kRankBlock + tid) >> 5;
   const uint32_t it = __ldcg(&ctl->it_cur);
   const int par = it & 1;
@@ -326,16 +346,52 @@ __global__ void __launch_bounds__(kRankBlock, MODE == 1 ? kDfMinBlocks : kSweepM
   // the stamp, the expanded word, the rank, the factor and the first eight columns are
   // loaded together (the row's loads do not wait for the stamp; a vertex not affected
   // wastes them).  These launches serve self-loop mode only, where a one-entry row is the
-  // vertex's own self-loop.  Every tier loads the items of its next round ahead (the
-  // round's loads then wait for no item).
+  // vertex's own self-loop.
+  //
+  // Every tier has the items of its next round on the way while it works on the current
+  // one, so a round's row loads wait for no item: the next round's items are loaded into
+  // registers, except in tier 0 of a compacted sweep, which stages each round's 32
+  // compacted items (512 contiguous bytes) into the warp's shared-memory slot with one
+  // bulk copy issued a round ahead (two slots per warp; round r uses slot r & 1 for the
+  // (r >> 1)-th time, hence that phase parity).
   const uint4 zero4 = make_uint4(0, 0, 0, 0);
+  const uint32_t sbar = smem_addr(&s_ibar[CMP ? wib : 0][0]), sbuf = smem_addr(&s_items[CMP ? wib : 0][0][0]);
+  uint32_t rr = 0;
+  auto stage = [&](uint32_t first, uint32_t cnt, uint32_t slot) {
+    if (lane == 0) bulk_stage(sbuf + slot * 512u, T + first, cnt * 16u, sbar + slot * 8u);
+  };
+  // wait for round rr's items; on a copy that never lands, record the error, wait once
+  // more (bounded) for the copies in flight and tell the tier to stop
+  auto landed = [&](bool next_staged) -> bool {
+    const uint32_t slot = rr & 1u;
+    if (mbar_wait(sbar + slot * 8u, (rr >> 1) & 1u, kStageTimeoutNs)) return true;
+    if (lane == 0) atomicOr(&ctl->err, 2u);
+    mbar_wait(sbar + slot * 8u, (rr >> 1) & 1u, kStageTimeoutNs);
+    if (next_staged) mbar_wait(sbar + (slot ^ 1u) * 8u, ((rr + 1) >> 1) & 1u, kStageTimeoutNs);
+    return false;
+  };
   auto tier0 = [&]() {
-  uint4 item_nx = (uint64_t)gwarp * 32 + lane < n0 ? ldcg(T + gwarp * 32 + lane) : zero4;
-  for (uint32_t b0 = gwarp * 32; b0 < n0; b0 += nwarps * 32) {
+  uint4 item_nx = zero4;
+  if constexpr (CMP) {
+    if ((uint64_t)gwarp * 32 < n0) stage(gwarp * 32, min(32u, n0 - gwarp * 32), rr & 1u);
+  } else {
+    if ((uint64_t)gwarp * 32 + lane < n0) item_nx = ldcg(T + gwarp * 32 + lane);
+  }
+  for (uint32_t b0 = gwarp * 32; b0 < n0; b0 += nwarps * 32, rr++) {
     const uint32_t i = b0 + lane;
     bool act = false, join = false, push = false;
-    const uint4 item = item_nx;
-    if ((uint64_t)i + nwarps * 32 < n0) item_nx = ldcg(T + i + nwarps * 32);
+    uint4 item;
+    if constexpr (CMP) {
+      const uint32_t slot = rr & 1u;
+      __syncwarp();  // the other slot was read by every lane in the previous round
+      const bool nx = (uint64_t)b0 + nwarps * 32 < n0;
+      if (nx) stage(b0 + nwarps * 32, min(32u, n0 - b0 - nwarps * 32), slot ^ 1u);
+      if (!landed(nx)) break;
+      item = i < n0 ? s_items[wib][slot][lane] : zero4;
+    } else {
+      item = item_nx;
+      if ((uint64_t)i + nwarps * 32 < n0) item_nx = ldcg(T + i + nwarps * 32);
+    }
     uint16_t st = 0;
     uint32_t xw = 0;
     R rold = (R)0;
@@ -384,7 +440,7 @@ __global__ void __launch_bounds__(kRankBlock, MODE == 1 ? kDfMinBlocks : kSweepM
       const B dr = finish(v, sum, rold, ad);
       if constexpr (ALL) push = book(v, dr, join ? itk : st, join, xw, item.w, i);
       if constexpr (CMP) {
-        if (expand && dr > a.ftol && !item.w) expand_cmp(ctl, a.stamp, a.xbits, a.xlist, a.items_cmp, v, i, true);
+        if (expand && dr > a.ftol && !item.w) expand_cmp(ctl, a.stamp, a.xbits, a.xlist, a.items_cmp, a.out_rd, v, i, true);
       }
       if constexpr (!CMP) my_v++;
       if constexpr (!CMP) my_e += item.z;
@@ -395,7 +451,7 @@ __global__ void __launch_bounds__(kRankBlock, MODE == 1 ? kDfMinBlocks : kSweepM
 
   // tier 1: rows of lo < len <= group_max (<= kGroupMax) by 8-lane groups, four vertices per warp
   auto tier1 = [&]() {
-    const uint32_t grp = lane >> 3, gl = lane & 7;
+      const uint32_t grp = lane >> 3, gl = lane & 7;
     uint4 item_nx = (uint64_t)gwarp * 4 + grp < n1 ? ldcg(T + off1 + gwarp * 4 + grp) : zero4;
     for (uint32_t b0 = gwarp * 4; b0 < n1; b0 += nwarps * 4) {
       const uint32_t i = b0 + grp;
@@ -451,7 +507,7 @@ __global__ void __launch_bounds__(kRankBlock, MODE == 1 ? kDfMinBlocks : kSweepM
         if constexpr (ALL) push = book(item.x, dr, join ? itk : st, join, xw, item.w, off1 + i);
         if constexpr (CMP) {
           if (expand && dr > a.ftol && !item.w)
-            expand_cmp(ctl, a.stamp, a.xbits, a.xlist, a.items_cmp, item.x, off1 + i, true);
+            expand_cmp(ctl, a.stamp, a.xbits, a.xlist, a.items_cmp, a.out_rd, item.x, off1 + i, true);
         }
         if constexpr (!CMP) my_v++;
         if constexpr (!CMP) my_e += item.z;
@@ -535,7 +591,7 @@ __global__ void __launch_bounds__(kRankBlock, MODE == 1 ? kDfMinBlocks : kSweepM
       }
       if constexpr (CMP) {
         if (expand && dr > a.ftol && !(st & kStampExp))
-          expand_cmp(ctl, a.stamp, a.xbits, a.xlist, a.items_cmp, v, 0, false);
+          expand_cmp(ctl, a.stamp, a.xbits, a.xlist, a.items_cmp, a.out_rd, v, 0, false);
       }
       if constexpr (!CMP) my_v++;
       if constexpr (!CMP) my_e += deg;
@@ -696,6 +752,7 @@ __global__ void k_dense_init(const DenseInit p) {
   ctl->m_cur = p.m;
   ctl->xdone = ctl->xcnt;
   ctl->xcap = max(kPullMin, p.n / kPullDiv) + 1;  // first iteration: a pull may follow
+  ctl->x_long = 0;
   ctl->jtotal = 0;
   ctl->eprev = ctl->eproc;
   ctl->dense_ran = 1;
@@ -885,6 +942,42 @@ __global__ void __launch_bounds__(kRankBlock, 2) k_df_push(const RankArgs<F32> a
   }
 }
 
+// Prologue of a compacted iteration after which a few vertices expanded for the first time,
+// none of them with an out-row longer than kInlineOut: the warps that read them from the
+// expansion list mark their out-rows and append the items of the newly marked vertices,
+// with no grid barrier (the hub queue is not needed), so it costs a plain launch instead
+// of a cooperative one with barriers.
+template <bool F32>
+__global__ void __launch_bounds__(kRankBlock, 2) k_df_push_light(const RankArgs<F32> a) {
+  __shared__ uint32_t s_mbuf[kWarps][4 * kMarkBuf];
+  RankCtl *ctl = a.ctl;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
+  const uint32_t nwarps = (gridDim.x * kRankBlock) >> 5, gwarp = (blockIdx.x * kRankBlock + tid) >> 5;
+  const uint32_t it = ldcg_u32(&ctl->it_cur);
+  if (blockIdx.x == 0 && tid == 0) atomicAdd(&ctl->launches, 1u);
+  uint32_t cnt[3];
+#pragma unroll
+  for (int b = 0; b < 3; b++) cnt[b] = ldcg_u32(&ctl->dcnt[b]);
+  const uint32_t pn = ldcg_u32(&ctl->push_n), lo = ldcg_u32(&ctl->push_lo);
+  WarpBuf wb{s_mbuf[wib], {0u, 0u, 0u, 0u}, false, it, true};
+  unsigned long long app = 0, xv = 0, xe = 0;
+  for (uint32_t k0 = gwarp * 32; k0 < pn; k0 += nwarps * 32) {
+    const bool p = k0 + lane < pn;
+    const uint32_t x = p ? ldcg_u32(a.xlist + lo + k0 + lane) : 0u;
+    const ExpandOut o = expand_lanes(a, p ? 1 : 0, x, it, cnt[0], cnt[1], cnt[2], &wb);
+    app += o.app;
+    xv += o.xv;
+    xe += o.xe;
+  }
+  flush_marks(a, it, cnt, lane, wb);
+  const unsigned long long s0 = warp_sum(app), s1 = warp_sum(xv), s2 = warp_sum(xe);
+  if (lane == 0) {
+    if (s0) atomicAdd(&ctl->appended, s0);
+    if (s1) atomicAdd(&ctl->expv, s1);
+    if (s2) atomicAdd(&ctl->expe, s2);
+  }
+}
+
 // Writeback of a dense Dynamic Frontier call: every affected vertex (stamp set) gets its
 // final values in both parities (parity iterations & 1), its per-call marks and change
 // flags are cleared, and it is listed in list 0 (each block lists its own range of
@@ -1031,6 +1124,7 @@ SweepArgs<F32> sweep_args(const Graph *g, bool async) {
   a.xbits = g->xbits;
   a.xlist = g->xlist;
   a.emap = g->emap;
+  a.out_rd = g->out.rd;
   a.ctl = g->ctl;
   const double n = (double)g->n;
   if constexpr (F32) {
@@ -1174,9 +1268,9 @@ pr_status dense_impl(Graph *g, RankMode mode, const RankArgs<F32> &ra_in) {
     a.h_pro = lg.h_pro;
     a.h_mode = lg.h_mode;
     a.h_inner = lg.h_inner;
-    // SWITCH on the prologue: 0 = none, 1 = tier-2 pull, 2 = push (and compaction)
-    cudaGraph_t pb[3] = {nullptr, nullptr, nullptr};
-    CKG(add_conditional(&inode, body, nullptr, 0, lg.h_pro, cudaGraphCondTypeSwitch, pb, 3));
+    // SWITCH on the prologue: 0 = none, 1 = tier-2 pull, 2 = push (and compaction), 3 = light push
+    cudaGraph_t pb[4] = {nullptr, nullptr, nullptr, nullptr};
+    CKG(add_conditional(&inode, body, nullptr, 0, lg.h_pro, cudaGraphCondTypeSwitch, pb, 4));
     cudaGraphNode_t enode = nullptr, pull_node = nullptr;
     CKG(cudaGraphAddEmptyNode(&enode, pb[0], nullptr, 0));
     void *pargs[] = {(void *)&ra};
@@ -1184,6 +1278,9 @@ pr_status dense_impl(Graph *g, RankMode mode, const RankArgs<F32> &ra_in) {
                    dim3(kRankBlock), pargs, false));
     CKG(add_kernel(&pnode, pb[2], nullptr, 0, (const void *)k_df_push<F32>, dim3(g->pro_grid), dim3(kRankBlock), pargs,
                    true));
+    cudaGraphNode_t lnode = nullptr;
+    CKG(add_kernel(&lnode, pb[3], nullptr, 0, (const void *)k_df_push_light<F32>, dim3(std::max(1, g->sm_count)),
+                   dim3(kRankBlock), pargs, false));
     // SWITCH on the iteration's mode: 0 = compacted items, 1 = every item
     cudaGraph_t sw[2] = {nullptr, nullptr};
     cudaGraphNode_t swnode = nullptr, s0 = nullptr, s1 = nullptr;
