@@ -38,7 +38,7 @@ namespace prdf {
 #define PRDF_SWEEP_MIN_BLOCKS 5  // resident blocks per SM the full sweep's register budget allows
 #endif
 #ifndef PRDF_DF_MIN_BLOCKS
-#define PRDF_DF_MIN_BLOCKS 4  // dense Dynamic Frontier sweeps: four, for a budget without spills
+#define PRDF_DF_MIN_BLOCKS 5  // all-item Dynamic Frontier sweeps: five (some spills, measured faster than four)
 #endif
 constexpr int kSweepMinBlocks = PRDF_SWEEP_MIN_BLOCKS;
 constexpr int kDfMinBlocks = PRDF_DF_MIN_BLOCKS;
@@ -859,10 +859,12 @@ __global__ void __launch_bounds__(kRankBlock, 2) k_df_push(const RankArgs<F32> a
     if (items && !compact && ldcg_u32(&ctl->app_since) > ldcg_u32(&ctl->cmp_total) / 16) compact = true;
   }
   if (compact) {
-    // keep the items of vertices stamped <= it, in tier order within each block's range:
-    // each block counts its range, takes its offset with one atomic per tier, then writes
-    // its kept items in order (block-wide prefix per round of 256 items)
-    __shared__ uint32_t s_w[kWarps], s_base;
+    // keep the items of vertices stamped <= it, one pass: a block takes rounds of 2048
+    // items (eight per thread, each a coalesced warp-wide load), counts the kept ones per
+    // (load, warp), reserves their places with one atomic per round and writes them in the
+    // round's item order (rounds land in the order of their atomics); the stamp also sets
+    // each tier-0/1 item's cache bit
+    __shared__ uint32_t s_cnt[8][kWarps], s_base;
     const uint32_t seg[3][2] = {{0u, ldcg_u32(&ctl->sw_all[0])},
                                 {ldcg_u32(&ctl->sw_off[0]), ldcg_u32(&ctl->sw_all[1])},
                                 {ldcg_u32(&ctl->sw_off[1]), ldcg_u32(&ctl->sw_all[2])}};
@@ -877,49 +879,50 @@ __global__ void __launch_bounds__(kRankBlock, 2) k_df_push(const RankArgs<F32> a
         item.w = ((st & kStampExp) || (__ldcg(a.xbits + (item.x >> 5)) >> (item.x & 31)) & 1u) ? 1u : 0u;
       return keep;
     };
+    constexpr uint32_t kRound = 8 * kRankBlock;
     for (uint32_t t = 0; t < 3; t++) {
       const uint32_t cntt = seg[t][1];
-      const uint32_t per = ((cntt + gridDim.x - 1) / gridDim.x + kRankBlock - 1) / kRankBlock * kRankBlock;
-      const uint32_t lo = min(cntt, blockIdx.x * per), hi = min(cntt, lo + per);
-      uint32_t c = 0, e = 0;
-      for (uint32_t idx = lo + tid; idx < hi; idx += kRankBlock) {
-        uint4 item;
-        if (kept(t, idx, item)) {
-          c++;
-          e += t < 2 ? item.z : (item.z & 0x3FFu);
+      uint32_t e = 0;
+      for (uint32_t r0 = blockIdx.x * kRound; r0 < cntt; r0 += gridDim.x * kRound) {
+        uint4 item[8];
+        uint32_t keepm = 0;
+#pragma unroll
+        for (uint32_t j = 0; j < 8; j++) {
+          const uint32_t idx = r0 + j * kRankBlock + tid;
+          item[j] = make_uint4(0, 0, 0, 0);
+          if (idx < cntt && kept(t, idx, item[j])) {
+            keepm |= 1u << j;
+            e += t < 2 ? item[j].z : (item[j].z & 0x3FFu);
+          }
         }
+#pragma unroll
+        for (uint32_t j = 0; j < 8; j++) {
+          const uint32_t m = __ballot_sync(kFull, (keepm >> j) & 1u);
+          if (lane == 0) s_cnt[j][wib] = __popc(m);
+        }
+        __syncthreads();
+        if (tid == 0) {
+          uint32_t tot = 0;
+          for (int j = 0; j < 8; j++)
+            for (int w = 0; w < kWarps; w++) {
+              const uint32_t c = s_cnt[j][w];
+              s_cnt[j][w] = tot;
+              tot += c;
+            }
+          s_base = tot ? atomicAdd(&ctl->cmp[slot][t], tot) : 0u;
+        }
+        __syncthreads();
+        const uint32_t base = s_base;
+#pragma unroll
+        for (uint32_t j = 0; j < 8; j++) {
+          const bool k = (keepm >> j) & 1u;
+          const uint32_t m = __ballot_sync(kFull, k);
+          if (k) a.items_cmp[seg[t][0] + base + s_cnt[j][wib] + __popc(m & lanemask_lt())] = item[j];
+        }
+        __syncthreads();  // s_cnt and s_base are reused by the next round
       }
-      c = warp_sum(c);
       e = warp_sum(e);
-      if (lane == 0) {
-        s_w[wib] = c;
-        if (e) atomicAdd(&ctl->cmp[slot][3], e);
-      }
-      __syncthreads();
-      if (tid == 0) {
-        uint32_t tot = 0;
-        for (int w = 0; w < kWarps; w++) tot += s_w[w];
-        s_base = tot ? atomicAdd(&ctl->cmp[slot][t], tot) : 0u;
-      }
-      __syncthreads();
-      uint32_t at = s_base;
-      for (uint32_t i0 = lo; i0 < hi; i0 += kRankBlock) {
-        const uint32_t idx = i0 + tid;
-        uint4 item = make_uint4(0, 0, 0, 0);
-        const bool keep = idx < hi && kept(t, idx, item);
-        const uint32_t mask = __ballot_sync(kFull, keep);
-        __syncthreads();
-        if (lane == 0) s_w[wib] = __popc(mask);
-        __syncthreads();
-        uint32_t before = 0, all = 0;
-        for (int w = 0; w < kWarps; w++) {
-          before += w < (int)wib ? s_w[w] : 0u;
-          all += s_w[w];
-        }
-        if (keep) a.items_cmp[seg[t][0] + at + before + __popc(mask & lanemask_lt())] = item;
-        at += all;
-      }
-      __syncthreads();
+      if (lane == 0 && e) atomicAdd(&ctl->cmp[slot][3], e);
     }
     if (!grid_sync(ctl, epoch, &s_err)) return;
     if (blockIdx.x == 0 && tid == 0) {

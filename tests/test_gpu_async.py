@@ -6,7 +6,8 @@ Every run stops under the same L-inf test (tau = 1e-10); the oracle's asynchrono
 synchronous readings differ from each other and from the exact solution by about
 5 tau / (1 - alpha) ~ 6e-10 on these graphs, so the GPU result must lie within 2e-9 of
 both (FP32: 1e-6), converge, and need no more iterations than the synchronous form, run
-on the GPU in the same precision, plus one.
+on the GPU in the same precision, plus one (FP32: plus three, since its stop near tau
+rests on a few float ulps).
 """
 import numpy as np
 import pytest
@@ -60,7 +61,11 @@ def _async_case(prdf, g, fracs, seed, params=None, tol=LOOSE64):
             R_a, aff_a, st_a = oracle.df_async(G, H, ed, ei, R_or)
             R_s, aff_s, st_s = oracle.df_sync(G, H, ed, ei, R_or)
             assert st.converged
-            assert st.iterations <= st_sync.iterations + 1, (st.iterations, st_sync.iterations, st_s.iterations)
+            # FP32: near the fixed point the L-inf change of either form is a few float ulps
+            # of the largest ranks (~1e-10 = tau), so where the in-place reads land moves its
+            # stop by up to a few iterations; 64-bit: at most one more
+            slack = 3 if tol == LOOSE32 else 1
+            assert st.iterations <= st_sync.iterations + slack, (st.iterations, st_sync.iterations, st_s.iterations)
             assert np.max(np.abs(R - R_a)) <= tol
             assert np.max(np.abs(R - R_s)) <= tol
             got = set(dg.affected().tolist())
