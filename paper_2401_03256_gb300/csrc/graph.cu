@@ -460,54 +460,117 @@ __global__ void k_pack_rows(const uint2 *rd, uint32_t n, const uint32_t *col, co
   for (uint32_t j = lane; j < d.y; j += 32) packed[o + j] = col[d.x + j];
 }
 
-__global__ void k_bin_flags(const uint2 *rd, uint32_t n, uint32_t lo, uint32_t gmax, int bin, uint32_t *flags) {
-  uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= n) return;
-  flags[v] = sweep_tier(rd[v].y, lo, gmax) == bin;
-}
-
-// Chunks per long-row vertex (tier 2 of the sweep order).
-// A chunk's index within its row has 21 bits in the item (chunk_item): `over` is set when a
-// row needs more than 2^21 chunks.
-__global__ void k_chunk_counts(const uint32_t *big, uint32_t nb, const uint2 *rd, uint32_t chunk, uint32_t *cnt,
-                               uint32_t *over) {
-  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < nb) {
-    const uint32_t c = (rd[big[i]].y + chunk - 1) / chunk;
-    cnt[i] = c;
-    if (c > (1u << 21)) *over = 1u;
-  } else if (i == nb) {
-    cnt[i] = 0;
-  }
-}
-
-__global__ void k_items_simple(const uint32_t *ident, uint32_t cnt, const uint2 *rd, uint4 *items,
-                               uint32_t *item_pos) {
-  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= cnt) return;
-  uint32_t v = ident[i];
-  uint2 d = rd[v];
-  items[i] = make_uint4(v, d.x, d.y, 0u);
-  item_pos[v] = i;
-}
-
-__global__ void k_items_chunks(const uint32_t *big, uint32_t nb, const uint2 *rd, const uint32_t *start,
-                               uint32_t base, uint32_t chunk, uint4 *items, uint32_t *item_pos) {
-  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nb) return;
-  uint32_t v = big[i];
-  uint2 d = rd[v];
-  uint32_t nch = (d.y + chunk - 1) / chunk, s = start[i];
-  for (uint32_t c = 0; c < nch; c++) items[base + s + c] = chunk_item(v, d, c, nch, s + c, chunk);
-  item_pos[v] = base + s;
-}
-
 __global__ void k_dead_flags(const uint2 *rd, uint32_t n, uint32_t *flags) {
   uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v < n) flags[v] = rd[v].y == 0;
 }
 
 // Stable compaction of the ids whose flag is set; count = total.
+// Sweep-item rebuild in two passes over the vertices (tile of kIdentTile per block): the
+// first counts each tile's vertices per tier and the chunk items of its tier-2 rows; after
+// one exclusive scan of those counts (tier 0, 1, 2 tiles back to back, then the chunk
+// counts), the second writes every vertex's item(s) at its place, in ascending vertex order
+// within each tier.
+constexpr uint32_t kIdentTile = 4096;
+
+__global__ void k_tier_counts(const uint2 *rd, uint32_t n, uint32_t lo, uint32_t gmax, uint32_t chunk,
+                              uint32_t nblk, uint32_t *bcnt, uint32_t *over) {
+  __shared__ uint32_t s[4][8];
+  const uint32_t tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const uint32_t base = blockIdx.x * kIdentTile;
+  uint32_t c[4] = {0u, 0u, 0u, 0u};
+  for (uint32_t k = tid; k < kIdentTile; k += 256) {
+    const uint32_t v = base + k;
+    if (v < n) {
+      const uint32_t d = rd[v].y;
+      const int t = sweep_tier(d, lo, gmax);
+      c[t]++;
+      if (t == 2) {
+        const uint32_t ch = (d + chunk - 1) / chunk;
+        c[3] += ch;
+        if (ch > (1u << 21)) *over = 1u;  // a chunk's index within its row has 21 bits
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; j++) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c[j] += __shfl_xor_sync(0xffffffffu, c[j], o);
+    if (lane == 0) s[j][w] = c[j];
+  }
+  __syncthreads();
+  if (tid < 4) {
+    uint32_t t = 0;
+    for (int k = 0; k < 8; k++) t += s[tid][k];
+    // tiers 0-2 back to back, a zero, the chunk counts, a zero
+    bcnt[tid < 3 ? tid * nblk + blockIdx.x : 3 * nblk + 1 + blockIdx.x] = t;
+  }
+  if (blockIdx.x == 0 && tid == 0) {
+    bcnt[3 * nblk] = 0u;
+    bcnt[4 * nblk + 1] = 0u;
+  }
+}
+
+__global__ void k_items_write(const uint2 *rd, uint32_t n, uint32_t lo, uint32_t gmax, uint32_t chunk,
+                              uint32_t nblk, const uint32_t *bpos, uint4 *items, uint32_t *item_pos) {
+  __shared__ uint32_t s[4][8];
+  __shared__ uint32_t s_at[4];
+  const uint32_t tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const uint32_t base = blockIdx.x * kIdentTile;
+  // item positions of this tile's first vertex of tiers 0 and 1, and of its first chunk item
+  // (the chunk items follow the items of tiers 0 and 1, bpos[2 * nblk] of them)
+  const uint32_t c01 = bpos[2 * nblk];
+  if (tid < 3) s_at[tid] = bpos[tid * nblk + blockIdx.x];
+  if (tid == 3) s_at[3] = c01 + bpos[3 * nblk + 1 + blockIdx.x] - bpos[3 * nblk + 1];
+  __syncthreads();
+  for (uint32_t r0 = 0; r0 < kIdentTile; r0 += 256) {
+    const uint32_t v = base + r0 + tid;
+    uint2 d = make_uint2(0u, 0u);
+    int t = -1;
+    uint32_t ch = 0;
+    if (v < n) {
+      d = rd[v];
+      t = sweep_tier(d.y, lo, gmax);
+      if (t == 2) ch = (d.y + chunk - 1) / chunk;
+    }
+    // rank within the warp per tier, chunk prefix within the warp
+    uint32_t m[3], incl = ch;
+#pragma unroll
+    for (int j = 0; j < 3; j++) m[j] = __ballot_sync(0xffffffffu, t == j);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= (uint32_t)o) incl += y;
+    }
+    if (lane == 31) s[3][w] = incl;
+    if (lane < 3) s[lane][w] = __popc(m[lane]);
+    __syncthreads();
+    uint32_t before[4] = {0u, 0u, 0u, 0u}, all[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+      for (int k = 0; k < 8; k++) {
+        before[j] += k < (int)w ? s[j][k] : 0u;
+        all[j] += s[j][k];
+      }
+    if (t >= 0 && t < 2) {
+      const uint32_t pos = s_at[t] + before[t] + __popc(m[t] & ((1u << lane) - 1u));
+      items[pos] = make_uint4(v, d.x, d.y, 0u);
+      item_pos[v] = pos;
+    } else if (t == 2) {
+      const uint32_t first = s_at[3] + before[3] + incl - ch;  // index of the row's first chunk item
+      const uint32_t number = first - c01;                     // its chunk number
+      for (uint32_t c = 0; c < ch; c++) {
+        const uint32_t len = min(chunk, d.y - c * chunk);
+        items[first + c] = make_uint4(v, d.x + c * chunk, len | (c << 10) | (ch > 1 ? 0x80000000u : 0u), number + c);
+      }
+      item_pos[v] = first;
+    }
+    __syncthreads();
+    if (tid < 4) s_at[tid] += all[tid];
+    __syncthreads();
+  }
+}
+
 __global__ void k_compact_ids(const uint32_t *flags, const uint32_t *pos, uint32_t n, uint32_t *out, uint32_t *count) {
   uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= n) return;
@@ -646,11 +709,11 @@ pr_status graph_build(Graph *g, uint64_t m_in, const uint32_t *src_d, const uint
   CK(dalloc(&g->hub_base, n));
   for (int i = 0; i < 3; i++) CK(dalloc(&g->list[i], n));
   CK(dalloc(&g->xlist, n));
-  CK(dalloc(&g->ident, n));
   CK(dalloc(&g->dead, n));
-  CK(dalloc(&g->gen_tmp, (uint64_t)n + 2));
-  CK(dalloc(&g->gen_tmp2, (uint64_t)n + 2));
-  CK(dalloc(&g->scan_tmp, scan_tmp_words((uint64_t)n + 2) + 1));
+  // (n + 8 words: also the sweep-item rebuild's 4 ceil(n / 4096) + 2 tile counts)
+  CK(dalloc(&g->gen_tmp, (uint64_t)n + 8));
+  CK(dalloc(&g->gen_tmp2, (uint64_t)n + 8));
+  CK(dalloc(&g->scan_tmp, scan_tmp_words((uint64_t)n + 8) + 1));
   g->pend_cap = std::max<uint32_t>(1u << 16, std::min<uint32_t>(n, 1u << 22));
   CK(dalloc(&g->pend_src, g->pend_cap));
   CK(dalloc(&g->pend_tgt, g->pend_cap));
@@ -928,35 +991,25 @@ pr_status graph_refresh_ident(Graph *g) {
   if (!g->ident_dirty) return PR_OK;
   const uint32_t n = g->n;
   cudaStream_t st = g->st;
-  uint32_t *cnt = (uint32_t *)&g->actl->n_seg_out;  // reuse a device word
-  uint32_t base = 0;
-  for (int bin = 0; bin < 3; bin++) {
-    k_bin_flags<<<grid_for(n), 256, 0, st>>>(g->in.rd, n, (uint32_t)g->p.bin_lo, g->group_max, bin, g->gen_tmp);
-    count_launch();
-    exclusive_scan_u32(g->gen_tmp, g->gen_tmp2, n, g->scan_tmp, st);
-    k_compact_ids<<<grid_for(n), 256, 0, st>>>(g->gen_tmp, g->gen_tmp2, n, g->ident + base, cnt); count_launch();
-    uint32_t c = 0;
-    CK(cudaMemcpyAsync(&c, cnt, 4, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    g->ident_cnt[bin] = c;
-    base += c;
-  }
-  // sweep items: tier 0 and 1 one per vertex, tier-2 rows as chunks of chunk_len edges
-  const uint32_t c01 = g->ident_cnt[0] + g->ident_cnt[1];
-  const uint32_t nb = g->ident_cnt[2];
-  const uint32_t *big = g->ident + c01;
-  CK(cudaMemsetAsync(cnt, 0, 4, st));
-  k_chunk_counts<<<grid_for((uint64_t)nb + 1), 256, 0, st>>>(big, nb, g->in.rd, g->chunk_len, g->gen_tmp, cnt);
+  uint32_t *over = (uint32_t *)&g->actl->n_seg_out;  // reuse a device word
+  const uint32_t lo = (uint32_t)g->p.bin_lo, gmax = g->group_max, chunk = g->chunk_len;
+  const uint32_t nblk = (uint32_t)(((uint64_t)n + kIdentTile - 1) / kIdentTile);
+  const uint64_t len = 4ull * nblk + 2;  // tiers 0-2, 0, chunk counts, 0 (<= n + 8: fits gen_tmp)
+  CK(cudaMemsetAsync(over, 0, 4, st));
+  k_tier_counts<<<nblk, 256, 0, st>>>(g->in.rd, n, lo, gmax, chunk, nblk, g->gen_tmp, over);
   count_launch();
-  exclusive_scan_u32(g->gen_tmp, g->gen_tmp2, (uint64_t)nb + 1, g->scan_tmp, st);
-  uint32_t total = 0, over = 0;
-  CK(cudaMemcpyAsync(&total, g->gen_tmp2 + nb, 4, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(&over, cnt, 4, cudaMemcpyDeviceToHost, st));
+  exclusive_scan_u32(g->gen_tmp, g->gen_tmp2, len, g->scan_tmp, st);
+  uint32_t h[4] = {0, 0, 0, 0};  // tier-0 count, tiers 0+1, n + chunk items, over
+  CK(cudaMemcpyAsync(&h[0], g->gen_tmp2 + nblk, 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&h[1], g->gen_tmp2 + 2 * nblk, 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&h[2], g->gen_tmp2 + len - 1, 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&h[3], over, 4, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  if (over) {
+  if (h[3]) {
     g->err = "a vertex has more in-edges than 2^21 sweep chunks hold (raise chunk_len)";
     return PR_ERR_CAPACITY;
   }
+  const uint32_t c01 = h[1], total = h[2] - n;
   if ((uint64_t)c01 + total > g->items_cap || total > g->chunk_cap) {  // items, and partials by chunk number
     cudaFree(g->items);
     cudaFree(g->items_cmp);
@@ -972,18 +1025,11 @@ pr_status graph_refresh_ident(Graph *g) {
     g->items_cap = cap;
     g->chunk_cap = chunks;
   }
-  if (c01) {
-    k_items_simple<<<grid_for(c01), 256, 0, st>>>(g->ident, c01, g->in.rd, g->items, g->item_pos);
-    count_launch();
-  }
-  if (nb) {
-    k_items_chunks<<<grid_for(nb), 256, 0, st>>>(big, nb, g->in.rd, g->gen_tmp2, c01, g->chunk_len, g->items,
-                                                  g->item_pos);
-    count_launch();
-  }
+  k_items_write<<<nblk, 256, 0, st>>>(g->in.rd, n, lo, gmax, chunk, nblk, g->gen_tmp2, g->items, g->item_pos);
+  count_launch();
   CK(cudaGetLastError());
-  g->item_cnt[0] = g->ident_cnt[0];
-  g->item_cnt[1] = g->ident_cnt[1];
+  g->item_cnt[0] = h[0];
+  g->item_cnt[1] = c01 - h[0];
   g->item_cnt[2] = total;
   g->ident_dirty = false;
   return PR_OK;
@@ -1134,7 +1180,6 @@ void graph_free(Graph *g) {
   cudaFree(g->chunk_done);
   for (int i = 0; i < 3; i++) cudaFree(g->list[i]);
   cudaFree(g->xlist);
-  cudaFree(g->ident);
   cudaFree(g->dead);
   cudaFree(g->pend_src);
   cudaFree(g->pend_tgt);

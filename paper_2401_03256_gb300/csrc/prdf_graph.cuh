@@ -40,8 +40,6 @@ struct Graph {
   uint16_t *stamp = nullptr;         // iteration a vertex joins the affected set, 0xFFFF between calls
   uint32_t *list[3] = {nullptr, nullptr, nullptr};  // affected vertices by in-degree bin
   uint32_t *xlist = nullptr;         // vertices a continuation launch recorded for expansion
-  uint32_t *ident = nullptr;         // all vertices grouped by bin (for full sweeps)
-  uint32_t ident_cnt[3] = {0, 0, 0};
   bool ident_dirty = true;
   // Sweep items (16 B each) in tier order: tier 0 and 1 items {v, start, len, 0}, then the
   // chunk_len-edge chunks of tier-2 rows {v, start of chunk, len | index in row << 10 |
@@ -87,7 +85,7 @@ struct Graph {
   ApplyCtl *actl = nullptr, *actl_h = nullptr;
   uint32_t *big = nullptr;           // scratch for rows longer than shared memory
   uint64_t big_cap = 0;
-  uint32_t *gen_tmp = nullptr;       // general scratch (scans, flags) sized n + 1
+  uint32_t *gen_tmp = nullptr;       // general scratch (scans, flags) sized n + 8
   uint32_t *gen_tmp2 = nullptr;
   uint32_t *scan_tmp = nullptr;      // block sums of scans over n
   double ms_apply = 0.0;
