@@ -39,8 +39,10 @@ typedef enum {
     PR_ERR_VERTEX_RANGE = 2,   /* a vertex id >= n */
     PR_ERR_OUT_OF_MEMORY = 3,  /* device allocation failed; the handle is unchanged */
     PR_ERR_CUDA = 4,           /* a CUDA runtime call failed (message in pr_last_error) */
-    PR_ERR_DEVICE_TIMEOUT = 5, /* a bounded device-side wait gave up; ranks are undefined */
-    PR_ERR_CAPACITY = 6        /* the graph would exceed 2^32 - 1 stored edges */
+    PR_ERR_DEVICE_TIMEOUT = 5, /* a bounded device-side wait (a grid barrier, or a staged copy
+                                  into shared memory) gave up; ranks are undefined */
+    PR_ERR_CAPACITY = 6        /* a size limit: more than 2^32 - 1 stored edges, a row needing
+                                  more than 2^21 sweep chunks, or pr_static_noalloc's vertex cap */
 } pr_status;
 
 /* Rank arithmetic.  The paper computes in FP64 (Section 5.1.2); its tests are absolute

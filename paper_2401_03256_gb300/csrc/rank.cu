@@ -331,7 +331,10 @@ __device__ __noinline__ DtOut dt_search(const RankArgs<F32> &a, uint32_t epoch, 
   return o;
 }
 
-template <bool F32, bool DF>
+// SPLIT: the marking launch of a split call (single graph, self-loop mode), which hands the
+// call to the per-iteration launches before its first dense iteration and before any
+// iteration over every vertex; its instance carries no dense or full sweep code.
+template <bool F32, bool DF, bool SPLIT = false>
 __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const RankArgs<F32> a) {
   using S = Store<F32>;
   using R = typename S::R;
@@ -352,8 +355,10 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
   RankCtl *ctl = a.ctl;
   uint32_t epoch = 0;
   constexpr bool df = DF;
-  // per-component state (batched form), identical in every block
-  const bool multi = a.ncomp > 1;
+  // per-component state (batched form), identical in every block; a split call's marking
+  // launch serves one graph in self-loop mode (no components, no teleport)
+  const bool multi = !SPLIT && a.ncomp > 1;
+  const bool tele = !SPLIT && a.teleport;
   const uint32_t nc = a.ncomp;
   extern __shared__ unsigned long long dsm[];
   unsigned long long *s_kmax = dsm;                         // block max key / counter per component
@@ -444,9 +449,9 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
       a.C0[v] = c;
       a.C1[v] = c;
     }
-    if (a.teleport)
+    if (tele)
       for (uint32_t k = gtid; k < a.n_dead; k += nthreads) dacc.add(a.init);
-  } else if (a.teleport) {
+  } else if (tele) {
     for (uint32_t k = gtid; k < a.n_dead; k += nthreads) dacc.add(ldcg(a.R0 + __ldg(a.dead + k)));
   }
   const uint32_t zero_cnt[3] = {0, 0, 0};
@@ -472,7 +477,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
     }
   }
   flush_marks(a, 0u, zero_cnt, lane, wb);
-  if (a.teleport) block_dead_partial(0);
+  if (tele) block_dead_partial(0);
   if (!grid_sync(ctl, epoch, &s_err)) return;
   if (df && __ldcg(&ctl->hubq[0]) != 0) {
     my_app += hub_pass(a, 0, zero_cnt, lane, gwarp, nwarps, wb);
@@ -541,8 +546,8 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
   }
   long long Dn = 0;
   double Dd = 0.0;
-  if (a.teleport) Dn = grid_dead_total(0, &Dd);
-  R tele_prev = a.teleport ? tele_of(a.D_ref_n, a.D_ref_d) : (R)0;
+  if (tele) Dn = grid_dead_total(0, &Dd);
+  R tele_prev = tele ? tele_of(a.D_ref_n, a.D_ref_d) : (R)0;
   bool ever_full = !df || a.start_full || dt_all;
   uint32_t iters = 0;
   bool converged = false;
@@ -557,8 +562,8 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
   // ------------------------------------------------------------- iterations
   for (int it = 0; it < a.max_iter; it++) {
     Iter<F32> I;
-    I.tele = a.teleport ? tele_of(Dn, Dd) : (R)0;
-    if (df && a.teleport && !ever_full && Num<F32>::delta(I.tele, tele_prev) > a.ftol) {
+    I.tele = tele ? tele_of(Dn, Dd) : (R)0;
+    if (df && tele && !ever_full && Num<F32>::delta(I.tele, tele_prev) > a.ftol) {
       // the teleport term of every vertex moved by more than tau_f: all of V is affected
       ever_full = true;
       if (blockIdx.x == 0 && tid == 0) ctl->full_from = (uint32_t)it + 1;
@@ -642,7 +647,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
       return big && first_expansion(a.xbits, v);
     };
 
-    if (I.full || dense) {
+    if (!SPLIT && (I.full || dense)) {
       const uint32_t off1 = a.it_c0, off2 = a.it_c0 + a.it_c1;
       const uint4 *T = a.items;
       uint32_t n0 = a.it_c0, n1 = a.it_c1, n2 = a.it_c2;
@@ -845,7 +850,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
         if (bm) atomicMax(&ctl->dR_bits[it], bm);
       }
     }
-    if (a.teleport) block_dead_partial((it + 1) & 1);
+    if (tele) block_dead_partial((it + 1) & 1);
     if (!grid_sync(ctl, epoch, &s_err)) return;
     if (expand) {
       // out-rows of the vertices this iteration's sweep queued, 32 per warp round, one
@@ -909,7 +914,7 @@ __global__ void __launch_bounds__(kRankBlock, PRDF_RANK_MIN_BLOCKS) k_rank(const
 #pragma unroll
       for (int bb = 0; bb < 3; bb++) cnt[bb] += ldcg(&ctl->tail[slot][bb]);
     }
-    if (a.teleport) {
+    if (tele) {
       double pd = 0.0;
       long long pn = grid_dead_total((it + 1) & 1, &pd);
       if (I.full) {
@@ -1182,7 +1187,8 @@ static pr_status launch(Graph *g, RankMode mode, bool start_full) {
     CK(launch_full_sweep<F32>(g, a));
     return copy_async_parity();
   }
-  const void *fn = marking ? (const void *)k_rank<F32, true> : (const void *)k_rank<F32, false>;
+  const void *fn = marking ? (a.split && !g->use_graph ? (const void *)k_rank<F32, true, true> : (const void *)k_rank<F32, true>)
+                           : (const void *)k_rank<F32, false>;
   if (!g->use_graph) {
     CK(cudaLaunchCooperativeKernel(fn, dim3(g->rank_grid), dim3(kRankBlock), args,
                                    rank_smem(g->ncomp), g->st));
