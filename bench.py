@@ -53,6 +53,21 @@ def geomean(xs):
     return math.exp(sum(math.log(x) for x in xs) / len(xs)) if xs else None
 
 
+def source_digest(names) -> str:
+    """sha256 of the kernel sources with comments and blank space removed (a capture stays
+    valid across comment edits, not across code changes)."""
+    import hashlib
+    import re
+
+    h = hashlib.sha256()
+    for name in names:
+        text = open(os.path.join(ROOT, "paper_2401_03256_gb300", "csrc", name)).read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
+    return h.hexdigest()
+
+
 def hbm_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -793,12 +808,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     try:
         with open(tr_path) as f:
             tr = json.load(f)
-        import hashlib
-
-        h = hashlib.sha256()
-        for name in tr.get("sources", []):
-            h.update(open(os.path.join(ROOT, "paper_2401_03256_gb300", "csrc", name), "rb").read())
-        if tr.get("sources_sha256") == h.hexdigest() and tr.get("precision") == args.precision:
+        if tr.get("sources_code_sha256") == source_digest(tr.get("sources", [])) and tr.get("precision") == args.precision:
             traffic = tr.get("launch_dram_bytes_full_size")
     except Exception:
         traffic = None

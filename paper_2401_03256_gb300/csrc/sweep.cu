@@ -4,9 +4,9 @@
 // of Dynamic Frontier (Algorithm 1), its asynchronous form (Section 4.2) and Dynamic
 // Traversal (Section 3.3.2) run here on single-graph handles in self-loop mode.  One
 // iteration of Eq. 1 is one launch of k_sweep: no grid barrier and no loop state, so its
-// register budget allows six resident blocks per SM (the persistent kernel holds four),
-// and the dependent item -> column -> contribution loads of the sweep have half again as
-// many warps to overlap them.  The last block to finish an iteration reads its L-inf
+// register budget allows five resident blocks per SM (the persistent kernel holds four),
+// and the dependent item -> column -> contribution loads of the sweep have more warps to
+// overlap them.  The last block to finish an iteration reads its L-inf
 // change, decides whether another iteration follows (L-inf <= tau stops, as does
 // max_iter) and sets the condition of the graph's WHILE node; the host is not involved
 // between iterations.
@@ -23,9 +23,11 @@
 //         of a vertex mark nothing new), and appends the sweep items of every newly
 //         marked vertex to the compacted items, which the sweep then visits alone.
 // After an iteration with many first expansions the next one pulls (its cost is about a
-// full sweep, while pushing millions of out-rows costs several); otherwise it pushes.
+// full sweep, while pushing millions of out-rows costs several); otherwise it pushes (a
+// few expansions without long out-rows by a plain launch, the rest by a cooperative one).
 // Leaving pull for push rebuilds the compacted items, as does a set that grew by more
-// than 1/16 since they were last rebuilt.  Sums are taken per vertex exactly as in the
+// than 1/16 since they were last rebuilt.  The settled compacted iterations, which need
+// no prologue, run in an inner loop of the graph.  Sums are taken per vertex exactly as in the
 // persistent kernel's dense sweeps, so results equal a single marking launch bit for bit.
 #include <cstring>
 #include <vector>
