@@ -78,7 +78,14 @@ typedef struct {
     int32_t dead_end;     /* pr_deadend */
     int32_t bin_lo;       /* in-degree <= bin_lo: one thread per vertex (0 = default 8) */
     int32_t bin_hi;       /* in-degree >  bin_hi: one block per vertex (0 = default 4096) */
-    int32_t reserved;     /* must be 0 */
+    int32_t vertex_order; /* 0 (default): a single-graph handle numbers its vertices internally
+                             breadth-first from the vertex of largest degree (at most 1024
+                             levels; the rest keep their relative order), so the contributions
+                             that warps gather side by side lie close together (ids are
+                             translated at every call: results, ranks, affected sets and the
+                             CSR export are in the caller's numbering); 1: keep the caller's
+                             numbering.  Batched handles keep it always.  Other values:
+                             PR_ERR_INVALID_ARG. */
 } pr_params;
 
 typedef struct {

@@ -54,7 +54,7 @@ pr_status check_params(const pr_params &p, std::string *why) {
   if (p.precision != PR_F64 && p.precision != PR_F32) { *why = "unknown precision"; return PR_ERR_INVALID_ARG; }
   if (p.dead_end != PR_DEADEND_SELFLOOP && p.dead_end != PR_DEADEND_TELEPORT) { *why = "unknown dead-end mode"; return PR_ERR_INVALID_ARG; }
   if (p.bin_lo < 0 || p.bin_hi < 0 || p.bin_hi < p.bin_lo) { *why = "need 0 <= bin_lo <= bin_hi"; return PR_ERR_INVALID_ARG; }
-  if (p.reserved != 0) { *why = "reserved must be 0"; return PR_ERR_INVALID_ARG; }
+  if (p.vertex_order != 0 && p.vertex_order != 1) { *why = "vertex_order must be 0 or 1"; return PR_ERR_INVALID_ARG; }
   return PR_OK;
 }
 
@@ -90,7 +90,7 @@ void pr_params_default(pr_params *p) {
   p->dead_end = PR_DEADEND_SELFLOOP;
   p->bin_lo = 8;
   p->bin_hi = 4096;
-  p->reserved = 0;
+  p->vertex_order = 0;
 }
 
 const char *pr_status_string(pr_status s) {
@@ -338,13 +338,42 @@ static pr_status create_impl(uint32_t n, int64_t m, const uint32_t *src, const u
     if (e != cudaSuccess) { rc = prdf::cuda_fail(&g, e, "device query"); break; }
     if (!coop) { g.err = "device does not support cooperative launch"; rc = PR_ERR_CUDA; break; }
     const uint32_t *sd = src, *dd = dst;
-    if (m > 0 && !(is_device_ptr(src) && is_device_ptr(dst))) {
+    // single-graph handles number their vertices breadth-first (order.cu) unless asked not
+    // to; the edges are then rewritten, so they need a device copy of their own
+    const bool reorder = !comp_n && p.vertex_order == 0 && m > 0;
+    if (m > 0 && (reorder || !(is_device_ptr(src) && is_device_ptr(dst)))) {
       e = cudaMalloc((void **)&tmp, 8ull * (uint64_t)m);
       if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, src, 4ull * m, cudaMemcpyDefault, g.st);
       if (e == cudaSuccess) e = cudaMemcpyAsync(tmp + m, dst, 4ull * m, cudaMemcpyDefault, g.st);
       if (e != cudaSuccess) { rc = prdf::cuda_fail(&g, e, "upload edges"); break; }
       sd = tmp;
       dd = tmp + m;
+    }
+    if (reorder) {
+      // the numbering comes from a first build of the graph in the caller's numbering
+      Graph g0;
+      g0.n = n;
+      g0.p = p;
+      g0.f32 = g.f32;
+      g0.teleport = g.teleport;
+      g0.st = g.st;
+      g0.device = g.device;
+      g0.sm_count = g.sm_count;
+      rc = prdf::graph_build(&g0, (uint64_t)m, sd, dd);
+      if (rc == PR_OK) {
+        e = cudaMalloc((void **)&g.perm, 4ull * n);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&g.inv, 4ull * n);
+        if (e != cudaSuccess) rc = prdf::cuda_fail(&g0, e, "vertex numbering");
+      }
+      if (rc == PR_OK) rc = prdf::vertex_order(&g0, g.perm, g.inv);
+      if (rc != PR_OK) g.err = g0.err;
+      prdf::graph_free(&g0);
+      if (rc != PR_OK) break;
+      prdf::map_ids(g.inv, tmp, 2ull * (uint64_t)m, g.st);
+      g.perm_h.resize(n);
+      e = cudaMemcpyAsync(g.perm_h.data(), g.perm, 4ull * n, cudaMemcpyDeviceToHost, g.st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(g.st);
+      if (e != cudaSuccess) { rc = prdf::cuda_fail(&g, e, "vertex numbering"); break; }
     }
     rc = prdf::graph_build(&g, (uint64_t)m, sd, dd);
     if (rc != PR_OK) break;
@@ -564,6 +593,8 @@ pr_status pr_get_affected(pr_graph *h, uint32_t *out, int64_t cap, int64_t *coun
   }
   cudaError_t e = cudaStreamSynchronize(g.st);
   if (e != cudaSuccess) return prdf::cuda_fail(&g, e, "get affected");
+  if (!g.perm_h.empty())  // back to the caller's numbering
+    for (int64_t i = 0; i < std::min<int64_t>(total, cap); i++) out[i] = g.perm_h[out[i]];
   *count = total;
   return PR_OK;
 }

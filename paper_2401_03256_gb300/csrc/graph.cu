@@ -186,7 +186,8 @@ __device__ __forceinline__ uint32_t batch_of(const uint32_t *off, int nb, uint64
 // (nb + 1)], or null for a single batch.
 __global__ void k_seq_keys(const uint32_t *ds, const uint32_t *dd, uint64_t nd, const uint32_t *is,
                            const uint32_t *id, uint64_t ni, int nb, const uint32_t *off, uint32_t n, int b,
-                           uint64_t *keys, uint32_t *vals, const uint16_t *comp, ApplyCtl *actl) {
+                           uint64_t *keys, uint32_t *vals, const uint16_t *comp, const uint32_t *inv,
+                           ApplyCtl *actl) {
   uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nd + ni) return;
   uint64_t u, v, at;
@@ -211,6 +212,10 @@ __global__ void k_seq_keys(const uint32_t *ds, const uint32_t *dd, uint64_t nd, 
     atomicOr(&actl->bad_comp, 1u);
     key = kSentinel;
   } else {
+    if (inv) {  // the handle's internal numbering
+      u = inv[u];
+      v = inv[v];
+    }
     key = u == v ? kSentinel : ((u << b) | v);
   }
   keys[at] = key;
@@ -819,7 +824,7 @@ pr_status graph_apply(Graph *g, uint64_t nd, const uint32_t *ds, const uint32_t 
   CK(cudaMemcpyAsync(g->actl, &h, sizeof(ApplyCtl), cudaMemcpyHostToDevice, st));
 
   k_seq_keys<<<grid_for(N), 256, 0, st>>>(ds, dd, nd, is, id, ni, nb, off, g->n, b, s.kd, s.vals, g->comp,
-                                          g->actl); count_launch();
+                                          g->inv, g->actl); count_launch();
   uint64_t *keys = s.kd;
   uint32_t *vals = s.vals;
   sort_u64_kv(&keys, &vals, s.tmp, s.vals2, N, 2 * b, s.radix_hist, s.scan_tmp, st);
@@ -978,12 +983,30 @@ pr_status graph_export(Graph *g, int dir, uint64_t *offs_h, uint32_t *cols_h) {
   CK(dalloc(&packed, std::max<uint64_t>(g->m, 1)));
   k_pack_rows<<<grid_for((uint64_t)n * 32), 256, 0, st>>>(A.rd, n, A.col, g->gen_tmp2, packed); count_launch();
   std::vector<uint32_t> off(n + 1);
+  std::vector<uint32_t> icols;
+  if (g->perm) icols.resize(g->m);
+  uint32_t *dst_cols = g->perm ? icols.data() : cols_h;
   cudaError_t e = cudaMemcpyAsync(off.data(), g->gen_tmp2, 4ull * (n + 1), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(cols_h, packed, 4ull * g->m, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dst_cols, packed, 4ull * g->m, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFree(packed);
   if (e != cudaSuccess) return cuda_fail(g, e, "export csr");
-  for (uint32_t v = 0; v <= n; v++) offs_h[v] = off[v];
+  if (!g->perm) {
+    for (uint32_t v = 0; v <= n; v++) offs_h[v] = off[v];
+    return PR_OK;
+  }
+  // rows and columns back in the caller's numbering, each row sorted
+  const std::vector<uint32_t> &perm = g->perm_h;
+  std::vector<uint32_t> inv(n);
+  for (uint32_t r = 0; r < n; r++) inv[perm[r]] = r;
+  uint64_t at = 0;
+  for (uint32_t v = 0; v < n; v++) {
+    offs_h[v] = at;
+    const uint32_t r = inv[v];
+    for (uint32_t j = off[r]; j < off[r + 1]; j++) cols_h[at++] = perm[icols[j]];
+    std::sort(cols_h + offs_h[v], cols_h + at);
+  }
+  offs_h[n] = at;
   return PR_OK;
 }
 
@@ -1196,6 +1219,8 @@ void graph_free(Graph *g) {
   cudaFree(g->big);
   cudaFree(g->gen_tmp);
   cudaFree(g->gen_tmp2);
+  cudaFree(g->perm);
+  cudaFree(g->inv);
   cudaFree(g->scan_tmp);
   if (g->cg_exec) cudaGraphExecDestroy(g->cg_exec);
   if (g->cg) cudaGraphDestroy(g->cg);

@@ -41,6 +41,10 @@ struct Graph {
   uint32_t *list[3] = {nullptr, nullptr, nullptr};  // affected vertices by in-degree bin
   uint32_t *xlist = nullptr;         // vertices a continuation launch recorded for expansion
   bool ident_dirty = true;
+  // internal numbering (single-graph handles): perm[internal] = caller's id, inv the inverse;
+  // null when the handle keeps the caller's numbering
+  uint32_t *perm = nullptr, *inv = nullptr;
+  std::vector<uint32_t> perm_h;
   // Sweep items (16 B each) in tier order: tier 0 and 1 items {v, start, len, 0}, then the
   // chunk_len-edge chunks of tier-2 rows {v, start of chunk, len | index in row << 10 |
   // several-chunks flag << 31, chunk number}.  items_cmp holds the affected subset during
@@ -127,6 +131,8 @@ pr_status graph_build(Graph *g, uint64_t m_in, const uint32_t *src_d, const uint
 pr_status graph_apply(Graph *g, uint64_t nd, const uint32_t *ds_d, const uint32_t *dd_d, uint64_t ni,
                       const uint32_t *is_d, const uint32_t *id_d, int nb, const uint32_t *off_d);
 pr_status apply_scratch(Graph *g, uint64_t N);
+pr_status vertex_order(Graph *g, uint32_t *perm, uint32_t *inv);  // order.cu, on a built graph
+void map_ids(const uint32_t *inv, uint32_t *a, uint64_t m, cudaStream_t st);
 pr_status graph_export(Graph *g, int dir, uint64_t *offs_h, uint32_t *cols_h);
 pr_status graph_refresh_ident(Graph *g);
 pr_status graph_refresh_dead(Graph *g);

@@ -1370,11 +1370,11 @@ pr_status rank_run(Graph *g, RankMode mode, pr_stats *stats) {
 template <bool F32>
 __global__ void k_set_ranks(const double *in, uint32_t n, const typename Store<F32>::A *adeg,
                             typename Store<F32>::R *R0, typename Store<F32>::R *R1, typename Store<F32>::C *C0,
-                            typename Store<F32>::C *C1) {
+                            typename Store<F32>::C *C1, const uint32_t *perm) {
   using S = Store<F32>;
   uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= n) return;
-  typename S::R r = S::from_double(in[v]);
+  typename S::R r = S::from_double(in[perm ? perm[v] : v]);  // in: the caller's numbering
   typename S::C c = S::contrib(r, adeg[v]);
   R0[v] = r;
   R1[v] = r;
@@ -1383,9 +1383,9 @@ __global__ void k_set_ranks(const double *in, uint32_t n, const typename Store<F
 }
 
 template <bool F32>
-__global__ void k_get_ranks(const typename Store<F32>::R *Rv, uint32_t n, double *out) {
+__global__ void k_get_ranks(const typename Store<F32>::R *Rv, uint32_t n, double *out, const uint32_t *perm) {
   uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v < n) out[v] = Store<F32>::to_double(Rv[v]);
+  if (v < n) out[perm ? perm[v] : v] = Store<F32>::to_double(Rv[v]);  // out: the caller's numbering
 }
 
 // Dead-end mass of the current ranks: exact in 64-bit mode, plain per-thread sums and an
@@ -1507,11 +1507,11 @@ pr_status rank_set(Graph *g, const double *in_d) {
   if (g->f32) {
     using S = Store<true>;
     k_set_ranks<true><<<grid, 256, 0, g->st>>>(in_d, g->n, (const S::A *)g->adeg, (S::R *)g->R[0], (S::R *)g->R[1],
-                                               (S::C *)g->C[0], (S::C *)g->C[1]);
+                                               (S::C *)g->C[0], (S::C *)g->C[1], g->perm);
   } else {
     using S = Store<false>;
     k_set_ranks<false><<<grid, 256, 0, g->st>>>(in_d, g->n, (const S::A *)g->adeg, (S::R *)g->R[0],
-                                                (S::R *)g->R[1], (S::C *)g->C[0], (S::C *)g->C[1]);
+                                                (S::R *)g->R[1], (S::C *)g->C[0], (S::C *)g->C[1], g->perm);
   }
   count_launch();
   CK(cudaGetLastError());
@@ -1542,9 +1542,9 @@ pr_status rank_set(Graph *g, const double *in_d) {
 pr_status rank_get(Graph *g, double *out_d) {
   unsigned grid = (g->n + 255) / 256;
   if (g->f32)
-    k_get_ranks<true><<<grid, 256, 0, g->st>>>((const float *)g->R[0], g->n, out_d);
+    k_get_ranks<true><<<grid, 256, 0, g->st>>>((const float *)g->R[0], g->n, out_d, g->perm);
   else
-    k_get_ranks<false><<<grid, 256, 0, g->st>>>((const long long *)g->R[0], g->n, out_d);
+    k_get_ranks<false><<<grid, 256, 0, g->st>>>((const long long *)g->R[0], g->n, out_d, g->perm);
   count_launch();
   CK(cudaGetLastError());
   return PR_OK;

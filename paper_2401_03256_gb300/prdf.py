@@ -45,7 +45,7 @@ PR_NOALLOC_MAX_VERTICES = 1 << 18
 class pr_params(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("tol", ctypes.c_double), ("frontier_tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int32), ("precision", ctypes.c_int32), ("dead_end", ctypes.c_int32),
-                ("bin_lo", ctypes.c_int32), ("bin_hi", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("bin_lo", ctypes.c_int32), ("bin_hi", ctypes.c_int32), ("vertex_order", ctypes.c_int32)]
 
 
 class pr_stats(ctypes.Structure):

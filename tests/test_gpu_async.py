@@ -5,9 +5,14 @@ thread timing, so results are not reproducible bit for bit and are compared loos
 Every run stops under the same L-inf test (tau = 1e-10); the oracle's asynchronous and
 synchronous readings differ from each other and from the exact solution by about
 5 tau / (1 - alpha) ~ 6e-10 on these graphs, so the GPU result must lie within 2e-9 of
-both (FP32: 1e-6), converge, and need no more iterations than the synchronous form, run
-on the GPU in the same precision, plus one (FP32: plus three, since its stop near tau
-rests on a few float ulps).
+both (FP32: 1e-6) and converge.  Section 4.2 gives no bound on the iteration count of the
+in-place form, and it depends on the order of the updates: the oracle's sequential
+in-place sweep over the breadth-first numbering a handle uses internally needs up to three
+iterations more than the synchronous form on these graphs (72 against 71 and 76 against
+73 on the scale-14 R-MAT stream below, where the caller's numbering needs 71 and 74).  So
+the GPU form may take the synchronous count, run on the GPU in the same precision, plus
+four (the sequential order's three and one for thread timing; FP32: plus six, since its
+stop near tau also rests on a few float ulps).
 """
 import numpy as np
 import pytest
@@ -61,10 +66,10 @@ def _async_case(prdf, g, fracs, seed, params=None, tol=LOOSE64):
             R_a, aff_a, st_a = oracle.df_async(G, H, ed, ei, R_or)
             R_s, aff_s, st_s = oracle.df_sync(G, H, ed, ei, R_or)
             assert st.converged
-            # FP32: near the fixed point the L-inf change of either form is a few float ulps
-            # of the largest ranks (~1e-10 = tau), so where the in-place reads land moves its
-            # stop by up to a few iterations; 64-bit: at most one more
-            slack = 3 if tol == LOOSE32 else 1
+            # the order of the in-place updates moves the stop by up to three iterations and
+            # thread timing by one more; FP32: near the fixed point the L-inf change of either
+            # form is a few float ulps of the largest ranks (~1e-10 = tau), two more again
+            slack = 6 if tol == LOOSE32 else 4
             assert st.iterations <= st_sync.iterations + slack, (st.iterations, st_sync.iterations, st_s.iterations)
             assert np.max(np.abs(R - R_a)) <= tol
             assert np.max(np.abs(R - R_s)) <= tol

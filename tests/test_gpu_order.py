@@ -1,0 +1,135 @@
+"""The internal vertex numbering of single-graph handles is invisible at the boundary.
+
+A handle created with vertex_order 0 renumbers its vertices breadth-first; one created with
+vertex_order 1 keeps the caller's ids.  In 64-bit mode every in-edge sum is exact, so the
+two must agree bit for bit: ranks after Static, Naive-dynamic, Dynamic Traversal and
+Dynamic Frontier (Algorithm 1) calls, iteration counts, the affected sets (a set of caller
+ids) and the exported CSR.  FP32 sums round in another order, so there the two agree
+within the FP32 parity tolerance.  Graphs with vertices that no path reaches from the
+seed (isolated vertices, several components) exercise the id-ordered tail.
+"""
+import numpy as np
+import pytest
+
+import __graft_entry__
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 5e-6
+
+
+@pytest.fixture(scope="module")
+def prdf():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    __graft_entry__.build()
+    from paper_2401_03256_gb300 import prdf as mod
+
+    mod.load()
+    return mod
+
+
+def _params(prdf, order, f32=False):
+    p = prdf.pr_params_default()
+    p.vertex_order = order
+    p.precision = prdf.PR_F32 if f32 else prdf.PR_F64
+    return p
+
+
+def _two_islands():
+    # two R-MAT graphs side by side plus isolated vertices at the end
+    a, b = synth.rmat(10, 8, seed=3), synth.rmat(9, 8, seed=4)
+    src = np.concatenate([a.src, b.src + a.n]).astype(np.uint32)
+    dst = np.concatenate([a.dst, b.dst + a.n]).astype(np.uint32)
+    return synth.from_pairs(a.n + b.n + 37, zip(src.tolist(), dst.tolist()), "two-islands")
+
+
+def _graphs():
+    return [synth.rmat(12, 8, seed=5), synth.grid(40, 30, seed=6), _two_islands()]
+
+
+def _sorted_rows(off, col):
+    return [np.sort(col[off[v]:off[v + 1]]) for v in range(len(off) - 1)]
+
+
+@pytest.mark.parametrize("gi", range(3))
+def test_numbering_is_invisible_fp64(prdf, gi):
+    g = _graphs()[gi]
+    bs = synth.BatchStream(g, seed=7)
+    batches = [bs.next(f) for f in (1e-4, 1e-3, 1e-2)]
+    with prdf.Graph(g.n, g.src, g.dst, _params(prdf, 0)) as A, \
+            prdf.Graph(g.n, g.src, g.dst, _params(prdf, 1)) as B:
+        sa, sb = A.static(), B.static()
+        assert sa.iterations == sb.iterations
+        assert np.array_equal(A.ranks(), B.ranks())
+        for d in (0, 1):
+            oa, ca = A.csr(d)
+            ob, cb = B.csr(d)
+            assert np.array_equal(oa, ob)
+            assert all(np.array_equal(x, y) for x, y in zip(_sorted_rows(oa, ca), _sorted_rows(ob, cb)))
+        for k, b in enumerate(batches):
+            for H in (A, B):
+                H.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+            mode = ("frontier", "traversal", "naive")[k % 3]
+            sa, sb = getattr(A, mode)(), getattr(B, mode)()
+            assert sa.iterations == sb.iterations, mode
+            assert sa.affected_final == sb.affected_final, mode
+            assert np.array_equal(A.ranks(), B.ranks()), mode
+            if mode != "naive":
+                assert np.array_equal(np.sort(A.affected()), np.sort(B.affected())), mode
+        oa, ca = A.csr(1)
+        ob, cb = B.csr(1)
+        assert np.array_equal(oa, ob) and np.array_equal(ca, cb)
+
+
+def test_numbering_set_ranks_round_trip(prdf):
+    g = synth.rmat(11, 8, seed=8)
+    rng = np.random.default_rng(9)
+    r = rng.random(g.n)
+    r /= r.sum() * 1.0001
+    with prdf.Graph(g.n, g.src, g.dst, _params(prdf, 0)) as A, \
+            prdf.Graph(g.n, g.src, g.dst, _params(prdf, 1)) as B:
+        A.set_ranks(r)
+        B.set_ranks(r)
+        assert np.array_equal(A.ranks(), B.ranks())
+        b = synth.BatchStream(g, seed=10).next(1e-3)
+        for H in (A, B):
+            H.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+        sa, sb = A.frontier(), B.frontier()
+        assert sa.iterations == sb.iterations
+        assert np.array_equal(A.ranks(), B.ranks())
+
+
+def test_numbering_fp32_within_tolerance(prdf):
+    g = synth.rmat(12, 8, seed=11)
+    bs = synth.BatchStream(g, seed=12)
+    b = bs.next(1e-3)
+    h = bs.current()
+    G = oracle.Graph.build(g.n, g.src, g.dst)
+    with prdf.Graph(g.n, g.src, g.dst, _params(prdf, 0, f32=True)) as A:
+        A.static()
+        assert np.max(np.abs(A.ranks() - oracle.static_pr(G)[0])) <= TOL32
+        A.apply(b.del_src, b.del_dst, b.ins_src, b.ins_dst)
+        A.frontier()
+        G2 = oracle.Graph.build(h.n, h.src, h.dst)
+        assert np.max(np.abs(A.ranks() - oracle.static_pr(G2)[0])) <= TOL32
+
+
+def test_vertex_order_out_of_range_rejected(prdf):
+    g = synth.rmat(8, 4, seed=13)
+    with pytest.raises(prdf.PrdfError):
+        prdf.Graph(g.n, g.src, g.dst, _params(prdf, 2))
+
+
+@pytest.mark.parametrize("n", [1, 5])
+def test_numbering_degenerate(prdf, n):
+    # one vertex and no edges; five vertices, two edges, two of them unreached from the seed
+    src = np.array([], np.uint32) if n == 1 else np.array([4, 0], np.uint32)
+    dst = np.array([], np.uint32) if n == 1 else np.array([0, 3], np.uint32)
+    with prdf.Graph(n, src, dst, _params(prdf, 0)) as A, prdf.Graph(n, src, dst, _params(prdf, 1)) as B:
+        A.static()
+        B.static()
+        assert np.array_equal(A.ranks(), B.ranks())
