@@ -54,7 +54,7 @@ pr_status check_params(const pr_params &p, std::string *why) {
   if (p.precision != PR_F64 && p.precision != PR_F32) { *why = "unknown precision"; return PR_ERR_INVALID_ARG; }
   if (p.dead_end != PR_DEADEND_SELFLOOP && p.dead_end != PR_DEADEND_TELEPORT) { *why = "unknown dead-end mode"; return PR_ERR_INVALID_ARG; }
   if (p.bin_lo < 0 || p.bin_hi < 0 || p.bin_hi < p.bin_lo) { *why = "need 0 <= bin_lo <= bin_hi"; return PR_ERR_INVALID_ARG; }
-  if (p.vertex_order != 0 && p.vertex_order != 1) { *why = "vertex_order must be 0 or 1"; return PR_ERR_INVALID_ARG; }
+  if (p.vertex_order < 0 || p.vertex_order > 3) { *why = "vertex_order must be 0, 1, 2 or 3"; return PR_ERR_INVALID_ARG; }
   return PR_OK;
 }
 
@@ -338,9 +338,9 @@ static pr_status create_impl(uint32_t n, int64_t m, const uint32_t *src, const u
     if (e != cudaSuccess) { rc = prdf::cuda_fail(&g, e, "device query"); break; }
     if (!coop) { g.err = "device does not support cooperative launch"; rc = PR_ERR_CUDA; break; }
     const uint32_t *sd = src, *dd = dst;
-    // single-graph handles number their vertices breadth-first (order.cu) unless asked not
-    // to; the edges are then rewritten, so they need a device copy of their own
-    const bool reorder = !comp_n && p.vertex_order == 0 && m > 0;
+    // single-graph handles may number their vertices breadth-first (order.cu) unless asked
+    // not to; the edges are then rewritten, so they need a device copy of their own
+    const bool reorder = !comp_n && p.vertex_order != 1 && m > 0;
     if (m > 0 && (reorder || !(is_device_ptr(src) && is_device_ptr(dst)))) {
       e = cudaMalloc((void **)&tmp, 8ull * (uint64_t)m);
       if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, src, 4ull * m, cudaMemcpyDefault, g.st);
@@ -360,20 +360,41 @@ static pr_status create_impl(uint32_t n, int64_t m, const uint32_t *src, const u
       g0.device = g.device;
       g0.sm_count = g.sm_count;
       rc = prdf::graph_build(&g0, (uint64_t)m, sd, dd);
-      if (rc == PR_OK) {
-        e = cudaMalloc((void **)&g.perm, 4ull * n);
-        if (e == cudaSuccess) e = cudaMalloc((void **)&g.inv, 4ull * n);
-        if (e != cudaSuccess) rc = prdf::cuda_fail(&g0, e, "vertex numbering");
+      // vertex_order 0: both numberings, the one with the cheaper modelled gathers kept if
+      // it beats the caller's by 5%; 2 and 3: the one asked for, always
+      const int kinds[2] = {prdf::kOrderFromMax, prdf::kOrderFromSeeds};
+      uint32_t *cp[2] = {nullptr, nullptr}, *ci[2] = {nullptr, nullptr};
+      uint64_t cost[2][2] = {{0, 0}, {0, 0}};
+      int best = -1;
+      for (int k = 0; k < 2 && rc == PR_OK; k++) {
+        if (p.vertex_order >= 2 && p.vertex_order - 2 != k) continue;
+        e = cudaMalloc((void **)&cp[k], 4ull * n);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&ci[k], 4ull * n);
+        if (e != cudaSuccess) { rc = prdf::cuda_fail(&g0, e, "vertex numbering"); break; }
+        rc = prdf::vertex_order(&g0, kinds[k], cp[k], ci[k]);
+        if (rc == PR_OK && p.vertex_order == 0) rc = prdf::order_cost(&g0, cp[k], ci[k], cost[k]);
+        if (rc == PR_OK && (best < 0 || cost[k][1] < cost[best][1])) best = k;
       }
-      if (rc == PR_OK) rc = prdf::vertex_order(&g0, g.perm, g.inv);
+      bool keep = rc == PR_OK && best >= 0 && (p.vertex_order >= 2 || cost[best][1] * 20 < cost[best][0] * 19);
+      for (int k = 0; k < 2; k++) {
+        if (keep && k == best) {
+          g.perm = cp[k];
+          g.inv = ci[k];
+        } else {
+          cudaFree(cp[k]);
+          cudaFree(ci[k]);
+        }
+      }
       if (rc != PR_OK) g.err = g0.err;
       prdf::graph_free(&g0);
       if (rc != PR_OK) break;
-      prdf::map_ids(g.inv, tmp, 2ull * (uint64_t)m, g.st);
-      g.perm_h.resize(n);
-      e = cudaMemcpyAsync(g.perm_h.data(), g.perm, 4ull * n, cudaMemcpyDeviceToHost, g.st);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(g.st);
-      if (e != cudaSuccess) { rc = prdf::cuda_fail(&g, e, "vertex numbering"); break; }
+      if (keep) {
+        prdf::map_ids(g.inv, tmp, 2ull * (uint64_t)m, g.st);
+        g.perm_h.resize(n);
+        e = cudaMemcpyAsync(g.perm_h.data(), g.perm, 4ull * n, cudaMemcpyDeviceToHost, g.st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g.st);
+        if (e != cudaSuccess) { rc = prdf::cuda_fail(&g, e, "vertex numbering"); break; }
+      }
     }
     rc = prdf::graph_build(&g, (uint64_t)m, sd, dd);
     if (rc != PR_OK) break;

@@ -1,18 +1,26 @@
 // order.cu - the internal vertex numbering of single-graph handles.
 //
 // The sweeps gather one contribution per in-edge, and their cost is the number of distinct
-// 32-byte sectors those gathers touch.  A breadth-first numbering from the vertex of
-// largest degree (over out- and in-edges together) gives the vertices discovered from one
-// vertex consecutive numbers, so the short rows that a warp sweeps side by side gather
-// from nearby contributions; on R-MAT scale 22 a full sweep takes 8% less time than under a
-// random numbering.  The numbering is deterministic: level by level, a newly reached vertex
-// takes its place after the vertices reached from earlier-numbered vertices of the
-// previous level (the earliest adjacent one decides), ties by vertex id; vertices not
-// reached within kMaxLevels levels follow in id order.  Each level costs a few launches and
-// one host synchronisation, so graphs of huge diameter (chains of k-mers: one level per
-// few dozen vertices) keep their own numbering past the cap instead of paying seconds at
-// creation.  Ranks, results and the update semantics do not depend on the numbering: ids
-// are translated at the boundary (batches, ranks in and out, affected sets, CSR export).
+// 32-byte sectors those gathers touch.  A breadth-first numbering (over out- and in-edges
+// together) gives the vertices discovered from one vertex consecutive numbers, so the
+// short rows that a warp sweeps side by side gather from nearby contributions.  Two are
+// computed, from different first levels:
+//  kOrderFromMax: the vertex of largest degree (graphs with hubs, such as R-MAT: its
+//    neighbourhood is most of the graph within a few levels);
+//  kOrderFromSeeds: kSeeds vertices evenly spaced in the caller's numbering (graphs of
+//    large diameter, such as chains of k-mers, which one seed would cover only at one
+//    level per few dozen vertices).
+// Level by level, a newly reached vertex takes its place after the vertices reached from
+// earlier-numbered vertices of the previous level (the earliest adjacent one decides),
+// ties by vertex id; vertices not reached within kMaxLevels levels follow in id order.
+// Each level costs a few launches and one host synchronisation.  A handle keeps the
+// numbering whose modelled short-row gathers (order_cost) touch the fewest sectors, if
+// that is at least 5% fewer than under the caller's numbering: a grid numbered row by row
+// already gathers consecutive contributions.  (Putting the vertices of largest out-degree
+// side by side was measured slower: a fifth of the gathers then fall in one 64 KB run,
+// whose few L2 slices serve them while the others wait.)  Ranks, results and the update
+// semantics do not depend on the numbering: ids are translated at the boundary (batches,
+// ranks in and out, affected sets, CSR export).
 #include <algorithm>
 #include <cstdint>
 
@@ -30,6 +38,7 @@ namespace {
 
 constexpr uint32_t kUnset = 0xFFFFFFFFu;
 constexpr int kMaxLevels = 1024;
+constexpr uint32_t kSeeds = 8192;
 
 __global__ void k_order_init(uint32_t n, uint32_t *label, uint32_t *cand) {
   const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
@@ -56,6 +65,15 @@ __global__ void k_order_start(const unsigned long long *best, uint32_t *label, u
   const uint32_t s = ~(uint32_t)(*best & 0xFFFFFFFFull);
   label[s] = 0;
   perm[0] = s;
+}
+
+// level 0 of kOrderFromSeeds: seed i is vertex i * step
+__global__ void k_order_seeds(uint32_t k, uint32_t step, uint32_t *label, uint32_t *perm) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < k) {
+    label[i * step] = i;
+    perm[i] = i * step;
+  }
 }
 
 // One level: every vertex of the frontier (perm[lo, hi), numbered lo..hi-1) offers its
@@ -110,6 +128,54 @@ __global__ void k_order_rest(const uint32_t *flags, const uint32_t *pos, uint32_
   }
 }
 
+// The gather cost model that decides whether the new numbering is kept: the rows of at
+// most kScoreRowMax in-edges are swept 32 consecutive rows a warp, one in-edge per lane per
+// step, as the short-row tiers do; each step costs one request per distinct 32-byte sector
+// among the lanes' contributions.  cnt[0] sums those sectors under the caller's
+// numbering, cnt[1] under the new one.  (Long rows gather about one sector per in-edge in
+// any numbering: their in-neighbours are spread over the graph.)
+constexpr uint32_t kScoreRowMax = 64;
+
+__global__ void k_order_score(const uint2 *in_rd, const uint32_t *in_col, const uint32_t *perm,
+                              const uint32_t *inv, uint32_t n, int sec_shift, unsigned long long *cnt) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t ngroups = (uint32_t)(((uint64_t)n + 31) / 32);
+  unsigned long long sec[2] = {0, 0};
+  for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < ngroups; w += nwarps) {
+    const uint32_t pos = w * 32 + lane;
+    for (int mode = 0; mode < 2; mode++) {
+      uint2 d = make_uint2(0, 0);
+      if (pos < n) {
+        d = in_rd[mode ? perm[pos] : pos];
+        if (d.y > kScoreRowMax) d.y = 0;
+      }
+      uint32_t dmax = d.y;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+      for (uint32_t k = 0; k < dmax; k++) {
+        const bool act = k < d.y;
+        const unsigned am = __ballot_sync(0xffffffffu, act);
+        if (act) {
+          uint32_t c = in_col[d.x + k];
+          if (mode) c = inv[c];
+          const unsigned peers = __match_any_sync(am, c >> sec_shift);
+          if ((uint32_t)(__ffs(peers) - 1) == lane) sec[mode]++;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sec[0] += __shfl_xor_sync(0xffffffffu, sec[0], o);
+    sec[1] += __shfl_xor_sync(0xffffffffu, sec[1], o);
+  }
+  if (lane == 0) {
+    if (sec[0]) atomicAdd(&cnt[0], sec[0]);
+    if (sec[1]) atomicAdd(&cnt[1], sec[1]);
+  }
+}
+
 __global__ void k_map_ids(const uint32_t *inv, uint32_t *a, uint64_t m) {
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < m) a[i] = inv[a[i]];
@@ -119,24 +185,33 @@ unsigned grid_of(uint64_t n) { return (unsigned)std::max<uint64_t>(1, (n + 255) 
 
 }  // namespace
 
-pr_status vertex_order(Graph *g, uint32_t *perm, uint32_t *inv) {
+pr_status vertex_order(Graph *g, int kind, uint32_t *perm, uint32_t *inv) {
   const uint32_t n = g->n;
   cudaStream_t st = g->st;
   pr_status rc = apply_scratch(g, n);
   if (rc != PR_OK) return rc;
   ApplyScratch &s = g->sc;
   uint32_t *cand = s.flags, *next = s.pos, *cnt = (uint32_t *)&g->actl->n_seg_out;
-  unsigned long long *keys = (unsigned long long *)s.kd, *best = (unsigned long long *)s.tmp2;
+  unsigned long long *keys = (unsigned long long *)s.kd;
   k_order_init<<<grid_of(n), 256, 0, st>>>(n, inv, cand);
-  count_launch();
-  CK(cudaMemsetAsync(best, 0, 8, st));
-  k_order_seed<<<grid_of(n), 256, 0, st>>>(g->out.rd, g->in.rd, n, best);
-  count_launch();
-  k_order_start<<<1, 1, 0, st>>>(best, inv, perm);
   count_launch();
   int b = 0;
   while (b < 32 && (1ull << b) < (uint64_t)n) b++;
-  uint32_t lo = 0, hi = 1;
+  uint32_t lo = 0, hi;
+  if (kind == kOrderFromSeeds) {
+    const uint32_t k = std::min(n, kSeeds), step = n / k;
+    k_order_seeds<<<grid_of(k), 256, 0, st>>>(k, step, inv, perm);
+    count_launch();
+    hi = k;
+  } else {
+    unsigned long long *best = (unsigned long long *)s.tmp2;
+    CK(cudaMemsetAsync(best, 0, 8, st));
+    k_order_seed<<<grid_of(n), 256, 0, st>>>(g->out.rd, g->in.rd, n, best);
+    count_launch();
+    k_order_start<<<1, 1, 0, st>>>(best, inv, perm);
+    count_launch();
+    hi = 1;
+  }
   const unsigned egrid = (unsigned)std::max(1, g->sm_count * 8);
   for (int level = 0; hi > lo && level < kMaxLevels; level++) {
     CK(cudaMemsetAsync(cnt, 0, 4, st));
@@ -158,15 +233,32 @@ pr_status vertex_order(Graph *g, uint32_t *perm, uint32_t *inv) {
     hi += c;
   }
   if (hi < n) {
-    // vertices no edge path reaches from the seed, or none within kMaxLevels, in id order
+    // vertices no edge path reaches from the first level, or none within kMaxLevels, in id order
     k_order_unset_flags<<<grid_of(n), 256, 0, st>>>(inv, n, g->gen_tmp);
     count_launch();
     exclusive_scan_u32(g->gen_tmp, g->gen_tmp2, n, g->scan_tmp, st);
     k_order_rest<<<grid_of(n), 256, 0, st>>>(g->gen_tmp, g->gen_tmp2, n, hi, inv, perm);
     count_launch();
   }
+
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(st));
+  return PR_OK;
+}
+
+pr_status order_cost(Graph *g, const uint32_t *perm, const uint32_t *inv, uint64_t cost[2]) {
+  cudaStream_t st = g->st;
+  const uint32_t n = g->n;
+  unsigned long long *cnt = (unsigned long long *)g->sc.tmp2, h[2] = {0, 0};
+  CK(cudaMemsetAsync(cnt, 0, 16, st));
+  const unsigned grid = (unsigned)std::max(1, g->sm_count * 8);
+  // 8-byte contributions: 4 to a sector; 4-byte: 8
+  k_order_score<<<grid, 256, 0, st>>>(g->in.rd, g->in.col, perm, inv, n, g->f32 ? 3 : 2, cnt);
+  count_launch();
+  CK(cudaMemcpyAsync(h, cnt, 16, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  cost[0] = h[0];
+  cost[1] = h[1];
   return PR_OK;
 }
 

@@ -204,11 +204,15 @@ __device__ __forceinline__ uint4 ld_cols(const uint32_t *p, unsigned long long p
   return r;
 }
 // Contribution gathers.  C of the iteration's input parity is not written during the
-// iteration, and the grid barrier's acquire orders every block after all writes of the
-// previous iteration, so the gathers may be served by L1 (PRDF_GATHER_L2_ONLY=0); measured
-// slower on GB300 than keeping them at L2 (the default).
+// iteration, and a kernel boundary or the grid barrier's acquire orders every block after
+// all writes of the previous iteration, so the gathers may be served by L1 (the default).
+// Under the internal breadth-first numbering the short rows that one warp sweeps gather
+// from nearby contributions, and L1-allocating gathers make a scale-22 R-MAT full sweep 2%
+// faster in 64-bit mode and 5% in FP32 than L2-only ones (PRDF_GATHER_L2_ONLY=1), which
+// were ahead under a random numbering.  (The asynchronous form reads C while it is
+// written; a line that L1 still holds gives an older value, which that form allows.)
 #ifndef PRDF_GATHER_L2_ONLY
-#define PRDF_GATHER_L2_ONLY 1
+#define PRDF_GATHER_L2_ONLY 0
 #endif
 #if PRDF_GATHER_L2_ONLY
 #define PRDF_GATHER_COP "cg"
