@@ -82,8 +82,9 @@ typedef struct {
                              breadth-first numbering (at most 1024 levels; the vertices not
                              reached keep their relative order after them) puts the
                              contributions that warps gather side by side close together:
-                             from the vertex of largest degree (2) or from 8192 vertices
-                             evenly spaced in the caller's numbering as the first level (3).
+                             from the vertex of largest degree (2) or from max(8192, n / 2048)
+                             vertices evenly spaced in the caller's numbering as the first
+                             level (3).
                              0 (default): both are computed at creation and the one whose
                              short-row gathers a model finds cheapest is kept if it touches
                              at least 5% fewer 32-byte sectors than the caller's numbering (a

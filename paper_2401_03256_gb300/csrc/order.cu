@@ -7,9 +7,9 @@
 // computed, from different first levels:
 //  kOrderFromMax: the vertex of largest degree (graphs with hubs, such as R-MAT: its
 //    neighbourhood is most of the graph within a few levels);
-//  kOrderFromSeeds: kSeeds vertices evenly spaced in the caller's numbering (graphs of
-//    large diameter, such as chains of k-mers, which one seed would cover only at one
-//    level per few dozen vertices).
+//  kOrderFromSeeds: max(kSeeds, n / kSeedCell) vertices evenly spaced in the caller's
+//    numbering (graphs of large diameter, such as chains of k-mers, which one seed would
+//    cover only at one level per few dozen vertices).
 // Level by level, a newly reached vertex takes its place after the vertices reached from
 // earlier-numbered vertices of the previous level (the earliest adjacent one decides),
 // ties by vertex id; vertices not reached within kMaxLevels levels follow in id order.
@@ -38,7 +38,8 @@ namespace {
 
 constexpr uint32_t kUnset = 0xFFFFFFFFu;
 constexpr int kMaxLevels = 1024;
-constexpr uint32_t kSeeds = 8192;
+constexpr uint32_t kSeeds = 8192;     // at least this many seeds,
+constexpr uint32_t kSeedCell = 2048;  // and one per this many vertices (a cell of a few hundred levels at most)
 
 __global__ void k_order_init(uint32_t n, uint32_t *label, uint32_t *cand) {
   const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
@@ -199,7 +200,7 @@ pr_status vertex_order(Graph *g, int kind, uint32_t *perm, uint32_t *inv) {
   while (b < 32 && (1ull << b) < (uint64_t)n) b++;
   uint32_t lo = 0, hi;
   if (kind == kOrderFromSeeds) {
-    const uint32_t k = std::min(n, kSeeds), step = n / k;
+    const uint32_t k = std::min(n, std::max(kSeeds, n / kSeedCell)), step = n / k;
     k_order_seeds<<<grid_of(k), 256, 0, st>>>(k, step, inv, perm);
     count_launch();
     hi = k;
