@@ -84,14 +84,16 @@ typedef struct {
                              contributions that warps gather side by side close together:
                              from the vertex of largest degree (2) or from max(8192, n / 2048)
                              vertices evenly spaced in the caller's numbering as the first
-                             level (3).
-                             0 (default): both are computed at creation and the one whose
-                             short-row gathers a model finds cheapest is kept if it touches
-                             at least 5% fewer 32-byte sectors than the caller's numbering (a
-                             grid numbered row by row keeps its own); 1: keep the caller's
-                             numbering.  Ids are translated at
-                             every call: results, ranks, affected sets and the CSR export are
-                             in the caller's numbering.  Batched handles keep the caller's
+                             level (3).  0 (default): both are computed at creation and the
+                             one whose short-row gathers a model finds cheapest is kept if it
+                             touches at least 5% fewer 32-byte sectors than the caller's
+                             numbering (a grid numbered row by row keeps its own); 1: keep
+                             the caller's numbering.  Ids are translated at every call:
+                             results, ranks, affected sets and the CSR export are in the
+                             caller's numbering.  Computing a numbering takes a second,
+                             transient build of the graph on the device; without room for it
+                             the caller's numbering is kept (0) or creation fails with
+                             PR_ERR_OUT_OF_MEMORY (2, 3).  Batched handles keep the caller's
                              numbering always.  Other values: PR_ERR_INVALID_ARG. */
 } pr_params;
 

@@ -385,8 +385,11 @@ static pr_status create_impl(uint32_t n, int64_t m, const uint32_t *src, const u
           cudaFree(ci[k]);
         }
       }
-      if (rc != PR_OK) g.err = g0.err;
+      // no room for the numbering's transient build: the caller's numbering (vertex_order 0)
+      const bool fallback = rc == PR_ERR_OUT_OF_MEMORY && p.vertex_order == 0;
+      if (rc != PR_OK && !fallback) g.err = g0.err;
       prdf::graph_free(&g0);
+      if (fallback) rc = PR_OK;
       if (rc != PR_OK) break;
       if (keep) {
         prdf::map_ids(g.inv, tmp, 2ull * (uint64_t)m, g.st);

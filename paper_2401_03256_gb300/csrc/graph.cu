@@ -354,13 +354,23 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(uint2 *rd, uint32_t *ca
   for (uint32_t j = tid; j < len; j += kMergeThreads) src_row[j] = col[d.x + j];
   __syncthreads();
   uint32_t *dst = col + s_dest;
+  // A thread's entries ascend, so the first change with column >= x lies at or after the
+  // one found for its previous entry: a galloping search from there (a hub row's entries
+  // are each a few changes apart, not a whole binary search over them).
+  uint32_t lo_prev = s0;
   for (uint32_t j = tid; j < len; j += kMergeThreads) {
     uint32_t x = src_row[j];
-    uint32_t lo = s0, hi = e;  // first change with column >= x
-    while (lo < hi) {
+    uint32_t lo = lo_prev, hi = lo_prev, step = 1;  // changes before lo have columns < x
+    while (hi < e && chg_col(chg[hi], b) < x) {
+      lo = hi + 1;
+      hi = e - hi > step ? hi + step : e;
+      step <<= 1;
+    }
+    while (lo < hi) {  // first change with column >= x, in [lo, hi]
       uint32_t mid = (lo + hi) >> 1;
       if (chg_col(chg[mid], b) < x) lo = mid + 1; else hi = mid;
     }
+    lo_prev = lo;
     if (lo < e && chg_col(chg[lo], b) == x) continue;  // deleted
     uint32_t ib = tagpref[lo] - tagpref[s0];
     uint32_t db = (lo - s0) - ib;

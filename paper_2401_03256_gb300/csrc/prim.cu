@@ -1,6 +1,7 @@
 // prim.cu - data-parallel primitives used by graph construction and batch updates:
 // an exclusive scan of uint32 values and a stable LSD radix sort of 64-bit keys
 // (one-block bitonic sort for small inputs).
+#include <algorithm>
 #include <utility>
 
 #include "prdf_common.cuh"
@@ -111,14 +112,18 @@ __global__ void __launch_bounds__(1024) k_block_sort(uint64_t *keys, uint32_t n)
 
 // ------------------------------------------------------------------ radix sort ---
 
+// A block sorts a tile of ITEMS keys per thread: 16 (4096 keys) for large sorts, 4 (1024
+// keys) below kSmallTileKeys, where 4096-key tiles leave most SMs idle and every pass is
+// bound by one block's serial work (the sorts of a graph update are of this size).
 constexpr int kRadixThreads = 256;
-constexpr int kRadixItems = 16;                       // keys per thread
-constexpr int kRadixTile = kRadixThreads * kRadixItems;  // 4096 keys per block
 constexpr int kRadixWarps = kRadixThreads / 32;
-constexpr int kWarpKeys = kRadixTile / kRadixWarps;   // 512 consecutive keys per warp
+constexpr int kRadixItemsSmall = 4, kRadixItemsLarge = 16;
+constexpr uint64_t kSmallTileKeys = 2500000;
 
+template <int ITEMS>
 __global__ void __launch_bounds__(kRadixThreads) k_radix_hist(const uint64_t *keys, uint64_t n, int shift,
                                                               uint32_t *hist, uint32_t nblocks) {
+  constexpr int kRadixTile = kRadixThreads * ITEMS;
   __shared__ uint32_t cnt[256];
   cnt[threadIdx.x] = 0;
   __syncthreads();
@@ -131,11 +136,13 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_hist(const uint64_t *ke
   hist[(uint64_t)threadIdx.x * nblocks + blockIdx.x] = cnt[threadIdx.x];
 }
 
-// Stable scatter: warp w ranks its 512 consecutive keys round by round with
+// Stable scatter: warp w ranks its 32 * ITEMS consecutive keys round by round with
 // __match_any_sync; per-warp digit counts are then offset across warps (warp order =
 // index order) and by the block's global digit base.
+template <int ITEMS>
 __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(const uint64_t *keys, uint64_t *out, uint64_t n,
                                                                  int shift, const uint32_t *hist, uint32_t nblocks) {
+  constexpr int kRadixItems = ITEMS, kRadixTile = kRadixThreads * ITEMS, kWarpKeys = kRadixTile / kRadixWarps;
   __shared__ uint32_t wcnt[kRadixWarps][256];
   __shared__ uint32_t gbase[256];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -217,10 +224,12 @@ __global__ void __launch_bounds__(1024) k_block_sort_kv(uint64_t *keys, uint32_t
   }
 }
 
+template <int ITEMS>
 __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter_kv(const uint64_t *keys, const uint32_t *vals,
                                                                     uint64_t *out, uint32_t *vout, uint64_t n,
                                                                     int shift, const uint32_t *hist,
                                                                     uint32_t nblocks) {
+  constexpr int kRadixItems = ITEMS, kRadixTile = kRadixThreads * ITEMS, kWarpKeys = kRadixTile / kRadixWarps;
   __shared__ uint32_t wcnt[kRadixWarps][256];
   __shared__ uint32_t gbase[256];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -266,22 +275,18 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter_kv(const uint64
   }
 }
 
-void sort_u64_kv(uint64_t **keys, uint32_t **vals, uint64_t *alt_k, uint32_t *alt_v, uint64_t n, int bits,
-                 uint32_t *hist, uint32_t *scan_tmp, cudaStream_t st) {
-  if (n < 2) return;
-  if (n <= kSmallSort / 2) {
-    k_block_sort_kv<<<1, 1024, 0, st>>>(*keys, *vals, (uint32_t)n);
-    count_launch();
-    return;
-  }
+template <int ITEMS>
+void radix_kv(uint64_t **keys, uint32_t **vals, uint64_t *alt_k, uint32_t *alt_v, uint64_t n, int bits,
+              uint32_t *hist, uint32_t *scan_tmp, cudaStream_t st) {
+  constexpr int kRadixTile = kRadixThreads * ITEMS;
   const uint32_t nblocks = (uint32_t)((n + kRadixTile - 1) / kRadixTile);
   uint64_t *sk = *keys, *dk = alt_k;
   uint32_t *sv = *vals, *dv = alt_v;
   for (int shift = 0; shift < bits; shift += 8) {
-    k_radix_hist<<<nblocks, kRadixThreads, 0, st>>>(sk, n, shift, hist, nblocks);
+    k_radix_hist<ITEMS><<<nblocks, kRadixThreads, 0, st>>>(sk, n, shift, hist, nblocks);
     count_launch();
     exclusive_scan_u32(hist, hist, (uint64_t)256 * nblocks, scan_tmp, st);
-    k_radix_scatter_kv<<<nblocks, kRadixThreads, 0, st>>>(sk, sv, dk, dv, n, shift, hist, nblocks);
+    k_radix_scatter_kv<ITEMS><<<nblocks, kRadixThreads, 0, st>>>(sk, sv, dk, dv, n, shift, hist, nblocks);
     count_launch();
     std::swap(sk, dk);
     std::swap(sv, dv);
@@ -290,15 +295,47 @@ void sort_u64_kv(uint64_t **keys, uint32_t **vals, uint64_t *alt_k, uint32_t *al
   *vals = sv;
 }
 
+void sort_u64_kv(uint64_t **keys, uint32_t **vals, uint64_t *alt_k, uint32_t *alt_v, uint64_t n, int bits,
+                 uint32_t *hist, uint32_t *scan_tmp, cudaStream_t st) {
+  if (n < 2) return;
+  if (n <= kSmallSort / 2) {
+    k_block_sort_kv<<<1, 1024, 0, st>>>(*keys, *vals, (uint32_t)n);
+    count_launch();
+    return;
+  }
+  if (n < kSmallTileKeys) radix_kv<kRadixItemsSmall>(keys, vals, alt_k, alt_v, n, bits, hist, scan_tmp, st);
+  else radix_kv<kRadixItemsLarge>(keys, vals, alt_k, alt_v, n, bits, hist, scan_tmp, st);
+}
+
 size_t radix_hist_words(uint64_t n) {
-  uint64_t nb = (n + kRadixTile - 1) / kRadixTile;
-  return 256 * nb;
+  // the most tiles n keys can need: small tiles below kSmallTileKeys, large ones above
+  const uint64_t small = std::min<uint64_t>(n, kSmallTileKeys);
+  const uint64_t tiles = std::max<uint64_t>((small + kRadixThreads * kRadixItemsSmall - 1) / (kRadixThreads * kRadixItemsSmall),
+                                            (n + kRadixThreads * kRadixItemsLarge - 1) / (kRadixThreads * kRadixItemsLarge));
+  return 256 * tiles;
 }
 
 int bits_for(uint32_t n) {
   int b = 1;
   while (b < 32 && (1ull << b) < (uint64_t)n) b++;
   return b;
+}
+
+template <int ITEMS>
+uint64_t *radix_keys(uint64_t *keys, uint64_t *alt, uint64_t n, int bits, uint32_t *hist, uint32_t *scan_tmp,
+                     cudaStream_t st) {
+  constexpr int kRadixTile = kRadixThreads * ITEMS;
+  const uint32_t nblocks = (uint32_t)((n + kRadixTile - 1) / kRadixTile);
+  uint64_t *src = keys, *dst = alt;
+  for (int shift = 0; shift < bits; shift += 8) {
+    k_radix_hist<ITEMS><<<nblocks, kRadixThreads, 0, st>>>(src, n, shift, hist, nblocks); count_launch();
+    exclusive_scan_u32(hist, hist, (uint64_t)256 * nblocks, scan_tmp, st);
+    k_radix_scatter<ITEMS><<<nblocks, kRadixThreads, 0, st>>>(src, dst, n, shift, hist, nblocks); count_launch();
+    uint64_t *t = src;
+    src = dst;
+    dst = t;
+  }
+  return src;
 }
 
 uint64_t *sort_u64(uint64_t *keys, uint64_t *alt, uint64_t n, int bits, uint32_t *hist, uint32_t *scan_tmp,
@@ -308,17 +345,8 @@ uint64_t *sort_u64(uint64_t *keys, uint64_t *alt, uint64_t n, int bits, uint32_t
     k_block_sort<<<1, 1024, 0, st>>>(keys, (uint32_t)n); count_launch();
     return keys;
   }
-  const uint32_t nblocks = (uint32_t)((n + kRadixTile - 1) / kRadixTile);
-  uint64_t *src = keys, *dst = alt;
-  for (int shift = 0; shift < bits; shift += 8) {
-    k_radix_hist<<<nblocks, kRadixThreads, 0, st>>>(src, n, shift, hist, nblocks); count_launch();
-    exclusive_scan_u32(hist, hist, (uint64_t)256 * nblocks, scan_tmp, st);
-    k_radix_scatter<<<nblocks, kRadixThreads, 0, st>>>(src, dst, n, shift, hist, nblocks); count_launch();
-    uint64_t *t = src;
-    src = dst;
-    dst = t;
-  }
-  return src;
+  return n < kSmallTileKeys ? radix_keys<kRadixItemsSmall>(keys, alt, n, bits, hist, scan_tmp, st)
+                            : radix_keys<kRadixItemsLarge>(keys, alt, n, bits, hist, scan_tmp, st);
 }
 
 }  // namespace prdf

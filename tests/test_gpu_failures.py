@@ -90,6 +90,24 @@ def test_allocation_failure_leaves_the_graph_unchanged(prdf):
             assert np.array_equal(off, eoff) and np.array_equal(col, ecol)
 
 
+@pytest.mark.parametrize("order", [0, 2])
+def test_creation_out_of_memory_is_reported(prdf, order):
+    # every graph allocation fails: the numbering's transient build (vertex_order 0 falls
+    # back to the caller's numbering) and then the handle's own build report it
+    g = synth.rmat(12, 8, seed=34)
+    p = prdf.pr_params_default()
+    p.vertex_order = order
+    prdf.pr_inject_alloc_failure(0)
+    try:
+        with pytest.raises(prdf.PrdfError) as ei:
+            prdf.Graph(g.n, g.src, g.dst, p)
+    finally:
+        prdf.pr_inject_alloc_failure(-1)
+    assert ei.value.status == PR_ERR_OUT_OF_MEMORY
+    with prdf.Graph(g.n, g.src, g.dst, p) as dg:  # nothing left behind
+        assert dg.static().converged
+
+
 def test_set_ranks_rejects_what_is_not_a_distribution(prdf):
     torch = pytest.importorskip("torch")
     g = synth.rmat(10, 8, seed=33)
