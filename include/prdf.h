@@ -93,8 +93,11 @@ typedef struct {
                              caller's numbering.  Computing a numbering takes a second,
                              transient build of the graph on the device; without room for it
                              the caller's numbering is kept (0) or creation fails with
-                             PR_ERR_OUT_OF_MEMORY (2, 3).  Batched handles keep the caller's
-                             numbering always.  Other values: PR_ERR_INVALID_ARG. */
+                             PR_ERR_OUT_OF_MEMORY (2, 3).  Batched handles number each
+                             graph within its own id range, breadth-first from its vertex of
+                             largest degree (0: if the model finds it cheaper; 2: always; 3
+                             is PR_ERR_INVALID_ARG for them).  Other values:
+                             PR_ERR_INVALID_ARG. */
 } pr_params;
 
 typedef struct {

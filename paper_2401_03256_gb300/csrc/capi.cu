@@ -338,9 +338,15 @@ static pr_status create_impl(uint32_t n, int64_t m, const uint32_t *src, const u
     if (e != cudaSuccess) { rc = prdf::cuda_fail(&g, e, "device query"); break; }
     if (!coop) { g.err = "device does not support cooperative launch"; rc = PR_ERR_CUDA; break; }
     const uint32_t *sd = src, *dd = dst;
-    // single-graph handles may number their vertices breadth-first (order.cu) unless asked
-    // not to; the edges are then rewritten, so they need a device copy of their own
-    const bool reorder = !comp_n && p.vertex_order != 1 && m > 0;
+    // handles may number their vertices breadth-first (order.cu) unless asked not to (a
+    // batched handle graph by graph, each within its id range); the edges are then
+    // rewritten, so they need a device copy of their own
+    if (comp_n && p.vertex_order == 3) {
+      g.err = "vertex_order 3 is for single-graph handles";
+      rc = PR_ERR_INVALID_ARG;
+      break;
+    }
+    const bool reorder = p.vertex_order != 1 && m > 0;
     if (m > 0 && (reorder || !(is_device_ptr(src) && is_device_ptr(dst)))) {
       e = cudaMalloc((void **)&tmp, 8ull * (uint64_t)m);
       if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, src, 4ull * m, cudaMemcpyDefault, g.st);
@@ -362,16 +368,16 @@ static pr_status create_impl(uint32_t n, int64_t m, const uint32_t *src, const u
       rc = prdf::graph_build(&g0, (uint64_t)m, sd, dd);
       // vertex_order 0: both numberings, the one with the cheaper modelled gathers kept if
       // it beats the caller's by 5%; 2 and 3: the one asked for, always
-      const int kinds[2] = {prdf::kOrderFromMax, prdf::kOrderFromSeeds};
+      const int kinds[2] = {comp_n ? prdf::kOrderPerGraph : prdf::kOrderFromMax, prdf::kOrderFromSeeds};
       uint32_t *cp[2] = {nullptr, nullptr}, *ci[2] = {nullptr, nullptr};
       uint64_t cost[2][2] = {{0, 0}, {0, 0}};
       int best = -1;
       for (int k = 0; k < 2 && rc == PR_OK; k++) {
-        if (p.vertex_order >= 2 && p.vertex_order - 2 != k) continue;
+        if ((p.vertex_order >= 2 && p.vertex_order - 2 != k) || (comp_n && k == 1)) continue;
         e = cudaMalloc((void **)&cp[k], 4ull * n);
         if (e == cudaSuccess) e = cudaMalloc((void **)&ci[k], 4ull * n);
         if (e != cudaSuccess) { rc = prdf::cuda_fail(&g0, e, "vertex numbering"); break; }
-        rc = prdf::vertex_order(&g0, kinds[k], cp[k], ci[k]);
+        rc = prdf::vertex_order(&g0, kinds[k], cp[k], ci[k], comp_n);
         if (rc == PR_OK && p.vertex_order == 0) rc = prdf::order_cost(&g0, cp[k], ci[k], cost[k]);
         if (rc == PR_OK && (best < 0 || cost[k][1] < cost[best][1])) best = k;
       }

@@ -10,6 +10,9 @@
 //  kOrderFromSeeds: max(kSeeds, n / kSeedCell) vertices evenly spaced in the caller's
 //    numbering (graphs of large diameter, such as chains of k-mers, which one seed would
 //    cover only at one level per few dozen vertices).
+//  kOrderPerGraph (batched handles): the vertex of largest degree of every graph, then a
+//    stable sort by graph, so that each graph keeps its id range and within it the order
+//    of its own breadth-first search from that vertex.
 // Level by level, a newly reached vertex takes its place after the vertices reached from
 // earlier-numbered vertices of the previous level (the earliest adjacent one decides),
 // ties by vertex id; vertices not reached within kMaxLevels levels follow in id order.
@@ -66,6 +69,55 @@ __global__ void k_order_start(const unsigned long long *best, uint32_t *label, u
   const uint32_t s = ~(uint32_t)(*best & 0xFFFFFFFFull);
   label[s] = 0;
   perm[0] = s;
+}
+
+// graph of each vertex (first[c] <= v < first[c + 1]; nc <= kMaxComponents)
+__global__ void k_order_graph_of(const uint32_t *first, uint32_t nc, uint32_t n, uint32_t *gid) {
+  const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  uint32_t lo = 0, hi = nc;  // last c with first[c] <= v
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (first[mid] <= v) lo = mid; else hi = mid;
+  }
+  gid[v] = lo;
+}
+
+// every graph's vertex of largest out + in degree (smallest id on ties)
+__global__ void k_order_graph_seed(const uint2 *out_rd, const uint2 *in_rd, const uint32_t *gid, uint32_t n,
+                                   unsigned long long *best) {
+  const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < n) atomicMax(best + gid[v], ((unsigned long long)(out_rd[v].y + in_rd[v].y) << 32) | (unsigned long long)(~v));
+}
+
+// level 0 of kOrderPerGraph: the graphs' seeds in graph order (graphs without vertices
+// have none); one thread
+__global__ void k_order_graph_start(const unsigned long long *best, uint32_t nc, uint32_t *label, uint32_t *perm,
+                                    uint32_t *count) {
+  uint32_t k = 0;
+  for (uint32_t c = 0; c < nc; c++) {
+    if (!best[c]) continue;
+    const uint32_t s = ~(uint32_t)(best[c] & 0xFFFFFFFFull);
+    label[s] = k;
+    perm[k++] = s;
+  }
+  *count = k;
+}
+
+// sort keys of the final order: graph, then breadth-first number
+__global__ void k_order_graph_keys(const uint32_t *gid, const uint32_t *label, uint32_t n, unsigned long long *keys) {
+  const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < n) keys[v] = ((unsigned long long)gid[v] << 32) | label[v];
+}
+
+__global__ void k_order_graph_perm(const unsigned long long *sorted, const uint32_t *rank_perm, uint32_t n,
+                                   uint32_t *perm, uint32_t *inv) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const uint32_t v = rank_perm[(uint32_t)(sorted[i] & 0xFFFFFFFFull)];
+    perm[i] = v;
+    inv[v] = i;
+  }
 }
 
 // level 0 of kOrderFromSeeds: seed i is vertex i * step
@@ -186,7 +238,7 @@ unsigned grid_of(uint64_t n) { return (unsigned)std::max<uint64_t>(1, (n + 255) 
 
 }  // namespace
 
-pr_status vertex_order(Graph *g, int kind, uint32_t *perm, uint32_t *inv) {
+pr_status vertex_order(Graph *g, int kind, uint32_t *perm, uint32_t *inv, const std::vector<uint32_t> *comp_n) {
   const uint32_t n = g->n;
   cudaStream_t st = g->st;
   pr_status rc = apply_scratch(g, n);
@@ -199,7 +251,30 @@ pr_status vertex_order(Graph *g, int kind, uint32_t *perm, uint32_t *inv) {
   int b = 0;
   while (b < 32 && (1ull << b) < (uint64_t)n) b++;
   uint32_t lo = 0, hi;
-  if (kind == kOrderFromSeeds) {
+  uint32_t *gid = nullptr;
+  if (kind == kOrderPerGraph) {
+    // graphs of a batched handle: one seed each
+    const uint32_t nc = comp_n ? (uint32_t)comp_n->size() : 0u;
+    if (!nc || nc > kMaxComponents) {
+      g->err = "per-graph numbering needs the graphs' sizes";
+      return PR_ERR_INVALID_ARG;
+    }
+    std::vector<uint32_t> first(nc + 1, 0);
+    for (uint32_t c = 0; c < nc; c++) first[c + 1] = first[c] + (*comp_n)[c];
+    uint32_t *first_d = g->gen_tmp;  // needed only until every vertex has its graph
+    unsigned long long *best = (unsigned long long *)s.tmp2;
+    CK(cudaMemcpyAsync(first_d, first.data(), 4ull * (nc + 1), cudaMemcpyHostToDevice, st));
+    k_order_graph_of<<<grid_of(n), 256, 0, st>>>(first_d, nc, n, s.vals);
+    count_launch();
+    gid = s.vals;
+    CK(cudaMemsetAsync(best, 0, 8ull * nc, st));
+    k_order_graph_seed<<<grid_of(n), 256, 0, st>>>(g->out.rd, g->in.rd, gid, n, best);
+    count_launch();
+    k_order_graph_start<<<1, 1, 0, st>>>(best, nc, inv, perm, cnt);
+    count_launch();
+    CK(cudaMemcpyAsync(&hi, cnt, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  } else if (kind == kOrderFromSeeds) {
     const uint32_t k = std::min(n, std::max(kSeeds, n / kSeedCell)), step = n / k;
     k_order_seeds<<<grid_of(k), 256, 0, st>>>(k, step, inv, perm);
     count_launch();
@@ -239,6 +314,19 @@ pr_status vertex_order(Graph *g, int kind, uint32_t *perm, uint32_t *inv) {
     count_launch();
     exclusive_scan_u32(g->gen_tmp, g->gen_tmp2, n, g->scan_tmp, st);
     k_order_rest<<<grid_of(n), 256, 0, st>>>(g->gen_tmp, g->gen_tmp2, n, hi, inv, perm);
+    count_launch();
+  }
+  if (kind == kOrderPerGraph) {
+    // stable by graph: each graph keeps its id range, ordered by its own search
+    const uint32_t nc = (uint32_t)comp_n->size();
+    int cb = 1;
+    while ((1u << cb) < nc) cb++;
+    k_order_graph_keys<<<grid_of(n), 256, 0, st>>>(gid, inv, n, keys);
+    count_launch();
+    const unsigned long long *sorted =
+        (const unsigned long long *)sort_u64((uint64_t *)keys, s.tmp, n, 32 + cb, s.radix_hist, s.scan_tmp, st);
+    CK(cudaMemcpyAsync(next, perm, 4ull * n, cudaMemcpyDeviceToDevice, st));
+    k_order_graph_perm<<<grid_of(n), 256, 0, st>>>(sorted, next, n, perm, inv);
     count_launch();
   }
 

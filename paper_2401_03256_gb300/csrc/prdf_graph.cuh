@@ -131,8 +131,9 @@ pr_status graph_build(Graph *g, uint64_t m_in, const uint32_t *src_d, const uint
 pr_status graph_apply(Graph *g, uint64_t nd, const uint32_t *ds_d, const uint32_t *dd_d, uint64_t ni,
                       const uint32_t *is_d, const uint32_t *id_d, int nb, const uint32_t *off_d);
 pr_status apply_scratch(Graph *g, uint64_t N);
-constexpr int kOrderFromMax = 0, kOrderFromSeeds = 1;
-pr_status vertex_order(Graph *g, int kind, uint32_t *perm, uint32_t *inv);
+constexpr int kOrderFromMax = 0, kOrderFromSeeds = 1, kOrderPerGraph = 2;
+pr_status vertex_order(Graph *g, int kind, uint32_t *perm, uint32_t *inv,
+                       const std::vector<uint32_t> *comp_n = nullptr);
 pr_status order_cost(Graph *g, const uint32_t *perm, const uint32_t *inv, uint64_t cost[2]);  // order.cu, on a built graph
 void map_ids(const uint32_t *inv, uint32_t *a, uint64_t m, cudaStream_t st);
 pr_status graph_export(Graph *g, int dir, uint64_t *offs_h, uint32_t *cols_h);

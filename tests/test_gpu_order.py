@@ -138,3 +138,48 @@ def test_numbering_degenerate(prdf, n, order):
         A.static()
         B.static()
         assert np.array_equal(A.ranks(), B.ranks())
+
+
+def _union(gs):
+    firsts = np.cumsum([0] + [g.n for g in gs])
+    src = np.concatenate([g.src.astype(np.uint64) + firsts[i] for i, g in enumerate(gs)]).astype(np.uint32)
+    dst = np.concatenate([g.dst.astype(np.uint64) + firsts[i] for i, g in enumerate(gs)]).astype(np.uint32)
+    return firsts, src, dst
+
+
+@pytest.mark.parametrize("order", [2, 0])
+def test_batched_numbering_is_invisible_fp64(prdf, order):
+    # each graph numbered within its own id range; results bit-identical to the caller's ids
+    gs = [synth.rmat(11, 8, seed=21), synth.grid(30, 20, seed=22), synth.rmat(9, 4, seed=23), _two_islands()]
+    firsts, src, dst = _union(gs)
+    sizes = [g.n for g in gs]
+    bss = [synth.BatchStream(g, seed=24 + i) for i, g in enumerate(gs)]
+    with prdf.Graph.batched(sizes, src, dst, _params(prdf, order)) as A, \
+            prdf.Graph.batched(sizes, src, dst, _params(prdf, 1)) as B:
+        A.static()
+        B.static()
+        assert np.array_equal(A.ranks(), B.ranks())
+        for f in (1e-3, 1e-2):
+            bs = [s.next(f) for s in bss]
+            parts = [np.concatenate([(getattr(b, k).astype(np.uint64) + firsts[i]).astype(np.uint32)
+                                     for i, b in enumerate(bs)]) for k in ("del_src", "del_dst", "ins_src", "ins_dst")]
+            for H in (A, B):
+                H.apply(*parts)
+            A.frontier()
+            B.frontier()
+            assert np.array_equal(A.ranks(), B.ranks())
+            assert np.array_equal(np.sort(A.affected()), np.sort(B.affected()))
+            ca, cb = A.component_stats(), B.component_stats()
+            assert [c.iterations for c in ca] == [c.iterations for c in cb]
+        for d in (0, 1):
+            oa, xa = A.csr(d)
+            ob, xb = B.csr(d)
+            assert np.array_equal(oa, ob) and np.array_equal(xa, xb)
+
+
+def test_batched_rejects_seeded_numbering(prdf):
+    gs = [synth.rmat(8, 4, seed=25), synth.rmat(8, 4, seed=26)]
+    firsts, src, dst = _union(gs)
+    with pytest.raises(prdf.PrdfError) as e:
+        prdf.Graph.batched([g.n for g in gs], src, dst, _params(prdf, 3))
+    assert e.value.status == prdf.PR_ERR_INVALID_ARG
