@@ -90,7 +90,9 @@ typedef struct {
                              numbering (a grid numbered row by row keeps its own); 1: keep
                              the caller's numbering.  Ids are translated at every call:
                              results, ranks, affected sets and the CSR export are in the
-                             caller's numbering.  Computing a numbering takes a second,
+                             caller's numbering (a renumbered handle keeps 8 B per vertex of
+                             translation tables on the device and 4 B on the host).
+                             Computing a numbering takes a second,
                              transient build of the graph on the device; without room for it
                              the caller's numbering is kept (0) or creation fails with
                              PR_ERR_OUT_OF_MEMORY (2, 3).  Batched handles number each
