@@ -78,28 +78,26 @@ typedef struct {
     int32_t dead_end;     /* pr_deadend */
     int32_t bin_lo;       /* in-degree <= bin_lo: one thread per vertex (0 = default 8) */
     int32_t bin_hi;       /* in-degree >  bin_hi: one block per vertex (0 = default 4096) */
-    int32_t vertex_order; /* Internal vertex numbering of a single-graph handle.  A
-                             breadth-first numbering (at most 1024 levels; the vertices not
-                             reached keep their relative order after them) puts the
-                             contributions that warps gather side by side close together:
-                             from the vertex of largest degree (2) or from max(8192, n / 2048)
-                             vertices evenly spaced in the caller's numbering as the first
-                             level (3).  0 (default): both are computed at creation and the
-                             one whose short-row gathers a model finds cheapest is kept if it
-                             touches at least 5% fewer 32-byte sectors than the caller's
-                             numbering (a grid numbered row by row keeps its own); 1: keep
-                             the caller's numbering.  Ids are translated at every call:
-                             results, ranks, affected sets and the CSR export are in the
-                             caller's numbering (a renumbered handle keeps 8 B per vertex of
-                             translation tables on the device and 4 B on the host).
-                             Computing a numbering takes a second,
+    int32_t vertex_order; /* Internal vertex numbering of a handle.  A breadth-first
+                             numbering (at most 1024 levels; the vertices not reached keep
+                             their relative order after them) puts the contributions that
+                             warps gather side by side close together: from the vertex of
+                             largest degree (2) or from max(8192, n / 2048) vertices evenly
+                             spaced in the caller's numbering as the first level (3).
+                             0 (default): both are computed at creation and the one whose
+                             short-row gathers a model finds cheapest is kept if it touches
+                             at least 5% fewer 32-byte sectors than the caller's numbering (a
+                             grid numbered row by row keeps its own); 1: keep the caller's
+                             numbering.  Batched handles number each graph within its own id
+                             range, breadth-first from its vertex of largest degree (0: if
+                             the model finds it cheaper; 2: always; 3: PR_ERR_INVALID_ARG).
+                             Ids are translated at every call: results, ranks, affected sets
+                             and the CSR export are in the caller's numbering (a renumbered
+                             handle keeps 8 B per vertex of translation tables on the device
+                             and 4 B on the host).  Computing a numbering takes a second,
                              transient build of the graph on the device; without room for it
                              the caller's numbering is kept (0) or creation fails with
-                             PR_ERR_OUT_OF_MEMORY (2, 3).  Batched handles number each
-                             graph within its own id range, breadth-first from its vertex of
-                             largest degree (0: if the model finds it cheaper; 2: always; 3
-                             is PR_ERR_INVALID_ARG for them).  Other values:
-                             PR_ERR_INVALID_ARG. */
+                             PR_ERR_OUT_OF_MEMORY (2, 3).  Other values: PR_ERR_INVALID_ARG. */
 } pr_params;
 
 typedef struct {
