@@ -46,7 +46,12 @@ static inline unsigned grid_for(uint64_t n, int threads = 256) {
 }
 
 constexpr int kMergeThreads = 256;
-constexpr uint32_t kSmemRow = 2048;  // rows up to this length are staged in shared memory
+constexpr int kMergeThreadsLong = 1024;
+constexpr uint32_t kSmemRow = 2048;   // rows up to this length are staged in shared memory
+#ifndef PRDF_LONG_ROW
+#define PRDF_LONG_ROW 8192
+#endif
+constexpr uint32_t kLongRow = PRDF_LONG_ROW;  // longer rows are merged by blocks of kMergeThreadsLong
 
 // ------------------------------------------------------------------- kernels ----
 
@@ -318,18 +323,16 @@ __device__ __forceinline__ int degree_bin(uint32_t d, uint32_t lo, uint32_t hi) 
   return d <= lo ? 0 : (d <= hi ? 1 : 2);
 }
 
-// One block per touched row: merges the row with its sorted changes.
-template <bool F32>
-__global__ void __launch_bounds__(kMergeThreads) k_merge(uint2 *rd, uint32_t *cap, uint32_t *col, const uint64_t *chg,
-                                                         int b, const uint32_t *seg, const uint32_t *nseg,
-                                                         const uint32_t *tagpref, unsigned long long *tail,
-                                                         unsigned long long *garbage, uint32_t *big,
-                                                         unsigned long long *big_cursor, uint64_t col_cap,
-                                                         uint64_t big_cap, ApplyCtl *actl, RowHook<F32> hook) {
+// Merges one touched row (segment s of the sorted changes) with its changes; called by a
+// whole block.
+template <bool F32, int THREADS>
+__device__ void merge_row(uint32_t s, uint2 *rd, uint32_t *cap, uint32_t *col, const uint64_t *chg, int b,
+                          const uint32_t *seg, const uint32_t *tagpref, unsigned long long *tail,
+                          unsigned long long *garbage, uint32_t *big, unsigned long long *big_cursor,
+                          uint64_t col_cap, uint64_t big_cap, ApplyCtl *actl, const RowHook<F32> &hook) {
+  constexpr int kMergeThreads = THREADS;
   __shared__ uint32_t srow[kSmemRow];
   __shared__ uint32_t s_dest, s_big;
-  const uint32_t s = blockIdx.x;
-  if (s >= *nseg) return;
   const uint32_t tid = threadIdx.x;
   const uint32_t s0 = seg[s], e = seg[s + 1];
   const uint32_t r = chg_row(chg[s0], b);
@@ -437,6 +440,44 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(uint2 *rd, uint32_t *ca
           hook.items[pos + c] = chunk_item(r, nd, c, nch, number0 + c, hook.chunk);
       }
     }
+  }
+}
+
+// One block per touched row of at most kLongRow entries; the longer rows are listed (their
+// segments in long_seg) for k_merge_long, whose blocks of kMergeThreadsLong take them in
+// turn: a hub row's entries are four times as many threads' work, and only as many blocks
+// as the GPU holds are launched for them.
+template <bool F32>
+__global__ void __launch_bounds__(kMergeThreads) k_merge(uint2 *rd, uint32_t *cap, uint32_t *col, const uint64_t *chg,
+                                                         int b, const uint32_t *seg, const uint32_t *nseg,
+                                                         const uint32_t *tagpref, unsigned long long *tail,
+                                                         unsigned long long *garbage, uint32_t *big,
+                                                         unsigned long long *big_cursor, uint64_t col_cap,
+                                                         uint64_t big_cap, ApplyCtl *actl, RowHook<F32> hook,
+                                                         uint32_t *long_seg) {
+  const uint32_t s = blockIdx.x;
+  if (s >= *nseg) return;
+  if (rd[chg_row(chg[seg[s]], b)].y > kLongRow) {
+    if (threadIdx.x == 0) long_seg[atomicAdd(&actl->n_long, 1u)] = s;
+    return;
+  }
+  merge_row<F32, kMergeThreads>(s, rd, cap, col, chg, b, seg, tagpref, tail, garbage, big, big_cursor, col_cap,
+                                big_cap, actl, hook);
+}
+
+template <bool F32>
+__global__ void __launch_bounds__(kMergeThreadsLong) k_merge_long(uint2 *rd, uint32_t *cap, uint32_t *col,
+                                                                  const uint64_t *chg, int b, const uint32_t *seg,
+                                                                  const uint32_t *tagpref, unsigned long long *tail,
+                                                                  unsigned long long *garbage, uint32_t *big,
+                                                                  unsigned long long *big_cursor, uint64_t col_cap,
+                                                                  uint64_t big_cap, ApplyCtl *actl,
+                                                                  RowHook<F32> hook, const uint32_t *long_seg) {
+  const uint32_t n_long = *(volatile uint32_t *)&actl->n_long;
+  for (uint32_t k = blockIdx.x; k < n_long; k += gridDim.x) {
+    merge_row<F32, kMergeThreadsLong>(long_seg[k], rd, cap, col, chg, b, seg, tagpref, tail, garbage, big, big_cursor,
+                                      col_cap, big_cap, actl, hook);
+    __syncthreads();  // the block's shared staging is reused by its next row
   }
 }
 
@@ -921,6 +962,7 @@ pr_status graph_apply(Graph *g, uint64_t nd, const uint32_t *ds, const uint32_t 
   CK(cudaMemsetAsync(&dctl->big_cursor, 0, 8, st));
 
   const uint32_t lo = (uint32_t)g->p.bin_lo, hi_b = (uint32_t)g->p.bin_hi;
+  const unsigned long_grid = (unsigned)std::max(1, 2 * g->sm_count);
   if (g->f32) {
     using S = Store<true>;
     RowHook<true> ho{true, g->p.alpha, (S::A *)g->adeg, (S::R *)g->R[0], (S::C *)g->C[0], (S::C *)g->C[1],
@@ -928,13 +970,23 @@ pr_status graph_apply(Graph *g, uint64_t nd, const uint32_t *ds, const uint32_t 
     RowHook<true> hin{false,   g->p.alpha,   nullptr,      nullptr,       nullptr, nullptr, nullptr,
                       nullptr, 0,            lo,           hi_b,          g->group_max, g->chunk_len,
                       g->items, g->item_pos};
+    CK(cudaMemsetAsync(&dctl->n_long, 0, 4, st));
     k_merge<true><<<K, kMergeThreads, 0, st>>>(g->out.rd, g->out.cap, g->out.col, co, b, seg_o, &dctl->n_seg_out,
                                                tp_o, &dctl->tail_out, &dctl->garbage_out, g->big, &dctl->big_cursor,
-                                               g->out.col_cap, g->big_cap, dctl, ho);
+                                               g->out.col_cap, g->big_cap, dctl, ho, s.flags);
     count_launch();
+    k_merge_long<true><<<long_grid, kMergeThreadsLong, 0, st>>>(g->out.rd, g->out.cap, g->out.col, co, b, seg_o,
+                                               tp_o, &dctl->tail_out, &dctl->garbage_out, g->big, &dctl->big_cursor,
+                                               g->out.col_cap, g->big_cap, dctl, ho, s.flags);
+    count_launch();
+    CK(cudaMemsetAsync(&dctl->n_long, 0, 4, st));
     k_merge<true><<<K, kMergeThreads, 0, st>>>(g->in.rd, g->in.cap, g->in.col, ci, b, seg_i, &dctl->n_seg_in, tp_i,
                                                &dctl->tail_in, &dctl->garbage_in, g->big, &dctl->big_cursor,
-                                               g->in.col_cap, g->big_cap, dctl, hin);
+                                               g->in.col_cap, g->big_cap, dctl, hin, s.flags);
+    count_launch();
+    k_merge_long<true><<<long_grid, kMergeThreadsLong, 0, st>>>(g->in.rd, g->in.cap, g->in.col, ci, b, seg_i, tp_i,
+                                               &dctl->tail_in, &dctl->garbage_in, g->big, &dctl->big_cursor,
+                                               g->in.col_cap, g->big_cap, dctl, hin, s.flags);
     count_launch();
   } else {
     using S = Store<false>;
@@ -943,13 +995,23 @@ pr_status graph_apply(Graph *g, uint64_t nd, const uint32_t *ds, const uint32_t 
     RowHook<false> hin{false,   g->p.alpha,   nullptr,      nullptr,       nullptr, nullptr, nullptr,
                        nullptr, 0,            lo,           hi_b,          g->group_max, g->chunk_len,
                        g->items, g->item_pos};
+    CK(cudaMemsetAsync(&dctl->n_long, 0, 4, st));
     k_merge<false><<<K, kMergeThreads, 0, st>>>(g->out.rd, g->out.cap, g->out.col, co, b, seg_o, &dctl->n_seg_out,
                                                 tp_o, &dctl->tail_out, &dctl->garbage_out, g->big, &dctl->big_cursor,
-                                                g->out.col_cap, g->big_cap, dctl, ho);
+                                                g->out.col_cap, g->big_cap, dctl, ho, s.flags);
     count_launch();
+    k_merge_long<false><<<long_grid, kMergeThreadsLong, 0, st>>>(g->out.rd, g->out.cap, g->out.col, co, b, seg_o,
+                                                tp_o, &dctl->tail_out, &dctl->garbage_out, g->big, &dctl->big_cursor,
+                                                g->out.col_cap, g->big_cap, dctl, ho, s.flags);
+    count_launch();
+    CK(cudaMemsetAsync(&dctl->n_long, 0, 4, st));
     k_merge<false><<<K, kMergeThreads, 0, st>>>(g->in.rd, g->in.cap, g->in.col, ci, b, seg_i, &dctl->n_seg_in, tp_i,
                                                 &dctl->tail_in, &dctl->garbage_in, g->big, &dctl->big_cursor,
-                                                g->in.col_cap, g->big_cap, dctl, hin);
+                                                g->in.col_cap, g->big_cap, dctl, hin, s.flags);
+    count_launch();
+    k_merge_long<false><<<long_grid, kMergeThreadsLong, 0, st>>>(g->in.rd, g->in.cap, g->in.col, ci, b, seg_i, tp_i,
+                                                &dctl->tail_in, &dctl->garbage_in, g->big, &dctl->big_cursor,
+                                                g->in.col_cap, g->big_cap, dctl, hin, s.flags);
     count_launch();
   }
   CK(cudaGetLastError());

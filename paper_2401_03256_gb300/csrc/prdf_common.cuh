@@ -220,6 +220,7 @@ struct ApplyCtl {
   uint32_t bins_changed;                    // an in-degree crossed a bin threshold
   uint32_t bad_comp;                        // a pair joins two graphs of a batched handle
   unsigned long long big_cursor;            // global scratch cursor for long rows
+  uint32_t n_long;                          // rows left by the merge for its long-row pass
 };
 
 // ------------------------------------------------------------------- primitives ---
