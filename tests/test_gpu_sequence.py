@@ -127,3 +127,45 @@ def test_sequence_rejects_bad_offsets_and_ids(prdf):
         assert st == prdf.PR_ERR_INVALID_ARG
         after = Q.csr(0)
         assert np.array_equal(before[0], after[0]) and np.array_equal(before[1], after[1])
+
+
+@pytest.mark.parametrize("order", [1, 0])
+def test_long_row_merges(prdf, order):
+    # a hub with 20,000 in- and out-edges: its rows are merged by the long-row pass (rows of
+    # more than 8192 entries); insertions below, between and above its present columns and
+    # deletions among them must give the oracle's CSR bit for bit, then its ranks
+    rng = np.random.default_rng(41)
+    n = 60000
+    hub = 777
+    others = rng.choice(np.setdiff1d(np.arange(n), [hub]), size=40000, replace=False)
+    ins_to, outs_from = others[:20000], others[20000:]
+    pairs = [(int(u), hub) for u in ins_to] + [(hub, int(v)) for v in outs_from]
+    extra = rng.integers(0, n, size=(120000, 2))
+    pairs += [(int(a), int(b)) for a, b in extra]
+    g = synth.from_pairs(n, pairs, "hub")
+    G = oracle.Graph.build(g.n, g.src, g.dst)
+    R0, _ = oracle.static_pr(G)
+    free_in = np.setdiff1d(np.arange(n), np.concatenate([ins_to, [hub]]))
+    new_in = rng.choice(free_in, size=3000, replace=False)
+    del_in = rng.choice(ins_to, size=2500, replace=False)
+    free_out = np.setdiff1d(np.arange(n), np.concatenate([outs_from, [hub]]))
+    new_out = rng.choice(free_out, size=3000, replace=False)
+    del_out = rng.choice(outs_from, size=2500, replace=False)
+    u32 = lambda a: np.asarray(a, np.uint32)
+    ds = u32(np.concatenate([del_in, np.full(len(del_out), hub)]))
+    dd = u32(np.concatenate([np.full(len(del_in), hub), del_out]))
+    is_ = u32(np.concatenate([new_in, np.full(len(new_out), hub)]))
+    id_ = u32(np.concatenate([np.full(len(new_in), hub), new_out]))
+    p = prdf.pr_params_default()
+    p.vertex_order = order
+    with prdf.Graph(g.n, g.src, g.dst, p) as Q:
+        Q.set_ranks(R0)
+        Q.apply(ds, dd, is_, id_)
+        H, ed, ei = G.apply(ds, dd, is_, id_)
+        for d in (0, 1):
+            off, col = Q.csr(d)
+            eoff, ecol = H.csr(d)
+            assert np.array_equal(off, eoff) and np.array_equal(col, ecol)
+        Q.frontier()
+        R_df, _, _ = oracle.df_sync(G, H, ed, ei, R0)
+        assert np.max(np.abs(Q.ranks() - R_df)) <= TOL64
